@@ -1,0 +1,223 @@
+/*
+ * nbcluster -- cluster-pair non-bonded interactions on one GB300 (sm_103a).
+ *
+ * C ABI of the method of Pall & Hess, "A flexible algorithm for calculating
+ * pair interactions on SIMD architectures": particles are gridded into
+ * fixed-size spatial clusters (Sec. 2.3), a buffered cluster-pair list with
+ * exclusion bitmasks is built (Sec. 2.3, Fig. 3, Sec. 2.4), pruned with a
+ * particle-pair distance criterion (Sec. 2.3), and Lennard-Jones plus Coulomb
+ * (reaction-field or Ewald real-space) forces and energies are computed per
+ * cluster pair (Sec. 3, Fig. 6).
+ *
+ * Conventions
+ *  - Units: nm, kJ/mol, elementary charge; forces in kJ mol^-1 nm^-1.
+ *  - Rectangular periodic box; every cut-off and list radius must be below
+ *    half of every box edge (minimum image).
+ *  - Particle arrays are in the caller's order.  xyz is float [n][3].
+ *  - Every pointer argument named *_dev is a device pointer owned by the
+ *    caller; host arrays are named explicitly.  The library never allocates
+ *    device memory: it works inside the workspace the caller provides.
+ *  - Every call that takes a stream is asynchronous on that stream (a
+ *    cudaStream_t; NULL = the legacy default stream) and performs no host
+ *    synchronisation, so a sequence of calls can be captured in a CUDA graph.
+ *    Errors that only the device can detect (list capacity overflow, a
+ *    particle outside [-L, 2L), a column too long to sort on-chip) raise a
+ *    device flag that nb_check() reads.
+ *  - Return value: NB_OK or an nb_status_code; nb_last_error() gives text.
+ */
+#ifndef NBCLUSTER_H
+#define NBCLUSTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nb_ctx nb_ctx;
+typedef void* nb_stream; /* cudaStream_t */
+typedef int nb_status;
+
+enum nb_status_code {
+    NB_OK = 0,
+    NB_ERR_ARG = 1,      /* null pointer, size or option out of range */
+    NB_ERR_BOX = 2,      /* box edge <= 0, or a radius >= half a box edge */
+    NB_ERR_CAPACITY = 3, /* workspace or list capacity exceeded */
+    NB_ERR_CUDA = 4,     /* a CUDA runtime call failed */
+    NB_ERR_STATE = 5,    /* call out of order (no workspace, no grid, no list) */
+    NB_ERR_TIMEOUT = 6,  /* a bounded device wait expired */
+    NB_ERR_COORD = 7     /* a coordinate outside [-L, 2L) at gridding */
+};
+
+enum nb_elec {
+    NB_ELEC_RF = 0,    /* reaction field, g(r) = -2 k r (Sec. 3.2) */
+    NB_ELEC_EWALD = 1  /* Ewald real space, g(r) = d/dr[erf(beta r)/r] (Sec. 3.2) */
+};
+
+enum nb_comb {
+    NB_COMB_LB = 0,   /* Lorentz-Berthelot: sigma_ij = (s_i+s_j)/2, eps_ij = sqrt(e_i e_j) */
+    NB_COMB_GEOM = 1  /* geometric: C6_ij = sqrt(C6_i C6_j), C12_ij = sqrt(C12_i C12_j) */
+};
+
+/* Creation options. */
+typedef struct {
+    int cluster_size; /* particles per cluster C (M = N = C); 4 or 8.  Sec. 2.2-2.3 */
+    int device;       /* CUDA device ordinal the context is bound to */
+} nb_options;
+
+/* Interaction parameters (Sec. 3.2). */
+typedef struct {
+    int elec;          /* enum nb_elec */
+    int want_energy;   /* 0: forces only; 1: also energies and virial */
+    float rc;          /* interaction cut-off for LJ and Coulomb (nm) */
+    float eps_rf;      /* reaction-field dielectric; <= 0 or inf means infinity */
+    float beta;        /* Ewald splitting parameter (nm^-1) */
+} nb_params;
+
+/* Sizes of the current grid and lists (read back by nb_check). */
+typedef struct {
+    int n_atoms;          /* particles gridded */
+    int nx, ny;           /* grid columns along x and y */
+    int n_clusters;       /* clusters, including padded ones */
+    int64_t n_ientries;   /* i-entries of the outer (rlist) list */
+    int64_t n_jentries;   /* j-entries of the outer list */
+    int64_t n_jentries_pruned; /* j-entries kept by the last nb_prune (-1: none) */
+    int64_t ient_capacity, jent_capacity;
+    uint32_t flags;       /* device error flags (bit mask of 1 << nb_status_code) */
+} nb_info;
+
+/* --- context ------------------------------------------------------------ */
+
+/* Create a context bound to opt->device (opt may be NULL: C = 8, device 0).
+ * Errors: NB_ERR_ARG (C not 4 or 8), NB_ERR_CUDA. */
+nb_status nb_create(nb_ctx** ctx, const nb_options* opt);
+
+/* Destroy a context.  Does not free the caller's workspace. */
+nb_status nb_destroy(nb_ctx* ctx);
+
+/* Text of the last error on this context (never NULL). */
+const char* nb_last_error(const nb_ctx* ctx);
+
+/* Name of a status code. */
+const char* nb_status_string(nb_status s);
+
+/* --- host helpers -------------------------------------------------------- */
+
+/* LJ pair table from per-type sigma (nm) and epsilon (kJ/mol) with a
+ * combination rule (Sec. 3.2: geometric or Lorentz-Berthelot; C6 = 4 eps
+ * sigma^6, C12 = 4 eps sigma^12).  Host arrays; c6c12_host is written as
+ * float [ntypes][ntypes][2] = {C6, C12}.  Errors: NB_ERR_ARG. */
+nb_status nb_lj_combine(int ntypes, const double* sigma_host, const double* eps_host, int comb,
+                        float* c6c12_host);
+
+/* --- workspace ------------------------------------------------------------ */
+
+/* Bytes of device workspace needed for n_atoms particles in a box of edges
+ * box_host[3] (nm), lists up to radius rlist_max (nm) and ntypes <= 64 LJ
+ * types.  list_factor (>= 1; 0 = default 1.5) scales the density-based
+ * estimate of the cluster-pair list capacity.
+ * Errors: NB_ERR_ARG, NB_ERR_BOX. */
+nb_status nb_workspace_query(nb_ctx* ctx, int n_atoms, const double* box_host, double rlist_max,
+                             int ntypes, double list_factor, size_t* bytes);
+
+/* Hand the context a device buffer of at least the queried size (256-byte
+ * aligned).  The caller owns it and keeps it alive while the context uses
+ * it.  Resets all state.  Errors: NB_ERR_ARG, NB_ERR_CAPACITY (too small). */
+nb_status nb_set_workspace(nb_ctx* ctx, void* ws_dev, size_t bytes);
+
+/* --- the hot path ---------------------------------------------------------- */
+
+/* Particle charges (float [n]), LJ types (int [n], 0 <= type < ntypes) and the
+ * LJ pair table c6c12_dev (float [ntypes][ntypes][2], e.g. nb_lj_combine) are
+ * copied into the workspace on the stream.  Sec. 3.2.
+ * Errors: NB_ERR_ARG, NB_ERR_STATE (no workspace), NB_ERR_CAPACITY (n or
+ * ntypes above the workspace's sizes), NB_ERR_CUDA. */
+nb_status nb_set_atoms(nb_ctx* ctx, int n, const float* q_dev, const int* type_dev, int ntypes,
+                       const float* c6c12_dev, nb_stream stream);
+
+/* Spatial clustering (Sec. 2.3, Fig. 2): wrap xyz_dev (float [n][3], each
+ * coordinate in [-L, 2L)) into the box, grid x/y into columns of spacing
+ * (C/rho)^(1/3), sort each column on z, cut clusters of C with dummy padding,
+ * compute bounding boxes.  box_host: double[3] edge lengths (nm), used as
+ * FP32.  Invalidates the lists.
+ * Errors: NB_ERR_ARG, NB_ERR_BOX, NB_ERR_STATE (no atoms set),
+ * NB_ERR_CAPACITY (more columns/slots than the workspace holds), NB_ERR_CUDA;
+ * device flags NB_ERR_COORD, NB_ERR_CAPACITY (column > 8192 particles). */
+nb_status nb_grid_put(nb_ctx* ctx, const float* xyz_dev, const double* box_host, nb_stream stream);
+
+/* Cluster-pair search (Sec. 2.3, Fig. 3) with exclusion bitmasks (Sec. 2.4):
+ * every cluster pair (a <= b, periodic shift s applied to a; for a == b only
+ * s = 0 and the positive half of the shifts) whose bounding boxes are closer
+ * than rlist and either closer than rbb or holding a particle pair closer
+ * than rlist.  Bit i*C+j of a pair's mask is 1 iff particles i of a and j of b
+ * get the full interaction.  excl_off_dev (int [n+1]) and excl_idx_dev (int
+ * [excl_off[n]]) give each particle's force-field exclusions (CSR, caller
+ * order, both directions); both may be NULL for none.  They are read on the
+ * stream and must stay valid until it reaches this call.
+ * Errors: NB_ERR_ARG, NB_ERR_BOX (rlist >= L/2), NB_ERR_STATE (no grid),
+ * NB_ERR_CUDA; device flag NB_ERR_CAPACITY (list or exclusion overflow). */
+nb_status nb_pairlist_build(nb_ctx* ctx, float rlist, float rbb, const int* excl_off_dev,
+                            const int* excl_idx_dev, nb_stream stream);
+
+/* New coordinates for the current grid and lists (float [n][3], caller order,
+ * same periodic image as at nb_grid_put: the wrap offset applied then is
+ * added again, so particles do not jump between images while a list lives).
+ * Errors: NB_ERR_ARG, NB_ERR_STATE (no grid), NB_ERR_CUDA. */
+nb_status nb_set_coords(nb_ctx* ctx, const float* xyz_dev, nb_stream stream);
+
+/* Prune the outer list (Sec. 2.3): keep a cluster pair iff one of its counted
+ * particle pairs (full or force-field-excluded; on the unshifted diagonal only
+ * j > i) is closer than r_prune under the current coordinates.  Writes the
+ * pruned list beside the outer list (which is kept for later prunes);
+ * nb_compute uses the pruned list from then on.  xyz_dev may be NULL (keep
+ * the current coordinates), else it is applied as by nb_set_coords.
+ * Errors: NB_ERR_ARG, NB_ERR_STATE (no list), NB_ERR_BOX, NB_ERR_CUDA. */
+nb_status nb_prune(nb_ctx* ctx, const float* xyz_dev, float r_prune, nb_stream stream);
+
+/* Forces (and with p->want_energy, energies and virial) over the current list
+ * (the pruned one after nb_prune, else the outer one) -- Sec. 3, Fig. 6:
+ * per cluster pair, LJ (type table) plus Coulomb (RF or Ewald real space),
+ * normal pairs by mask bit, force-field-excluded pairs within rc with the
+ * correction only.  xyz_dev may be NULL (current coordinates).
+ * f_dev: float [n][3], caller order, overwritten.
+ * e_dev: double [2] {E_LJ, E_Coulomb} (kJ/mol), overwritten; may be NULL.
+ * vir_dev: double [9], W = sum over pairs r_ij (x) F_ij (row-major), with
+ * r_ij = x_i - x_j and F_ij the force on i; overwritten; may be NULL.
+ * Errors: NB_ERR_ARG, NB_ERR_BOX (rc >= L/2 or rc > rlist), NB_ERR_STATE (no
+ * list), NB_ERR_CUDA. */
+nb_status nb_compute(nb_ctx* ctx, const nb_params* p, const float* xyz_dev, float* f_dev,
+                     double* e_dev, double* vir_dev, nb_stream stream);
+
+/* Synchronise the stream, read the device flags and sizes into *info (may be
+ * NULL) and turn a raised flag into its status.  Clears the flags. */
+nb_status nb_check(nb_ctx* ctx, nb_stream stream, nb_info* info);
+
+/* --- introspection (tests) -------------------------------------------------- */
+
+/* Copy the grid (device to device, on the stream).  Any pointer may be NULL.
+ * atom_of_slot_dev: int [nslots] (-1 for dummies), slot_of_atom_dev: int [n],
+ * col_clu_start_dev: int [nx*ny+1], xyzq_dev: float [nslots][4] (wrapped
+ * coordinates and charge; dummies far outside the box), type_slot_dev: int
+ * [nslots], bb_dev: float [nclusters][6] (min xyz, max xyz), col_of_atom_dev:
+ * int [n].  nslots = n_clusters * C from nb_check's info.
+ * Errors: NB_ERR_STATE, NB_ERR_CUDA. */
+nb_status nb_get_grid(nb_ctx* ctx, int* atom_of_slot_dev, int* slot_of_atom_dev,
+                      int* col_clu_start_dev, float* xyzq_dev, int* type_slot_dev, float* bb_dev,
+                      int* col_of_atom_dev, nb_stream stream);
+
+/* Copy a list (which = 0: outer, 1: pruned) in its storage form, device to
+ * device: ient_dev int [n_ientries][4] = {ci, shift, j_begin, j_end}, cj_dev
+ * int [n_jentries], mask_dev uint64 [n_jentries].  Shift index s encodes
+ * (sx, sy, sz) in {-1,0,1}^3 as (sx+1)*9 + (sy+1)*3 + (sz+1).  Sizes from
+ * nb_check (j-entries are indexed by the i-entries' ranges; for the pruned
+ * list use the outer list's n_jentries as the array size).
+ * Errors: NB_ERR_STATE, NB_ERR_CUDA. */
+nb_status nb_get_list(nb_ctx* ctx, int which, int* ient_dev, int* cj_dev, uint64_t* mask_dev,
+                      nb_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBCLUSTER_H */

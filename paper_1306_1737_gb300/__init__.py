@@ -1,0 +1,264 @@
+"""Python binding of libnbcluster (the C ABI in include/nbcluster.h).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name; device arrays are torch CUDA tensors (their data_ptr is
+passed), streams default to torch's current stream.  All the computation runs
+in the library's CUDA kernels; there is no CPU fallback.  If the library has
+not been built (``__graft_entry__.build()`` or ``python -m
+paper_1306_1737_gb300.build``), loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libnbcluster.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "nbcluster.h")
+
+NB_OK = 0
+NB_ERR_ARG = 1
+NB_ERR_BOX = 2
+NB_ERR_CAPACITY = 3
+NB_ERR_CUDA = 4
+NB_ERR_STATE = 5
+NB_ERR_TIMEOUT = 6
+NB_ERR_COORD = 7
+
+NB_ELEC_RF = 0
+NB_ELEC_EWALD = 1
+NB_COMB_LB = 0
+NB_COMB_GEOM = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class nb_options(C.Structure):
+    _fields_ = [("cluster_size", C.c_int), ("device", C.c_int)]
+
+
+class nb_params(C.Structure):
+    _fields_ = [("elec", C.c_int), ("want_energy", C.c_int), ("rc", C.c_float),
+                ("eps_rf", C.c_float), ("beta", C.c_float)]
+
+
+class nb_info(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("n_clusters", C.c_int),
+                ("n_ientries", C.c_int64), ("n_jentries", C.c_int64),
+                ("n_jentries_pruned", C.c_int64), ("ient_capacity", C.c_int64),
+                ("jent_capacity", C.c_int64), ("flags", C.c_uint32)]
+
+
+class NbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+def load():
+    """Load libnbcluster.so (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -m paper_1306_1737_gb300.build)")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        i = C.c_int
+        st = C.c_int
+        sig = {
+            "nb_create": ([C.POINTER(P), C.POINTER(nb_options)], st),
+            "nb_destroy": ([P], st),
+            "nb_last_error": ([P], C.c_char_p),
+            "nb_status_string": ([i], C.c_char_p),
+            "nb_lj_combine": ([i, P, P, i, P], st),
+            "nb_workspace_query": ([P, i, P, C.c_double, i, C.c_double, C.POINTER(C.c_size_t)], st),
+            "nb_set_workspace": ([P, P, C.c_size_t], st),
+            "nb_set_atoms": ([P, i, P, P, i, P, P], st),
+            "nb_grid_put": ([P, P, P, P], st),
+            "nb_pairlist_build": ([P, C.c_float, C.c_float, P, P, P], st),
+            "nb_set_coords": ([P, P, P], st),
+            "nb_prune": ([P, P, C.c_float, P], st),
+            "nb_compute": ([P, C.POINTER(nb_params), P, P, P, P, P], st),
+            "nb_check": ([P, P, C.POINTER(nb_info)], st),
+            "nb_get_grid": ([P, P, P, P, P, P, P, P, P], st),
+            "nb_get_list": ([P, i, P, P, P, P], st),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return L
+
+
+def exported_symbols():
+    """Names declared in include/nbcluster.h (for the ABI test)."""
+    import re
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:nb_status|const char\*)\s+(nb_\w+)\s*\(", txt, re.M)))
+
+
+def status_name(s: int) -> str:
+    return load().nb_status_string(int(s)).decode()
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (or an int / None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(ctx, s):
+    if s != NB_OK:
+        msg = load().nb_last_error(ctx).decode() if ctx else ""
+        raise NbError(s, msg)
+
+
+# --- entry points (same names as the C ABI) --------------------------------
+
+def nb_create(cluster_size: int = 8, device: int = 0):
+    h = C.c_void_p()
+    opt = nb_options(cluster_size, device)
+    _check(None, load().nb_create(C.byref(h), C.byref(opt)))
+    return h
+
+
+def nb_destroy(ctx):
+    _check(None, load().nb_destroy(ctx))
+
+
+def nb_last_error(ctx) -> str:
+    return load().nb_last_error(ctx).decode()
+
+
+def nb_lj_combine(sigma, eps, comb: int = NB_COMB_LB):
+    """Host LJ pair table float32 [nt, nt, 2] from per-type sigma/epsilon."""
+    import numpy as np
+    s = np.ascontiguousarray(sigma, dtype=np.float64)
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    nt = s.shape[0]
+    out = np.zeros((nt, nt, 2), np.float32)
+    _check(None, load().nb_lj_combine(nt, s.ctypes.data, e.ctypes.data, int(comb), out.ctypes.data))
+    return out
+
+
+def nb_workspace_query(ctx, n_atoms: int, box, rlist_max: float, ntypes: int,
+                       list_factor: float = 0.0) -> int:
+    b = (C.c_double * 3)(*[float(v) for v in box])
+    nbytes = C.c_size_t()
+    _check(ctx, load().nb_workspace_query(ctx, int(n_atoms), b, float(rlist_max), int(ntypes),
+                                          float(list_factor), C.byref(nbytes)))
+    return nbytes.value
+
+
+def nb_set_workspace(ctx, ws, nbytes: int):
+    _check(ctx, load().nb_set_workspace(ctx, _ptr(ws), int(nbytes)))
+
+
+def nb_set_atoms(ctx, n, q, types, ntypes, c6c12, stream=None):
+    _check(ctx, load().nb_set_atoms(ctx, int(n), _ptr(q), _ptr(types), int(ntypes), _ptr(c6c12),
+                                    _stream(stream)))
+
+
+def nb_grid_put(ctx, xyz, box, stream=None):
+    b = (C.c_double * 3)(*[float(v) for v in box])
+    _check(ctx, load().nb_grid_put(ctx, _ptr(xyz), b, _stream(stream)))
+
+
+def nb_pairlist_build(ctx, rlist, rbb=0.0, excl_off=None, excl_idx=None, stream=None):
+    _check(ctx, load().nb_pairlist_build(ctx, float(rlist), float(rbb), _ptr(excl_off),
+                                         _ptr(excl_idx), _stream(stream)))
+
+
+def nb_set_coords(ctx, xyz, stream=None):
+    _check(ctx, load().nb_set_coords(ctx, _ptr(xyz), _stream(stream)))
+
+
+def nb_prune(ctx, xyz, r_prune, stream=None):
+    _check(ctx, load().nb_prune(ctx, _ptr(xyz), float(r_prune), _stream(stream)))
+
+
+def make_params(elec: str, rc: float, eps_rf: float = float("inf"), beta: float = 0.0,
+                want_energy: bool = True) -> nb_params:
+    return nb_params(NB_ELEC_RF if elec == "rf" else NB_ELEC_EWALD, int(bool(want_energy)),
+                     float(rc), float(eps_rf), float(beta))
+
+
+def nb_compute(ctx, params: nb_params, xyz, f, e=None, vir=None, stream=None):
+    _check(ctx, load().nb_compute(ctx, C.byref(params), _ptr(xyz), _ptr(f), _ptr(e), _ptr(vir),
+                                  _stream(stream)))
+
+
+def nb_check(ctx, stream=None, raise_on_error: bool = True) -> nb_info:
+    info = nb_info()
+    s = load().nb_check(ctx, _stream(stream), C.byref(info))
+    if raise_on_error:
+        _check(ctx, s)
+    info.status = s
+    return info
+
+
+def nb_get_grid(ctx, atom_of_slot=None, slot_of_atom=None, col_clu_start=None, xyzq=None,
+                type_slot=None, bb=None, col_of_atom=None, stream=None):
+    _check(ctx, load().nb_get_grid(ctx, _ptr(atom_of_slot), _ptr(slot_of_atom), _ptr(col_clu_start),
+                                   _ptr(xyzq), _ptr(type_slot), _ptr(bb), _ptr(col_of_atom),
+                                   _stream(stream)))
+
+
+def nb_get_list(ctx, which, ient=None, cj=None, mask=None, stream=None):
+    _check(ctx, load().nb_get_list(ctx, int(which), _ptr(ient), _ptr(cj), _ptr(mask),
+                                   _stream(stream)))
+
+
+# --- convenience: one box with its torch-allocated workspace ---------------
+
+class Context:
+    """A context bound to one box: allocates the workspace with torch and
+    keeps the per-particle inputs on the device."""
+
+    def __init__(self, n, box, rlist_max, q, types, c6c12, cluster_size=8, device=0,
+                 list_factor=0.0, stream=None):
+        import torch
+        self.torch = torch
+        self.dev = torch.device("cuda", device)
+        self.n = int(n)
+        self.C = cluster_size
+        self.ctx = nb_create(cluster_size, device)
+        nt = int(c6c12.shape[0])
+        self.ws_bytes = nb_workspace_query(self.ctx, self.n, box, rlist_max, nt, list_factor)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.dev)
+        base = self.ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        nb_set_workspace(self.ctx, aligned, self.ws_bytes)
+        self.q = torch.as_tensor(q, dtype=torch.float32).to(self.dev).contiguous()
+        self.types = torch.as_tensor(types, dtype=torch.int32).to(self.dev).contiguous()
+        self.c6c12 = torch.as_tensor(c6c12, dtype=torch.float32).to(self.dev).contiguous()
+        nb_set_atoms(self.ctx, self.n, self.q, self.types, nt, self.c6c12, stream)
+
+    def close(self):
+        if self.ctx is not None:
+            nb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

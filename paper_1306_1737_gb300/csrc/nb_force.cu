@@ -1,0 +1,393 @@
+// Cluster-pair force/energy kernel (Sec. 3, Fig. 6) and the FP64 reductions.
+//
+// k_force8: one warp per i-entry {ci, shift, j-range} of 8-particle clusters.
+// Lane (ih = lane / 8, j = lane % 8) owns particle pairs (ih, j) and (ih+4, j)
+// of every j-cluster, so the 8 x 8 cluster pair is two 8 x 4 halves spread
+// over the warp (one particle pair per thread and half).  The i-cluster stays
+// in registers, shifted by the entry's periodic image as an unevaluated FP32
+// sum hi + lo; each j-particle is one coalesced float4 load.  A pair is
+// computed when r^2 < rc^2 and either its mask bit is set (full LJ + Coulomb)
+// or it is a counted pair without the bit (force-field exclusion: only the
+// RF/Ewald correction, Sec. 2.4); the mask bit multiplies the plain terms
+// (Sec. 3.1: masking by multiplication, conditional on the cut-off).
+// j-forces are reduced over the 4 lanes sharing j with two shuffles and
+// added with one vector atomic per j-particle; i-forces are reduced at the
+// end of the entry and added once per i-particle.
+//
+// Pair functions (Sec. 3.2), with qq = f q_i q_j and e = mask bit:
+//   LJ      F/r = e (12 C12 r^-6 - 6 C6) r^-8,  V = e (C12 r^-6 - C6) r^-6
+//   RF      F/r = qq (e r^-3 - 2k),             V = qq (e r^-1 + k r^2 - c_rf)
+//   Ewald   F/r = qq (erfc(br) - (1-e) + 2br/sqrt(pi) exp(-b^2 r^2)) r^-3,
+//           V = qq (erfc(br) - (1-e)) r^-1
+#include "nb_internal.cuh"
+
+namespace nbc {
+
+struct ForceArgs {
+    const DevState* st;
+    const float4* xyzq;
+    const int* type_slot;
+    const float2* c6c12;
+    const int4* ient;
+    const int* cj;
+    const unsigned long long* mask;
+    float4* fslot;
+    Accum* acc;
+    ForceParams p;
+};
+
+constexpr int kForceWarps = 4;
+
+template <int ELEC, bool ENERGY>
+__device__ __forceinline__ void pair_fn(const ForceParams& P, bool inc, float bit, float r2, float qq,
+                                        float2 lj, float& fs, float& vlj, float& vc) {
+    const float r2s = inc ? r2 : 1.0f;
+    const float rinv = rsqrtf(r2s);
+    const float rinv2 = rinv * rinv;
+    const float rinv6 = rinv2 * rinv2 * rinv2;
+    // lj = {6 C6, 12 C12}
+    const float flj = bit * (lj.y * rinv6 - lj.x) * rinv6 * rinv2;
+    float fc;
+    if (ELEC == NB_ELEC_RF) {
+        fc = qq * (bit * rinv * rinv2 - P.two_k_rf);
+        if (ENERGY) vc = inc ? qq * (bit * rinv + P.k_rf * r2s - P.c_rf) : 0.0f;
+    } else {
+        const float r = r2s * rinv;
+        const float br = P.beta * r;
+        const float ec = erfcf(br) - (1.0f - bit);
+        const float ex = __expf(-br * br);
+        fc = qq * (ec + P.two_beta_sqrtpi * r * ex) * rinv * rinv2;
+        if (ENERGY) vc = inc ? qq * ec * rinv : 0.0f;
+    }
+    fs = inc ? flj + fc : 0.0f;
+    if (ENERGY)
+        vlj = inc ? bit * (lj.y * (1.0f / 12.0f) * rinv6 - lj.x * (1.0f / 6.0f)) * rinv6 : 0.0f;
+}
+
+template <int ELEC, bool ENERGY>
+__global__ void __launch_bounds__(32 * kForceWarps) k_force8(ForceArgs A) {
+    extern __shared__ float2 s_lj[];
+    const unsigned full = 0xffffffffu;
+    const int nt2 = A.p.ntypes * A.p.ntypes;
+    for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
+        const float2 v = A.c6c12[k];
+        s_lj[k] = make_float2(6.0f * v.x, 12.0f * v.y);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int j = lane & 7, ih = lane >> 3;
+    const long long nient = min((long long)A.st->n_ient, A.p.ient_cap);
+    float e_lj = 0.0f, e_c = 0.0f;
+    for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < nient;
+         e += (long long)gridDim.x * kForceWarps) {
+        const int4 ie = A.ient[e];
+        const int ci = ie.x, s = ie.y, jb = ie.z, je = ie.w;
+        if (jb >= je) continue;
+        const float sh[3] = {(float)(s / 9 - 1) * A.p.L[0], (float)((s / 3) % 3 - 1) * A.p.L[1],
+                             (float)(s % 3 - 1) * A.p.L[2]};
+        const float4 x0 = A.xyzq[ci * 8 + ih];
+        const float4 x1 = A.xyzq[ci * 8 + ih + 4];
+        float x0h[3], x0l[3], x1h[3], x1l[3];
+        two_sum(x0.x, sh[0], x0h[0], x0l[0]);
+        two_sum(x0.y, sh[1], x0h[1], x0l[1]);
+        two_sum(x0.z, sh[2], x0h[2], x0l[2]);
+        two_sum(x1.x, sh[0], x1h[0], x1l[0]);
+        two_sum(x1.y, sh[1], x1h[1], x1l[1]);
+        two_sum(x1.z, sh[2], x1h[2], x1l[2]);
+        const float qi0 = x0.w * A.p.fcoul, qi1 = x1.w * A.p.fcoul;
+        const int ti0 = A.type_slot[ci * 8 + ih] * A.p.ntypes;
+        const int ti1 = A.type_slot[ci * 8 + ih + 4] * A.p.ntypes;
+        const bool center = (s == kShiftCenter);
+        const int bitpos = ih * 8 + j;
+        float f0[3] = {0.f, 0.f, 0.f}, f1[3] = {0.f, 0.f, 0.f};
+        for (int base = jb; base < je; base += 32) {
+            const int nt = min(32, je - base);
+            int my_cj = 0;
+            unsigned long long my_m = 0;
+            if (lane < nt) {
+                my_cj = A.cj[base + lane];
+                my_m = A.mask[base + lane];
+            }
+            for (int t = 0; t < nt; ++t) {
+                const int cjt = __shfl_sync(full, my_cj, t);
+                const unsigned mlo = __shfl_sync(full, (unsigned)my_m, t);
+                const unsigned mhi = __shfl_sync(full, (unsigned)(my_m >> 32), t);
+                const float4 xj = A.xyzq[cjt * 8 + j];
+                const int tj = A.type_slot[cjt * 8 + j];
+                const bool diag = center && (cjt == ci);
+                const float b0 = (float)((mlo >> bitpos) & 1u);
+                const float b1 = (float)((mhi >> bitpos) & 1u);
+                const float d0x = (x0h[0] - xj.x) + x0l[0];
+                const float d0y = (x0h[1] - xj.y) + x0l[1];
+                const float d0z = (x0h[2] - xj.z) + x0l[2];
+                const float d1x = (x1h[0] - xj.x) + x1l[0];
+                const float d1y = (x1h[1] - xj.y) + x1l[1];
+                const float d1z = (x1h[2] - xj.z) + x1l[2];
+                const float r2_0 = fmaf(d0x, d0x, fmaf(d0y, d0y, d0z * d0z));
+                const float r2_1 = fmaf(d1x, d1x, fmaf(d1y, d1y, d1z * d1z));
+                const bool inc0 = (r2_0 < A.p.rc2) && (b0 != 0.0f || !(diag && j <= ih));
+                const bool inc1 = (r2_1 < A.p.rc2) && (b1 != 0.0f || !(diag && j <= ih + 4));
+                if (!__any_sync(full, inc0 || inc1)) continue;
+                float fs0, fs1, vl0 = 0.f, vl1 = 0.f, vc0 = 0.f, vc1 = 0.f;
+                pair_fn<ELEC, ENERGY>(A.p, inc0, b0, r2_0, qi0 * xj.w, s_lj[ti0 + tj], fs0, vl0, vc0);
+                pair_fn<ELEC, ENERGY>(A.p, inc1, b1, r2_1, qi1 * xj.w, s_lj[ti1 + tj], fs1, vl1, vc1);
+                if (ENERGY) {
+                    e_lj += vl0 + vl1;
+                    e_c += vc0 + vc1;
+                }
+                f0[0] = fmaf(fs0, d0x, f0[0]);
+                f0[1] = fmaf(fs0, d0y, f0[1]);
+                f0[2] = fmaf(fs0, d0z, f0[2]);
+                f1[0] = fmaf(fs1, d1x, f1[0]);
+                f1[1] = fmaf(fs1, d1y, f1[1]);
+                f1[2] = fmaf(fs1, d1z, f1[2]);
+                float fjx = -fmaf(fs0, d0x, fs1 * d1x);
+                float fjy = -fmaf(fs0, d0y, fs1 * d1y);
+                float fjz = -fmaf(fs0, d0z, fs1 * d1z);
+                fjx += __shfl_xor_sync(full, fjx, 8);
+                fjy += __shfl_xor_sync(full, fjy, 8);
+                fjz += __shfl_xor_sync(full, fjz, 8);
+                fjx += __shfl_xor_sync(full, fjx, 16);
+                fjy += __shfl_xor_sync(full, fjy, 16);
+                fjz += __shfl_xor_sync(full, fjz, 16);
+                if (ih == 0) atomicAdd(&A.fslot[cjt * 8 + j], make_float4(fjx, fjy, fjz, 0.0f));
+            }
+        }
+        // i-forces: sum over the 8 lanes of each i row
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                f0[d] += __shfl_xor_sync(full, f0[d], o);
+                f1[d] += __shfl_xor_sync(full, f1[d], o);
+            }
+        }
+        if (j == 0) {
+            atomicAdd(&A.fslot[ci * 8 + ih], make_float4(f0[0], f0[1], f0[2], 0.0f));
+            atomicAdd(&A.fslot[ci * 8 + ih + 4], make_float4(f1[0], f1[1], f1[2], 0.0f));
+        }
+        if (ENERGY && !center) {
+            // i-side force of this shifted entry, for the virial
+            float t[3] = {f0[0] + f1[0], f0[1] + f1[1], f0[2] + f1[2]};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                t[d] += __shfl_xor_sync(full, t[d], 8);
+                t[d] += __shfl_xor_sync(full, t[d], 16);
+            }
+            if (lane == 0)
+                for (int d = 0; d < 3; ++d) atomicAdd(&A.acc->fshift[s][d], (double)t[d]);
+        }
+    }
+    if (ENERGY) {
+        for (int o = 16; o > 0; o >>= 1) {
+            e_lj += __shfl_xor_sync(full, e_lj, o);
+            e_c += __shfl_xor_sync(full, e_c, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&A.acc->energy[0], (double)e_lj);
+            atomicAdd(&A.acc->energy[1], (double)e_c);
+        }
+    }
+}
+
+// Generic C = 4 kernel: one warp per i-entry, lanes 0..15 hold the 4 x 4
+// pairs of one j-cluster and lanes 16..31 those of the next.
+template <int ELEC, bool ENERGY>
+__global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
+    extern __shared__ float2 s_lj[];
+    const unsigned full = 0xffffffffu;
+    const int nt2 = A.p.ntypes * A.p.ntypes;
+    for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
+        const float2 v = A.c6c12[k];
+        s_lj[k] = make_float2(6.0f * v.x, 12.0f * v.y);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int half = lane >> 4, i = (lane >> 2) & 3, j = lane & 3;
+    const long long nient = min((long long)A.st->n_ient, A.p.ient_cap);
+    float e_lj = 0.0f, e_c = 0.0f;
+    for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < nient;
+         e += (long long)gridDim.x * kForceWarps) {
+        const int4 ie = A.ient[e];
+        const int ci = ie.x, s = ie.y, jb = ie.z, je = ie.w;
+        if (jb >= je) continue;
+        const float sh[3] = {(float)(s / 9 - 1) * A.p.L[0], (float)((s / 3) % 3 - 1) * A.p.L[1],
+                             (float)(s % 3 - 1) * A.p.L[2]};
+        const float4 x0 = A.xyzq[ci * 4 + i];
+        float xh[3], xl[3];
+        two_sum(x0.x, sh[0], xh[0], xl[0]);
+        two_sum(x0.y, sh[1], xh[1], xl[1]);
+        two_sum(x0.z, sh[2], xh[2], xl[2]);
+        const float qi = x0.w * A.p.fcoul;
+        const int ti = A.type_slot[ci * 4 + i] * A.p.ntypes;
+        const bool center = (s == kShiftCenter);
+        float fi[3] = {0.f, 0.f, 0.f};
+        for (int k = jb; k < je; k += 2) {
+            const int kk = k + half;
+            const bool live = kk < je;
+            const int cjt = live ? A.cj[kk] : ci;
+            const unsigned long long m = live ? A.mask[kk] : 0ull;
+            const float4 xj = A.xyzq[cjt * 4 + j];
+            const int tj = A.type_slot[cjt * 4 + j];
+            const bool diag = center && (cjt == ci);
+            const float b = (float)((m >> (i * 4 + j)) & 1ull);
+            const float dx = (xh[0] - xj.x) + xl[0];
+            const float dy = (xh[1] - xj.y) + xl[1];
+            const float dz = (xh[2] - xj.z) + xl[2];
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const bool inc = live && (r2 < A.p.rc2) && (b != 0.0f || !(diag && j <= i));
+            if (!__any_sync(full, inc)) continue;
+            float fs, vl = 0.f, vc = 0.f;
+            pair_fn<ELEC, ENERGY>(A.p, inc, b, r2, qi * xj.w, s_lj[ti + tj], fs, vl, vc);
+            if (ENERGY) {
+                e_lj += vl;
+                e_c += vc;
+            }
+            fi[0] = fmaf(fs, dx, fi[0]);
+            fi[1] = fmaf(fs, dy, fi[1]);
+            fi[2] = fmaf(fs, dz, fi[2]);
+            float fjx = -fs * dx, fjy = -fs * dy, fjz = -fs * dz;
+            for (int o = 4; o < 16; o <<= 1) {
+                fjx += __shfl_xor_sync(full, fjx, o);
+                fjy += __shfl_xor_sync(full, fjy, o);
+                fjz += __shfl_xor_sync(full, fjz, o);
+            }
+            if (i == 0 && live) atomicAdd(&A.fslot[cjt * 4 + j], make_float4(fjx, fjy, fjz, 0.0f));
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            fi[d] += __shfl_xor_sync(full, fi[d], 1);
+            fi[d] += __shfl_xor_sync(full, fi[d], 2);
+            fi[d] += __shfl_xor_sync(full, fi[d], 16);
+        }
+        if (j == 0 && half == 0) atomicAdd(&A.fslot[ci * 4 + i], make_float4(fi[0], fi[1], fi[2], 0.0f));
+        if (ENERGY && !center) {
+            float t[3] = {fi[0], fi[1], fi[2]};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                t[d] += __shfl_xor_sync(full, t[d], 4);
+                t[d] += __shfl_xor_sync(full, t[d], 8);
+            }
+            if (lane == 0)
+                for (int d = 0; d < 3; ++d) atomicAdd(&A.acc->fshift[s][d], (double)t[d]);
+        }
+    }
+    if (ENERGY) {
+        for (int o = 16; o > 0; o >>= 1) {
+            e_lj += __shfl_xor_sync(full, e_lj, o);
+            e_c += __shfl_xor_sync(full, e_c, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&A.acc->energy[0], (double)e_lj);
+            atomicAdd(&A.acc->energy[1], (double)e_c);
+        }
+    }
+}
+
+template <int ELEC, bool ENERGY>
+static cudaError_t launch_force_t(const ForceArgs& A, int C, int n_sm, cudaStream_t s) {
+    const size_t smem = sizeof(float2) * A.p.ntypes * A.p.ntypes;
+    auto kern = (C == 8) ? k_force8<ELEC, ENERGY> : k_force4<ELEC, ENERGY>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kForceWarps, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    kern<<<n_sm * per_sm, 32 * kForceWarps, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n_sm,
+                         long long n_slots_cap, cudaStream_t s) {
+    (void)n_slots_cap;
+    ForceArgs A;
+    A.st = ws.st;
+    A.xyzq = ws.xyzq;
+    A.type_slot = ws.type_slot;
+    A.c6c12 = ws.c6c12;
+    A.ient = p.use_pruned ? ws.ient_p : ws.ient;
+    A.cj = p.use_pruned ? ws.cj_p : ws.cj;
+    A.mask = p.use_pruned ? ws.mask_p : ws.mask;
+    A.fslot = ws.fslot;
+    A.acc = ws.acc;
+    A.p = p;
+    cudaError_t e = cudaMemsetAsync(ws.acc, 0, sizeof(Accum), s);
+    if (e != cudaSuccess) return e;
+    if (p.elec == NB_ELEC_RF)
+        return p.want_energy ? launch_force_t<NB_ELEC_RF, true>(A, C, n_sm, s)
+                             : launch_force_t<NB_ELEC_RF, false>(A, C, n_sm, s);
+    return p.want_energy ? launch_force_t<NB_ELEC_EWALD, true>(A, C, n_sm, s)
+                         : launch_force_t<NB_ELEC_EWALD, false>(A, C, n_sm, s);
+}
+
+// Forces back to the caller's order (and zeroed for the next evaluation);
+// with energies, the FP64 sum over slots of x (x) f for the virial.
+__global__ void k_finalize(int n, const int* __restrict__ slot_of_atom, float4* __restrict__ fslot,
+                           const float4* __restrict__ xyzq, float* __restrict__ f_out, int want_vir,
+                           Accum* acc) {
+    double w[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int s = slot_of_atom[p];
+        const float4 f = fslot[s];
+        fslot[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        f_out[3 * p] = f.x;
+        f_out[3 * p + 1] = f.y;
+        f_out[3 * p + 2] = f.z;
+        if (want_vir) {
+            const float4 x = xyzq[s];
+            const double xa[3] = {x.x, x.y, x.z}, fb[3] = {f.x, f.y, f.z};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) w[3 * a + b] += xa[a] * fb[b];
+        }
+    }
+    if (!want_vir) return;
+    __shared__ double s_w[9][8];
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        for (int o = 16; o > 0; o >>= 1) w[k] += __shfl_xor_sync(full, w[k], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 9; ++k) s_w[k][warp] = w[k];
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double v = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += s_w[threadIdx.x][q];
+        atomicAdd(&acc->vir_xf[threadIdx.x], v);
+    }
+}
+
+__global__ void k_finalize_small(const Accum* acc, float Lx, float Ly, float Lz, double* e_out,
+                                 double* vir_out) {
+    if (threadIdx.x != 0) return;
+    if (e_out) {
+        e_out[0] = acc->energy[0];
+        e_out[1] = acc->energy[1];
+    }
+    if (vir_out) {
+        double w[9];
+        for (int k = 0; k < 9; ++k) w[k] = acc->vir_xf[k];
+        for (int s = 0; s < 27; ++s) {
+            const double sv[3] = {(double)(s / 9 - 1) * Lx, (double)((s / 3) % 3 - 1) * Ly,
+                                  (double)(s % 3 - 1) * Lz};
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) w[3 * a + b] += sv[a] * acc->fshift[s][b];
+        }
+        for (int k = 0; k < 9; ++k) vir_out[k] = w[k];
+    }
+}
+
+cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int n, float* f_out,
+                            double* e_out, double* vir_out, cudaStream_t s) {
+    const int want_vir = (p.want_energy && vir_out) ? 1 : 0;
+    int blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_finalize<<<blocks, 256, 0, s>>>(n, ws.slot_of_atom, ws.fslot, ws.xyzq, f_out, want_vir, ws.acc);
+    if (p.want_energy && (e_out || vir_out))
+        k_finalize_small<<<1, 32, 0, s>>>(ws.acc, p.L[0], p.L[1], p.L[2], e_out, vir_out);
+    return cudaGetLastError();
+}
+
+}  // namespace nbc

@@ -1,0 +1,50 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports
+every entry point include/nbcluster.h declares (no compute calls)."""
+import ctypes
+import re
+import subprocess
+
+import pytest
+
+import paper_1306_1737_gb300 as nb
+from paper_1306_1737_gb300 import build as nbbuild
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nbbuild.build()
+    return nb.load()
+
+
+def test_header_declares_the_hot_path(lib):
+    names = nb.exported_symbols()
+    for required in ("nb_grid_put", "nb_pairlist_build", "nb_prune", "nb_compute", "nb_create",
+                     "nb_destroy", "nb_workspace_query", "nb_set_workspace", "nb_set_atoms",
+                     "nb_check", "nb_set_coords"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", nb.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (nb_\w+)$", out, re.M))
+    for name in nb.exported_symbols():
+        assert name in exported, name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_status_strings_and_host_helpers(lib):
+    assert nb.status_name(nb.NB_OK) == "NB_OK"
+    assert nb.status_name(nb.NB_ERR_CAPACITY) == "NB_ERR_CAPACITY"
+    t = nb.nb_lj_combine([0.3166, 0.0], [0.65, 0.0])
+    # C6 = 4 eps sigma^6, C12 = 4 eps sigma^12 for the O-O pair
+    assert t[0, 0, 0] == pytest.approx(4 * 0.65 * 0.3166 ** 6, rel=1e-6)
+    assert t[0, 0, 1] == pytest.approx(4 * 0.65 * 0.3166 ** 12, rel=1e-6)
+    assert (t[1] == 0).all() and (t[:, 1] == 0).all()
+    with pytest.raises(nb.NbError):
+        nb.nb_lj_combine([0.3], [0.5], comb=7)
+
+
+def test_null_context_is_rejected(lib):
+    assert lib.nb_destroy(None) == nb.NB_ERR_ARG
+    assert lib.nb_grid_put(None, None, None, None) == nb.NB_ERR_ARG

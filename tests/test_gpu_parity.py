@@ -1,0 +1,213 @@
+"""GPU parity against the FP64 oracle, through the C ABI.
+
+Grid ordering and exclusion masks bit-exact; cluster-pair lists equal as
+canonical key sets (keys whose minimum particle distance is within 1e-6 nm
+of the list radius exempt); forces within 1e-4 of the RMS force (max over
+particles); energies and virial reported and bounded by 1e-5 relative."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1306_1737_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-4   # max |dF| / RMS |F|  (spec bound)
+EXEMPT_NM = 1e-6   # list keys this close to the threshold may differ
+E_TOL = 1e-5       # relative error of FP64 totals of FP32 pair terms
+
+
+@pytest.fixture(scope="module")
+def gp():
+    pytest.importorskip("torch")
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1306_1737_gb300 as nb
+    nb.load()
+    import gpu_path
+    return gpu_path
+
+
+def check_grid(g_gpu, g_or):
+    assert g_gpu["info"].nx == g_or.nx and g_gpu["info"].ny == g_or.ny
+    assert g_gpu["info"].n_clusters == g_or.nclu
+    assert np.array_equal(g_gpu["col_clu_start"], g_or.col_clu_start)
+    assert np.array_equal(g_gpu["col_of_atom"], g_or.col_of_atom)
+    assert np.array_equal(g_gpu["atom_of_slot"], g_or.atom_of_slot)
+    assert np.array_equal(g_gpu["slot_of_atom"], g_or.slot_of_atom)
+    assert np.array_equal(g_gpu["type_slot"], g_or.type_slot)
+    # bit-exact float data
+    assert np.array_equal(g_gpu["xyzq"].view(np.uint32), g_or.xyzq.view(np.uint32))
+    assert np.array_equal(g_gpu["bb"].view(np.uint32), g_or.bb.view(np.uint32))
+
+
+def check_list(gb, g_or, pl_or, rlist, which=0, r_thresh=None, xyzq=None):
+    """Compare the GPU list (which = 0 outer, 1 pruned) with the oracle's keys;
+    differing keys must lie within EXEMPT_NM of the threshold (the list
+    radius, or for the pruned list the prune radius under xyzq)."""
+    gp_ = __import__("gpu_path")
+    info, ient, cj, mask = gb.list_arrays(which)
+    keys_gpu, dup = gp_.canonical_keys(ient, cj, mask)
+    assert dup == 0
+    keys_or = pl_or.key_mask()
+    only_gpu = set(keys_gpu) - set(keys_or)
+    only_or = set(keys_or) - set(keys_gpu)
+    r = rlist if r_thresh is None else r_thresh
+    for ks in (only_gpu, only_or):
+        if ks:
+            a = np.array([k[0] for k in ks], np.int32)
+            b = np.array([k[1] for k in ks], np.int32)
+            s = np.array([k[2] for k in ks], np.int32)
+            if which == 0:
+                dm, _ = oracle.key_distances(g_or, a, b, s, xyzq)
+            else:
+                _, dm = oracle.prune(g_or, oracle.PairList(a, b, s, np.zeros(a.size, np.uint64)),
+                                     r, xyzq)
+            assert np.all(np.abs(dm - r) < EXEMPT_NM), (len(ks), dm[np.abs(dm - r) >= EXEMPT_NM][:5])
+    common = set(keys_gpu) & set(keys_or)
+    bad = [k for k in common if keys_gpu[k] != keys_or[k]]
+    assert not bad, bad[:5]
+    # j-lists are chunked: each i-entry holds at most 64 j-entries
+    assert np.all(ient[:, 3] - ient[:, 2] <= 64)
+    return len(keys_gpu), len(only_gpu) + len(only_or)
+
+
+@pytest.mark.parametrize("C", [8, 4])
+def test_config1_grid_list_forces_rf(gp, cfg1, C):
+    b, p = cfg1
+    gb = gp.GpuBox(b, p["rlist"], C=C)
+    try:
+        gb.grid()
+        g_or = oracle.grid(b.xyz, b.q, b.types, b.box, C)
+        check_grid(gb.grid_arrays(), g_or)
+        rl = float(np.float32(p["rlist"]))
+        gb.build(rl)
+        pl = oracle.pairlist(g_or, rl, 0.0, b.excl_off, b.excl_idx)
+        check_list(gb, g_or, pl, rl)
+        import paper_1306_1737_gb300 as nb
+        prm = nb.make_params("rf", p["rc"], eps_rf=math.inf)
+        f, e, vir = gb.compute(prm)
+        fo, eo, vo = oracle.forces_brute(b.xyz, b.q, b.types, b.sigma, b.eps, b.excl_off,
+                                         b.excl_idx, b.box, oracle.make_params("rf", float(np.float32(p["rc"]))))
+        emax, erms, rms = gp.force_errors(f, fo)
+        assert emax < FORCE_TOL, (emax, erms)
+        assert np.abs(e - eo).max() / np.abs(eo).max() < E_TOL, (e, eo)
+        assert np.abs(vir - vo).max() / np.abs(vo).max() < E_TOL, (vir, vo)
+    finally:
+        gb.close()
+
+
+def test_config2_grid_list_prune_forces_ewald(gp, cfg2):
+    b, p = cfg2
+    gb = gp.GpuBox(b, p["rlist"])
+    try:
+        gb.grid()
+        g_or = oracle.grid(b.xyz, b.q, b.types, b.box, 8)
+        check_grid(gb.grid_arrays(), g_or)
+        rl = float(np.float32(p["rlist"]))
+        gb.build(rl)
+        pl = oracle.pairlist(g_or, rl, 0.0, b.excl_off, b.excl_idx)
+        nkeys, nex = check_list(gb, g_or, pl, rl)
+        assert nkeys > 0.9 * len(pl)
+        import paper_1306_1737_gb300 as nb
+        prm = nb.make_params("ewald", p["rc"], beta=p["beta"])
+        oprm = oracle.make_params("ewald", float(np.float32(p["rc"])), beta=p["beta"])
+        f, e, vir = gb.compute(prm)
+        fo, eo, vo = oracle.forces_brute(b.xyz, b.q, b.types, b.sigma, b.eps, b.excl_off,
+                                         b.excl_idx, b.box, oprm)
+        emax, erms, rms = gp.force_errors(f, fo)
+        assert emax < FORCE_TOL, (emax, erms)
+        assert np.abs(e - eo).max() / np.abs(eo).max() < E_TOL, (e, eo)
+        assert np.abs(vir - vo).max() / np.abs(vo).max() < E_TOL
+        # prune at a radius after moving the particles
+        disp = w.frame_displacements(b.mass, 5, seed=2002).sum(0)
+        x5 = b.xyz + disp
+        rp = float(np.float32(w.prune_radius(p["rc"], p["rlist"], p["nstprune"])))
+        gb.prune(rp, x5)
+        x5s = oracle.slot_coords(g_or, x5)
+        keep, dmin = oracle.prune(g_or, pl, rp, x5s)
+        kept = oracle.PairList(pl.a[keep], pl.b[keep], pl.s[keep], pl.mask[keep])
+        check_list(gb, g_or, kept, rl, which=1, r_thresh=rp, xyzq=x5s)
+        f5, e5, v5 = gb.compute(prm)
+        fo5, eo5, vo5 = oracle.forces_brute(x5, b.q, b.types, b.sigma, b.eps, b.excl_off,
+                                            b.excl_idx, b.box, oprm)
+        emax, erms, _ = gp.force_errors(f5, fo5)
+        assert emax < FORCE_TOL, (emax, erms)
+        assert np.abs(e5 - eo5).max() / np.abs(eo5).max() < E_TOL
+    finally:
+        gb.close()
+
+
+def test_small_boxes_multiple_images(gp):
+    # boxes barely above 2 rlist: cluster pairs in range under two shifts
+    import paper_1306_1737_gb300 as nb
+    for nmol, L, rl in ((70, 2.05, 1.0), (100, 1.45, 0.7)):
+        b = w.water_box(nmol, L, seed=nmol)
+        gb = gp.GpuBox(b, rl)
+        try:
+            gb.grid()
+            g_or = oracle.grid(b.xyz, b.q, b.types, b.box, 8)
+            check_grid(gb.grid_arrays(), g_or)
+            rlf = float(np.float32(rl))
+            gb.build(rlf)
+            pl = oracle.pairlist(g_or, rlf, 0.0, b.excl_off, b.excl_idx)
+            check_list(gb, g_or, pl, rlf)
+            rc = rl - 0.05
+            f, e, vir = gb.compute(nb.make_params("ewald", rc, beta=3.12))
+            fo, eo, vo = oracle.forces_brute(b.xyz, b.q, b.types, b.sigma, b.eps, b.excl_off,
+                                             b.excl_idx, b.box,
+                                             oracle.make_params("ewald", float(np.float32(rc)), beta=3.12))
+            emax, _, _ = gp.force_errors(f, fo)
+            assert emax < FORCE_TOL
+            assert np.abs(e - eo).max() / np.abs(eo).max() < E_TOL
+        finally:
+            gb.close()
+
+
+def test_rbb_shortcut(gp, cfg1):
+    b, p = cfg1
+    gb = gp.GpuBox(b, p["rlist"])
+    try:
+        gb.grid()
+        g_or = oracle.grid(b.xyz, b.q, b.types, b.box, 8)
+        rl, rbb = float(np.float32(1.0)), float(np.float32(0.5))
+        gb.build(rl, rbb)
+        pl = oracle.pairlist(g_or, rl, rbb, b.excl_off, b.excl_idx)
+        check_list(gb, g_or, pl, rl)
+    finally:
+        gb.close()
+
+
+def test_error_paths(gp, cfg1):
+    import paper_1306_1737_gb300 as nb
+    b, p = cfg1
+    gb = gp.GpuBox(b, 0.45)
+    try:
+        with pytest.raises(nb.NbError) as ei:
+            nb.nb_pairlist_build(gb.ctx, 1.0)
+        assert ei.value.status == nb.NB_ERR_STATE
+        gb.grid()
+        with pytest.raises(nb.NbError) as ei:
+            nb.nb_pairlist_build(gb.ctx, 1.3)      # >= L/2
+        assert ei.value.status == nb.NB_ERR_BOX
+        # list capacity sized for 0.45 nm, built at 1.2 nm: device overflow flag
+        nb.nb_pairlist_build(gb.ctx, 1.2, 0.0, gb.excl_off, gb.excl_idx)
+        info = nb.nb_check(gb.ctx, raise_on_error=False)
+        assert info.status == nb.NB_ERR_CAPACITY
+        # a coordinate outside [-L, 2L)
+        bad = b.xyz.copy()
+        bad[5, 1] = 3.5 * b.box[1]
+        nb.nb_grid_put(gb.ctx, gb.torch.as_tensor(bad).to(gb.dev), b.box)
+        info = nb.nb_check(gb.ctx, raise_on_error=False)
+        assert info.status == nb.NB_ERR_COORD
+        # flags are cleared by nb_check
+        gb.grid()
+        gb.build(0.45)
+        with pytest.raises(nb.NbError) as ei:
+            nb.nb_compute(gb.ctx, nb.make_params("rf", 0.9), None, gb.f)   # rc > rlist
+        assert ei.value.status == nb.NB_ERR_BOX
+    finally:
+        gb.close()
