@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the cluster-pair non-bonded hot path on one GB300 per rank.
+
+A step is one pair-list lifetime of the workload: grid the box
+(nb_grid_put), build the buffered cluster-pair list (nb_pairlist_build), then
+nstlist frames, each with new coordinates (pruning every nstprune frames,
+nb_prune) and one force evaluation (nb_compute; energies and virial on the
+first and last frame).  The headline value is force evaluations per second
+over the whole job.  Default workload: 24,000-atom water box, Ewald real
+space rc 1.0 nm, beta 3.12 nm^-1, rlist 1.1 nm, nstlist 20, prune every 5.
+
+--impl reference times the FP64 CPU oracle (brute-force minimum-image pair
+loop) on the same workload and metric: one force+energy evaluation per step.
+
+Under torchrun each rank runs an independent replica of the workload on its
+own GPU (the boxes share nothing); value = evaluations of all ranks / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "force evals/s & pair interactions/s vs plain kernel, force err ≤1e-4 RMS"
+UNIT = "force evals/s"
+L2_FLUSH_BYTES = 512 << 20
+
+# Algorithmic FP32 work per pair (paper, Tables 1-2: flops per pair of the
+# analytical kernels): every listed pair costs a distance test (9 flops);
+# pairs inside rc add the interaction (Ewald analytical 69, RF 40, minus the
+# distance part).
+FLOPS_DIST = 9
+FLOPS_PAIR = {"ewald": 69, "rf": 40}
+
+
+def workloads():
+    from paper_1306_1737_gb300 import workloads as w
+    return {
+        "water24k": ("24,000-atom water box, Ewald, rc 1.0, rlist 1.1, nstlist 20, prune/5", w.config2),
+        "water3m": ("3,000,000-atom water box + 8 LJ types (LB), Ewald, rlist 1.1, nstlist 40, prune/5",
+                    w.config3),
+        "water1536": ("1,536-atom water box, reaction field, rc 0.9, rlist 1.0", w.config1),
+    }
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            p["hbm_gbs"] = float(d.get("hbm_gbs", p["hbm_gbs"]))
+            p["sm_max_mhz"] = float(d.get("sm_max_mhz", p["sm_max_mhz"]))
+            p["source"] = "measured"
+        except Exception:
+            pass
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except Exception:
+                pass
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_eval(box, p):
+    import numpy as np
+    import oracle
+    prm = oracle.make_params(p["elec"], float(np.float32(p["rc"])), eps_rf=p.get("eps_rf", math.inf),
+                             beta=p.get("beta", 0.0), comb=p.get("comb", "lb"))
+    return oracle.forces_brute(box.xyz, box.q, box.types, box.sigma, box.eps, box.excl_off,
+                               box.excl_idx, box.box, prm)
+
+
+def cpu_baseline(box, p, budget_s=15.0):
+    """The oracle (brute-force FP64 pair loop) on a bounded sample: whole
+    force+energy evaluations of the same box, as many as fit ~budget_s."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle_eval(box, p)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(20, int(budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(n):
+        oracle_eval(box, p)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} full brute-force O(N^2) force+energy evaluations of the {box.n}-atom box "
+                      f"(FP64, OpenMP), after one untimed evaluation"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    desc, fn = workloads()[args.workload]
+    box, p = fn()
+    import oracle
+    for _ in range(args.warmup):
+        oracle_eval(box, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_eval(box, p)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(args, box, p, desc),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"each step one brute-force O(N^2) force+energy evaluation of the "
+                                   f"{box.n}-atom box (FP64, OpenMP)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(args, box, p, desc):
+    return {"workload": args.workload, "description": desc, "n_atoms": int(box.n),
+            "box_nm": [round(float(v), 6) for v in box.box], "elec": p["elec"], "rc_nm": p["rc"],
+            "rlist_nm": p["rlist"], "beta_nm-1": p.get("beta"), "nstlist": p.get("nstlist", 1),
+            "nstprune": p.get("nstprune", 0), "cluster": "8x8 pairs, computed as two 8x4 halves per warp",
+            "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}",
+            "seed": int(box.seed)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1306_1737_gb300 as nb
+    from paper_1306_1737_gb300 import workloads as w
+
+    ws_n, rank, local = dist_env()
+    if ws_n > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nb.load()
+    desc, fn = workloads()[args.workload]
+    box, p = fn()
+    nstlist = int(p.get("nstlist", 1))
+    nstprune = int(p.get("nstprune", 0))
+    rc, rlist = float(p["rc"]), float(p["rlist"])
+    rprune = w.prune_radius(rc, rlist, nstprune) if nstprune else rlist
+    elec = p["elec"]
+    comb = nb.NB_COMB_LB if p.get("comb", "lb") == "lb" else nb.NB_COMB_GEOM
+
+    cx = nb.Context(box.n, box.box, rlist, box.q, box.types, nb.nb_lj_combine(box.sigma, box.eps, comb),
+                    device=dev.index)
+    ctx = cx.ctx
+    stream = torch.cuda.current_stream()
+    # frame coordinates, resident in HBM before timing
+    disp = w.frame_displacements(box.mass, max(nstlist - 1, 1), seed=2000 + box.seed)
+    frames = np.empty((nstlist, box.n, 3), np.float32)
+    frames[0] = box.xyz
+    if nstlist > 1:
+        frames[1:] = box.xyz[None] + np.cumsum(disp, axis=0)[: nstlist - 1]
+    xs = torch.as_tensor(frames).to(dev)
+    eo = torch.as_tensor(box.excl_off).to(dev)
+    ei = torch.as_tensor(box.excl_idx).to(dev)
+    F = torch.zeros((box.n, 3), dtype=torch.float32, device=dev)
+    E = torch.zeros(2, dtype=torch.float64, device=dev)
+    V = torch.zeros(9, dtype=torch.float64, device=dev)
+    prm_e = nb.make_params(elec, rc, eps_rf=p.get("eps_rf", math.inf), beta=p.get("beta", 0.0), want_energy=True)
+    prm_f = nb.make_params(elec, rc, eps_rf=p.get("eps_rf", math.inf), beta=p.get("beta", 0.0), want_energy=False)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def energy_frame(f):
+        return f == 0 or f == nstlist - 1
+
+    def step(xdev=None, host=None):
+        """One list lifetime; xdev: device frames; host: (pinned frames, F, E) for e2e."""
+        if host is not None:
+            hx, hF, hE, xbuf = host
+            xbuf.copy_(hx[0], non_blocking=True)
+            x0 = xbuf
+        else:
+            x0 = xdev[0]
+        nb.nb_grid_put(ctx, x0, box.box, stream)
+        nb.nb_pairlist_build(ctx, rlist, 0.0, eo, ei, stream)
+        for f in range(nstlist):
+            if host is not None and f > 0:
+                xbuf.copy_(hx[f], non_blocking=True)
+                xf = xbuf
+            else:
+                xf = x0 if host is not None else xdev[f]
+            if nstprune and f > 0 and f % nstprune == 0:
+                nb.nb_prune(ctx, xf, rprune, stream)
+                xarg = None
+            else:
+                xarg = xf if f > 0 else None
+            prm = prm_e if energy_frame(f) else prm_f
+            nb.nb_compute(ctx, prm, xarg, F, E, V, stream)
+            if host is not None:
+                hF[f].copy_(F, non_blocking=True)
+                if energy_frame(f):
+                    hE.copy_(E, non_blocking=True)
+
+    # warm-up and a status check (capacity, coordinates)
+    for _ in range(args.warmup):
+        step(xs)
+    info0 = nb.nb_check(ctx, stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # timed region (device time per step with CUDA events on the launch stream)
+    nb.nb_profile(ctx, True)
+    nb.nb_profile_read(ctx)
+    spans = []
+    step_ms = []
+    launches0 = nb.nb_check(ctx, stream).n_launches
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    barrier()
+    if sampler:
+        sampler.start()
+    for k in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(xs)
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        spans.extend(nb.nb_profile_read(ctx))
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    info = nb.nb_check(ctx, stream)
+    launches = info.n_launches - launches0
+    nb.nb_profile(ctx, False)
+    total_s = sum(step_ms) / 1000.0
+    if dist is not None:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = ws_n * args.steps * nstlist / total_s
+
+    # force-kernel roofline (FP32 ALU): algorithmic flops per launch / duration
+    force_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_FORCE]
+    prune_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_PRUNE]
+    search_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_SEARCH]
+    grid_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_GRID]
+    pairs_outer = int(info.n_jentries) * 64
+    pairs_pruned = int(info.n_jentries_pruned) * 64 if info.n_jentries_pruned >= 0 else pairs_outer
+    # frames before the first prune use the outer list
+    n_outer = min(nstprune, nstlist) if nstprune else nstlist
+    listed = (n_outer * pairs_outer + (nstlist - n_outer) * pairs_pruned) / nstlist
+    pairs_rc = int(info.n_pairs_rc)
+    flops = FLOPS_DIST * listed + (FLOPS_PAIR[elec] - FLOPS_DIST) * pairs_rc
+    t_force = statistics.mean(force_ms) / 1000.0 if force_ms else float("nan")
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * pk["sm_max_mhz"] * 1e6
+    achieved = flops / t_force
+    roofline = {"bound": "alu", "kernel": "k_force8 (Ewald)" if elec == "ewald" else "k_force8 (RF)",
+                "achieved": achieved / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {pk['sm_max_mhz']:.0f} MHz "
+                               f"(max SM clock, {pk['source']})",
+                "algorithmic_flops_per_launch": flops, "listed_pairs_per_launch": listed,
+                "pairs_within_rc_per_launch": pairs_rc, "launch_ms": t_force * 1e3}
+
+    out = None
+    if rank == 0:
+        # end to end through the C ABI with host buffers: H2D of each frame's
+        # coordinates and D2H of each frame's forces (and energies) inside
+        # the timed region
+        hx = torch.as_tensor(frames).pin_memory()
+        hF = torch.empty((nstlist, box.n, 3), dtype=torch.float32).pin_memory()
+        hE = torch.empty(2, dtype=torch.float64).pin_memory()
+        xbuf = torch.empty((box.n, 3), dtype=torch.float32, device=dev)
+        host = (hx, hF, hE, xbuf)
+        for _ in range(2):
+            step(host=host)
+        torch.cuda.synchronize()
+        e2e_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step(host=host)
+            torch.cuda.synchronize()
+            e2e_ms.append(1000 * (time.perf_counter() - t0))
+        e2e_value = args.steps * nstlist / (sum(e2e_ms) / 1000.0)
+        h2d = nstlist * box.n * 12
+        d2h = nstlist * box.n * 12 + 16
+        cpu = cpu_baseline(box, p) if ws_n == 1 else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_s * 1000 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_dict(args, box, p, desc),
+            "pair_interactions_per_s": listed * nstlist * args.steps * ws_n / total_s,
+            "effective_pair_interactions_per_s": pairs_rc * nstlist * args.steps * ws_n / total_s,
+            "force_kernel": {"ms": t_force * 1e3, "listed_pairs_per_s": listed / t_force,
+                             "pairs_within_rc_per_s": pairs_rc / t_force,
+                             "effective_ratio": pairs_rc / listed if listed else None},
+            "kernel_ms": {"grid": statistics.mean(grid_ms) if grid_ms else None,
+                          "search": statistics.mean(search_ms) if search_ms else None,
+                          "prune": statistics.mean(prune_ms) if prune_ms else None,
+                          "force": t_force * 1e3},
+            "list": {"clusters": int(info.n_clusters), "ientries": int(info.n_ientries),
+                     "jentries": int(info.n_jentries), "jentries_pruned": int(info.n_jentries_pruned),
+                     "r_prune_nm": rprune},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "status": nb.status_name(info0.status),
+        }
+    cx.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water24k", choices=["water24k", "water3m", "water1536"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

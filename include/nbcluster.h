@@ -84,8 +84,18 @@ typedef struct {
     int64_t n_jentries;   /* j-entries of the outer list */
     int64_t n_jentries_pruned; /* j-entries kept by the last nb_prune (-1: none) */
     int64_t ient_capacity, jent_capacity;
+    int64_t n_pairs_rc;   /* particle pairs inside rc in the last energy evaluation */
+    int64_t n_launches;   /* kernels this context has launched */
     uint32_t flags;       /* device error flags (bit mask of 1 << nb_status_code) */
 } nb_info;
+
+/* Kernel kinds reported by nb_profile_read. */
+enum nb_kernel_kind {
+    NB_KERNEL_GRID = 0,    /* the gridding kernels of nb_grid_put, as one span */
+    NB_KERNEL_SEARCH = 1,  /* nb_pairlist_build's search kernel */
+    NB_KERNEL_PRUNE = 2,   /* nb_prune's prune kernel */
+    NB_KERNEL_FORCE = 3    /* nb_compute's force/energy kernel */
+};
 
 /* --- context ------------------------------------------------------------ */
 
@@ -192,6 +202,18 @@ nb_status nb_compute(nb_ctx* ctx, const nb_params* p, const float* xyz_dev, floa
 /* Synchronise the stream, read the device flags and sizes into *info (may be
  * NULL) and turn a raised flag into its status.  Clears the flags. */
 nb_status nb_check(nb_ctx* ctx, nb_stream stream, nb_info* info);
+
+/* --- timing --------------------------------------------------------------- */
+
+/* enable != 0: from now on record a pair of CUDA events on the launching
+ * stream around each hot-path kernel (kinds above; at most 256 spans are kept
+ * until read).  enable == 0 stops recording.  Errors: NB_ERR_CUDA. */
+nb_status nb_profile(nb_ctx* ctx, int enable);
+
+/* Wait for the recorded spans and return them in launch order: kinds[k] and
+ * ms[k] for k < *count (at most max), then forget them.  Host arrays.
+ * Errors: NB_ERR_ARG, NB_ERR_CUDA. */
+nb_status nb_profile_read(nb_ctx* ctx, int* kinds_host, float* ms_host, int max, int* count);
 
 /* --- introspection (tests) -------------------------------------------------- */
 

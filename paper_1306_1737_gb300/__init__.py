@@ -31,6 +31,11 @@ NB_ELEC_EWALD = 1
 NB_COMB_LB = 0
 NB_COMB_GEOM = 1
 
+NB_KERNEL_GRID = 0
+NB_KERNEL_SEARCH = 1
+NB_KERNEL_PRUNE = 2
+NB_KERNEL_FORCE = 3
+
 _lock = threading.Lock()
 _lib = None
 
@@ -48,7 +53,8 @@ class nb_info(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("n_clusters", C.c_int),
                 ("n_ientries", C.c_int64), ("n_jentries", C.c_int64),
                 ("n_jentries_pruned", C.c_int64), ("ient_capacity", C.c_int64),
-                ("jent_capacity", C.c_int64), ("flags", C.c_uint32)]
+                ("jent_capacity", C.c_int64), ("n_pairs_rc", C.c_int64), ("n_launches", C.c_int64),
+                ("flags", C.c_uint32)]
 
 
 class NbError(RuntimeError):
@@ -87,6 +93,8 @@ def load():
             "nb_check": ([P, P, C.POINTER(nb_info)], st),
             "nb_get_grid": ([P, P, P, P, P, P, P, P, P], st),
             "nb_get_list": ([P, i, P, P, P, P], st),
+            "nb_profile": ([P, i], st),
+            "nb_profile_read": ([P, P, P, i, C.POINTER(C.c_int)], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -225,6 +233,19 @@ def nb_get_grid(ctx, atom_of_slot=None, slot_of_atom=None, col_clu_start=None, x
 def nb_get_list(ctx, which, ient=None, cj=None, mask=None, stream=None):
     _check(ctx, load().nb_get_list(ctx, int(which), _ptr(ient), _ptr(cj), _ptr(mask),
                                    _stream(stream)))
+
+
+def nb_profile(ctx, enable=True):
+    _check(ctx, load().nb_profile(ctx, int(bool(enable))))
+
+
+def nb_profile_read(ctx, max_spans=256):
+    """[(kind, ms), ...] of the spans recorded since the last read."""
+    kinds = (C.c_int * max_spans)()
+    ms = (C.c_float * max_spans)()
+    cnt = C.c_int()
+    _check(ctx, load().nb_profile_read(ctx, kinds, ms, int(max_spans), C.byref(cnt)))
+    return [(kinds[k], ms[k]) for k in range(cnt.value)]
 
 
 # --- convenience: one box with its torch-allocated workspace ---------------

@@ -30,6 +30,7 @@ def nvcc() -> str:
 def _deps():
     paths = [os.path.join(CSRC, s) for s in SOURCES]
     paths.append(os.path.join(CSRC, "nb_internal.cuh"))
+    paths.append(os.path.join(CSRC, "nb_ewald_fit.h"))
     paths.append(os.path.join(ROOT, "include", "nbcluster.h"))
     paths.append(os.path.abspath(__file__))
     return paths

@@ -9,6 +9,7 @@
 #include <new>
 
 #include "nb_internal.cuh"
+#include "nb_ewald_fit.h"
 
 using namespace nbc;
 
@@ -32,8 +33,28 @@ struct nb_ctx {
     float rlist = 0.f, r_prune = 0.f;
     DevState last{};
     bool last_valid = false;
+    long long n_launches = 0;
+    // timing spans (nb_profile)
+    static constexpr int kMaxSpans = 256;
+    bool prof = false;
+    cudaEvent_t ev[2 * kMaxSpans] = {};
+    int ev_kind[kMaxSpans] = {};
+    int ev_n = 0;
     char err[512] = {0};
 };
+
+// Record the start of a timed span (returns its slot or -1).
+static int span_begin(nb_ctx* c, int kind, cudaStream_t s) {
+    if (!c->prof || c->ev_n >= nb_ctx::kMaxSpans) return -1;
+    const int k = c->ev_n++;
+    c->ev_kind[k] = kind;
+    cudaEventRecord(c->ev[2 * k], s);
+    return k;
+}
+
+static void span_end(nb_ctx* c, int k, cudaStream_t s) {
+    if (k >= 0) cudaEventRecord(c->ev[2 * k + 1], s);
+}
 
 static nb_status fail(nb_ctx* c, nb_status s, const char* fmt, ...) {
     if (c) {
@@ -200,6 +221,8 @@ nb_status nb_create(nb_ctx** out, const nb_options* opt) {
 nb_status nb_destroy(nb_ctx* c) {
     if (!c) return NB_ERR_ARG;
     if (c->st_host) cudaFreeHost(c->st_host);
+    for (int k = 0; k < 2 * nb_ctx::kMaxSpans; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
     return NB_OK;
 }
@@ -314,8 +337,11 @@ nb_status nb_grid_put(nb_ctx* c, const float* xyz, const double* box, nb_stream 
     g.inv_y = (float)((double)g.ny / (double)g.L[1]);
     g.dummy_g = dummy_spacing(g.L);
     NB_CUDA(c, cudaSetDevice(c->device));
+    const int sp = span_begin(c, NB_KERNEL_GRID, (cudaStream_t)stream);
     cudaError_t e = launch_grid(c->ws, g, c->n, c->C, c->ntypes, xyz, c->n_sm, (cudaStream_t)stream);
+    span_end(c, sp, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "grid kernels");
+    c->n_launches += kLaunchesGrid;
     c->geom = g;
     c->have_grid = true;
     c->have_list = c->have_pruned = false;
@@ -334,9 +360,12 @@ nb_status nb_pairlist_build(nb_ctx* c, float rlist, float rbb, const int* excl_o
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(c, cudaSetDevice(c->device));
     NB_CUDA(c, cudaMemsetAsync(c->ws.st, 0, 2 * sizeof(unsigned long long), s));
+    const int sp = span_begin(c, NB_KERNEL_SEARCH, s);
     cudaError_t e = launch_search(c->ws, c->geom, c->C, c->nclu_cap, rlist, rbb, excl_off, excl_idx,
                                   c->ient_cap, c->jent_cap, c->n, c->n_sm, s);
+    span_end(c, sp, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "search kernel");
+    c->n_launches += kLaunchesSearch;
     c->rlist = rlist;
     c->have_list = true;
     c->have_pruned = false;
@@ -351,6 +380,7 @@ nb_status nb_set_coords(nb_ctx* c, const float* xyz, nb_stream stream) {
     NB_CUDA(c, cudaSetDevice(c->device));
     cudaError_t e = launch_set_coords(c->ws, (int)c->nslot_cap, c->C, xyz, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_coords kernel");
+    c->n_launches += kLaunchesSetCoords;
     return NB_OK;
 }
 
@@ -364,8 +394,11 @@ nb_status nb_prune(nb_ctx* c, const float* xyz, float r_prune, nb_stream stream)
         nb_status st = nb_set_coords(c, xyz, stream);
         if (st != NB_OK) return st;
     }
+    const int sp = span_begin(c, NB_KERNEL_PRUNE, (cudaStream_t)stream);
     cudaError_t e = launch_prune(c->ws, c->geom, c->C, r_prune, c->ient_cap, c->n_sm, (cudaStream_t)stream);
+    span_end(c, sp, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "prune kernel");
+    c->n_launches += kLaunchesPrune;
     c->r_prune = r_prune;
     c->have_pruned = true;
     c->last_valid = false;
@@ -402,16 +435,22 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     fp.c_rf = (float)(1.0 / rc + k * rc * rc);
     fp.beta = p->beta;
     fp.two_beta_sqrtpi = (float)(2.0 * (double)p->beta / std::sqrt(M_PI));
+    fp.beta2 = (float)((double)p->beta * p->beta);
+    fp.beta3 = (float)((double)p->beta * p->beta * p->beta);
+    fp.use_fit = ((double)p->beta * p->beta * rc * rc <= (double)kEwaldFitWMax) ? 1 : 0;
     fp.ntypes = c->ntypes;
     for (int d = 0; d < 3; ++d) fp.L[d] = c->geom.L[d];
     fp.use_pruned = c->have_pruned ? 1 : 0;
     fp.ient_cap = c->ient_cap;
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(c, cudaSetDevice(c->device));
+    const int sp = span_begin(c, NB_KERNEL_FORCE, s);
     cudaError_t e = launch_force(c->ws, fp, c->C, c->n_sm, c->nslot_cap, s);
+    span_end(c, sp, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "force kernel");
     e = launch_finalize(c->ws, fp, c->n, f, e_out, vir_out, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
+    c->n_launches += 2 + (fp.want_energy ? 1 : 0);
     return NB_OK;
 }
 
@@ -439,6 +478,8 @@ nb_status nb_check(nb_ctx* c, nb_stream stream, nb_info* info) {
         info->n_jentries_pruned = c->have_pruned ? (int64_t)c->last.n_jent_pruned : -1;
         info->ient_capacity = c->ient_cap;
         info->jent_capacity = c->jent_cap;
+        info->n_pairs_rc = (int64_t)c->last.n_pairs_rc;
+        info->n_launches = c->n_launches;
         info->flags = flags;
     }
     if (flags & (1u << NB_ERR_COORD)) return fail(c, NB_ERR_COORD, "a coordinate was outside [-L, 2L)");
@@ -447,6 +488,29 @@ nb_status nb_check(nb_ctx* c, nb_stream stream, nb_info* info) {
                     (unsigned long long)c->last.n_jent, c->jent_cap, c->last.max_col);
     if (flags & (1u << NB_ERR_TIMEOUT)) return fail(c, NB_ERR_TIMEOUT, "a bounded device wait expired");
     if (flags) return fail(c, NB_ERR_CUDA, "device flags 0x%x", flags);
+    return NB_OK;
+}
+
+nb_status nb_profile(nb_ctx* c, int enable) {
+    if (!c) return NB_ERR_ARG;
+    if (enable && !c->ev[0]) {
+        NB_CUDA(c, cudaSetDevice(c->device));
+        for (int k = 0; k < 2 * nb_ctx::kMaxSpans; ++k) NB_CUDA(c, cudaEventCreate(&c->ev[k]));
+    }
+    c->prof = enable != 0;
+    return NB_OK;
+}
+
+nb_status nb_profile_read(nb_ctx* c, int* kinds, float* ms, int max, int* count) {
+    if (!c || !count || max < 0 || (max > 0 && (!kinds || !ms))) return fail(c, NB_ERR_ARG, "profile_read: bad argument");
+    const int n = c->ev_n < max ? c->ev_n : max;
+    for (int k = 0; k < n; ++k) {
+        NB_CUDA(c, cudaEventSynchronize(c->ev[2 * k + 1]));
+        NB_CUDA(c, cudaEventElapsedTime(&ms[k], c->ev[2 * k], c->ev[2 * k + 1]));
+        kinds[k] = c->ev_kind[k];
+    }
+    *count = n;
+    c->ev_n = 0;
     return NB_OK;
 }
 

@@ -20,6 +20,7 @@
 //   Ewald   F/r = qq (erfc(br) - (1-e) + 2br/sqrt(pi) exp(-b^2 r^2)) r^-3,
 //           V = qq (erfc(br) - (1-e)) r^-1
 #include "nb_internal.cuh"
+#include "nb_ewald_fit.h"
 
 namespace nbc {
 
@@ -38,7 +39,9 @@ struct ForceArgs {
 
 constexpr int kForceWarps = 4;
 
-template <int ELEC, bool ENERGY>
+// One particle pair.  FIT selects the fitted rational approximation of the
+// Ewald correction (Sec. 3.2: quotient of two polynomials) over erfcf/expf.
+template <int ELEC, bool ENERGY, bool FIT>
 __device__ __forceinline__ void pair_fn(const ForceParams& P, bool inc, float bit, float r2, float qq,
                                         float2 lj, float& fs, float& vlj, float& vc) {
     const float r2s = inc ? r2 : 1.0f;
@@ -51,6 +54,14 @@ __device__ __forceinline__ void pair_fn(const ForceParams& P, bool inc, float bi
     if (ELEC == NB_ELEC_RF) {
         fc = qq * (bit * rinv * rinv2 - P.two_k_rf);
         if (ENERGY) vc = inc ? qq * (bit * rinv + P.k_rf * r2s - P.c_rf) : 0.0f;
+    } else if (FIT) {
+        const float w = P.beta2 * r2s;
+        const float g = ewald_fit_g(w);
+        fc = qq * (bit * rinv * rinv2 - P.beta3 * g);
+        if (ENERGY) {
+            const float h = ewald_fit_h(w);
+            vc = inc ? qq * (bit * rinv - P.beta * h) : 0.0f;
+        }
     } else {
         const float r = r2s * rinv;
         const float br = P.beta * r;
@@ -64,8 +75,87 @@ __device__ __forceinline__ void pair_fn(const ForceParams& P, bool inc, float bi
         vlj = inc ? bit * (lj.y * (1.0f / 12.0f) * rinv6 - lj.x * (1.0f / 6.0f)) * rinv6 : 0.0f;
 }
 
-template <int ELEC, bool ENERGY>
-__global__ void __launch_bounds__(32 * kForceWarps) k_force8(ForceArgs A) {
+struct Lane8 {
+    int j, ih;
+    bool lower0, lower1;  // (ih, j) and (ih+4, j) on or below the diagonal
+    int bitpos;
+};
+
+// All j-entries [jb, je) (at most 32) of one i-entry; SHIFTED adds the low
+// part of the shifted i coordinates.
+template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED>
+__device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s_lj, const Lane8& L,
+                                             int ci, bool center, int jb, int je, const float (&x0h)[3],
+                                             const float (&x0l)[3], const float (&x1h)[3],
+                                             const float (&x1l)[3], float qi0, float qi1, int ti0,
+                                             int ti1, float (&f0)[3], float (&f1)[3], float& e_lj,
+                                             float& e_c, unsigned& n_inc) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nt = je - jb;
+    int my_cj = 0;
+    unsigned long long my_m = 0;
+    if (lane < nt) {
+        my_cj = A.cj[jb + lane];
+        my_m = A.mask[jb + lane];
+    }
+    int cjn = __shfl_sync(full, my_cj, 0);
+    float4 xjn = A.xyzq[cjn * 8 + L.j];
+    int tjn = A.type_slot[cjn * 8 + L.j];
+    for (int t = 0; t < nt; ++t) {
+        const int cjt = cjn;
+        const float4 xj = xjn;
+        const int tj = tjn;
+        if (t + 1 < nt) {
+            cjn = __shfl_sync(full, my_cj, t + 1);
+            xjn = A.xyzq[cjn * 8 + L.j];
+            tjn = A.type_slot[cjn * 8 + L.j];
+        }
+        const unsigned mlo = __shfl_sync(full, (unsigned)my_m, t);
+        const unsigned mhi = __shfl_sync(full, (unsigned)(my_m >> 32), t);
+        const bool diag = center && (cjt == ci);
+        const unsigned u0 = (mlo >> L.bitpos) & 1u;
+        const unsigned u1 = (mhi >> L.bitpos) & 1u;
+        float d0x = x0h[0] - xj.x, d0y = x0h[1] - xj.y, d0z = x0h[2] - xj.z;
+        float d1x = x1h[0] - xj.x, d1y = x1h[1] - xj.y, d1z = x1h[2] - xj.z;
+        if (SHIFTED) {
+            d0x += x0l[0]; d0y += x0l[1]; d0z += x0l[2];
+            d1x += x1l[0]; d1y += x1l[1]; d1z += x1l[2];
+        }
+        const float r2_0 = fmaf(d0x, d0x, fmaf(d0y, d0y, d0z * d0z));
+        const float r2_1 = fmaf(d1x, d1x, fmaf(d1y, d1y, d1z * d1z));
+        const bool inc0 = (r2_0 < A.p.rc2) && (u0 || !(diag && L.lower0));
+        const bool inc1 = (r2_1 < A.p.rc2) && (u1 || !(diag && L.lower1));
+        if (!__any_sync(full, inc0 || inc1)) continue;
+        float fs0, fs1, vl0 = 0.f, vl1 = 0.f, vc0 = 0.f, vc1 = 0.f;
+        pair_fn<ELEC, ENERGY, FIT>(A.p, inc0, (float)u0, r2_0, qi0 * xj.w, s_lj[ti0 + tj], fs0, vl0, vc0);
+        pair_fn<ELEC, ENERGY, FIT>(A.p, inc1, (float)u1, r2_1, qi1 * xj.w, s_lj[ti1 + tj], fs1, vl1, vc1);
+        if (ENERGY) {
+            e_lj += vl0 + vl1;
+            e_c += vc0 + vc1;
+            n_inc += (unsigned)inc0 + (unsigned)inc1;
+        }
+        f0[0] = fmaf(fs0, d0x, f0[0]);
+        f0[1] = fmaf(fs0, d0y, f0[1]);
+        f0[2] = fmaf(fs0, d0z, f0[2]);
+        f1[0] = fmaf(fs1, d1x, f1[0]);
+        f1[1] = fmaf(fs1, d1y, f1[1]);
+        f1[2] = fmaf(fs1, d1z, f1[2]);
+        float fjx = -fmaf(fs0, d0x, fs1 * d1x);
+        float fjy = -fmaf(fs0, d0y, fs1 * d1y);
+        float fjz = -fmaf(fs0, d0z, fs1 * d1z);
+        fjx += __shfl_xor_sync(full, fjx, 8);
+        fjy += __shfl_xor_sync(full, fjy, 8);
+        fjz += __shfl_xor_sync(full, fjz, 8);
+        fjx += __shfl_xor_sync(full, fjx, 16);
+        fjy += __shfl_xor_sync(full, fjy, 16);
+        fjz += __shfl_xor_sync(full, fjz, 16);
+        if (L.ih == 0) atomicAdd(&A.fslot[cjt * 8 + L.j], make_float4(fjx, fjy, fjz, 0.0f));
+    }
+}
+
+template <int ELEC, bool ENERGY, bool FIT>
+__global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 6 : 8) k_force8(ForceArgs A) {
     extern __shared__ float2 s_lj[];
     const unsigned full = 0xffffffffu;
     const int nt2 = A.p.ntypes * A.p.ntypes;
@@ -75,9 +165,15 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force8(ForceArgs A) {
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int j = lane & 7, ih = lane >> 3;
+    Lane8 L;
+    L.j = lane & 7;
+    L.ih = lane >> 3;
+    L.lower0 = L.j <= L.ih;
+    L.lower1 = L.j <= L.ih + 4;
+    L.bitpos = L.ih * 8 + L.j;
     const long long nient = min((long long)A.st->n_ient, A.p.ient_cap);
     float e_lj = 0.0f, e_c = 0.0f;
+    unsigned n_inc = 0;
     for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < nient;
          e += (long long)gridDim.x * kForceWarps) {
         const int4 ie = A.ient[e];
@@ -85,8 +181,8 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force8(ForceArgs A) {
         if (jb >= je) continue;
         const float sh[3] = {(float)(s / 9 - 1) * A.p.L[0], (float)((s / 3) % 3 - 1) * A.p.L[1],
                              (float)(s % 3 - 1) * A.p.L[2]};
-        const float4 x0 = A.xyzq[ci * 8 + ih];
-        const float4 x1 = A.xyzq[ci * 8 + ih + 4];
+        const float4 x0 = A.xyzq[ci * 8 + L.ih];
+        const float4 x1 = A.xyzq[ci * 8 + L.ih + 4];
         float x0h[3], x0l[3], x1h[3], x1l[3];
         two_sum(x0.x, sh[0], x0h[0], x0l[0]);
         two_sum(x0.y, sh[1], x0h[1], x0l[1]);
@@ -95,63 +191,18 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force8(ForceArgs A) {
         two_sum(x1.y, sh[1], x1h[1], x1l[1]);
         two_sum(x1.z, sh[2], x1h[2], x1l[2]);
         const float qi0 = x0.w * A.p.fcoul, qi1 = x1.w * A.p.fcoul;
-        const int ti0 = A.type_slot[ci * 8 + ih] * A.p.ntypes;
-        const int ti1 = A.type_slot[ci * 8 + ih + 4] * A.p.ntypes;
+        const int ti0 = A.type_slot[ci * 8 + L.ih] * A.p.ntypes;
+        const int ti1 = A.type_slot[ci * 8 + L.ih + 4] * A.p.ntypes;
         const bool center = (s == kShiftCenter);
-        const int bitpos = ih * 8 + j;
         float f0[3] = {0.f, 0.f, 0.f}, f1[3] = {0.f, 0.f, 0.f};
         for (int base = jb; base < je; base += 32) {
-            const int nt = min(32, je - base);
-            int my_cj = 0;
-            unsigned long long my_m = 0;
-            if (lane < nt) {
-                my_cj = A.cj[base + lane];
-                my_m = A.mask[base + lane];
-            }
-            for (int t = 0; t < nt; ++t) {
-                const int cjt = __shfl_sync(full, my_cj, t);
-                const unsigned mlo = __shfl_sync(full, (unsigned)my_m, t);
-                const unsigned mhi = __shfl_sync(full, (unsigned)(my_m >> 32), t);
-                const float4 xj = A.xyzq[cjt * 8 + j];
-                const int tj = A.type_slot[cjt * 8 + j];
-                const bool diag = center && (cjt == ci);
-                const float b0 = (float)((mlo >> bitpos) & 1u);
-                const float b1 = (float)((mhi >> bitpos) & 1u);
-                const float d0x = (x0h[0] - xj.x) + x0l[0];
-                const float d0y = (x0h[1] - xj.y) + x0l[1];
-                const float d0z = (x0h[2] - xj.z) + x0l[2];
-                const float d1x = (x1h[0] - xj.x) + x1l[0];
-                const float d1y = (x1h[1] - xj.y) + x1l[1];
-                const float d1z = (x1h[2] - xj.z) + x1l[2];
-                const float r2_0 = fmaf(d0x, d0x, fmaf(d0y, d0y, d0z * d0z));
-                const float r2_1 = fmaf(d1x, d1x, fmaf(d1y, d1y, d1z * d1z));
-                const bool inc0 = (r2_0 < A.p.rc2) && (b0 != 0.0f || !(diag && j <= ih));
-                const bool inc1 = (r2_1 < A.p.rc2) && (b1 != 0.0f || !(diag && j <= ih + 4));
-                if (!__any_sync(full, inc0 || inc1)) continue;
-                float fs0, fs1, vl0 = 0.f, vl1 = 0.f, vc0 = 0.f, vc1 = 0.f;
-                pair_fn<ELEC, ENERGY>(A.p, inc0, b0, r2_0, qi0 * xj.w, s_lj[ti0 + tj], fs0, vl0, vc0);
-                pair_fn<ELEC, ENERGY>(A.p, inc1, b1, r2_1, qi1 * xj.w, s_lj[ti1 + tj], fs1, vl1, vc1);
-                if (ENERGY) {
-                    e_lj += vl0 + vl1;
-                    e_c += vc0 + vc1;
-                }
-                f0[0] = fmaf(fs0, d0x, f0[0]);
-                f0[1] = fmaf(fs0, d0y, f0[1]);
-                f0[2] = fmaf(fs0, d0z, f0[2]);
-                f1[0] = fmaf(fs1, d1x, f1[0]);
-                f1[1] = fmaf(fs1, d1y, f1[1]);
-                f1[2] = fmaf(fs1, d1z, f1[2]);
-                float fjx = -fmaf(fs0, d0x, fs1 * d1x);
-                float fjy = -fmaf(fs0, d0y, fs1 * d1y);
-                float fjz = -fmaf(fs0, d0z, fs1 * d1z);
-                fjx += __shfl_xor_sync(full, fjx, 8);
-                fjy += __shfl_xor_sync(full, fjy, 8);
-                fjz += __shfl_xor_sync(full, fjz, 8);
-                fjx += __shfl_xor_sync(full, fjx, 16);
-                fjy += __shfl_xor_sync(full, fjy, 16);
-                fjz += __shfl_xor_sync(full, fjz, 16);
-                if (ih == 0) atomicAdd(&A.fslot[cjt * 8 + j], make_float4(fjx, fjy, fjz, 0.0f));
-            }
+            const int bend = min(je, base + 32);
+            if (center)
+                force_entry8<ELEC, ENERGY, FIT, false>(A, s_lj, L, ci, center, base, bend, x0h, x0l, x1h,
+                                                       x1l, qi0, qi1, ti0, ti1, f0, f1, e_lj, e_c, n_inc);
+            else
+                force_entry8<ELEC, ENERGY, FIT, true>(A, s_lj, L, ci, center, base, bend, x0h, x0l, x1h,
+                                                      x1l, qi0, qi1, ti0, ti1, f0, f1, e_lj, e_c, n_inc);
         }
         // i-forces: sum over the 8 lanes of each i row
 #pragma unroll
@@ -162,9 +213,9 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force8(ForceArgs A) {
                 f1[d] += __shfl_xor_sync(full, f1[d], o);
             }
         }
-        if (j == 0) {
-            atomicAdd(&A.fslot[ci * 8 + ih], make_float4(f0[0], f0[1], f0[2], 0.0f));
-            atomicAdd(&A.fslot[ci * 8 + ih + 4], make_float4(f1[0], f1[1], f1[2], 0.0f));
+        if (L.j == 0) {
+            atomicAdd(&A.fslot[ci * 8 + L.ih], make_float4(f0[0], f0[1], f0[2], 0.0f));
+            atomicAdd(&A.fslot[ci * 8 + L.ih + 4], make_float4(f1[0], f1[1], f1[2], 0.0f));
         }
         if (ENERGY && !center) {
             // i-side force of this shifted entry, for the virial
@@ -182,17 +233,19 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force8(ForceArgs A) {
         for (int o = 16; o > 0; o >>= 1) {
             e_lj += __shfl_xor_sync(full, e_lj, o);
             e_c += __shfl_xor_sync(full, e_c, o);
+            n_inc += __shfl_xor_sync(full, n_inc, o);
         }
         if (lane == 0) {
             atomicAdd(&A.acc->energy[0], (double)e_lj);
             atomicAdd(&A.acc->energy[1], (double)e_c);
+            atomicAdd(&A.acc->n_inc, (unsigned long long)n_inc);
         }
     }
 }
 
 // Generic C = 4 kernel: one warp per i-entry, lanes 0..15 hold the 4 x 4
 // pairs of one j-cluster and lanes 16..31 those of the next.
-template <int ELEC, bool ENERGY>
+template <int ELEC, bool ENERGY, bool FIT>
 __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
     extern __shared__ float2 s_lj[];
     const unsigned full = 0xffffffffu;
@@ -206,6 +259,7 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
     const int half = lane >> 4, i = (lane >> 2) & 3, j = lane & 3;
     const long long nient = min((long long)A.st->n_ient, A.p.ient_cap);
     float e_lj = 0.0f, e_c = 0.0f;
+    unsigned n_inc = 0;
     for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < nient;
          e += (long long)gridDim.x * kForceWarps) {
         const int4 ie = A.ient[e];
@@ -238,10 +292,11 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
             const bool inc = live && (r2 < A.p.rc2) && (b != 0.0f || !(diag && j <= i));
             if (!__any_sync(full, inc)) continue;
             float fs, vl = 0.f, vc = 0.f;
-            pair_fn<ELEC, ENERGY>(A.p, inc, b, r2, qi * xj.w, s_lj[ti + tj], fs, vl, vc);
+            pair_fn<ELEC, ENERGY, FIT>(A.p, inc, b, r2, qi * xj.w, s_lj[ti + tj], fs, vl, vc);
             if (ENERGY) {
                 e_lj += vl;
                 e_c += vc;
+                n_inc += (unsigned)inc;
             }
             fi[0] = fmaf(fs, dx, fi[0]);
             fi[1] = fmaf(fs, dy, fi[1]);
@@ -276,24 +331,32 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
         for (int o = 16; o > 0; o >>= 1) {
             e_lj += __shfl_xor_sync(full, e_lj, o);
             e_c += __shfl_xor_sync(full, e_c, o);
+            n_inc += __shfl_xor_sync(full, n_inc, o);
         }
         if (lane == 0) {
             atomicAdd(&A.acc->energy[0], (double)e_lj);
             atomicAdd(&A.acc->energy[1], (double)e_c);
+            atomicAdd(&A.acc->n_inc, (unsigned long long)n_inc);
         }
     }
 }
 
-template <int ELEC, bool ENERGY>
+template <int ELEC, bool ENERGY, bool FIT>
 static cudaError_t launch_force_t(const ForceArgs& A, int C, int n_sm, cudaStream_t s) {
     const size_t smem = sizeof(float2) * A.p.ntypes * A.p.ntypes;
-    auto kern = (C == 8) ? k_force8<ELEC, ENERGY> : k_force4<ELEC, ENERGY>;
+    auto kern = (C == 8) ? k_force8<ELEC, ENERGY, FIT> : k_force4<ELEC, ENERGY, FIT>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kForceWarps, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     kern<<<n_sm * per_sm, 32 * kForceWarps, smem, s>>>(A);
     return cudaGetLastError();
+}
+
+template <int ELEC, bool ENERGY>
+static cudaError_t launch_force_e(const ForceArgs& A, int C, int n_sm, cudaStream_t s) {
+    if (ELEC == NB_ELEC_EWALD && A.p.use_fit) return launch_force_t<ELEC, ENERGY, true>(A, C, n_sm, s);
+    return launch_force_t<ELEC, ENERGY, false>(A, C, n_sm, s);
 }
 
 cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n_sm,
@@ -313,10 +376,10 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
     cudaError_t e = cudaMemsetAsync(ws.acc, 0, sizeof(Accum), s);
     if (e != cudaSuccess) return e;
     if (p.elec == NB_ELEC_RF)
-        return p.want_energy ? launch_force_t<NB_ELEC_RF, true>(A, C, n_sm, s)
-                             : launch_force_t<NB_ELEC_RF, false>(A, C, n_sm, s);
-    return p.want_energy ? launch_force_t<NB_ELEC_EWALD, true>(A, C, n_sm, s)
-                         : launch_force_t<NB_ELEC_EWALD, false>(A, C, n_sm, s);
+        return p.want_energy ? launch_force_e<NB_ELEC_RF, true>(A, C, n_sm, s)
+                             : launch_force_e<NB_ELEC_RF, false>(A, C, n_sm, s);
+    return p.want_energy ? launch_force_e<NB_ELEC_EWALD, true>(A, C, n_sm, s)
+                         : launch_force_e<NB_ELEC_EWALD, false>(A, C, n_sm, s);
 }
 
 // Forces back to the caller's order (and zeroed for the next evaluation);
@@ -358,9 +421,10 @@ __global__ void k_finalize(int n, const int* __restrict__ slot_of_atom, float4* 
     }
 }
 
-__global__ void k_finalize_small(const Accum* acc, float Lx, float Ly, float Lz, double* e_out,
-                                 double* vir_out) {
+__global__ void k_finalize_small(const Accum* acc, DevState* st, float Lx, float Ly, float Lz,
+                                 double* e_out, double* vir_out) {
     if (threadIdx.x != 0) return;
+    st->n_pairs_rc = acc->n_inc;
     if (e_out) {
         e_out[0] = acc->energy[0];
         e_out[1] = acc->energy[1];
@@ -385,8 +449,8 @@ cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int n, fl
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
     k_finalize<<<blocks, 256, 0, s>>>(n, ws.slot_of_atom, ws.fslot, ws.xyzq, f_out, want_vir, ws.acc);
-    if (p.want_energy && (e_out || vir_out))
-        k_finalize_small<<<1, 32, 0, s>>>(ws.acc, p.L[0], p.L[1], p.L[2], e_out, vir_out);
+    if (p.want_energy)
+        k_finalize_small<<<1, 32, 0, s>>>(ws.acc, ws.st, p.L[0], p.L[1], p.L[2], e_out, vir_out);
     return cudaGetLastError();
 }
 

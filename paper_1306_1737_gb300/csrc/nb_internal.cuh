@@ -17,7 +17,7 @@ namespace nbc {
 constexpr int kMaxTypes = 64;          // LJ types (type table staged in shared memory)
 constexpr int kMaxColumn = 8192;       // particles per grid column sorted on-chip
 constexpr int kShiftCenter = 13;       // shift index of (0, 0, 0)
-constexpr int kJChunk = 64;            // j-entries per i-entry at most (load balance)
+constexpr int kJChunk = 32;            // j-entries per i-entry at most (load balance)
 constexpr int kMaxExclPerCluster = 256;
 
 // Device-resident state: counters written by kernels, read back by nb_check.
@@ -28,7 +28,8 @@ struct DevState {
     int nclu;                           // clusters of the current grid
     unsigned int flags;                 // 1 << nb_status_code
     int max_col;                        // largest column seen by the grid
-    int pad[3];
+    int pad;
+    unsigned long long n_pairs_rc;      // pairs inside rc in the last energy evaluation
 };
 
 // FP64 accumulators of one force evaluation.
@@ -36,6 +37,7 @@ struct Accum {
     double fshift[27][3];   // i-side force per periodic shift (virial bookkeeping)
     double energy[2];       // E_LJ, E_Coulomb
     double vir_xf[9];       // sum over slots x (x) f
+    unsigned long long n_inc;  // pairs inside the cut-off (energy kernels only)
 };
 
 struct Workspace {
@@ -101,6 +103,8 @@ struct ForceParams {
     float k_rf, two_k_rf, c_rf;
     // Ewald
     float beta, two_beta_sqrtpi;
+    float beta2, beta3;   // beta^2, beta^3 for the fitted correction
+    int use_fit;          // (beta rc)^2 within the fitted range
     int ntypes;
     float L[3];
     int use_pruned;
@@ -111,6 +115,9 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
                          long long n_slots_cap, cudaStream_t s);
 cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int n, float* f_out,
                             double* e_out, double* vir_out, cudaStream_t s);
+
+// Kernels each launcher issues (for launch accounting).
+constexpr int kLaunchesGrid = 4, kLaunchesSearch = 1, kLaunchesPrune = 1, kLaunchesSetCoords = 1;
 
 // ---------------------------------------------------------------------------
 // Device helpers

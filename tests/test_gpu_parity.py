@@ -70,8 +70,8 @@ def check_list(gb, g_or, pl_or, rlist, which=0, r_thresh=None, xyzq=None):
     common = set(keys_gpu) & set(keys_or)
     bad = [k for k in common if keys_gpu[k] != keys_or[k]]
     assert not bad, bad[:5]
-    # j-lists are chunked: each i-entry holds at most 64 j-entries
-    assert np.all(ient[:, 3] - ient[:, 2] <= 64)
+    # j-lists are chunked: each i-entry holds at most 32 j-entries
+    assert np.all(ient[:, 3] - ient[:, 2] <= 32)
     return len(keys_gpu), len(only_gpu) + len(only_or)
 
 
