@@ -238,6 +238,44 @@ nb_status nb_get_grid(nb_ctx* ctx, int* atom_of_slot_dev, int* slot_of_atom_dev,
 nb_status nb_get_list(nb_ctx* ctx, int which, int* ient_dev, int* cj_dev, uint64_t* mask_dev,
                       nb_stream stream);
 
+/* --- gridding without device allocation ------------------------------------ */
+
+/* nb_grid_put's gridding (wrap, columns, z sort, clusters with dummies,
+ * bounding boxes) for callers that cannot allocate device memory at all:
+ * code that must not call cudaMalloc (for example inside a host callback or
+ * a graph node, a plug-in whose device memory is owned and capped by its
+ * host application, or a process whose allocations go through another
+ * runtime's allocator).  It needs no context and no workspace: its scratch
+ * lives in a fixed-size array that the library's module carries on every GPU
+ * that loads it (about 2.7 MB, held until the process exits).  The paper has
+ * no counterpart to this entry point; the results are bit-identical to
+ * nb_grid_put followed by nb_get_grid.
+ *
+ * Limits: n <= 32768 particles, at most 4096 grid columns, and
+ * n + columns * (C - 1) <= 61440 slots; beyond them the call returns
+ * NB_ERR_CAPACITY and does nothing.
+ * Inputs (device): xyz float [n][3] (each coordinate in [-L, 2L)), q float
+ * [n], type int [n] (0 <= type < ntypes <= 64); box_host double[3].
+ * Outputs (device, written on the stream): atom_of_slot int [max_slots]
+ * (-1 for a dummy), xyzq float [max_slots][4] (wrapped coordinates and
+ * charge), type_slot int [max_slots], bb float [max_slots / C][8]
+ * ({xmin, ymin, zmin, 0, xmax, ymax, zmax, 0} per cluster), col_clu_start
+ * int [max_columns + 1], info int [2] = {number of clusters, device flags
+ * (1 << NB_ERR_COORD for a coordinate outside [-L, 2L), 1 << NB_ERR_ARG for
+ * a type out of range)}.  Only the first clusters * C slots and nx * ny + 1
+ * column entries are written.  xyzq and bb must be 16-byte aligned.
+ * The first call on a device (with that device current) looks up the
+ * scratch array's device address; make that first call before any stream
+ * capture.  All calls share the one array and each call clears the parts
+ * that must start at zero, so calls whose work overlaps on the GPU race:
+ * serialise them (one stream, or events between streams).
+ * Errors: NB_ERR_ARG, NB_ERR_BOX, NB_ERR_CAPACITY, NB_ERR_CUDA. */
+nb_status nb_grid_put_noalloc(int n, const float* xyz_dev, const float* q_dev, const int* type_dev,
+                              int ntypes, const double* box_host, int cluster_size,
+                              int* atom_of_slot_dev, float* xyzq_dev, int* type_slot_dev,
+                              float* bb_dev, int* col_clu_start_dev, int* info_dev, int max_slots,
+                              int max_columns, nb_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,7 @@ def load():
             "nb_get_list": ([P, i, P, P, P, P], st),
             "nb_profile": ([P, i], st),
             "nb_profile_read": ([P, P, P, i, C.POINTER(C.c_int)], st),
+            "nb_grid_put_noalloc": ([i, P, P, P, i, P, i, P, P, P, P, P, P, i, i, P], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -246,6 +247,18 @@ def nb_profile_read(ctx, max_spans=256):
     cnt = C.c_int()
     _check(ctx, load().nb_profile_read(ctx, kinds, ms, int(max_spans), C.byref(cnt)))
     return [(kinds[k], ms[k]) for k in range(cnt.value)]
+
+
+def nb_grid_put_noalloc(n, xyz, q, types, ntypes, box, cluster_size, atom_of_slot, xyzq, type_slot,
+                        bb, col_clu_start, info, max_slots, max_columns, stream=None):
+    """Gridding into caller-provided outputs with no device allocation
+    anywhere (scratch in a fixed array inside the library); see the header."""
+    b = (C.c_double * 3)(*[float(v) for v in box])
+    s = load().nb_grid_put_noalloc(int(n), _ptr(xyz), _ptr(q), _ptr(types), int(ntypes), b,
+                                   int(cluster_size), _ptr(atom_of_slot), _ptr(xyzq), _ptr(type_slot),
+                                   _ptr(bb), _ptr(col_clu_start), _ptr(info), int(max_slots),
+                                   int(max_columns), _stream(stream))
+    _check(None, s)
 
 
 # --- convenience: one box with its torch-allocated workspace ---------------

@@ -1,0 +1,136 @@
+// nb_grid_put_noalloc: the gridding kernels of nb_grid_put run on scratch
+// memory that is a file-scope __device__ array instead of a caller-provided
+// workspace, for callers that cannot allocate device memory at all (code that
+// runs where cudaMalloc is forbidden or unavailable, e.g. inside a host
+// callback, a memory-capped plug-in, or a process whose allocator belongs to
+// another runtime).  The paper has no counterpart to this entry point.
+//
+// The array is loaded with the module on every GPU that uses the library and
+// stays allocated until the process exits.  Host code cannot use the array's
+// name as a device address, so the first call on each device (with that
+// device current) asks the runtime for the address with cudaGetSymbolAddress
+// and keeps it; that first call should therefore happen before any stream
+// capture.  Every call shares the one array: calls whose work overlaps on the
+// GPU (different streams, or different host threads on one device) race.
+#include <cmath>
+#include <mutex>
+
+#include "nb_internal.cuh"
+
+namespace nbc {
+
+constexpr int kNoallocMaxAtoms = 32768;
+constexpr int kNoallocMaxColumns = 4096;
+constexpr long long kNoallocMaxSlots = kNoallocMaxAtoms + (long long)kNoallocMaxColumns * 7;
+constexpr int kNoallocMaxDevices = 64;
+
+constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Scratch layout (byte offsets).
+constexpr size_t kOffState = 0;
+constexpr size_t kOffXw = align256(kOffState + sizeof(DevState));
+constexpr size_t kOffWoff = align256(kOffXw + sizeof(float4) * kNoallocMaxAtoms);
+constexpr size_t kOffColOfAtom = align256(kOffWoff + sizeof(float4) * kNoallocMaxAtoms);
+constexpr size_t kOffRank = align256(kOffColOfAtom + sizeof(int) * kNoallocMaxAtoms);
+constexpr size_t kOffSlotOfAtom = align256(kOffRank + sizeof(int) * kNoallocMaxAtoms);
+constexpr size_t kOffKeys = align256(kOffSlotOfAtom + sizeof(int) * kNoallocMaxAtoms);
+constexpr size_t kOffColCount = align256(kOffKeys + sizeof(unsigned long long) * kNoallocMaxAtoms);
+constexpr size_t kOffColAtomStart = align256(kOffColCount + sizeof(int) * kNoallocMaxColumns);
+constexpr size_t kOffFslot = align256(kOffColAtomStart + sizeof(int) * kNoallocMaxColumns);
+constexpr size_t kNoallocScratchBytes = align256(kOffFslot + sizeof(float4) * kNoallocMaxSlots);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+static std::mutex g_noalloc_mutex;
+static unsigned char* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set-up on the
+// first call per device).
+static cudaError_t noalloc_scratch(int dev, unsigned char** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = (unsigned char*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace nbc
+
+using namespace nbc;
+
+extern "C" nb_status nb_grid_put_noalloc(int n, const float* xyz, const float* q, const int* type,
+                                         int ntypes, const double* box, int cluster_size,
+                                         int* atom_of_slot, float* xyzq, int* type_slot, float* bb,
+                                         int* col_clu_start, int* info, int max_slots, int max_columns,
+                                         nb_stream stream) {
+    const int C = cluster_size;
+    if (C != 4 && C != 8) return NB_ERR_ARG;
+    if (n <= 0 || !xyz || !q || !type || !atom_of_slot || !xyzq || !type_slot || !bb || !col_clu_start ||
+        !info || ntypes <= 0 || ntypes > kMaxTypes || max_slots <= 0 || max_columns <= 0)
+        return NB_ERR_ARG;
+    if (((uintptr_t)xyzq & 15) || ((uintptr_t)bb & 15)) return NB_ERR_ARG;
+    if (!box) return NB_ERR_BOX;
+    GridGeom g{};
+    for (int k = 0; k < 3; ++k) {
+        if (!(box[k] > 0.0) || !(box[k] < 1e30)) return NB_ERR_BOX;
+        g.L[k] = (float)box[k];
+    }
+    // grid dimensions: spacing (C / rho)^(1/3) along x and y
+    {
+        const double Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
+        const double s = std::cbrt((double)C / ((double)n / (Lx * Ly * Lz)));
+        g.nx = (int)std::floor(Lx / s);
+        g.ny = (int)std::floor(Ly / s);
+        if (g.nx < 1) g.nx = 1;
+        if (g.ny < 1) g.ny = 1;
+    }
+    const long long ncol = (long long)g.nx * g.ny;
+    const long long nslot_bound = (long long)n + ncol * (C - 1);
+    if (n > kNoallocMaxAtoms || ncol > kNoallocMaxColumns || nslot_bound > kNoallocMaxSlots)
+        return NB_ERR_CAPACITY;
+    if (nslot_bound > max_slots || ncol > max_columns) return NB_ERR_CAPACITY;
+    g.inv_x = (float)((double)g.nx / (double)g.L[0]);
+    g.inv_y = (float)((double)g.ny / (double)g.L[1]);
+    {
+        float m = g.L[0];
+        if (g.L[1] > m) m = g.L[1];
+        if (g.L[2] > m) m = g.L[2];
+        float d = 1.0f;
+        while (d < 4.0f * m) d *= 2.0f;
+        g.dummy_g = d;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return NB_ERR_CUDA;
+    unsigned char* base = nullptr;
+    if (noalloc_scratch(dev, &base) != cudaSuccess) return NB_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws{};
+    ws.st = (DevState*)(base + kOffState);
+    ws.xw = (float4*)(base + kOffXw);
+    ws.woff = (float4*)(base + kOffWoff);
+    ws.col_of_atom = (int*)(base + kOffColOfAtom);
+    ws.rank_in_col = (int*)(base + kOffRank);
+    ws.slot_of_atom = (int*)(base + kOffSlotOfAtom);
+    ws.keys = (unsigned long long*)(base + kOffKeys);
+    ws.col_count = (int*)(base + kOffColCount);
+    ws.col_atom_start = (int*)(base + kOffColAtomStart);
+    ws.fslot = (float4*)(base + kOffFslot);
+    ws.q = const_cast<float*>(q);
+    ws.type = const_cast<int*>(type);
+    ws.col_clu_start = col_clu_start;
+    ws.xyzq = (float4*)xyzq;
+    ws.atom_of_slot = atom_of_slot;
+    ws.type_slot = type_slot;
+    ws.bb = (float4*)bb;
+    // the device state keeps the previous call's flags and counts: clear it
+    if (cudaMemsetAsync(ws.st, 0, sizeof(DevState), s) != cudaSuccess) return NB_ERR_CUDA;
+    if (launch_grid(ws, g, n, C, ntypes, xyz, 0, s) != cudaSuccess) return NB_ERR_CUDA;
+    if (cudaMemcpyAsync(&info[0], &ws.st->nclu, sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(&info[1], &ws.st->flags, sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return NB_ERR_CUDA;
+    return NB_OK;
+}
