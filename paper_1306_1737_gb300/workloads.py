@@ -103,7 +103,7 @@ def _cell_grid(L: np.ndarray, cell_min: float) -> np.ndarray:
     return np.maximum(1, np.floor(L / cell_min).astype(np.int64))
 
 
-def pairs_within(p: np.ndarray, L: np.ndarray, rcut: float):
+def _pairs_within_np(p: np.ndarray, L: np.ndarray, rcut: float):
     """All index pairs (i < j) with minimum-image distance < rcut (FP64).
 
     Generic geometry for input generation only (cell hashing with cells no
@@ -152,78 +152,73 @@ def pairs_within(p: np.ndarray, L: np.ndarray, rcut: float):
     return i, j
 
 
+_geom = None
+
+
+def _geom_lib():
+    """The C geometry helper (gen_geom.c), built with gcc on first use."""
+    global _geom
+    if _geom is not None:
+        return _geom
+    import ctypes as C
+    import os
+    import subprocess
+    here = os.path.dirname(os.path.abspath(__file__))
+    src = os.path.join(here, "gen_geom.c")
+    out = os.path.join(here, "_build", "libgengeom.so")
+    if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        tmp = out + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, src, "-lm"], check=True)
+        os.replace(tmp, out)
+    lib = C.CDLL(out)
+    P = C.c_void_p
+    lib.gen_rsa_fill.argtypes = [P, C.c_double, P, P, P, P, P, C.c_int64, P, C.c_int64]
+    lib.gen_rsa_fill.restype = C.c_int64
+    lib.gen_close_pairs.argtypes = [P, C.c_double, C.c_int64, P, C.c_int64, P, P]
+    lib.gen_close_pairs.restype = C.c_int64
+    _geom = lib
+    return lib
+
+
+def pairs_within(p: np.ndarray, L: np.ndarray, rcut: float):
+    """All index pairs (i < j) with minimum-image distance < rcut (FP64)."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    if np.any(np.floor(L / rcut) < 3) or p.shape[0] < 64:
+        return _pairs_within_np(p, L, rcut)
+    lib = _geom_lib()
+    cap = max(1024, 4 * p.shape[0])
+    while True:
+        oi = np.empty(cap, np.int64)
+        oj = np.empty(cap, np.int64)
+        n = lib.gen_close_pairs(L.ctypes.data, float(rcut), p.shape[0], p.ctypes.data, cap,
+                                oi.ctypes.data, oj.ctypes.data)
+        if n <= cap:
+            return oi[:n], oj[:n]
+        cap = int(n)
+
+
 def rsa_points(n: int, L: np.ndarray, dmin: float, rng: np.random.Generator) -> np.ndarray:
     """n points in the periodic box L with pairwise minimum-image distance >= dmin.
 
-    Random sequential addition in batches: each batch of uniform candidates is
-    tested against the accepted points and against earlier candidates of the
-    same batch; survivors are accepted in order.
+    Random sequential addition: uniform candidates (drawn from rng in chunks)
+    are accepted in order when no accepted point is closer than dmin.
     """
-    L = np.asarray(L, dtype=np.float64)
-    nc = _cell_grid(L, dmin)
-    ncells = int(nc.prod())
-    K = 4
-    far = 1.0e9
-    slots = np.full((ncells, K, 3), far)
-    count = np.zeros(ncells, np.int64)
-    out = np.empty((n, 3))
-    placed = 0
-    w = L / nc
-    acc_rate = 1.0
-    d2min = dmin * dmin
-    while placed < n:
-        remaining = n - placed
-        batch = int(min(max(remaining / max(acc_rate, 0.02) * 1.1, 256), max(n // 3, 4096)))
-        cand = rng.random((batch, 3)) * L
-        c3 = np.minimum((cand / w).astype(np.int64), nc - 1)
-        bad = np.zeros(batch, bool)
-        for ox in (-1, 0, 1):
-            gx = c3[:, 0] + ox
-            wx = np.floor_divide(gx, nc[0])
-            for oy in (-1, 0, 1):
-                gy = c3[:, 1] + oy
-                wy = np.floor_divide(gy, nc[1])
-                for oz in (-1, 0, 1):
-                    gz = c3[:, 2] + oz
-                    wz = np.floor_divide(gz, nc[2])
-                    nb = ((gx - wx * nc[0]) * nc[1] + (gy - wy * nc[1])) * nc[2] + (gz - wz * nc[2])
-                    # image of the candidate seen from the neighbour cell
-                    cx = cand[:, 0] - wx * L[0]
-                    cy = cand[:, 1] - wy * L[1]
-                    cz = cand[:, 2] - wz * L[2]
-                    s = slots[nb]
-                    r2 = (s[:, :, 0] - cx[:, None]) ** 2 + (s[:, :, 1] - cy[:, None]) ** 2 \
-                        + (s[:, :, 2] - cz[:, None]) ** 2
-                    bad |= (r2 < d2min).any(axis=1)
-        full = count[(c3[:, 0] * nc[1] + c3[:, 1]) * nc[2] + c3[:, 2]] >= K
-        ok = np.nonzero(~(bad | full))[0]
-        if ok.size:
-            # conflicts among survivors of this batch: drop the later one
-            ci, cj = pairs_within(cand[ok], L, dmin)
-            drop = np.zeros(ok.size, bool)
-            drop[np.maximum(ci, cj)] = True
-            ok = ok[~drop]
-        # at most K points per cell: drop candidates that would overflow
-        cid = (c3[ok, 0] * nc[1] + c3[ok, 1]) * nc[2] + c3[ok, 2]
-        order = np.argsort(cid, kind="stable")
-        cid_s = cid[order]
-        first = np.searchsorted(cid_s, cid_s, side="left")
-        rank = np.arange(cid_s.size) - first
-        fits = (count[cid_s] + rank) < K
-        ok = np.sort(ok[order[fits]])[:remaining]
-        # insert the accepted candidates (in acceptance order)
-        cid = (c3[ok, 0] * nc[1] + c3[ok, 1]) * nc[2] + c3[ok, 2]
-        order = np.argsort(cid, kind="stable")
-        cid_s = cid[order]
-        first = np.searchsorted(cid_s, cid_s, side="left")
-        rank = np.arange(cid_s.size) - first
-        pos = count[cid_s] + rank
-        slots[cid_s, pos] = cand[ok[order]]
-        np.add.at(count, cid_s, 1)
-        out[placed: placed + ok.size] = cand[ok]
-        placed += ok.size
-        acc_rate = max(ok.size / batch, 1e-3)
-    return out
+    import ctypes as C
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    lib = _geom_lib()
+    nc = np.maximum(1, np.floor(L / dmin)).astype(np.int32)
+    head = np.full(int(np.prod(nc.astype(np.int64))), -1, np.int32)
+    nxt = np.empty(max(n, 1), np.int32)
+    pts = np.empty((max(n, 1), 3))
+    npts = C.c_int64(0)
+    while npts.value < n:
+        chunk = max(4096, 4 * (n - npts.value))
+        cand = np.ascontiguousarray(rng.random((chunk, 3)) * L)
+        lib.gen_rsa_fill(L.ctypes.data, float(dmin), nc.ctypes.data, head.ctypes.data, nxt.ctypes.data,
+                         pts.ctypes.data, C.byref(npts), n, cand.ctypes.data, chunk)
+    return pts[:n].copy()
 
 
 def water_box(n_mol: int, L: float | None = None, seed: int = 0,
