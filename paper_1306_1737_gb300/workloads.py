@@ -11,8 +11,9 @@ Table 3; Fig. 3 uses a 3-site water model at number density 100 nm^-3).
 No dataset is used; these boxes stand in for it.
 
 Recipe (all FP64, rounded to FP32 at the end):
-  * oxygen sites by random sequential addition (RSA) in batches under
-    periodic boundaries with a minimum O-O distance of 0.25 nm;
+  * oxygen sites by random sequential addition (RSA) under periodic
+    boundaries with a minimum O-O distance of 0.25 nm (candidates drawn from
+    the seeded PCG64 stream, tested with a linked-cell list in gen_geom.c);
   * a uniform random orientation per molecule from a normalised 4-vector of
     standard normals (quaternion); O-H 0.1 nm, H-O-H 109.47 degrees;
   * a molecule whose hydrogen comes closer than 0.10 nm to a hydrogen of
