@@ -1,0 +1,109 @@
+"""GPU parity on the 3,000,000-particle box (1,000,000 water-like molecules,
+10% re-typed among 8 LJ types combined by Lorentz-Berthelot), in the
+configuration bench.py times: the full grid bit-exact against the oracle,
+the cluster-pair list and the pruned list compared key by key for sampled
+clusters, and the forces of sampled particles (each against all 3M particles
+in the oracle) within 1e-4 of their RMS."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1306_1737_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-4
+EXEMPT_NM = 1e-6
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1306_1737_gb300 as nb
+    nb.load()
+    import gpu_path
+    from conftest import cached_config
+    return torch, nb, gpu_path, cached_config("config3")
+
+
+def gpu_keys(gb, which):
+    info, ient, cj, mask = gb.list_arrays(which)
+    lens = ient[:, 3] - ient[:, 2]
+    a = np.repeat(ient[:, 0], lens)
+    s = np.repeat(ient[:, 1], lens)
+    starts = np.cumsum(lens) - lens
+    idx = np.arange(int(lens.sum())) - np.repeat(starts, lens) + np.repeat(ient[:, 2], lens)
+    b = cj[idx]
+    m = mask[idx]
+    return a, b, s, m
+
+
+def compare_sampled(g_or, keys_gpu, samples, rl, excl_off, excl_idx, prune=None):
+    a, b, s, m = keys_gpu
+    assert np.all(a <= b)
+    for c in samples:
+        pl = oracle.pairlist_cluster(g_or, int(c), rl, 0.0, excl_off, excl_idx)
+        if prune is not None:
+            r_p, xs = prune
+            keep, _ = oracle.prune(g_or, pl, r_p, xs)
+            pl = oracle.PairList(pl.a[keep], pl.b[keep], pl.s[keep], pl.mask[keep])
+        sel = (a == c) | (b == c)
+        got = dict(zip(zip(a[sel].tolist(), b[sel].tolist(), s[sel].tolist()), m[sel].tolist()))
+        assert len(got) == int(sel.sum())          # no duplicate keys
+        want = pl.key_mask()
+        diff = set(got) ^ set(want)
+        if diff:
+            da = np.array([k[0] for k in diff], np.int32)
+            db = np.array([k[1] for k in diff], np.int32)
+            ds = np.array([k[2] for k in diff], np.int32)
+            if prune is None:
+                dm, _ = oracle.key_distances(g_or, da, db, ds)
+                thr = rl
+            else:
+                _, dm = oracle.prune(g_or, oracle.PairList(da, db, ds, np.zeros(da.size, np.uint64)),
+                                     prune[0], prune[1])
+                thr = prune[0]
+            assert np.all(np.abs(dm - thr) < EXEMPT_NM), (c, len(diff))
+        for k in set(got) & set(want):
+            assert got[k] == want[k], (c, k)
+
+
+def test_config3_grid_list_prune_forces(env):
+    torch, nb, gp, (b, p) = env
+    gb = gp.GpuBox(b, p["rlist"])
+    try:
+        gb.grid()
+        g_or = oracle.grid(b.xyz, b.q, b.types, b.box, 8)
+        from test_gpu_parity import check_grid
+        check_grid(gb.grid_arrays(), g_or)
+        rl = float(np.float32(p["rlist"]))
+        gb.build(rl)
+        rng = np.random.default_rng(33)
+        samples = rng.choice(g_or.nclu, 24, replace=False)
+        compare_sampled(g_or, gpu_keys(gb, 0), samples, rl, b.excl_off, b.excl_idx)
+        prm = nb.make_params("ewald", p["rc"], beta=p["beta"])
+        oprm = oracle.make_params("ewald", float(np.float32(p["rc"])), beta=p["beta"], comb="lb")
+        f, e, vir = gb.compute(prm)
+        sel = rng.choice(b.n, 2048, replace=False)
+        fo, _, _ = oracle.forces_brute(b.xyz, b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx,
+                                       b.box, oprm, sel=sel)
+        emax, erms, rms = gp.force_errors(f[sel], fo)
+        assert emax < FORCE_TOL, (emax, erms)
+        # Newton's third law over the whole box (FP32 accumulation)
+        assert np.abs(f.sum(0)).max() < 1e-3 * rms * np.sqrt(b.n)
+        # after 5 frames of displacements: prune and forces again
+        disp = w.frame_displacements(b.mass, 5, seed=3003).sum(0)
+        x5 = b.xyz + disp
+        rp = float(np.float32(w.prune_radius(p["rc"], p["rlist"], p["nstprune"])))
+        gb.prune(rp, x5)
+        x5s = oracle.slot_coords(g_or, x5)
+        compare_sampled(g_or, gpu_keys(gb, 1), samples[:12], rl, b.excl_off, b.excl_idx, prune=(rp, x5s))
+        f5, _, _ = gb.compute(prm)
+        fo5, _, _ = oracle.forces_brute(x5, b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx,
+                                        b.box, oprm, sel=sel)
+        emax, erms, _ = gp.force_errors(f5[sel], fo5)
+        assert emax < FORCE_TOL, (emax, erms)
+    finally:
+        gb.close()
