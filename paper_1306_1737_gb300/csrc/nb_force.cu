@@ -75,21 +75,137 @@ __device__ __forceinline__ void pair_fn(const ForceParams& P, bool inc, float bi
         vlj = inc ? bit * (lj.y * (1.0f / 12.0f) * rinv6 - lj.x * (1.0f / 6.0f)) * rinv6 : 0.0f;
 }
 
+// Packed FP32x2 helpers: component x is the lane's pair (ih, j), component y
+// its pair (ih + 4, j).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 sel2(bool p, bool q, float2 v) {
+    return make_float2(p ? v.x : 0.0f, q ? v.y : 0.0f);
+}
+
+// How a j-entry's pairs are counted: all-ones mask (no dummy, no
+// exclusion: every pair inside rc is a full interaction), general mask, or
+// the unshifted self-pair (only j > i counts).
+enum { kModeFull = 0, kModeMasked = 1, kModeDiag = 2 };
+
+// Two particle pairs of one lane.  lj0/lj1 = {-6 C6, 12 C12}; u: mask bit
+// (full interaction); inc: pair counted and inside rc.  Pairs that are not
+// counted are computed on whatever r2 they have and selected away.
+template <int ELEC, bool ENERGY, bool FIT, int MODE>
+__device__ __forceinline__ void pair2(const ForceParams& P, bool inc0, bool inc1, bool u0, bool u1,
+                                      float2 r2, float2 qq, float2 lj0, float2 lj1, float2& fs,
+                                      float& vlj, float& vc) {
+    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 rinv2 = mul2(rinv, rinv);
+    const float2 rinv6 = mul2(mul2(rinv2, rinv2), rinv2);
+    const float2 c6n = make_float2(lj0.x, lj1.x), c12 = make_float2(lj0.y, lj1.y);
+    float2 flj = mul2(mul2(fma2(c12, rinv6, c6n), rinv6), rinv2);
+    float2 rinv3e = mul2(rinv, rinv2);
+    if (MODE != kModeFull) {
+        flj = sel2(u0, u1, flj);
+        rinv3e = sel2(u0, u1, rinv3e);
+    }
+    float2 fc;
+    if (ELEC == NB_ELEC_RF) {
+        fc = mul2(qq, add2(rinv3e, bc2(-P.two_k_rf)));
+    } else if (FIT) {
+        const float2 w = mul2(bc2(P.beta2), r2);
+        fc = mul2(qq, fma2(ewald_fit_g2(w), bc2(-P.beta3), rinv3e));
+    } else {
+        float rr[2] = {r2.x, r2.y}, ri[2] = {rinv.x, rinv.y}, re[2] = {rinv3e.x, rinv3e.y}, o[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float r = rr[k] * ri[k];
+            const float br = P.beta * r;
+            // (erfc(br) - 1 + 2br/sqrt(pi) exp(-b^2 r^2)) / r^3 = -beta^3 G
+            o[k] = re[k] + (erfcf(br) - 1.0f + P.two_beta_sqrtpi * r * __expf(-br * br)) * ri[k] * ri[k] * ri[k];
+        }
+        fc = mul2(qq, make_float2(o[0], o[1]));
+    }
+    fs = sel2(inc0, inc1, add2(flj, fc));
+    if (ENERGY) {
+        // V_LJ = (C12 r^-6 - C6) r^-6
+        const float2 v6 = mul2(fma2(mul2(c12, bc2(1.0f / 12.0f)), rinv6, mul2(c6n, bc2(1.0f / 6.0f))), rinv6);
+        const float2 vl = sel2(inc0 && u0, inc1 && u1, v6);
+        const float2 rinve = MODE == kModeFull ? rinv : sel2(u0, u1, rinv);
+        float2 v;
+        if (ELEC == NB_ELEC_RF) {
+            v = mul2(qq, fma2(bc2(P.k_rf), r2, add2(rinve, bc2(-P.c_rf))));
+        } else if (FIT) {
+            const float2 w = mul2(bc2(P.beta2), r2);
+            v = mul2(qq, fma2(ewald_fit_h2(w), bc2(-P.beta), rinve));
+        } else {
+            const float r0 = r2.x * rinv.x, r1 = r2.y * rinv.y;
+            v = mul2(qq, make_float2((erfcf(P.beta * r0) - 1.0f) * rinv.x + rinve.x,
+                                     (erfcf(P.beta * r1) - 1.0f) * rinv.y + rinve.y));
+        }
+        const float2 vsel = sel2(inc0, inc1, v);
+        vlj += vl.x + vl.y;
+        vc += vsel.x + vsel.y;
+    }
+}
+
 struct Lane8 {
     int j, ih;
     bool lower0, lower1;  // (ih, j) and (ih+4, j) on or below the diagonal
-    int bitpos;
+    unsigned sel;         // bit of this lane's pairs within each 32-bit half of the mask
 };
 
-// All j-entries [jb, je) (at most 32) of one i-entry; SHIFTED adds the low
-// part of the shifted i coordinates.
+// The 2 x 32 pairs of one j-cluster.  Returns (uniformly) whether any pair
+// of the warp was inside rc; fj is this lane's share of the j-force.
+template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, int MODE>
+__device__ __forceinline__ bool jcluster8(const ForceParams& P, const float2* s_lj, const Lane8& L,
+                                          float4 xj, int tj, unsigned mlo, unsigned mhi, float2 xh,
+                                          float2 yh, float2 zh, float2 xl, float2 yl, float2 zl, float2 qi,
+                                          int ti0, int ti1, float2& fx, float2& fy, float2& fz,
+                                          float& e_lj, float& e_c, unsigned& n_inc, float& fjx,
+                                          float& fjy, float& fjz) {
+    float d0x = xh.x - xj.x, d1x = xh.y - xj.x;
+    float d0y = yh.x - xj.y, d1y = yh.y - xj.y;
+    float d0z = zh.x - xj.z, d1z = zh.y - xj.z;
+    if (SHIFTED) {
+        d0x += xl.x; d1x += xl.y;
+        d0y += yl.x; d1y += yl.y;
+        d0z += zl.x; d1z += zl.y;
+    }
+    const float2 dx = make_float2(d0x, d1x), dy = make_float2(d0y, d1y), dz = make_float2(d0z, d1z);
+    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    bool u0 = true, u1 = true;
+    if (MODE != kModeFull) {
+        u0 = (mlo & L.sel) != 0u;
+        u1 = (mhi & L.sel) != 0u;
+    }
+    bool inc0 = r2.x < P.rc2;
+    bool inc1 = r2.y < P.rc2;
+    if (MODE == kModeDiag) {
+        inc0 = inc0 && (u0 || !L.lower0);
+        inc1 = inc1 && (u1 || !L.lower1);
+    }
+    if (!__any_sync(0xffffffffu, inc0 || inc1)) return false;
+    const float2 lj0 = s_lj[ti0 + tj], lj1 = s_lj[ti1 + tj];
+    float2 fs;
+    pair2<ELEC, ENERGY, FIT, MODE>(P, inc0, inc1, u0, u1, r2, make_float2(qi.x * xj.w, qi.y * xj.w), lj0,
+                                   lj1, fs, e_lj, e_c);
+    if (ENERGY) n_inc += (unsigned)inc0 + (unsigned)inc1;
+    const float2 px = mul2(fs, dx), py = mul2(fs, dy), pz = mul2(fs, dz);
+    fx = add2(fx, px);
+    fy = add2(fy, py);
+    fz = add2(fz, pz);
+    fjx = -(px.x + px.y);
+    fjy = -(py.x + py.y);
+    fjz = -(pz.x + pz.y);
+    return true;
+}
+
+// All j-entries [jb, je) (at most 32) of one i-entry.
 template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED>
 __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s_lj, const Lane8& L,
-                                             int ci, bool center, int jb, int je, const float (&x0h)[3],
-                                             const float (&x0l)[3], const float (&x1h)[3],
-                                             const float (&x1l)[3], float qi0, float qi1, int ti0,
-                                             int ti1, float (&f0)[3], float (&f1)[3], float& e_lj,
-                                             float& e_c, unsigned& n_inc) {
+                                             int ci, bool center, int jb, int je, float2 xh, float2 yh,
+                                             float2 zh, float2 xl, float2 yl, float2 zl, float2 qi,
+                                             int ti0, int ti1, float2& fx, float2& fy, float2& fz,
+                                             float& e_lj, float& e_c, unsigned& n_inc) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int nt = je - jb;
@@ -99,51 +215,37 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
         my_cj = A.cj[jb + lane];
         my_m = A.mask[jb + lane];
     }
+    const float4* xyzq_j = A.xyzq + L.j;
+    const int* type_j = A.type_slot + L.j;
     int cjn = __shfl_sync(full, my_cj, 0);
-    float4 xjn = A.xyzq[cjn * 8 + L.j];
-    int tjn = A.type_slot[cjn * 8 + L.j];
+    float4 xjn = xyzq_j[cjn * 8];
+    int tjn = type_j[cjn * 8];
     for (int t = 0; t < nt; ++t) {
         const int cjt = cjn;
         const float4 xj = xjn;
         const int tj = tjn;
         if (t + 1 < nt) {
             cjn = __shfl_sync(full, my_cj, t + 1);
-            xjn = A.xyzq[cjn * 8 + L.j];
-            tjn = A.type_slot[cjn * 8 + L.j];
+            xjn = xyzq_j[cjn * 8];
+            tjn = type_j[cjn * 8];
         }
         const unsigned mlo = __shfl_sync(full, (unsigned)my_m, t);
         const unsigned mhi = __shfl_sync(full, (unsigned)(my_m >> 32), t);
-        const bool diag = center && (cjt == ci);
-        const unsigned u0 = (mlo >> L.bitpos) & 1u;
-        const unsigned u1 = (mhi >> L.bitpos) & 1u;
-        float d0x = x0h[0] - xj.x, d0y = x0h[1] - xj.y, d0z = x0h[2] - xj.z;
-        float d1x = x1h[0] - xj.x, d1y = x1h[1] - xj.y, d1z = x1h[2] - xj.z;
-        if (SHIFTED) {
-            d0x += x0l[0]; d0y += x0l[1]; d0z += x0l[2];
-            d1x += x1l[0]; d1y += x1l[1]; d1z += x1l[2];
-        }
-        const float r2_0 = fmaf(d0x, d0x, fmaf(d0y, d0y, d0z * d0z));
-        const float r2_1 = fmaf(d1x, d1x, fmaf(d1y, d1y, d1z * d1z));
-        const bool inc0 = (r2_0 < A.p.rc2) && (u0 || !(diag && L.lower0));
-        const bool inc1 = (r2_1 < A.p.rc2) && (u1 || !(diag && L.lower1));
-        if (!__any_sync(full, inc0 || inc1)) continue;
-        float fs0, fs1, vl0 = 0.f, vl1 = 0.f, vc0 = 0.f, vc1 = 0.f;
-        pair_fn<ELEC, ENERGY, FIT>(A.p, inc0, (float)u0, r2_0, qi0 * xj.w, s_lj[ti0 + tj], fs0, vl0, vc0);
-        pair_fn<ELEC, ENERGY, FIT>(A.p, inc1, (float)u1, r2_1, qi1 * xj.w, s_lj[ti1 + tj], fs1, vl1, vc1);
-        if (ENERGY) {
-            e_lj += vl0 + vl1;
-            e_c += vc0 + vc1;
-            n_inc += (unsigned)inc0 + (unsigned)inc1;
-        }
-        f0[0] = fmaf(fs0, d0x, f0[0]);
-        f0[1] = fmaf(fs0, d0y, f0[1]);
-        f0[2] = fmaf(fs0, d0z, f0[2]);
-        f1[0] = fmaf(fs1, d1x, f1[0]);
-        f1[1] = fmaf(fs1, d1y, f1[1]);
-        f1[2] = fmaf(fs1, d1z, f1[2]);
-        float fjx = -fmaf(fs0, d0x, fs1 * d1x);
-        float fjy = -fmaf(fs0, d0y, fs1 * d1y);
-        float fjz = -fmaf(fs0, d0z, fs1 * d1z);
+        float fjx, fjy, fjz;
+        bool any;
+        if (center && cjt == ci)
+            any = jcluster8<ELEC, ENERGY, FIT, SHIFTED, kModeDiag>(A.p, s_lj, L, xj, tj, mlo, mhi, xh, yh, zh, xl,
+                                                                  yl, zl, qi, ti0, ti1, fx, fy, fz, e_lj, e_c,
+                                                                  n_inc, fjx, fjy, fjz);
+        else if ((mlo & mhi) == full)
+            any = jcluster8<ELEC, ENERGY, FIT, SHIFTED, kModeFull>(A.p, s_lj, L, xj, tj, mlo, mhi, xh, yh, zh, xl,
+                                                                  yl, zl, qi, ti0, ti1, fx, fy, fz, e_lj, e_c,
+                                                                  n_inc, fjx, fjy, fjz);
+        else
+            any = jcluster8<ELEC, ENERGY, FIT, SHIFTED, kModeMasked>(A.p, s_lj, L, xj, tj, mlo, mhi, xh, yh, zh,
+                                                                    xl, yl, zl, qi, ti0, ti1, fx, fy, fz, e_lj,
+                                                                    e_c, n_inc, fjx, fjy, fjz);
+        if (!any) continue;
         fjx += __shfl_xor_sync(full, fjx, 8);
         fjy += __shfl_xor_sync(full, fjy, 8);
         fjz += __shfl_xor_sync(full, fjz, 8);
@@ -155,13 +257,13 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
 }
 
 template <int ELEC, bool ENERGY, bool FIT>
-__global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 6 : 8) k_force8(ForceArgs A) {
+__global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 6 : 7) k_force8(ForceArgs A) {
     extern __shared__ float2 s_lj[];
     const unsigned full = 0xffffffffu;
     const int nt2 = A.p.ntypes * A.p.ntypes;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
         const float2 v = A.c6c12[k];
-        s_lj[k] = make_float2(6.0f * v.x, 12.0f * v.y);
+        s_lj[k] = make_float2(-6.0f * v.x, 12.0f * v.y);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -170,7 +272,7 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 6 : 8) k_force8(For
     L.ih = lane >> 3;
     L.lower0 = L.j <= L.ih;
     L.lower1 = L.j <= L.ih + 4;
-    L.bitpos = L.ih * 8 + L.j;
+    L.sel = 1u << (L.ih * 8 + L.j);
     const long long nient = min((long long)A.st->n_ient, A.p.ient_cap);
     float e_lj = 0.0f, e_c = 0.0f;
     unsigned n_inc = 0;
@@ -190,21 +292,26 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 6 : 8) k_force8(For
         two_sum(x1.x, sh[0], x1h[0], x1l[0]);
         two_sum(x1.y, sh[1], x1h[1], x1l[1]);
         two_sum(x1.z, sh[2], x1h[2], x1l[2]);
-        const float qi0 = x0.w * A.p.fcoul, qi1 = x1.w * A.p.fcoul;
+        const float2 xh = make_float2(x0h[0], x1h[0]), yh = make_float2(x0h[1], x1h[1]),
+                     zh = make_float2(x0h[2], x1h[2]);
+        const float2 xl = make_float2(x0l[0], x1l[0]), yl = make_float2(x0l[1], x1l[1]),
+                     zl = make_float2(x0l[2], x1l[2]);
+        const float2 qi = make_float2(x0.w * A.p.fcoul, x1.w * A.p.fcoul);
         const int ti0 = A.type_slot[ci * 8 + L.ih] * A.p.ntypes;
         const int ti1 = A.type_slot[ci * 8 + L.ih + 4] * A.p.ntypes;
         const bool center = (s == kShiftCenter);
-        float f0[3] = {0.f, 0.f, 0.f}, f1[3] = {0.f, 0.f, 0.f};
+        float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx;
         for (int base = jb; base < je; base += 32) {
             const int bend = min(je, base + 32);
             if (center)
-                force_entry8<ELEC, ENERGY, FIT, false>(A, s_lj, L, ci, center, base, bend, x0h, x0l, x1h,
-                                                       x1l, qi0, qi1, ti0, ti1, f0, f1, e_lj, e_c, n_inc);
+                force_entry8<ELEC, ENERGY, FIT, false>(A, s_lj, L, ci, center, base, bend, xh, yh, zh, xl, yl,
+                                                       zl, qi, ti0, ti1, fx, fy, fz, e_lj, e_c, n_inc);
             else
-                force_entry8<ELEC, ENERGY, FIT, true>(A, s_lj, L, ci, center, base, bend, x0h, x0l, x1h,
-                                                      x1l, qi0, qi1, ti0, ti1, f0, f1, e_lj, e_c, n_inc);
+                force_entry8<ELEC, ENERGY, FIT, true>(A, s_lj, L, ci, center, base, bend, xh, yh, zh, xl, yl,
+                                                      zl, qi, ti0, ti1, fx, fy, fz, e_lj, e_c, n_inc);
         }
         // i-forces: sum over the 8 lanes of each i row
+        float f0[3] = {fx.x, fy.x, fz.x}, f1[3] = {fx.y, fy.y, fz.y};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
 #pragma unroll
