@@ -217,7 +217,7 @@ def config_dict(args, box, p, desc):
     return {"workload": args.workload, "description": desc, "n_atoms": int(box.n),
             "box_nm": [round(float(v), 6) for v in box.box], "elec": p["elec"], "rc_nm": p["rc"],
             "rlist_nm": p["rlist"], "beta_nm-1": p.get("beta"), "nstlist": p.get("nstlist", 1),
-            "nstprune": p.get("nstprune", 0), "cluster": "8x8 pairs, computed as two 8x4 halves per warp",
+            "nstprune": p.get("nstprune", 0), "cluster": "8x8 cluster pairs (two 8x4 halves per warp), super-clusters of 4 i-clusters sharing a j-list",
             "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}",
             "seed": int(box.seed)}
 
@@ -346,8 +346,8 @@ def run_ours(args):
     prune_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_PRUNE]
     search_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_SEARCH]
     grid_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_GRID]
-    pairs_outer = int(info.n_jentries) * 64
-    pairs_pruned = int(info.n_jentries_pruned) * 64 if info.n_jentries_pruned >= 0 else pairs_outer
+    pairs_outer = int(info.n_cluster_pairs) * 64
+    pairs_pruned = int(info.n_cluster_pairs_pruned) * 64 if info.n_cluster_pairs_pruned >= 0 else pairs_outer
     # frames before the first prune use the outer list
     n_outer = min(nstprune, nstlist) if nstprune else nstlist
     listed = (n_outer * pairs_outer + (nstlist - n_outer) * pairs_pruned) / nstlist
@@ -406,9 +406,11 @@ def run_ours(args):
                           "search": statistics.mean(search_ms) if search_ms else None,
                           "prune": statistics.mean(prune_ms) if prune_ms else None,
                           "force": t_force * 1e3},
-            "list": {"clusters": int(info.n_clusters), "ientries": int(info.n_ientries),
-                     "jentries": int(info.n_jentries), "jentries_pruned": int(info.n_jentries_pruned),
-                     "r_prune_nm": rprune},
+            "list": {"clusters": int(info.n_clusters), "superclusters": int(info.n_superclusters),
+                     "ientries": int(info.n_ientries), "jentries": int(info.n_jentries),
+                     "jentries_pruned": int(info.n_jentries_pruned),
+                     "cluster_pairs": int(info.n_cluster_pairs),
+                     "cluster_pairs_pruned": int(info.n_cluster_pairs_pruned), "r_prune_nm": rprune},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

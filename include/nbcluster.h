@@ -85,6 +85,10 @@ typedef struct {
     int64_t n_jentries_pruned; /* j-entries kept by the last nb_prune (-1: none) */
     int64_t ient_capacity, jent_capacity;
     int64_t n_pairs_rc;   /* particle pairs inside rc in the last energy evaluation */
+    int64_t n_cluster_pairs;        /* cluster pairs (i-cluster, j-cluster, shift) in the outer list */
+    int64_t n_cluster_pairs_pruned; /* cluster pairs kept by the last nb_prune (-1: none) */
+    int n_superclusters;  /* super-clusters (runs of up to super_size clusters of a column) */
+    int super_size;       /* i-clusters per super-cluster: 2 for C = 8, 1 for C = 4 */
     int64_t n_launches;   /* kernels this context has launched */
     uint32_t flags;       /* device error flags (bit mask of 1 << nb_status_code) */
 } nb_info;
@@ -222,18 +226,24 @@ nb_status nb_profile_read(nb_ctx* ctx, int* kinds_host, float* ms_host, int max,
  * col_clu_start_dev: int [nx*ny+1], xyzq_dev: float [nslots][4] (wrapped
  * coordinates and charge; dummies far outside the box), type_slot_dev: int
  * [nslots], bb_dev: float [nclusters][6] (min xyz, max xyz), col_of_atom_dev:
- * int [n].  nslots = n_clusters * C from nb_check's info.
+ * int [n], sc_info_dev: int [n_superclusters][2] = {first cluster, number of
+ * clusters} of each super-cluster.  nslots = n_clusters * C from nb_check.
  * Errors: NB_ERR_STATE, NB_ERR_CUDA. */
 nb_status nb_get_grid(nb_ctx* ctx, int* atom_of_slot_dev, int* slot_of_atom_dev,
                       int* col_clu_start_dev, float* xyzq_dev, int* type_slot_dev, float* bb_dev,
-                      int* col_of_atom_dev, nb_stream stream);
+                      int* col_of_atom_dev, int* sc_info_dev, nb_stream stream);
 
 /* Copy a list (which = 0: outer, 1: pruned) in its storage form, device to
- * device: ient_dev int [n_ientries][4] = {ci, shift, j_begin, j_end}, cj_dev
- * int [n_jentries], mask_dev uint64 [n_jentries].  Shift index s encodes
- * (sx, sy, sz) in {-1,0,1}^3 as (sx+1)*9 + (sy+1)*3 + (sz+1).  Sizes from
- * nb_check (j-entries are indexed by the i-entries' ranges; for the pruned
- * list use the outer list's n_jentries as the array size).
+ * device.  The list is kept per super-cluster (Sec. 3.1: several i-clusters
+ * share one j-list): ient_dev int [n_ientries][4] = {super-cluster, shift,
+ * j_begin, j_end}; cj_dev int [n_jentries], each the j-cluster index in bits
+ * 0..26 and, in bits 27.., one interaction bit per i-cluster k of the
+ * super-cluster (cluster first + k); mask_dev uint64 [super_size][n_jentries],
+ * the exclusion mask of i-cluster k with that j-cluster (bit i*C+j: full
+ * interaction).  Shift index s encodes (sx, sy, sz) in {-1,0,1}^3 as
+ * (sx+1)*9 + (sy+1)*3 + (sz+1), applied to the i side.  Sizes from nb_check
+ * (j-entries are indexed by the i-entries' ranges; for the pruned list use
+ * the outer list's n_jentries as the array size).
  * Errors: NB_ERR_STATE, NB_ERR_CUDA. */
 nb_status nb_get_list(nb_ctx* ctx, int which, int* ient_dev, int* cj_dev, uint64_t* mask_dev,
                       nb_stream stream);
@@ -247,7 +257,7 @@ nb_status nb_get_list(nb_ctx* ctx, int which, int* ient_dev, int* cj_dev, uint64
  * host application, or a process whose allocations go through another
  * runtime's allocator).  It needs no context and no workspace: its scratch
  * lives in a fixed-size array that the library's module carries on every GPU
- * that loads it (about 2.7 MB, held until the process exits).  The paper has
+ * that loads it (about 2.8 MB, held until the process exits).  The paper has
  * no counterpart to this entry point; the results are bit-identical to
  * nb_grid_put followed by nb_get_grid.
  *

@@ -53,7 +53,9 @@ class nb_info(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("n_clusters", C.c_int),
                 ("n_ientries", C.c_int64), ("n_jentries", C.c_int64),
                 ("n_jentries_pruned", C.c_int64), ("ient_capacity", C.c_int64),
-                ("jent_capacity", C.c_int64), ("n_pairs_rc", C.c_int64), ("n_launches", C.c_int64),
+                ("jent_capacity", C.c_int64), ("n_pairs_rc", C.c_int64),
+                ("n_cluster_pairs", C.c_int64), ("n_cluster_pairs_pruned", C.c_int64),
+                ("n_superclusters", C.c_int), ("super_size", C.c_int), ("n_launches", C.c_int64),
                 ("flags", C.c_uint32)]
 
 
@@ -91,7 +93,7 @@ def load():
             "nb_prune": ([P, P, C.c_float, P], st),
             "nb_compute": ([P, C.POINTER(nb_params), P, P, P, P, P], st),
             "nb_check": ([P, P, C.POINTER(nb_info)], st),
-            "nb_get_grid": ([P, P, P, P, P, P, P, P, P], st),
+            "nb_get_grid": ([P, P, P, P, P, P, P, P, P, P], st),
             "nb_get_list": ([P, i, P, P, P, P], st),
             "nb_profile": ([P, i], st),
             "nb_profile_read": ([P, P, P, i, C.POINTER(C.c_int)], st),
@@ -225,10 +227,10 @@ def nb_check(ctx, stream=None, raise_on_error: bool = True) -> nb_info:
 
 
 def nb_get_grid(ctx, atom_of_slot=None, slot_of_atom=None, col_clu_start=None, xyzq=None,
-                type_slot=None, bb=None, col_of_atom=None, stream=None):
+                type_slot=None, bb=None, col_of_atom=None, sc_info=None, stream=None):
     _check(ctx, load().nb_get_grid(ctx, _ptr(atom_of_slot), _ptr(slot_of_atom), _ptr(col_clu_start),
                                    _ptr(xyzq), _ptr(type_slot), _ptr(bb), _ptr(col_of_atom),
-                                   _stream(stream)))
+                                   _ptr(sc_info), _stream(stream)))
 
 
 def nb_get_list(ctx, which, ient=None, cj=None, mask=None, stream=None):

@@ -22,7 +22,7 @@ struct nb_ctx {
     size_t ws_bytes = 0;
     int n_cap = 0;
     int ncol_cap = 0;
-    long long nslot_cap = 0, nclu_cap = 0, ient_cap = 0, jent_cap = 0;
+    long long nslot_cap = 0, nclu_cap = 0, nsc_cap = 0, ient_cap = 0, jent_cap = 0;
     int ntypes_cap = 0;
     Workspace ws{};
     DevState* st_host = nullptr;  // pinned read-back buffer
@@ -109,8 +109,8 @@ static float dummy_spacing(const float L[3]) {
 }
 
 struct Sizes {
-    int n, ncol, ntypes;
-    long long nslot, nclu, ient, jent;
+    int n, ncol, ntypes, S;
+    long long nslot, nclu, nsc, ient, jent;
 };
 
 // Lay the workspace out from base (nullptr: only count bytes).
@@ -135,6 +135,8 @@ static size_t carve(const Sizes& z, char* base, Workspace* ws) {
     w.col_count = (int*)take(sizeof(int) * z.ncol);
     w.col_atom_start = (int*)take(sizeof(int) * z.ncol);
     w.col_clu_start = (int*)take(sizeof(int) * (z.ncol + 1));
+    w.col_sc_start = (int*)take(sizeof(int) * (z.ncol + 1));
+    w.sc_info = (int2*)take(sizeof(int2) * z.nsc);
     w.keys = (unsigned long long*)take(sizeof(unsigned long long) * z.n);
     w.xyzq = (float4*)take(sizeof(float4) * z.nslot);
     w.atom_of_slot = (int*)take(sizeof(int) * z.nslot);
@@ -143,17 +145,21 @@ static size_t carve(const Sizes& z, char* base, Workspace* ws) {
     w.bb = (float4*)take(sizeof(float4) * 2 * z.nclu);
     w.ient = (int4*)take(sizeof(int4) * z.ient);
     w.cj = (int*)take(sizeof(int) * z.jent);
-    w.mask = (unsigned long long*)take(sizeof(unsigned long long) * z.jent);
+    w.mask = (unsigned long long*)take(sizeof(unsigned long long) * z.jent * z.S);
     w.ient_p = (int4*)take(sizeof(int4) * z.ient);
     w.cj_p = (int*)take(sizeof(int) * z.jent);
-    w.mask_p = (unsigned long long*)take(sizeof(unsigned long long) * z.jent);
+    w.mask_p = (unsigned long long*)take(sizeof(unsigned long long) * z.jent * z.S);
+    w.jstride = z.jent;
     w.c6c12 = (float2*)take(sizeof(float2) * z.ntypes * z.ntypes);
     if (ws) *ws = w;
     return (off + 255) & ~(size_t)255;
 }
 
-// Sizes for n particles in box L with lists up to rlist (density estimate of
-// the cluster-pair count, scaled by factor).
+// Sizes for n particles in box L with lists up to rlist.  The number of
+// j-entries is estimated from the density: j-clusters whose bounding box is
+// within rlist of a super-cluster's box (half of them, Newton's third law),
+// i.e. the cluster density times the volume of the rounded box of side
+// (super-cluster extent + cluster extent) dilated by rlist, scaled by factor.
 static Sizes plan(int n, const float L[3], int C, double rlist, int ntypes, double factor) {
     Sizes z{};
     int nx, ny;
@@ -161,23 +167,23 @@ static Sizes plan(int n, const float L[3], int C, double rlist, int ntypes, doub
     z.n = n > 0 ? n : 1;
     z.ncol = nx * ny;
     z.ntypes = ntypes;
+    z.S = super_size(C);
     z.nslot = (long long)n + (long long)z.ncol * (C - 1);
     z.nclu = z.nslot / C + 1;
-    // j-clusters per i-cluster (half list): cluster-pair bounding boxes within
-    // rlist, estimated as the rounded box of side 2 w dilated by rlist
+    z.nsc = z.nclu / z.S + z.ncol + 1;
     const double V = (double)L[0] * L[1] * L[2];
     const double wx = (double)L[0] / nx, wy = (double)L[1] / ny;
     const double rho = n > 0 ? n / V : 1.0;
     const double hz = C / (rho * wx * wy);
-    const double a = 2 * wx, b = 2 * wy, c = 2 * hz, r = rlist;
+    const double a = 2 * wx, b = 2 * wy, c = (z.S + 1) * hz, r = rlist;
     const double vm = a * b * c + 2 * r * (a * b + b * c + c * a) + M_PI * r * r * (a + b + c) +
                       4.0 / 3.0 * M_PI * r * r * r;
     const double rho_c = (double)z.nclu / V;
-    double per = 0.5 * rho_c * vm + 1.0;
+    double per = 0.5 * rho_c * vm + z.S;
     const double maxper = 0.5 * 27.0 * (double)z.nclu + 1.0;
     if (per > maxper) per = maxper;
-    z.jent = (long long)std::ceil(factor * per * (double)z.nclu) + 1024;
-    z.ient = z.nclu * 27 + z.jent / kJChunk + 1024;
+    z.jent = (long long)std::ceil(factor * per * (double)z.nsc) + 1024;
+    z.ient = z.nsc * 27 + z.jent / kJChunk + 1024;
     return z;
 }
 
@@ -269,6 +275,7 @@ nb_status nb_workspace_query(nb_ctx* c, int n, const double* box, double rlist_m
     c->ncol_cap = z.ncol;
     c->nslot_cap = z.nslot;
     c->nclu_cap = z.nclu;
+    c->nsc_cap = z.nsc;
     c->ient_cap = z.ient;
     c->jent_cap = z.jent;
     c->ntypes_cap = kMaxTypes;
@@ -286,6 +293,8 @@ nb_status nb_set_workspace(nb_ctx* c, void* ws, size_t bytes) {
     z.ntypes = c->ntypes_cap;
     z.nslot = c->nslot_cap;
     z.nclu = c->nclu_cap;
+    z.nsc = c->nsc_cap;
+    z.S = super_size(c->C);
     z.ient = c->ient_cap;
     z.jent = c->jent_cap;
     const size_t need = carve(z, nullptr, nullptr);
@@ -360,6 +369,7 @@ nb_status nb_pairlist_build(nb_ctx* c, float rlist, float rbb, const int* excl_o
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(c, cudaSetDevice(c->device));
     NB_CUDA(c, cudaMemsetAsync(c->ws.st, 0, 2 * sizeof(unsigned long long), s));
+    NB_CUDA(c, cudaMemsetAsync(&c->ws.st->n_keys, 0, sizeof(unsigned long long), s));
     const int sp = span_begin(c, NB_KERNEL_SEARCH, s);
     cudaError_t e = launch_search(c->ws, c->geom, c->C, c->nclu_cap, rlist, rbb, excl_off, excl_idx,
                                   c->ient_cap, c->jent_cap, c->n, c->n_sm, s);
@@ -479,6 +489,10 @@ nb_status nb_check(nb_ctx* c, nb_stream stream, nb_info* info) {
         info->ient_capacity = c->ient_cap;
         info->jent_capacity = c->jent_cap;
         info->n_pairs_rc = (int64_t)c->last.n_pairs_rc;
+        info->n_superclusters = c->have_grid ? c->last.nsc : 0;
+        info->n_cluster_pairs = c->have_list ? (int64_t)c->last.n_keys : 0;
+        info->n_cluster_pairs_pruned = c->have_pruned ? (int64_t)c->last.n_keys_pruned : -1;
+        info->super_size = super_size(c->C);
         info->n_launches = c->n_launches;
         info->flags = flags;
     }
@@ -515,7 +529,7 @@ nb_status nb_profile_read(nb_ctx* c, int* kinds, float* ms, int max, int* count)
 }
 
 nb_status nb_get_grid(nb_ctx* c, int* atom_of_slot, int* slot_of_atom, int* col_clu_start, float* xyzq,
-                      int* type_slot, float* bb, int* col_of_atom, nb_stream stream) {
+                      int* type_slot, float* bb, int* col_of_atom, int* sc_info, nb_stream stream) {
     if (!c) return NB_ERR_ARG;
     if (!c->have_grid || !c->last_valid) return fail(c, NB_ERR_STATE, "need a grid and nb_check");
     cudaStream_t s = (cudaStream_t)stream;
@@ -532,6 +546,7 @@ nb_status nb_get_grid(nb_ctx* c, int* atom_of_slot, int* slot_of_atom, int* col_
     NB_CUDA(c, cp(xyzq, c->ws.xyzq, sizeof(float4) * ns));
     NB_CUDA(c, cp(type_slot, c->ws.type_slot, sizeof(int) * ns));
     NB_CUDA(c, cp(col_of_atom, c->ws.col_of_atom, sizeof(int) * c->n));
+    NB_CUDA(c, cp(sc_info, c->ws.sc_info, sizeof(int2) * (size_t)c->last.nsc));
     if (bb && nclu > 0) {
         // float4 pairs -> float [nclu][6]
         NB_CUDA(c, cudaMemcpy2DAsync(bb, 6 * sizeof(float), c->ws.bb, 8 * sizeof(float), 3 * sizeof(float),
@@ -555,7 +570,10 @@ nb_status nb_get_list(nb_ctx* c, int which, int* ient, int* cj, uint64_t* mask, 
     const unsigned long long* sm = which ? c->ws.mask_p : c->ws.mask;
     if (ient && ni) NB_CUDA(c, cudaMemcpyAsync(ient, si, sizeof(int4) * ni, cudaMemcpyDeviceToDevice, s));
     if (cj && nj) NB_CUDA(c, cudaMemcpyAsync(cj, sc, sizeof(int) * nj, cudaMemcpyDeviceToDevice, s));
-    if (mask && nj) NB_CUDA(c, cudaMemcpyAsync(mask, sm, sizeof(uint64_t) * nj, cudaMemcpyDeviceToDevice, s));
+    if (mask && nj)
+        for (int k = 0; k < super_size(c->C); ++k)
+            NB_CUDA(c, cudaMemcpyAsync(mask + (size_t)k * nj, sm + (size_t)k * c->ws.jstride, sizeof(uint64_t) * nj,
+                                       cudaMemcpyDeviceToDevice, s));
     return NB_OK;
 }
 

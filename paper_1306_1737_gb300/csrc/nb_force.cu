@@ -34,6 +34,8 @@ struct ForceArgs {
     const unsigned long long* mask;
     float4* fslot;
     Accum* acc;
+    const int2* sc_info;
+    long long jstride;
     ForceParams p;
 };
 
@@ -85,15 +87,11 @@ __device__ __forceinline__ float2 sel2(bool p, bool q, float2 v) {
     return make_float2(p ? v.x : 0.0f, q ? v.y : 0.0f);
 }
 
-// How a j-entry's pairs are counted: all-ones mask (no dummy, no
-// exclusion: every pair inside rc is a full interaction), general mask, or
-// the unshifted self-pair (only j > i counts).
-enum { kModeFull = 0, kModeMasked = 1, kModeDiag = 2 };
-
-// Two particle pairs of one lane.  lj0/lj1 = {-6 C6, 12 C12}; u: mask bit
-// (full interaction); inc: pair counted and inside rc.  Pairs that are not
-// counted are computed on whatever r2 they have and selected away.
-template <int ELEC, bool ENERGY, bool FIT, int MODE>
+// Two particle pairs of one lane (components x, y): lj0/lj1 = {-6 C6, 12 C12};
+// u: mask bit (full interaction); inc: pair counted and inside rc.  Pairs
+// that are not counted are computed on whatever r2 they have and selected
+// away (no NaN escapes the selects).
+template <int ELEC, bool ENERGY, bool FIT>
 __device__ __forceinline__ void pair2(const ForceParams& P, bool inc0, bool inc1, bool u0, bool u1,
                                       float2 r2, float2 qq, float2 lj0, float2 lj1, float2& fs,
                                       float& vlj, float& vc) {
@@ -101,18 +99,15 @@ __device__ __forceinline__ void pair2(const ForceParams& P, bool inc0, bool inc1
     const float2 rinv2 = mul2(rinv, rinv);
     const float2 rinv6 = mul2(mul2(rinv2, rinv2), rinv2);
     const float2 c6n = make_float2(lj0.x, lj1.x), c12 = make_float2(lj0.y, lj1.y);
-    float2 flj = mul2(mul2(fma2(c12, rinv6, c6n), rinv6), rinv2);
-    float2 rinv3e = mul2(rinv, rinv2);
-    if (MODE != kModeFull) {
-        flj = sel2(u0, u1, flj);
-        rinv3e = sel2(u0, u1, rinv3e);
-    }
+    const float2 flj = sel2(u0, u1, mul2(mul2(fma2(c12, rinv6, c6n), rinv6), rinv2));
+    const float2 rinv3e = sel2(u0, u1, mul2(rinv, rinv2));
     float2 fc;
     if (ELEC == NB_ELEC_RF) {
         fc = mul2(qq, add2(rinv3e, bc2(-P.two_k_rf)));
     } else if (FIT) {
         const float2 w = mul2(bc2(P.beta2), r2);
-        fc = mul2(qq, fma2(ewald_fit_g2(w), bc2(-P.beta3), rinv3e));
+        const float2 g = make_float2(ewald_fit_g(w.x), ewald_fit_g(w.y));
+        fc = mul2(qq, fma2(g, bc2(-P.beta3), rinv3e));
     } else {
         float rr[2] = {r2.x, r2.y}, ri[2] = {rinv.x, rinv.y}, re[2] = {rinv3e.x, rinv3e.y}, o[2];
 #pragma unroll
@@ -129,13 +124,14 @@ __device__ __forceinline__ void pair2(const ForceParams& P, bool inc0, bool inc1
         // V_LJ = (C12 r^-6 - C6) r^-6
         const float2 v6 = mul2(fma2(mul2(c12, bc2(1.0f / 12.0f)), rinv6, mul2(c6n, bc2(1.0f / 6.0f))), rinv6);
         const float2 vl = sel2(inc0 && u0, inc1 && u1, v6);
-        const float2 rinve = MODE == kModeFull ? rinv : sel2(u0, u1, rinv);
+        const float2 rinve = sel2(u0, u1, rinv);
         float2 v;
         if (ELEC == NB_ELEC_RF) {
             v = mul2(qq, fma2(bc2(P.k_rf), r2, add2(rinve, bc2(-P.c_rf))));
         } else if (FIT) {
             const float2 w = mul2(bc2(P.beta2), r2);
-            v = mul2(qq, fma2(ewald_fit_h2(w), bc2(-P.beta), rinve));
+            const float2 h = make_float2(ewald_fit_h(w.x), ewald_fit_h(w.y));
+            v = mul2(qq, fma2(h, bc2(-P.beta), rinve));
         } else {
             const float r0 = r2.x * rinv.x, r1 = r2.y * rinv.y;
             v = mul2(qq, make_float2((erfcf(P.beta * r0) - 1.0f) * rinv.x + rinve.x,
@@ -150,101 +146,168 @@ __device__ __forceinline__ void pair2(const ForceParams& P, bool inc0, bool inc1
 struct Lane8 {
     int j, ih;
     bool lower0, lower1;  // (ih, j) and (ih+4, j) on or below the diagonal
-    unsigned sel;         // bit of this lane's pairs within each 32-bit half of the mask
+    unsigned sel;         // bit of this lane's pairs within each 32-bit half of a mask
 };
 
-// The 2 x 32 pairs of one j-cluster.  Returns (uniformly) whether any pair
-// of the warp was inside rc; fj is this lane's share of the j-force.
-template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, int MODE>
-__device__ __forceinline__ bool jcluster8(const ForceParams& P, const float2* s_lj, const Lane8& L,
-                                          float4 xj, int tj, unsigned mlo, unsigned mhi, float2 xh,
-                                          float2 yh, float2 zh, float2 xl, float2 yl, float2 zl, float2 qi,
-                                          int ti0, int ti1, float2& fx, float2& fy, float2& fz,
-                                          float& e_lj, float& e_c, unsigned& n_inc, float& fjx,
-                                          float& fjy, float& fjz) {
-    float d0x = xh.x - xj.x, d1x = xh.y - xj.x;
-    float d0y = yh.x - xj.y, d1y = yh.y - xj.y;
-    float d0z = zh.x - xj.z, d1z = zh.y - xj.z;
+constexpr int kSuper8 = super_size(8);
+
+// Per-warp shared staging of the force kernel.
+struct WarpSmem {
+    float4 xi[kSuper8 * 8];   // shifted i coordinates (hi part) and f*q
+    float4 xl[kSuper8 * 8];   // low part of the shift
+    int row[kSuper8 * 8];     // LJ row offset (type * ntypes)
+    int w[32];                // j-entry words of the current chunk
+    unsigned long long m[kSuper8][32];  // their masks per i-cluster
+};
+
+// Force/energy of the lane's two pairs (x and y components) given squared
+// distances; scalar arithmetic wherever a parameter enters (constant
+// operands need no registers), packed only where both operands are pairs.
+// FULL: every pair inside rc is a full interaction (all-ones mask, no diagonal).
+template <int ELEC, bool ENERGY, bool FIT, bool FULL>
+__device__ __forceinline__ float2 pair_force2(const ForceParams& P, float2 r2, bool inc0, bool inc1,
+                                              bool u0, bool u1, float qq0, float qq1, float2 lj0,
+                                              float2 lj1, float& e_lj, float& e_c) {
+    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 rinv2 = mul2(rinv, rinv);
+    float2 rinv3 = mul2(rinv, rinv2);
+    const float2 rinv6 = mul2(rinv3, rinv3);
+    // LJ (12 C12 r^-6 - 6 C6) r^-8 with lj = {-6 C6, 12 C12}
+    float flj0 = fmaf(lj0.y, rinv6.x, lj0.x) * rinv6.x * rinv2.x;
+    float flj1 = fmaf(lj1.y, rinv6.y, lj1.x) * rinv6.y * rinv2.y;
+    if (!FULL) {
+        flj0 = u0 ? flj0 : 0.0f;
+        flj1 = u1 ? flj1 : 0.0f;
+        rinv3 = sel2(u0, u1, rinv3);
+    }
+    float fc0, fc1;
+    if (ELEC == NB_ELEC_RF) {
+        fc0 = qq0 * (rinv3.x - P.two_k_rf);
+        fc1 = qq1 * (rinv3.y - P.two_k_rf);
+    } else if (FIT) {
+        fc0 = qq0 * fmaf(-P.beta3, ewald_fit_g(P.beta2 * r2.x), rinv3.x);
+        fc1 = qq1 * fmaf(-P.beta3, ewald_fit_g(P.beta2 * r2.y), rinv3.y);
+    } else {
+        const float r0 = r2.x * rinv.x, r1 = r2.y * rinv.y;
+        const float b0 = P.beta * r0, b1 = P.beta * r1;
+        fc0 = qq0 * (rinv3.x + (erfcf(b0) - 1.0f + P.two_beta_sqrtpi * r0 * __expf(-b0 * b0)) * rinv2.x * rinv.x);
+        fc1 = qq1 * (rinv3.y + (erfcf(b1) - 1.0f + P.two_beta_sqrtpi * r1 * __expf(-b1 * b1)) * rinv2.y * rinv.y);
+    }
+    if (ENERGY) {
+        // V_LJ = (C12 r^-6 - C6) r^-6;  V_C = qq (e/r - correction)
+        float vl0 = fmaf(lj0.y * (1.0f / 12.0f), rinv6.x, lj0.x * (1.0f / 6.0f)) * rinv6.x;
+        float vl1 = fmaf(lj1.y * (1.0f / 12.0f), rinv6.y, lj1.x * (1.0f / 6.0f)) * rinv6.y;
+        const float re0 = FULL || u0 ? rinv.x : 0.0f, re1 = FULL || u1 ? rinv.y : 0.0f;
+        float vc0, vc1;
+        if (ELEC == NB_ELEC_RF) {
+            vc0 = qq0 * (re0 + fmaf(P.k_rf, r2.x, -P.c_rf));
+            vc1 = qq1 * (re1 + fmaf(P.k_rf, r2.y, -P.c_rf));
+        } else if (FIT) {
+            vc0 = qq0 * fmaf(-P.beta, ewald_fit_h(P.beta2 * r2.x), re0);
+            vc1 = qq1 * fmaf(-P.beta, ewald_fit_h(P.beta2 * r2.y), re1);
+        } else {
+            vc0 = qq0 * ((erfcf(P.beta * r2.x * rinv.x) - 1.0f) * rinv.x + re0);
+            vc1 = qq1 * ((erfcf(P.beta * r2.y * rinv.y) - 1.0f) * rinv.y + re1);
+        }
+        e_lj += (inc0 && (FULL || u0) ? vl0 : 0.0f) + (inc1 && (FULL || u1) ? vl1 : 0.0f);
+        e_c += (inc0 ? vc0 : 0.0f) + (inc1 ? vc1 : 0.0f);
+    }
+    return make_float2(inc0 ? flj0 + fc0 : 0.0f, inc1 ? flj1 + fc1 : 0.0f);
+}
+
+// The pairs of i-cluster k (of the super-cluster) with one j-cluster.
+// Returns (warp-uniformly) whether any pair was inside rc.
+template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, bool FULL>
+__device__ __forceinline__ bool icluster8(const ForceParams& P, const float2* s_lj, const WarpSmem& W,
+                                          const Lane8& L, int k, bool diag, unsigned long long m,
+                                          float4 xj, int tj, float2& fx, float2& fy, float2& fz,
+                                          float& fjx, float& fjy, float& fjz, float& e_lj, float& e_c,
+                                          unsigned& n_inc) {
+    const float4 a0 = W.xi[k * 8 + L.ih], a1 = W.xi[k * 8 + L.ih + 4];
+    float d0x = a0.x - xj.x, d1x = a1.x - xj.x;
+    float d0y = a0.y - xj.y, d1y = a1.y - xj.y;
+    float d0z = a0.z - xj.z, d1z = a1.z - xj.z;
     if (SHIFTED) {
-        d0x += xl.x; d1x += xl.y;
-        d0y += yl.x; d1y += yl.y;
-        d0z += zl.x; d1z += zl.y;
+        const float4 b0 = W.xl[k * 8 + L.ih], b1 = W.xl[k * 8 + L.ih + 4];
+        d0x += b0.x; d1x += b1.x;
+        d0y += b0.y; d1y += b1.y;
+        d0z += b0.z; d1z += b1.z;
     }
     const float2 dx = make_float2(d0x, d1x), dy = make_float2(d0y, d1y), dz = make_float2(d0z, d1z);
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     bool u0 = true, u1 = true;
-    if (MODE != kModeFull) {
-        u0 = (mlo & L.sel) != 0u;
-        u1 = (mhi & L.sel) != 0u;
+    if (!FULL) {
+        u0 = ((unsigned)m & L.sel) != 0u;
+        u1 = ((unsigned)(m >> 32) & L.sel) != 0u;
     }
     bool inc0 = r2.x < P.rc2;
     bool inc1 = r2.y < P.rc2;
-    if (MODE == kModeDiag) {
+    if (!FULL && diag) {
         inc0 = inc0 && (u0 || !L.lower0);
         inc1 = inc1 && (u1 || !L.lower1);
     }
     if (!__any_sync(0xffffffffu, inc0 || inc1)) return false;
-    const float2 lj0 = s_lj[ti0 + tj], lj1 = s_lj[ti1 + tj];
-    float2 fs;
-    pair2<ELEC, ENERGY, FIT, MODE>(P, inc0, inc1, u0, u1, r2, make_float2(qi.x * xj.w, qi.y * xj.w), lj0,
-                                   lj1, fs, e_lj, e_c);
+    const float2 lj0 = s_lj[W.row[k * 8 + L.ih] + tj], lj1 = s_lj[W.row[k * 8 + L.ih + 4] + tj];
+    const float2 fs = pair_force2<ELEC, ENERGY, FIT, FULL>(P, r2, inc0, inc1, u0, u1, a0.w * xj.w,
+                                                           a1.w * xj.w, lj0, lj1, e_lj, e_c);
     if (ENERGY) n_inc += (unsigned)inc0 + (unsigned)inc1;
     const float2 px = mul2(fs, dx), py = mul2(fs, dy), pz = mul2(fs, dz);
     fx = add2(fx, px);
     fy = add2(fy, py);
     fz = add2(fz, pz);
-    fjx = -(px.x + px.y);
-    fjy = -(py.x + py.y);
-    fjz = -(pz.x + pz.y);
+    fjx -= px.x + px.y;
+    fjy -= py.x + py.y;
+    fjz -= pz.x + pz.y;
     return true;
 }
 
-// All j-entries [jb, je) (at most 32) of one i-entry.
+// All j-entries [jb, je) (at most 32) of one super-cluster i-entry.
 template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED>
-__device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s_lj, const Lane8& L,
-                                             int ci, bool center, int jb, int je, float2 xh, float2 yh,
-                                             float2 zh, float2 xl, float2 yl, float2 zl, float2 qi,
-                                             int ti0, int ti1, float2& fx, float2& fy, float2& fz,
-                                             float& e_lj, float& e_c, unsigned& n_inc) {
+__device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s_lj, WarpSmem& W,
+                                             const Lane8& L, int g0, bool center, int jb, int je,
+                                             float2 (&fx)[kSuper8], float2 (&fy)[kSuper8],
+                                             float2 (&fz)[kSuper8], float& e_lj, float& e_c,
+                                             unsigned& n_inc) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int nt = je - jb;
-    int my_cj = 0;
-    unsigned long long my_m = 0;
     if (lane < nt) {
-        my_cj = A.cj[jb + lane];
-        my_m = A.mask[jb + lane];
+        W.w[lane] = A.cj[jb + lane];
+#pragma unroll
+        for (int k = 0; k < kSuper8; ++k) W.m[k][lane] = A.mask[k * A.jstride + jb + lane];
     }
+    __syncwarp();
     const float4* xyzq_j = A.xyzq + L.j;
     const int* type_j = A.type_slot + L.j;
-    int cjn = __shfl_sync(full, my_cj, 0);
+    int cjn = W.w[0] & kCjMask;
     float4 xjn = xyzq_j[cjn * 8];
     int tjn = type_j[cjn * 8];
     for (int t = 0; t < nt; ++t) {
-        const int cjt = cjn;
+        const unsigned w = (unsigned)W.w[t];
+        const int cjt = (int)(w & kCjMask);
+        const unsigned bits = w >> kSuperShift;
         const float4 xj = xjn;
         const int tj = tjn;
-        if (t + 1 < nt) {
-            cjn = __shfl_sync(full, my_cj, t + 1);
-            xjn = xyzq_j[cjn * 8];
-            tjn = type_j[cjn * 8];
+        cjn = W.w[min(t + 1, nt - 1)] & kCjMask;
+        xjn = xyzq_j[cjn * 8];
+        tjn = type_j[cjn * 8];
+        float fjx = 0.f, fjy = 0.f, fjz = 0.f;
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < kSuper8; ++k) {
+            if ((bits >> k) & 1u) {
+                const bool diag = center && (cjt == g0 + k);
+                const unsigned long long m = W.m[k][t];
+                if (!diag && m == ~0ull)
+                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true>(A.p, s_lj, W, L, k, false, m, xj, tj,
+                                                                       fx[k], fy[k], fz[k], fjx, fjy, fjz,
+                                                                       e_lj, e_c, n_inc);
+                else
+                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, false>(A.p, s_lj, W, L, k, diag, m, xj, tj,
+                                                                        fx[k], fy[k], fz[k], fjx, fjy, fjz,
+                                                                        e_lj, e_c, n_inc);
+            }
         }
-        const unsigned mlo = __shfl_sync(full, (unsigned)my_m, t);
-        const unsigned mhi = __shfl_sync(full, (unsigned)(my_m >> 32), t);
-        float fjx, fjy, fjz;
-        bool any;
-        if (center && cjt == ci)
-            any = jcluster8<ELEC, ENERGY, FIT, SHIFTED, kModeDiag>(A.p, s_lj, L, xj, tj, mlo, mhi, xh, yh, zh, xl,
-                                                                  yl, zl, qi, ti0, ti1, fx, fy, fz, e_lj, e_c,
-                                                                  n_inc, fjx, fjy, fjz);
-        else if ((mlo & mhi) == full)
-            any = jcluster8<ELEC, ENERGY, FIT, SHIFTED, kModeFull>(A.p, s_lj, L, xj, tj, mlo, mhi, xh, yh, zh, xl,
-                                                                  yl, zl, qi, ti0, ti1, fx, fy, fz, e_lj, e_c,
-                                                                  n_inc, fjx, fjy, fjz);
-        else
-            any = jcluster8<ELEC, ENERGY, FIT, SHIFTED, kModeMasked>(A.p, s_lj, L, xj, tj, mlo, mhi, xh, yh, zh,
-                                                                    xl, yl, zl, qi, ti0, ti1, fx, fy, fz, e_lj,
-                                                                    e_c, n_inc, fjx, fjy, fjz);
         if (!any) continue;
         fjx += __shfl_xor_sync(full, fjx, 8);
         fjy += __shfl_xor_sync(full, fjy, 8);
@@ -254,11 +317,13 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
         fjz += __shfl_xor_sync(full, fjz, 16);
         if (L.ih == 0) atomicAdd(&A.fslot[cjt * 8 + L.j], make_float4(fjx, fjy, fjz, 0.0f));
     }
+    __syncwarp();
 }
 
 template <int ELEC, bool ENERGY, bool FIT>
-__global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 6 : 7) k_force8(ForceArgs A) {
+__global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 5 : 6) k_force8(ForceArgs A) {
     extern __shared__ float2 s_lj[];
+    __shared__ WarpSmem s_w[kForceWarps];
     const unsigned full = 0xffffffffu;
     const int nt2 = A.p.ntypes * A.p.ntypes;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
@@ -267,6 +332,7 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 6 : 7) k_force8(For
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    WarpSmem& W = s_w[threadIdx.x >> 5];
     Lane8 L;
     L.j = lane & 7;
     L.ih = lane >> 3;
@@ -279,62 +345,70 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 6 : 7) k_force8(For
     for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < nient;
          e += (long long)gridDim.x * kForceWarps) {
         const int4 ie = A.ient[e];
-        const int ci = ie.x, s = ie.y, jb = ie.z, je = ie.w;
+        const int q = ie.x, s = ie.y, jb = ie.z, je = ie.w;
         if (jb >= je) continue;
+        const int2 info = A.sc_info[q];
+        const int g0 = info.x, n = info.y;
         const float sh[3] = {(float)(s / 9 - 1) * A.p.L[0], (float)((s / 3) % 3 - 1) * A.p.L[1],
                              (float)(s % 3 - 1) * A.p.L[2]};
-        const float4 x0 = A.xyzq[ci * 8 + L.ih];
-        const float4 x1 = A.xyzq[ci * 8 + L.ih + 4];
-        float x0h[3], x0l[3], x1h[3], x1l[3];
-        two_sum(x0.x, sh[0], x0h[0], x0l[0]);
-        two_sum(x0.y, sh[1], x0h[1], x0l[1]);
-        two_sum(x0.z, sh[2], x0h[2], x0l[2]);
-        two_sum(x1.x, sh[0], x1h[0], x1l[0]);
-        two_sum(x1.y, sh[1], x1h[1], x1l[1]);
-        two_sum(x1.z, sh[2], x1h[2], x1l[2]);
-        const float2 xh = make_float2(x0h[0], x1h[0]), yh = make_float2(x0h[1], x1h[1]),
-                     zh = make_float2(x0h[2], x1h[2]);
-        const float2 xl = make_float2(x0l[0], x1l[0]), yl = make_float2(x0l[1], x1l[1]),
-                     zl = make_float2(x0l[2], x1l[2]);
-        const float2 qi = make_float2(x0.w * A.p.fcoul, x1.w * A.p.fcoul);
-        const int ti0 = A.type_slot[ci * 8 + L.ih] * A.p.ntypes;
-        const int ti1 = A.type_slot[ci * 8 + L.ih + 4] * A.p.ntypes;
+        // stage the super-cluster's i particles: shifted coordinates as hi + lo
+        if (lane < n * 8) {
+            const float4 x = A.xyzq[g0 * 8 + lane];
+            float4 h, l;
+            two_sum(x.x, sh[0], h.x, l.x);
+            two_sum(x.y, sh[1], h.y, l.y);
+            two_sum(x.z, sh[2], h.z, l.z);
+            h.w = x.w * A.p.fcoul;
+            l.w = 0.0f;
+            W.xi[lane] = h;
+            W.xl[lane] = l;
+            W.row[lane] = A.type_slot[g0 * 8 + lane] * A.p.ntypes;
+        }
+        __syncwarp();
         const bool center = (s == kShiftCenter);
-        float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx;
+        float2 fx[kSuper8], fy[kSuper8], fz[kSuper8];
+#pragma unroll
+        for (int k = 0; k < kSuper8; ++k) fx[k] = fy[k] = fz[k] = make_float2(0.f, 0.f);
         for (int base = jb; base < je; base += 32) {
             const int bend = min(je, base + 32);
             if (center)
-                force_entry8<ELEC, ENERGY, FIT, false>(A, s_lj, L, ci, center, base, bend, xh, yh, zh, xl, yl,
-                                                       zl, qi, ti0, ti1, fx, fy, fz, e_lj, e_c, n_inc);
+                force_entry8<ELEC, ENERGY, FIT, false>(A, s_lj, W, L, g0, true, base, bend, fx, fy, fz, e_lj,
+                                                       e_c, n_inc);
             else
-                force_entry8<ELEC, ENERGY, FIT, true>(A, s_lj, L, ci, center, base, bend, xh, yh, zh, xl, yl,
-                                                      zl, qi, ti0, ti1, fx, fy, fz, e_lj, e_c, n_inc);
+                force_entry8<ELEC, ENERGY, FIT, true>(A, s_lj, W, L, g0, false, base, bend, fx, fy, fz, e_lj,
+                                                      e_c, n_inc);
         }
-        // i-forces: sum over the 8 lanes of each i row
-        float f0[3] = {fx.x, fy.x, fz.x}, f1[3] = {fx.y, fy.y, fz.y};
+        // i-forces: per i-cluster, sum over the 8 lanes of each i row
+        float tsum[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
+        for (int k = 0; k < kSuper8; ++k) {
+            if (k >= n) break;
+            float f0[3] = {fx[k].x, fy[k].x, fz[k].x}, f1[3] = {fx[k].y, fy[k].y, fz[k].y};
 #pragma unroll
-            for (int o = 1; o < 8; o <<= 1) {
-                f0[d] += __shfl_xor_sync(full, f0[d], o);
-                f1[d] += __shfl_xor_sync(full, f1[d], o);
+            for (int d = 0; d < 3; ++d) {
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) {
+                    f0[d] += __shfl_xor_sync(full, f0[d], o);
+                    f1[d] += __shfl_xor_sync(full, f1[d], o);
+                }
+                tsum[d] += f0[d] + f1[d];
             }
-        }
-        if (L.j == 0) {
-            atomicAdd(&A.fslot[ci * 8 + L.ih], make_float4(f0[0], f0[1], f0[2], 0.0f));
-            atomicAdd(&A.fslot[ci * 8 + L.ih + 4], make_float4(f1[0], f1[1], f1[2], 0.0f));
+            if (L.j == 0) {
+                atomicAdd(&A.fslot[(g0 + k) * 8 + L.ih], make_float4(f0[0], f0[1], f0[2], 0.0f));
+                atomicAdd(&A.fslot[(g0 + k) * 8 + L.ih + 4], make_float4(f1[0], f1[1], f1[2], 0.0f));
+            }
         }
         if (ENERGY && !center) {
             // i-side force of this shifted entry, for the virial
-            float t[3] = {f0[0] + f1[0], f0[1] + f1[1], f0[2] + f1[2]};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                t[d] += __shfl_xor_sync(full, t[d], 8);
-                t[d] += __shfl_xor_sync(full, t[d], 16);
+                tsum[d] += __shfl_xor_sync(full, tsum[d], 8);
+                tsum[d] += __shfl_xor_sync(full, tsum[d], 16);
             }
             if (lane == 0)
-                for (int d = 0; d < 3; ++d) atomicAdd(&A.acc->fshift[s][d], (double)t[d]);
+                for (int d = 0; d < 3; ++d) atomicAdd(&A.acc->fshift[s][d], (double)tsum[d]);
         }
+        __syncwarp();
     }
     if (ENERGY) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -350,8 +424,9 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 6 : 7) k_force8(For
     }
 }
 
-// Generic C = 4 kernel: one warp per i-entry, lanes 0..15 hold the 4 x 4
-// pairs of one j-cluster and lanes 16..31 those of the next.
+// Generic C = 4 kernel (super-clusters of one cluster): one warp per
+// i-entry, lanes 0..15 hold the 4 x 4 pairs of one j-cluster and lanes
+// 16..31 those of the next.
 template <int ELEC, bool ENERGY, bool FIT>
 __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
     extern __shared__ float2 s_lj[];
@@ -370,7 +445,7 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
     for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < nient;
          e += (long long)gridDim.x * kForceWarps) {
         const int4 ie = A.ient[e];
-        const int ci = ie.x, s = ie.y, jb = ie.z, je = ie.w;
+        const int ci = A.sc_info[ie.x].x, s = ie.y, jb = ie.z, je = ie.w;
         if (jb >= je) continue;
         const float sh[3] = {(float)(s / 9 - 1) * A.p.L[0], (float)((s / 3) % 3 - 1) * A.p.L[1],
                              (float)(s % 3 - 1) * A.p.L[2]};
@@ -386,7 +461,7 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
         for (int k = jb; k < je; k += 2) {
             const int kk = k + half;
             const bool live = kk < je;
-            const int cjt = live ? A.cj[kk] : ci;
+            const int cjt = live ? (A.cj[kk] & kCjMask) : ci;
             const unsigned long long m = live ? A.mask[kk] : 0ull;
             const float4 xj = A.xyzq[cjt * 4 + j];
             const int tj = A.type_slot[cjt * 4 + j];
@@ -479,6 +554,8 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
     A.mask = p.use_pruned ? ws.mask_p : ws.mask;
     A.fslot = ws.fslot;
     A.acc = ws.acc;
+    A.sc_info = ws.sc_info;
+    A.jstride = ws.jstride;
     A.p = p;
     cudaError_t e = cudaMemsetAsync(ws.acc, 0, sizeof(Accum), s);
     if (e != cudaSuccess) return e;

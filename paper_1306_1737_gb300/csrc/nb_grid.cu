@@ -50,49 +50,61 @@ __global__ void k_wrap_col(int n, const float* __restrict__ xyz, const float* __
 // column and the cluster count.
 __global__ void k_scan_cols(int ncol, int C, const int* __restrict__ col_count,
                             int* __restrict__ col_atom_start, int* __restrict__ col_clu_start,
-                            DevState* st) {
+                            int* __restrict__ col_sc_start, DevState* st) {
+    const int S = super_size(C);
     __shared__ int s_a[1024];
     __shared__ int s_c[1024];
+    __shared__ int s_g[1024];
     __shared__ int s_max;
     const int t = threadIdx.x;
     if (t == 0) s_max = 0;
     __syncthreads();
     const int per = (ncol + blockDim.x - 1) / blockDim.x;
     const int c0 = min(ncol, t * per), c1 = min(ncol, c0 + per);
-    int sa = 0, sc = 0, mx = 0;
+    int sa = 0, sc = 0, sg = 0, mx = 0;
     for (int c = c0; c < c1; ++c) {
         const int k = col_count[c];
+        const int nc = (k + C - 1) / C;
         sa += k;
-        sc += (k + C - 1) / C;
+        sc += nc;
+        sg += (nc + S - 1) / S;
         mx = max(mx, k);
     }
     s_a[t] = sa;
     s_c[t] = sc;
+    s_g[t] = sg;
     atomicMax(&s_max, mx);
     __syncthreads();
     // Hillis-Steele inclusive scan over the per-thread totals
     for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        int va = 0, vc = 0;
+        int va = 0, vc = 0, vg = 0;
         if (t >= off) {
             va = s_a[t - off];
             vc = s_c[t - off];
+            vg = s_g[t - off];
         }
         __syncthreads();
         s_a[t] += va;
         s_c[t] += vc;
+        s_g[t] += vg;
         __syncthreads();
     }
-    int ba = s_a[t] - sa, bc = s_c[t] - sc;
+    int ba = s_a[t] - sa, bc = s_c[t] - sc, bg = s_g[t] - sg;
     for (int c = c0; c < c1; ++c) {
         const int k = col_count[c];
+        const int nc = (k + C - 1) / C;
         col_atom_start[c] = ba;
         col_clu_start[c] = bc;
+        col_sc_start[c] = bg;
         ba += k;
-        bc += (k + C - 1) / C;
+        bc += nc;
+        bg += (nc + S - 1) / S;
     }
     if (t == blockDim.x - 1) {
         col_clu_start[ncol] = s_c[t];
+        col_sc_start[ncol] = s_g[t];
         st->nclu = s_c[t];
+        st->nsc = s_g[t];
     }
     if (t == 0) st->max_col = s_max;
 }
@@ -112,6 +124,7 @@ __global__ void k_scatter(int n, const int* __restrict__ col_of_atom,
 __global__ void __launch_bounds__(512) k_col_sort(
     int ncol, int C, int ntypes, float dummy_g, const int* __restrict__ col_count,
     const int* __restrict__ col_atom_start, const int* __restrict__ col_clu_start,
+    const int* __restrict__ col_sc_start, int2* __restrict__ sc_info,
     const unsigned long long* __restrict__ keys, const float4* __restrict__ xw,
     const int* __restrict__ type, float4* __restrict__ xyzq, int* __restrict__ atom_of_slot,
     int* __restrict__ slot_of_atom, int* __restrict__ type_slot, float4* __restrict__ bb,
@@ -122,6 +135,15 @@ __global__ void __launch_bounds__(512) k_col_sort(
     const int cnt = col_count[c];
     const int base = col_atom_start[c];
     const int g0 = col_clu_start[c], g1 = col_clu_start[c + 1];
+    {
+        // super-clusters: runs of up to S consecutive clusters of this column
+        const int S = super_size(C);
+        const int q0 = col_sc_start[c], q1 = col_sc_start[c + 1];
+        for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+            const int first = g0 + (q - q0) * S;
+            sc_info[q] = make_int2(first, min(S, g1 - first));
+        }
+    }
     if (cnt > kMaxColumn) {
         if (threadIdx.x == 0) set_flag(st, NB_ERR_CAPACITY);
         return;
@@ -199,7 +221,8 @@ cudaError_t launch_grid(const Workspace& ws, const GridGeom& g, int n, int C, in
                                                    g.inv_y, g.nx, g.ny, ws.xw, ws.woff,
                                                    ws.col_of_atom, ws.rank_in_col, ws.col_count, ws.st);
     }
-    k_scan_cols<<<1, 1024, 0, s>>>(ncol, C, ws.col_count, ws.col_atom_start, ws.col_clu_start, ws.st);
+    k_scan_cols<<<1, 1024, 0, s>>>(ncol, C, ws.col_count, ws.col_atom_start, ws.col_clu_start,
+                                   ws.col_sc_start, ws.st);
     if (n > 0) {
         k_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, ws.col_of_atom, ws.rank_in_col,
                                                   ws.col_atom_start, ws.xw, ws.keys);
@@ -212,7 +235,8 @@ cudaError_t launch_grid(const Workspace& ws, const GridGeom& g, int n, int C, in
         attr_set = true;
     }
     k_col_sort<<<ncol, 512, smem, s>>>(ncol, C, ntypes, g.dummy_g, ws.col_count, ws.col_atom_start,
-                                       ws.col_clu_start, ws.keys, ws.xw, ws.type, ws.xyzq,
+                                       ws.col_clu_start, ws.col_sc_start, ws.sc_info, ws.keys, ws.xw,
+                                       ws.type, ws.xyzq,
                                        ws.atom_of_slot, ws.slot_of_atom, ws.type_slot, ws.bb, ws.fslot,
                                        ws.st);
     return cudaGetLastError();

@@ -19,6 +19,13 @@ constexpr int kMaxColumn = 8192;       // particles per grid column sorted on-ch
 constexpr int kShiftCenter = 13;       // shift index of (0, 0, 0)
 constexpr int kJChunk = 32;            // j-entries per i-entry at most (load balance)
 constexpr int kMaxExclPerCluster = 256;
+// Super-clusters (Sec. 3.1, Fig. 6: several i-clusters share one j-list):
+// up to kSuper consecutive clusters of one grid column.  A j-entry's word
+// holds the j-cluster index in its low kSuperShift bits and one interaction
+// bit per i-cluster of the super-cluster above them.
+constexpr int kSuperShift = 27;
+constexpr int kCjMask = (1 << kSuperShift) - 1;
+__host__ __device__ constexpr int super_size(int C) { return C == 8 ? 2 : 1; }
 
 // Device-resident state: counters written by kernels, read back by nb_check.
 struct DevState {
@@ -28,8 +35,10 @@ struct DevState {
     int nclu;                           // clusters of the current grid
     unsigned int flags;                 // 1 << nb_status_code
     int max_col;                        // largest column seen by the grid
-    int pad;
+    int nsc;                            // super-clusters of the current grid
     unsigned long long n_pairs_rc;      // pairs inside rc in the last energy evaluation
+    unsigned long long n_keys;          // cluster pairs (i-cluster, j-cluster, shift) in the outer list
+    unsigned long long n_keys_pruned;   // cluster pairs kept by the last prune
 };
 
 // FP64 accumulators of one force evaluation.
@@ -55,6 +64,8 @@ struct Workspace {
     int* col_count;
     int* col_atom_start;
     int* col_clu_start;  // [ncol + 1]
+    int* col_sc_start;   // [ncol + 1] first super-cluster of each column
+    int2* sc_info;       // per super-cluster {first cluster, number of clusters}
     // sort keys (column order)
     unsigned long long* keys;
     // per slot
@@ -64,13 +75,15 @@ struct Workspace {
     float4* fslot;
     // per cluster
     float4* bb;          // [2 * nclu]
-    // lists
+    // lists: i-entry {super-cluster, shift, j_begin, j_end}; j-entry word
+    // = cj | (interaction bits << kSuperShift); masks [S][jent capacity]
     int4* ient;
     int* cj;
     unsigned long long* mask;
     int4* ient_p;
     int* cj_p;
     unsigned long long* mask_p;
+    long long jstride;   // j-entry capacity: stride between the S mask arrays
     // LJ table {C6, C12} [ntypes][ntypes]
     float2* c6c12;
 };

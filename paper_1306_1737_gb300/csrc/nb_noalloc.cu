@@ -36,7 +36,9 @@ constexpr size_t kOffSlotOfAtom = align256(kOffRank + sizeof(int) * kNoallocMaxA
 constexpr size_t kOffKeys = align256(kOffSlotOfAtom + sizeof(int) * kNoallocMaxAtoms);
 constexpr size_t kOffColCount = align256(kOffKeys + sizeof(unsigned long long) * kNoallocMaxAtoms);
 constexpr size_t kOffColAtomStart = align256(kOffColCount + sizeof(int) * kNoallocMaxColumns);
-constexpr size_t kOffFslot = align256(kOffColAtomStart + sizeof(int) * kNoallocMaxColumns);
+constexpr size_t kOffColScStart = align256(kOffColAtomStart + sizeof(int) * kNoallocMaxColumns);
+constexpr size_t kOffScInfo = align256(kOffColScStart + sizeof(int) * (kNoallocMaxColumns + 1));
+constexpr size_t kOffFslot = align256(kOffScInfo + sizeof(int2) * (kNoallocMaxSlots / 4 + kNoallocMaxColumns));
 constexpr size_t kNoallocScratchBytes = align256(kOffFslot + sizeof(float4) * kNoallocMaxSlots);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
@@ -119,6 +121,8 @@ extern "C" nb_status nb_grid_put_noalloc(int n, const float* xyz, const float* q
     ws.col_count = (int*)(base + kOffColCount);
     ws.col_atom_start = (int*)(base + kOffColAtomStart);
     ws.fslot = (float4*)(base + kOffFslot);
+    ws.col_sc_start = (int*)(base + kOffColScStart);
+    ws.sc_info = (int2*)(base + kOffScInfo);
     ws.q = const_cast<float*>(q);
     ws.type = const_cast<int*>(type);
     ws.col_clu_start = col_clu_start;

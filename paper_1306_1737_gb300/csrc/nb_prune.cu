@@ -1,12 +1,14 @@
 // Pruning of the cluster-pair list with a particle-pair distance criterion
 // (Sec. 2.3: done on the GPU, close to the cut-off).
 //
-// One warp per outer i-entry.  Each j-entry's C x C particle pairs are tested
-// by the whole warp (C = 8: two pairs per lane); an entry is kept iff a pair
-// the interaction counts (any pair except, on the unshifted diagonal, j <= i;
-// dummies sit far away and never pass) is closer than r_prune.  Kept entries
-// are compacted in order into the pruned arrays at the same offsets as the
-// outer list, so the pruned i-entry e covers [j_begin, j_begin + kept).
+// One warp per outer i-entry (a super-cluster and a shift).  For every
+// j-entry, each of its interacting i-clusters is re-tested: its C x C pairs
+// are checked by the whole warp (C = 8: two pairs per lane) and its bit stays
+// iff a pair the interaction counts (any pair except, on the unshifted
+// diagonal, j <= i; dummies sit far away and never pass) is closer than
+// r_prune.  Entries with a bit left are compacted in order into the pruned
+// arrays at the outer list's offsets, so pruned i-entry e covers
+// [j_begin, j_begin + kept).
 #include "nb_internal.cuh"
 
 namespace nbc {
@@ -14,12 +16,14 @@ namespace nbc {
 struct PruneArgs {
     DevState* st;
     const float4* xyzq;
+    const int2* sc_info;
     const int4* ient;
     const int* cj;
     const unsigned long long* mask;
     int4* ient_p;
     int* cj_p;
     unsigned long long* mask_p;
+    long long jstride;
     float L[3];
     float rp2;
     long long ient_cap;
@@ -27,73 +31,102 @@ struct PruneArgs {
 
 constexpr int kPruneWarps = 4;
 
-template <int C>
+template <int C, int S>
 __global__ void __launch_bounds__(32 * kPruneWarps) k_prune(PruneArgs A) {
     constexpr int PPL = (C * C + 31) / 32;
+    constexpr int NA = S * C;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    // shifted i particles of the current super-cluster: hi and lo parts
+    __shared__ float4 s_h[kPruneWarps][NA];
+    __shared__ float4 s_l[kPruneWarps][NA];
     const long long nient = min((long long)A.st->n_ient, A.ient_cap);
-    unsigned long long kept_total = 0;
-    for (long long e = (long long)blockIdx.x * kPruneWarps + (threadIdx.x >> 5); e < nient;
+    unsigned long long kept_total = 0, keys_total = 0;
+    int pi[PPL], pj[PPL];
+    bool pv[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        const int p = lane + 32 * k;
+        pv[k] = p < C * C;
+        pi[k] = pv[k] ? p / C : 0;
+        pj[k] = pv[k] ? p % C : 0;
+    }
+    for (long long e = (long long)blockIdx.x * kPruneWarps + wib; e < nient;
          e += (long long)gridDim.x * kPruneWarps) {
         const int4 ie = A.ient[e];
-        const int ci = ie.x, s = ie.y, jb = ie.z, je = ie.w;
+        const int q = ie.x, s = ie.y, jb = ie.z, je = ie.w;
+        const int2 info = A.sc_info[q];
+        const int g0 = info.x;
         const float sh[3] = {(float)(s / 9 - 1) * A.L[0], (float)((s / 3) % 3 - 1) * A.L[1],
                              (float)(s % 3 - 1) * A.L[2]};
-        float xh[PPL][3], xl[PPL][3];
-        int pi[PPL], pj[PPL];
-        bool pv[PPL];
-#pragma unroll
-        for (int k = 0; k < PPL; ++k) {
-            const int p = lane + 32 * k;
-            pv[k] = p < C * C;
-            pi[k] = pv[k] ? p / C : 0;
-            pj[k] = pv[k] ? p % C : 0;
-            const float4 x = A.xyzq[ci * C + pi[k]];
-            two_sum(x.x, sh[0], xh[k][0], xl[k][0]);
-            two_sum(x.y, sh[1], xh[k][1], xl[k][1]);
-            two_sum(x.z, sh[2], xh[k][2], xl[k][2]);
+        if (lane < info.y * C) {
+            const float4 x = A.xyzq[g0 * C + lane];
+            float4 h, l;
+            two_sum(x.x, sh[0], h.x, l.x);
+            two_sum(x.y, sh[1], h.y, l.y);
+            two_sum(x.z, sh[2], h.z, l.z);
+            h.w = l.w = 0.0f;
+            s_h[wib][lane] = h;
+            s_l[wib][lane] = l;
         }
+        __syncwarp();
         int kept = 0;
         for (int base = jb; base < je; base += 32) {
             const int nt = min(32, je - base);
-            int my_cj = 0;
-            unsigned long long my_m = 0;
-            if (lane < nt) {
-                my_cj = A.cj[base + lane];
-                my_m = A.mask[base + lane];
-            }
-            bool my_keep = false;
+            int my_w = 0;
+            if (lane < nt) my_w = A.cj[base + lane];
+            unsigned my_keep = 0;
             for (int t = 0; t < nt; ++t) {
-                const int cjt = __shfl_sync(full, my_cj, t);
-                const bool diag = (cjt == ci) && (s == kShiftCenter);
-                bool hit = false;
+                const int w = __shfl_sync(full, my_w, t);
+                const int cjt = w & kCjMask;
+                unsigned bits = (unsigned)w >> kSuperShift;
+                float4 xj[PPL];
 #pragma unroll
-                for (int k = 0; k < PPL; ++k) {
-                    if (!pv[k]) continue;
-                    const float4 xj = A.xyzq[cjt * C + pj[k]];
-                    const float dx = (xh[k][0] - xj.x) + xl[k][0];
-                    const float dy = (xh[k][1] - xj.y) + xl[k][1];
-                    const float dz = (xh[k][2] - xj.z) + xl[k][2];
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const bool counted = !(diag && pj[k] <= pi[k]);
-                    hit |= counted && (r2 < A.rp2);
+                for (int kk = 0; kk < PPL; ++kk) xj[kk] = A.xyzq[cjt * C + pj[kk]];
+                unsigned keep = 0;
+                while (bits) {
+                    const int k = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const bool diag = (cjt == g0 + k) && (s == kShiftCenter);
+                    bool hit = false;
+#pragma unroll
+                    for (int kk = 0; kk < PPL; ++kk) {
+                        if (!pv[kk]) continue;
+                        const float4 h = s_h[wib][k * C + pi[kk]], l = s_l[wib][k * C + pi[kk]];
+                        const float dx = (h.x - xj[kk].x) + l.x;
+                        const float dy = (h.y - xj[kk].y) + l.y;
+                        const float dz = (h.z - xj[kk].z) + l.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const bool counted = !(diag && pj[kk] <= pi[kk]);
+                        hit |= counted && (r2 < A.rp2);
+                    }
+                    if (__any_sync(full, hit)) keep |= 1u << k;
                 }
-                const bool any = __any_sync(full, hit);
-                if (lane == t) my_keep = any;
+                if (lane == t) my_keep = keep;
             }
-            const unsigned kb = __ballot_sync(full, my_keep);
+            const unsigned kb = __ballot_sync(full, my_keep != 0);
             const int pos = __popc(kb & ((1u << lane) - 1u));
             if (my_keep) {
-                A.cj_p[jb + kept + pos] = my_cj;
-                A.mask_p[jb + kept + pos] = my_m;
+                const long long o = jb + kept + pos;
+                A.cj_p[o] = (my_w & kCjMask) | (int)(my_keep << kSuperShift);
+#pragma unroll
+                for (int k = 0; k < S; ++k)
+                    A.mask_p[k * A.jstride + o] = ((my_keep >> k) & 1u) ? A.mask[k * A.jstride + base + lane] : 0ull;
             }
             kept += __popc(kb);
+            unsigned nk = __popc(my_keep);
+            for (int o = 16; o > 0; o >>= 1) nk += __shfl_xor_sync(full, nk, o);
+            keys_total += nk;
         }
-        if (lane == 0) A.ient_p[e] = make_int4(ci, s, jb, jb + kept);
+        if (lane == 0) A.ient_p[e] = make_int4(q, s, jb, jb + kept);
         kept_total += kept;
+        __syncwarp();
     }
-    if (lane == 0 && kept_total) atomicAdd(&A.st->n_jent_pruned, kept_total);
+    if (lane == 0 && kept_total) {
+        atomicAdd(&A.st->n_jent_pruned, kept_total);
+        atomicAdd(&A.st->n_keys_pruned, keys_total);
+    }
 }
 
 cudaError_t launch_prune(const Workspace& ws, const GridGeom& g, int C, float r_prune,
@@ -101,22 +134,25 @@ cudaError_t launch_prune(const Workspace& ws, const GridGeom& g, int C, float r_
     PruneArgs A;
     A.st = ws.st;
     A.xyzq = ws.xyzq;
+    A.sc_info = ws.sc_info;
     A.ient = ws.ient;
     A.cj = ws.cj;
     A.mask = ws.mask;
     A.ient_p = ws.ient_p;
     A.cj_p = ws.cj_p;
     A.mask_p = ws.mask_p;
+    A.jstride = ws.jstride;
     for (int k = 0; k < 3; ++k) A.L[k] = g.L[k];
     A.rp2 = r_prune * r_prune;
     A.ient_cap = ient_cap;
     cudaError_t e = cudaMemsetAsync(&ws.st->n_jent_pruned, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&ws.st->n_keys_pruned, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int blocks = n_sm * 16;
     if (C == 8)
-        k_prune<8><<<blocks, 32 * kPruneWarps, 0, s>>>(A);
+        k_prune<8, super_size(8)><<<blocks, 32 * kPruneWarps, 0, s>>>(A);
     else
-        k_prune<4><<<blocks, 32 * kPruneWarps, 0, s>>>(A);
+        k_prune<4, super_size(4)><<<blocks, 32 * kPruneWarps, 0, s>>>(A);
     return cudaGetLastError();
 }
 

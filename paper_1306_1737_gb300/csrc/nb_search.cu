@@ -1,15 +1,19 @@
-// Cluster-pair search (Sec. 2.3, Fig. 3) and exclusion masks (Sec. 2.4).
+// Cluster-pair search (Sec. 2.3, Fig. 3) and exclusion masks (Sec. 2.4),
+// emitted as super-cluster lists (Sec. 3.1: the GPU kernel reads one j-list
+// for several i-clusters, each j-entry carrying an interaction bit per
+// i-cluster and that pair's exclusion mask).
 //
-// One warp per i-cluster a.  For each periodic shift s applied to a, the
-// warp visits the grid columns whose x/y cells come within rlist of a's
-// shifted bounding box; in each column (clusters sorted on z) a binary search
-// bounds the j-clusters in z range.  Candidates b >= a (half list, Newton's
-// third law; for b == a only s = 0 and the positive half of the shifts) are
-// kept iff d_BB < rlist and (d_BB < rBB or some particle pair is closer than
-// rlist).  Shifted coordinates are carried as an unevaluated FP32 sum hi + lo
-// (TwoSum), so distances across the periodic boundary lose no precision.
-// Accepted pairs get their 64-bit mask (bit i*C+j: full interaction) and are
-// appended in chunks of at most kJChunk j-entries per i-entry.
+// One warp per super-cluster (up to S consecutive clusters g0..g0+n-1 of one
+// grid column).  For each periodic shift s applied to the i side, the warp
+// visits the grid columns whose x/y cells come within rlist of the shifted
+// union bounding box; in each column (clusters sorted on z) a binary search
+// bounds the candidates in z.  For every candidate cj and every i-cluster ck
+// with cj >= ck (half list, Newton's third law; cj == ck only for s = 0 and
+// the positive half of the shifts) the pair is kept iff d_BB < rlist and
+// (d_BB < rBB or some particle pair is closer than rlist).  Shifted
+// coordinates are carried as an unevaluated FP32 sum hi + lo (TwoSum).
+// Accepted j-clusters get their per-i-cluster 64-bit masks (bit i*C+j: full
+// interaction) and are appended in chunks of at most kJChunk per i-entry.
 #include "nb_internal.cuh"
 
 namespace nbc {
@@ -21,6 +25,7 @@ struct SearchArgs {
     const int* atom_of_slot;
     const int* slot_of_atom;
     const int* col_clu_start;
+    const int2* sc_info;
     const int* excl_off;
     const int* excl_idx;
     float L[3];
@@ -30,6 +35,7 @@ struct SearchArgs {
     int4* ient;
     int* cj;
     unsigned long long* mask;
+    long long jstride;
     long long ient_cap, jent_cap;
     int n_atoms;
 };
@@ -50,26 +56,40 @@ __host__ __device__ constexpr unsigned long long diag_mask() {
 }
 
 constexpr int kSearchWarps = 4;
+constexpr int kMaxExclPerSuper = 512;
 
-template <int C>
+template <int C, int S>
 __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
-    constexpr int PPL = (C * C + 31) / 32;  // particle pairs per lane
+    constexpr int PPL = (C * C + 31) / 32;  // particle pairs per lane in an atom test
+    constexpr int NA = S * C;               // i particles of a super-cluster (<= 32)
+    static_assert(NA <= 32, "a super-cluster's particles must fit one warp");
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    __shared__ int s_ex_i[kSearchWarps][kMaxExclPerCluster];
-    __shared__ int s_ex_s[kSearchWarps][kMaxExclPerCluster];
-    __shared__ int s_buf_cj[kSearchWarps][kJChunk];
-    __shared__ unsigned long long s_buf_m[kSearchWarps][kJChunk];
+    __shared__ float4 s_xi[kSearchWarps][NA];
+    __shared__ float s_bb[kSearchWarps][S][12];  // shifted BB: lo hi/lo, hi hi/lo per dimension
+    __shared__ int s_ex_r[kSearchWarps][kMaxExclPerSuper];
+    __shared__ int s_ex_s[kSearchWarps][kMaxExclPerSuper];
+    __shared__ int s_buf_w[kSearchWarps][kJChunk];
+    __shared__ unsigned long long s_buf_m[kSearchWarps][S][kJChunk];
 
-    const int nclu = A.st->nclu;
+    const int nsc = A.st->nsc;
     const float eps = 1e-4f;
-    for (int a = blockIdx.x * kSearchWarps + wib; a < nclu; a += gridDim.x * kSearchWarps) {
-        const float4 blo = A.bb[2 * a], bhi = A.bb[2 * a + 1];
-        const int aos = lane < C ? A.atom_of_slot[a * C + lane] : -1;
-        const unsigned realA = __ballot_sync(full, aos >= 0);
-
-        // force-field exclusions of a's particles as (row i, excluded slot)
+    for (int q = blockIdx.x * kSearchWarps + wib; q < nsc; q += gridDim.x * kSearchWarps) {
+        const int2 info = A.sc_info[q];
+        const int g0 = info.x, n = info.y;
+        // i particles of the super-cluster, real-slot bits per i-cluster
+        const int aos = lane < n * C ? A.atom_of_slot[g0 * C + lane] : -1;
+        if (lane < NA) s_xi[wib][lane] = lane < n * C ? A.xyzq[g0 * C + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const unsigned realAll = __ballot_sync(full, aos >= 0);
+        // union bounding box
+        float ulo[3] = {INFINITY, INFINITY, INFINITY}, uhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int k = 0; k < n; ++k) {
+            const float4 lo = A.bb[2 * (g0 + k)], hi = A.bb[2 * (g0 + k) + 1];
+            ulo[0] = fminf(ulo[0], lo.x); ulo[1] = fminf(ulo[1], lo.y); ulo[2] = fminf(ulo[2], lo.z);
+            uhi[0] = fmaxf(uhi[0], hi.x); uhi[1] = fmaxf(uhi[1], hi.y); uhi[2] = fmaxf(uhi[2], hi.z);
+        }
+        // force-field exclusions of the super-cluster's particles: (row, excluded slot)
         int nex = 0;
         if (A.excl_off) {
             int cnt = 0, off = 0;
@@ -83,50 +103,31 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
                 if (lane >= o) incl += v;
             }
             const int total = __shfl_sync(full, incl, 31);
-            if (total > kMaxExclPerCluster && lane == 0) set_flag(A.st, NB_ERR_CAPACITY);
+            if (total > kMaxExclPerSuper && lane == 0) set_flag(A.st, NB_ERR_CAPACITY);
             for (int k = 0; k < cnt; ++k) {
                 const int idx = incl - cnt + k;
-                if (idx < kMaxExclPerCluster) {
-                    const int q = A.excl_idx[off + k];
-                    const bool ok = q >= 0 && q < A.n_atoms;
+                if (idx < kMaxExclPerSuper) {
+                    const int qa = A.excl_idx[off + k];
+                    const bool ok = qa >= 0 && qa < A.n_atoms;
                     if (!ok) set_flag(A.st, NB_ERR_ARG);
-                    s_ex_i[wib][idx] = lane;
-                    s_ex_s[wib][idx] = ok ? A.slot_of_atom[q] : -1;
+                    s_ex_r[wib][idx] = lane;
+                    s_ex_s[wib][idx] = ok ? A.slot_of_atom[qa] : -1;
                 }
             }
-            nex = min(total, kMaxExclPerCluster);
+            nex = min(total, kMaxExclPerSuper);
         }
         __syncwarp();
-
-        // i particles of this lane's pairs
-        float xi[PPL][3];
-        int pj[PPL];
-        bool pv[PPL];
-#pragma unroll
-        for (int k = 0; k < PPL; ++k) {
-            const int p = lane + 32 * k;
-            pv[k] = p < C * C;
-            const int i = pv[k] ? p / C : 0;
-            pj[k] = pv[k] ? p % C : 0;
-            const float4 x = A.xyzq[a * C + i];
-            xi[k][0] = x.x;
-            xi[k][1] = x.y;
-            xi[k][2] = x.z;
-        }
 
         for (int s = 0; s < 27; ++s) {
             const float sh[3] = {(float)(s / 9 - 1) * A.L[0], (float)((s / 3) % 3 - 1) * A.L[1],
                                  (float)(s % 3 - 1) * A.L[2]};
-            // candidate columns (plain FP32 with a margin; the exact test follows)
-            const float lx = blo.x + sh[0], hx = bhi.x + sh[0];
-            const float ly = blo.y + sh[1], hy = bhi.y + sh[1];
-            const float lz = blo.z + sh[2], hz = bhi.z + sh[2];
-            int ix0 = (int)floorf((lx - A.rl - eps) * A.inv_cx);
-            int ix1 = (int)floorf((hx + A.rl + eps) * A.inv_cx);
-            int iy0 = (int)floorf((ly - A.rl - eps) * A.inv_cy);
-            int iy1 = (int)floorf((hy + A.rl + eps) * A.inv_cy);
+            // candidate columns from the shifted union box (plain FP32 with a margin)
+            int ix0 = (int)floorf((ulo[0] + sh[0] - A.rl - eps) * A.inv_cx);
+            int ix1 = (int)floorf((uhi[0] + sh[0] + A.rl + eps) * A.inv_cx);
+            int iy0 = (int)floorf((ulo[1] + sh[1] - A.rl - eps) * A.inv_cy);
+            int iy1 = (int)floorf((uhi[1] + sh[1] + A.rl + eps) * A.inv_cy);
             if (ix1 < 0 || ix0 > A.nx - 1 || iy1 < 0 || iy0 > A.ny - 1) continue;
-            const float zlo = lz - A.rl - eps, zhi = hz + A.rl + eps;
+            const float zlo = ulo[2] + sh[2] - A.rl - eps, zhi = uhi[2] + sh[2] + A.rl + eps;
             if (zhi < 0.0f || zlo >= A.L[2]) continue;
             ix0 = max(ix0, 0);
             ix1 = min(ix1, A.nx - 1);
@@ -134,28 +135,29 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
             iy1 = min(iy1, A.ny - 1);
             const int ncy = iy1 - iy0 + 1;
             const int ncols = (ix1 - ix0 + 1) * ncy;
-
-            // shifted bounding box and i particles as hi + lo
-            float alo_h[3], alo_l[3], ahi_h[3], ahi_l[3];
-            two_sum(blo.x, sh[0], alo_h[0], alo_l[0]);
-            two_sum(blo.y, sh[1], alo_h[1], alo_l[1]);
-            two_sum(blo.z, sh[2], alo_h[2], alo_l[2]);
-            two_sum(bhi.x, sh[0], ahi_h[0], ahi_l[0]);
-            two_sum(bhi.y, sh[1], ahi_h[1], ahi_l[1]);
-            two_sum(bhi.z, sh[2], ahi_h[2], ahi_l[2]);
-            float xh[PPL][3], xl[PPL][3];
-#pragma unroll
-            for (int k = 0; k < PPL; ++k)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) two_sum(xi[k][d], sh[d], xh[k][d], xl[k][d]);
+            // exact shifted boxes of the i-clusters as hi + lo
+            if (lane < n * 6) {
+                const int k = lane / 6, c = lane % 6, d = c % 3;
+                const float4 b = c < 3 ? A.bb[2 * (g0 + k)] : A.bb[2 * (g0 + k) + 1];
+                const float v = d == 0 ? b.x : (d == 1 ? b.y : b.z);
+                float h, l;
+                two_sum(v, sh[d], h, l);
+                s_bb[wib][k][2 * c] = h;
+                s_bb[wib][k][2 * c + 1] = l;
+            }
+            __syncwarp();
 
             int nbuf = 0;
             auto flush = [&]() {
                 __syncwarp();
                 unsigned long long jb = 0, ie = 0;
+                unsigned nk = 0;
+                for (int t = lane; t < nbuf; t += 32) nk += __popc((unsigned)s_buf_w[wib][t] >> kSuperShift);
+                for (int o = 16; o > 0; o >>= 1) nk += __shfl_xor_sync(full, nk, o);
                 if (lane == 0) {
                     jb = atomicAdd(&A.st->n_jent, (unsigned long long)nbuf);
                     ie = atomicAdd(&A.st->n_ient, 1ull);
+                    atomicAdd(&A.st->n_keys, (unsigned long long)nk);
                 }
                 jb = __shfl_sync(full, jb, 0);
                 ie = __shfl_sync(full, ie, 0);
@@ -163,14 +165,15 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
                     // keep every stored i-entry valid: an empty range on overflow
                     if (lane == 0) {
                         set_flag(A.st, NB_ERR_CAPACITY);
-                        if ((long long)ie < A.ient_cap) A.ient[ie] = make_int4(a, s, 0, 0);
+                        if ((long long)ie < A.ient_cap) A.ient[ie] = make_int4(q, s, 0, 0);
                     }
                 } else {
                     for (int t = lane; t < nbuf; t += 32) {
-                        A.cj[jb + t] = s_buf_cj[wib][t];
-                        A.mask[jb + t] = s_buf_m[wib][t];
+                        A.cj[jb + t] = s_buf_w[wib][t];
+#pragma unroll
+                        for (int k = 0; k < S; ++k) A.mask[k * A.jstride + jb + t] = s_buf_m[wib][k][t];
                     }
-                    if (lane == 0) A.ient[ie] = make_int4(a, s, (int)jb, (int)(jb + nbuf));
+                    if (lane == 0) A.ient[ie] = make_int4(q, s, (int)jb, (int)(jb + nbuf));
                 }
                 nbuf = 0;
                 __syncwarp();
@@ -181,19 +184,19 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
                 int k0 = 0, cnt = 0;
                 if (cidx < ncols) {
                     const int col = (ix0 + cidx / ncy) * A.ny + (iy0 + cidx % ncy);
-                    const int g0 = A.col_clu_start[col], g1 = A.col_clu_start[col + 1];
-                    int lo = g0, hi = g1;
+                    const int c0 = A.col_clu_start[col], c1 = A.col_clu_start[col + 1];
+                    int lo = c0, hi = c1;
                     while (lo < hi) {  // first cluster with zmax >= zlo
                         const int m = (lo + hi) >> 1;
                         if (A.bb[2 * m + 1].z < zlo) lo = m + 1; else hi = m;
                     }
                     const int f = lo;
-                    hi = g1;
+                    hi = c1;
                     while (lo < hi) {  // first cluster with zmin > zhi
                         const int m = (lo + hi) >> 1;
                         if (A.bb[2 * m].z <= zhi) lo = m + 1; else hi = m;
                     }
-                    const int f2 = max(f, a);
+                    const int f2 = max(f, g0);
                     if (lo > f2) {
                         k0 = f2;
                         cnt = lo - f2;
@@ -215,73 +218,96 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
                     }
                     const int ok0 = __shfl_sync(full, k0, owner);
                     const int oex = __shfl_sync(full, excl, owner);
-                    bool valid = idx < total;
+                    const bool valid = idx < total;
                     const int b = ok0 + (idx - oex);
-                    if (valid && b == a && s < kShiftCenter) valid = false;
-                    bool pass = false, in_rbb = false;
+                    unsigned need = 0, acc = 0;  // per candidate: i-clusters to test / accepted
                     if (valid) {
                         const float4 jlo = A.bb[2 * b], jhi = A.bb[2 * b + 1];
                         const float jl[3] = {jlo.x, jlo.y, jlo.z}, jh[3] = {jhi.x, jhi.y, jhi.z};
-                        float d2 = 0.0f;
+                        for (int k = 0; k < n; ++k) {
+                            const int ck = g0 + k;
+                            if (b < ck || (b == ck && s < kShiftCenter)) continue;
+                            float d2 = 0.0f;
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            const float g1 = (jl[d] - ahi_h[d]) - ahi_l[d];
-                            const float g2 = (alo_h[d] - jh[d]) + alo_l[d];
-                            const float g = fmaxf(0.0f, fmaxf(g1, g2));
-                            d2 = fmaf(g, g, d2);
-                        }
-                        pass = d2 < A.rl2;
-                        in_rbb = d2 < A.rbb2;
-                    }
-                    unsigned need = __ballot_sync(full, pass && !in_rbb);
-                    unsigned acc = __ballot_sync(full, pass && in_rbb);
-                    while (need) {
-                        const int t = __ffs(need) - 1;
-                        need &= need - 1;
-                        const int bt = __shfl_sync(full, b, t);
-                        bool hit = false;
-#pragma unroll
-                        for (int k = 0; k < PPL; ++k) {
-                            if (!pv[k]) continue;
-                            const float4 xj = A.xyzq[bt * C + pj[k]];
-                            const float dx = (xh[k][0] - xj.x) + xl[k][0];
-                            const float dy = (xh[k][1] - xj.y) + xl[k][1];
-                            const float dz = (xh[k][2] - xj.z) + xl[k][2];
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            hit |= r2 < A.rl2;
-                        }
-                        if (__any_sync(full, hit)) acc |= 1u << t;
-                    }
-                    while (acc) {
-                        const int t = __ffs(acc) - 1;
-                        acc &= acc - 1;
-                        const int bt = __shfl_sync(full, b, t);
-                        const int bos = lane < C ? A.atom_of_slot[bt * C + lane] : -1;
-                        const unsigned realB = __ballot_sync(full, bos >= 0);
-                        unsigned long long m = 0;
-#pragma unroll
-                        for (int i = 0; i < C; ++i)
-                            if ((realA >> i) & 1u) m |= (unsigned long long)realB << (i * C);
-                        if (bt == a) {
-                            if (s == kShiftCenter) m &= upper_mask<C>();
-                            else m &= ~diag_mask<C>();
-                        }
-                        unsigned lo32 = 0, hi32 = 0;
-                        for (int e = lane; e < nex; e += 32) {
-                            const int sl = s_ex_s[wib][e];
-                            if (sl >= 0 && sl / C == bt) {
-                                const int bit = s_ex_i[wib][e] * C + sl % C;
-                                if (bit < 32) lo32 |= 1u << bit;
-                                else hi32 |= 1u << (bit - 32);
+                            for (int d = 0; d < 3; ++d) {
+                                const float* sb = s_bb[wib][k];
+                                const float g1 = (jl[d] - sb[6 + 2 * d]) - sb[6 + 2 * d + 1];
+                                const float g2 = (sb[2 * d] - jh[d]) + sb[2 * d + 1];
+                                const float g = fmaxf(0.0f, fmaxf(g1, g2));
+                                d2 = fmaf(g, g, d2);
+                            }
+                            if (d2 < A.rl2) {
+                                if (d2 < A.rbb2) acc |= 1u << k;
+                                else need |= 1u << k;
                             }
                         }
-                        lo32 = __reduce_or_sync(full, lo32);
-                        hi32 = __reduce_or_sync(full, hi32);
-                        m &= ~(((unsigned long long)hi32 << 32) | lo32);
-                        if (lane == 0) {
-                            s_buf_cj[wib][nbuf] = bt;
-                            s_buf_m[wib][nbuf] = m;
+                    }
+                    // particle-distance tests, one warp-wide test per (candidate, i-cluster)
+                    unsigned pending = __ballot_sync(full, need != 0);
+                    while (pending) {
+                        const int t = __ffs(pending) - 1;
+                        pending &= pending - 1;
+                        const int bt = __shfl_sync(full, b, t);
+                        unsigned nk = __shfl_sync(full, need, t);
+                        while (nk) {
+                            const int k = __ffs(nk) - 1;
+                            nk &= nk - 1;
+                            bool hit = false;
+#pragma unroll
+                            for (int kk = 0; kk < PPL; ++kk) {
+                                const int p = lane + 32 * kk;
+                                if (p >= C * C) continue;
+                                const float4 xi = s_xi[wib][k * C + p / C];
+                                const float4 xj = A.xyzq[bt * C + p % C];
+                                float h, l;
+                                two_sum(xi.x, sh[0], h, l);
+                                const float dx = (h - xj.x) + l;
+                                two_sum(xi.y, sh[1], h, l);
+                                const float dy = (h - xj.y) + l;
+                                two_sum(xi.z, sh[2], h, l);
+                                const float dz = (h - xj.z) + l;
+                                hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < A.rl2;
+                            }
+                            if (__any_sync(full, hit) && lane == t) acc |= 1u << k;
                         }
+                    }
+                    unsigned accepted = __ballot_sync(full, acc != 0);
+                    while (accepted) {
+                        const int t = __ffs(accepted) - 1;
+                        accepted &= accepted - 1;
+                        const int bt = __shfl_sync(full, b, t);
+                        const unsigned at = __shfl_sync(full, acc, t);
+                        const int bos = lane < C ? A.atom_of_slot[bt * C + lane] : -1;
+                        const unsigned realB = __ballot_sync(full, bos >= 0);
+#pragma unroll
+                        for (int k = 0; k < S; ++k) {
+                            unsigned long long m = 0;
+                            if ((at >> k) & 1u) {
+                                const unsigned realA = (realAll >> (k * C)) & ((1u << C) - 1u);
+#pragma unroll
+                                for (int i = 0; i < C; ++i)
+                                    if ((realA >> i) & 1u) m |= (unsigned long long)realB << (i * C);
+                                if (bt == g0 + k) {
+                                    if (s == kShiftCenter) m &= upper_mask<C>();
+                                    else m &= ~diag_mask<C>();
+                                }
+                                unsigned lo32 = 0, hi32 = 0;
+                                for (int e = lane; e < nex; e += 32) {
+                                    const int sl = s_ex_s[wib][e];
+                                    const int r = s_ex_r[wib][e];
+                                    if (sl >= 0 && r / C == k && sl / C == bt) {
+                                        const int bit = (r % C) * C + sl % C;
+                                        if (bit < 32) lo32 |= 1u << bit;
+                                        else hi32 |= 1u << (bit - 32);
+                                    }
+                                }
+                                lo32 = __reduce_or_sync(full, lo32);
+                                hi32 = __reduce_or_sync(full, hi32);
+                                m &= ~(((unsigned long long)hi32 << 32) | lo32);
+                            }
+                            if (lane == 0) s_buf_m[wib][k][nbuf] = m;
+                        }
+                        if (lane == 0) s_buf_w[wib][nbuf] = bt | (int)(at << kSuperShift);
                         ++nbuf;
                         if (nbuf == kJChunk) flush();
                     }
@@ -304,6 +330,7 @@ cudaError_t launch_search(const Workspace& ws, const GridGeom& g, int C, long lo
     A.atom_of_slot = ws.atom_of_slot;
     A.slot_of_atom = ws.slot_of_atom;
     A.col_clu_start = ws.col_clu_start;
+    A.sc_info = ws.sc_info;
     A.excl_off = excl_off;
     A.excl_idx = excl_idx;
     for (int k = 0; k < 3; ++k) A.L[k] = g.L[k];
@@ -317,6 +344,7 @@ cudaError_t launch_search(const Workspace& ws, const GridGeom& g, int C, long lo
     A.ient = ws.ient;
     A.cj = ws.cj;
     A.mask = ws.mask;
+    A.jstride = ws.jstride;
     A.ient_cap = ient_cap;
     A.jent_cap = jent_cap;
     A.n_atoms = n_atoms;
@@ -325,9 +353,9 @@ cudaError_t launch_search(const Workspace& ws, const GridGeom& g, int C, long lo
     if (blocks > want) blocks = want;
     if (blocks < 1) blocks = 1;
     if (C == 8)
-        k_search<8><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
+        k_search<8, super_size(8)><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
     else
-        k_search<4><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
+        k_search<4, super_size(4)><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
     return cudaGetLastError();
 }
 

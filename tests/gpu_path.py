@@ -65,56 +65,68 @@ class GpuBox:
         ts = torch.zeros(ns, dtype=torch.int32, device=self.dev)
         bb = torch.zeros((info.n_clusters, 6), dtype=torch.float32, device=self.dev)
         coa = torch.zeros(self.b.n, dtype=torch.int32, device=self.dev)
-        nb.nb_get_grid(self.ctx, aos, soa, ccs, xyzq, ts, bb, coa)
+        sci = torch.zeros((max(info.n_superclusters, 1), 2), dtype=torch.int32, device=self.dev)
+        nb.nb_get_grid(self.ctx, aos, soa, ccs, xyzq, ts, bb, coa, sci)
         torch.cuda.synchronize()
         return dict(info=info, atom_of_slot=aos.cpu().numpy(), slot_of_atom=soa.cpu().numpy(),
                     col_clu_start=ccs.cpu().numpy(), xyzq=xyzq.cpu().numpy(),
-                    type_slot=ts.cpu().numpy(), bb=bb.cpu().numpy(), col_of_atom=coa.cpu().numpy())
+                    type_slot=ts.cpu().numpy(), bb=bb.cpu().numpy(), col_of_atom=coa.cpu().numpy(),
+                    sc_info=sci.cpu().numpy()[: info.n_superclusters])
 
     def list_arrays(self, which=0):
+        """(info, i-entries [ni, 4], j-words [nj], masks [S, nj], super-cluster
+        table [nsc, 2]) of the outer (0) or pruned (1) list."""
         torch = self.torch
         info = nb.nb_check(self.ctx)
-        ni, nj = int(info.n_ientries), int(info.n_jentries)
+        ni, nj, S = int(info.n_ientries), int(info.n_jentries), int(info.super_size)
         ient = torch.zeros((max(ni, 1), 4), dtype=torch.int32, device=self.dev)
         cj = torch.zeros(max(nj, 1), dtype=torch.int32, device=self.dev)
-        mask = torch.zeros(max(nj, 1), dtype=torch.int64, device=self.dev)
+        mask = torch.zeros((S, max(nj, 1)), dtype=torch.int64, device=self.dev)
         nb.nb_get_list(self.ctx, which, ient, cj, mask)
+        sci = torch.zeros((max(info.n_superclusters, 1), 2), dtype=torch.int32, device=self.dev)
+        nb.nb_get_grid(self.ctx, sc_info=sci)
         torch.cuda.synchronize()
-        return info, ient.cpu().numpy()[:ni], cj.cpu().numpy()[:nj], \
-            mask.cpu().numpy()[:nj].view(np.uint64)
+        masks = mask.cpu().numpy().view(np.uint64)
+        if nj < masks.shape[1]:
+            masks = masks[:, :nj]
+        return info, ient.cpu().numpy()[:ni], cj.cpu().numpy()[:nj], masks, \
+            sci.cpu().numpy()[: info.n_superclusters]
 
     def close(self):
         self.cx.close()
 
 
-def canonical_keys(ient, cj, mask):
-    """GPU list -> {(a, b, s): mask} with a <= b (the oracle's key form)."""
-    out = {}
-    dup = 0
-    for ci, s, jb, je in ient.tolist():
-        for k in range(jb, je):
-            b = int(cj[k])
-            m = int(mask[k])
-            if ci <= b:
-                key = (ci, b, s)
-            else:  # stored with the other cluster as i: shift negates
-                key = (b, ci, 26 - s)
-            if key in out:
-                dup += 1
-            out[key] = m
-    return out, dup
+SUPER_SHIFT = 27
 
 
-def expand_gpu_keys(ient, cj):
-    a = []
-    b = []
-    s = []
-    for ci, sh, jb, je in ient.tolist():
-        n = je - jb
-        a.extend([ci] * n)
-        s.extend([sh] * n)
-        b.extend(cj[jb:je].tolist())
-    return np.array(a, np.int32), np.array(b, np.int32), np.array(s, np.int32)
+def expand_keys(ient, cj, masks, sc_info):
+    """GPU super-cluster list -> arrays (a, b, s, mask) of cluster-pair keys."""
+    lens = ient[:, 3] - ient[:, 2]
+    starts = np.cumsum(lens) - lens
+    idx = np.arange(int(lens.sum())) - np.repeat(starts, lens) + np.repeat(ient[:, 2], lens)
+    q = np.repeat(ient[:, 0], lens)
+    s = np.repeat(ient[:, 1], lens)
+    w = cj[idx].astype(np.int64) & 0xFFFFFFFF
+    b = (w & ((1 << SUPER_SHIFT) - 1)).astype(np.int64)
+    bits = w >> SUPER_SHIFT
+    g0 = sc_info[q, 0].astype(np.int64)
+    A, B, Sh, M = [], [], [], []
+    for k in range(masks.shape[0]):
+        on = ((bits >> k) & 1).astype(bool)
+        A.append(g0[on] + k)
+        B.append(b[on])
+        Sh.append(s[on])
+        M.append(masks[k][idx[on]])
+    return (np.concatenate(A), np.concatenate(B), np.concatenate(Sh), np.concatenate(M))
+
+
+def canonical_keys(ient, cj, masks, sc_info):
+    """GPU list -> ({(a, b, s): mask} with a <= b, number of duplicate keys)."""
+    a, b, s, m = expand_keys(ient, cj, masks, sc_info)
+    assert np.all(a <= b)
+    keys = list(zip(a.tolist(), b.tolist(), s.tolist()))
+    out = dict(zip(keys, m.tolist()))
+    return out, len(keys) - len(out)
 
 
 def force_errors(f_gpu, f_ref):

@@ -29,15 +29,9 @@ def env():
 
 
 def gpu_keys(gb, which):
-    info, ient, cj, mask = gb.list_arrays(which)
-    lens = ient[:, 3] - ient[:, 2]
-    a = np.repeat(ient[:, 0], lens)
-    s = np.repeat(ient[:, 1], lens)
-    starts = np.cumsum(lens) - lens
-    idx = np.arange(int(lens.sum())) - np.repeat(starts, lens) + np.repeat(ient[:, 2], lens)
-    b = cj[idx]
-    m = mask[idx]
-    return a, b, s, m
+    import gpu_path
+    info, ient, cj, masks, sci = gb.list_arrays(which)
+    return gpu_path.expand_keys(ient, cj, masks, sci)
 
 
 def compare_sampled(g_or, keys_gpu, samples, rl, excl_off, excl_idx, prune=None):

@@ -33,6 +33,14 @@ def gp():
 
 def check_grid(g_gpu, g_or):
     assert g_gpu["info"].nx == g_or.nx and g_gpu["info"].ny == g_or.ny
+    # super-clusters: runs of up to S consecutive clusters of each column
+    S = g_gpu["info"].super_size
+    want = []
+    cs = g_or.col_clu_start
+    for c in range(len(cs) - 1):
+        for f in range(cs[c], cs[c + 1], S):
+            want.append((f, min(S, cs[c + 1] - f)))
+    assert [tuple(x) for x in g_gpu["sc_info"].tolist()] == want
     assert g_gpu["info"].n_clusters == g_or.nclu
     assert np.array_equal(g_gpu["col_clu_start"], g_or.col_clu_start)
     assert np.array_equal(g_gpu["col_of_atom"], g_or.col_of_atom)
@@ -49,8 +57,8 @@ def check_list(gb, g_or, pl_or, rlist, which=0, r_thresh=None, xyzq=None):
     differing keys must lie within EXEMPT_NM of the threshold (the list
     radius, or for the pruned list the prune radius under xyzq)."""
     gp_ = __import__("gpu_path")
-    info, ient, cj, mask = gb.list_arrays(which)
-    keys_gpu, dup = gp_.canonical_keys(ient, cj, mask)
+    info, ient, cj, masks, sci = gb.list_arrays(which)
+    keys_gpu, dup = gp_.canonical_keys(ient, cj, masks, sci)
     assert dup == 0
     keys_or = pl_or.key_mask()
     only_gpu = set(keys_gpu) - set(keys_or)
@@ -72,6 +80,10 @@ def check_list(gb, g_or, pl_or, rlist, which=0, r_thresh=None, xyzq=None):
     assert not bad, bad[:5]
     # j-lists are chunked: each i-entry holds at most 32 j-entries
     assert np.all(ient[:, 3] - ient[:, 2] <= 32)
+    # every stored j-entry interacts with at least one i-cluster
+    lens = ient[:, 3] - ient[:, 2]
+    used = np.concatenate([np.arange(b0, b1) for b0, b1 in ient[:, 2:4]]) if len(ient) else np.zeros(0, int)
+    assert np.all((cj[used].astype(np.int64) & 0xFFFFFFFF) >> gp_.SUPER_SHIFT != 0)
     return len(keys_gpu), len(only_gpu) + len(only_or)
 
 
