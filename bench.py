@@ -64,6 +64,35 @@ def water1m():
                "comb": "lb"}
 
 
+FORCE_SOURCES = ["paper_1306_1737_gb300/csrc/nb_force.cu", "paper_1306_1737_gb300/csrc/nb_internal.cuh",
+                 "paper_1306_1737_gb300/csrc/nb_ewald_fit.h"]
+
+
+def force_source_hash():
+    """Hash of the force kernel's sources (a profile's counters apply only to
+    the exact kernel they were taken on)."""
+    import hashlib
+    h = hashlib.sha1()
+    for rel in FORCE_SOURCES:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per force-kernel launch from the committed ncu summary of
+    this workload, or None when it was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"k_force8_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    src, traffic = None, None
+    for line in open(path):
+        if line.startswith("source-hash:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram-bytes-per-launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if src == force_source_hash() else None
+
+
 def peaks():
     p = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -361,7 +390,8 @@ def run_ours(args):
     achieved = flops / t_force
     roofline = {"bound": "alu", "kernel": "k_force8 (Ewald)" if elec == "ewald" else "k_force8 (RF)",
                 "achieved": achieved / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
+                "frac": achieved / fp32_peak, "traffic": profiled_traffic(args.workload),
+                "traffic_unit": "bytes per launch (dram read + write, ncu)",
                 "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {pk['sm_max_mhz']:.0f} MHz "
                                f"(max SM clock, {pk['source']})",
                 "algorithmic_flops_per_launch": flops, "listed_pairs_per_launch": listed,
