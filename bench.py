@@ -246,7 +246,7 @@ def config_dict(args, box, p, desc):
     return {"workload": args.workload, "description": desc, "n_atoms": int(box.n),
             "box_nm": [round(float(v), 6) for v in box.box], "elec": p["elec"], "rc_nm": p["rc"],
             "rlist_nm": p["rlist"], "beta_nm-1": p.get("beta"), "nstlist": p.get("nstlist", 1),
-            "nstprune": p.get("nstprune", 0), "cluster": "8x8 cluster pairs (two 8x4 halves per warp), super-clusters of 4 i-clusters sharing a j-list",
+            "nstprune": p.get("nstprune", 0), "cluster": "8x8 cluster pairs (two 8x4 halves per warp), super-clusters of 2 i-clusters sharing a j-list",
             "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}",
             "seed": int(box.seed)}
 

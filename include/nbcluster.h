@@ -75,10 +75,11 @@ typedef struct {
     float beta;        /* Ewald splitting parameter (nm^-1) */
 } nb_params;
 
-/* Sizes of the current grid and lists (read back by nb_check). */
+/* Sizes of the current grid and lists (read back by nb_check), summed over
+ * the boxes it covers (all boxes for nb_check, one for nb_box_info). */
 typedef struct {
     int n_atoms;          /* particles gridded */
-    int nx, ny;           /* grid columns along x and y */
+    int nx, ny;           /* grid columns along x and y (one box only; else 0) */
     int n_clusters;       /* clusters, including padded ones */
     int64_t n_ientries;   /* i-entries of the outer (rlist) list */
     int64_t n_jentries;   /* j-entries of the outer list */
@@ -91,6 +92,8 @@ typedef struct {
     int super_size;       /* i-clusters per super-cluster: 2 for C = 8, 1 for C = 4 */
     int64_t n_launches;   /* kernels this context has launched */
     uint32_t flags;       /* device error flags (bit mask of 1 << nb_status_code) */
+    int n_boxes;          /* boxes covered */
+    int atom_offset;      /* index of the first box's first particle in the particle arrays */
 } nb_info;
 
 /* Kernel kinds reported by nb_profile_read. */
@@ -130,10 +133,23 @@ nb_status nb_lj_combine(int ntypes, const double* sigma_host, const double* eps_
 /* Bytes of device workspace needed for n_atoms particles in a box of edges
  * box_host[3] (nm), lists up to radius rlist_max (nm) and ntypes <= 64 LJ
  * types.  list_factor (>= 1; 0 = default 1.5) scales the density-based
- * estimate of the cluster-pair list capacity.
+ * estimate of the cluster-pair list capacity.  Fixes the context's plan (one
+ * box); nb_set_workspace must follow.
  * Errors: NB_ERR_ARG, NB_ERR_BOX. */
 nb_status nb_workspace_query(nb_ctx* ctx, int n_atoms, const double* box_host, double rlist_max,
                              int ntypes, double list_factor, size_t* bytes);
+
+/* The same for a batch of nbox <= 4096 independent periodic boxes handled by
+ * every call of the context together (one launch per kernel for all boxes).
+ * Box b holds n_atoms_host[b] particles, which are the b-th consecutive range
+ * of every particle array (q, type, xyz, f, exclusion CSR indices are
+ * batch-global), in a box of edges boxes_host[3b..3b+2] (nm) used to size its
+ * grid and list capacity.  The plan (particles per box) is fixed until the
+ * next query; box edges may change at every nb_grid_put within the capacity.
+ * Errors: NB_ERR_ARG, NB_ERR_BOX. */
+nb_status nb_workspace_query_boxes(nb_ctx* ctx, int nbox, const int* n_atoms_host,
+                                   const double* boxes_host, double rlist_max, int ntypes,
+                                   double list_factor, size_t* bytes);
 
 /* Hand the context a device buffer of at least the queried size (256-byte
  * aligned).  The caller owns it and keeps it alive while the context uses
@@ -143,22 +159,23 @@ nb_status nb_set_workspace(nb_ctx* ctx, void* ws_dev, size_t bytes);
 /* --- the hot path ---------------------------------------------------------- */
 
 /* Particle charges (float [n]), LJ types (int [n], 0 <= type < ntypes) and the
- * LJ pair table c6c12_dev (float [ntypes][ntypes][2], e.g. nb_lj_combine) are
- * copied into the workspace on the stream.  Sec. 3.2.
- * Errors: NB_ERR_ARG, NB_ERR_STATE (no workspace), NB_ERR_CAPACITY (n or
- * ntypes above the workspace's sizes), NB_ERR_CUDA. */
+ * LJ pair table c6c12_dev (float [ntypes][ntypes][2], e.g. nb_lj_combine;
+ * shared by all boxes) are copied into the workspace on the stream.  Sec. 3.2.
+ * n must equal the planned number of particles (summed over the boxes).
+ * Errors: NB_ERR_ARG, NB_ERR_STATE (no workspace), NB_ERR_CAPACITY (n not the
+ * planned number, or ntypes above 64), NB_ERR_CUDA. */
 nb_status nb_set_atoms(nb_ctx* ctx, int n, const float* q_dev, const int* type_dev, int ntypes,
                        const float* c6c12_dev, nb_stream stream);
 
 /* Spatial clustering (Sec. 2.3, Fig. 2): wrap xyz_dev (float [n][3], each
- * coordinate in [-L, 2L)) into the box, grid x/y into columns of spacing
- * (C/rho)^(1/3), sort each column on z, cut clusters of C with dummy padding,
- * compute bounding boxes.  box_host: double[3] edge lengths (nm), used as
- * FP32.  Invalidates the lists.
+ * coordinate in [-L, 2L) of its own box) into its box, grid x/y into columns
+ * of spacing (C/rho)^(1/3), sort each column on z, cut clusters of C with
+ * dummy padding, compute bounding boxes.  boxes_host: double [nbox][3] edge
+ * lengths (nm) of every box, used as FP32.  Invalidates the lists.
  * Errors: NB_ERR_ARG, NB_ERR_BOX, NB_ERR_STATE (no atoms set),
  * NB_ERR_CAPACITY (more columns/slots than the workspace holds), NB_ERR_CUDA;
  * device flags NB_ERR_COORD, NB_ERR_CAPACITY (column > 8192 particles). */
-nb_status nb_grid_put(nb_ctx* ctx, const float* xyz_dev, const double* box_host, nb_stream stream);
+nb_status nb_grid_put(nb_ctx* ctx, const float* xyz_dev, const double* boxes_host, nb_stream stream);
 
 /* Cluster-pair search (Sec. 2.3, Fig. 3) with exclusion bitmasks (Sec. 2.4):
  * every cluster pair (a <= b, periodic shift s applied to a; for a == b only
@@ -167,9 +184,10 @@ nb_status nb_grid_put(nb_ctx* ctx, const float* xyz_dev, const double* box_host,
  * than rlist.  Bit i*C+j of a pair's mask is 1 iff particles i of a and j of b
  * get the full interaction.  excl_off_dev (int [n+1]) and excl_idx_dev (int
  * [excl_off[n]]) give each particle's force-field exclusions (CSR, caller
- * order, both directions); both may be NULL for none.  They are read on the
- * stream and must stay valid until it reaches this call.
- * Errors: NB_ERR_ARG, NB_ERR_BOX (rlist >= L/2), NB_ERR_STATE (no grid),
+ * order, both directions; an exclusion never links two boxes); both may be
+ * NULL for none.  They are read on the stream and must stay valid until it
+ * reaches this call.
+ * Errors: NB_ERR_ARG, NB_ERR_BOX (rlist >= L/2 of a box), NB_ERR_STATE (no grid),
  * NB_ERR_CUDA; device flag NB_ERR_CAPACITY (list or exclusion overflow). */
 nb_status nb_pairlist_build(nb_ctx* ctx, float rlist, float rbb, const int* excl_off_dev,
                             const int* excl_idx_dev, nb_stream stream);
@@ -195,17 +213,25 @@ nb_status nb_prune(nb_ctx* ctx, const float* xyz_dev, float r_prune, nb_stream s
  * normal pairs by mask bit, force-field-excluded pairs within rc with the
  * correction only.  xyz_dev may be NULL (current coordinates).
  * f_dev: float [n][3], caller order, overwritten.
- * e_dev: double [2] {E_LJ, E_Coulomb} (kJ/mol), overwritten; may be NULL.
- * vir_dev: double [9], W = sum over pairs r_ij (x) F_ij (row-major), with
- * r_ij = x_i - x_j and F_ij the force on i; overwritten; may be NULL.
+ * e_dev: double [nbox][2] {E_LJ, E_Coulomb} per box (kJ/mol), overwritten;
+ * may be NULL.
+ * vir_dev: double [nbox][9], per box W = sum over pairs r_ij (x) F_ij
+ * (row-major), with r_ij = x_i - x_j and F_ij the force on i; overwritten;
+ * may be NULL.
  * Errors: NB_ERR_ARG, NB_ERR_BOX (rc >= L/2 or rc > rlist), NB_ERR_STATE (no
  * list), NB_ERR_CUDA. */
 nb_status nb_compute(nb_ctx* ctx, const nb_params* p, const float* xyz_dev, float* f_dev,
                      double* e_dev, double* vir_dev, nb_stream stream);
 
-/* Synchronise the stream, read the device flags and sizes into *info (may be
- * NULL) and turn a raised flag into its status.  Clears the flags. */
+/* Synchronise the stream, read the device flags and sizes of every box into
+ * *info (totals; may be NULL) and turn a raised flag into its status (the
+ * message names the first box that raised it).  Clears the flags.  Not
+ * callable during stream capture. */
 nb_status nb_check(nb_ctx* ctx, nb_stream stream, nb_info* info);
+
+/* Sizes and flags of one box as read by the last nb_check (host only).
+ * Errors: NB_ERR_ARG (box out of range), NB_ERR_STATE (no nb_check yet). */
+nb_status nb_box_info(nb_ctx* ctx, int box, nb_info* info);
 
 /* --- timing --------------------------------------------------------------- */
 
@@ -228,6 +254,7 @@ nb_status nb_profile_read(nb_ctx* ctx, int* kinds_host, float* ms_host, int max,
  * [nslots], bb_dev: float [nclusters][6] (min xyz, max xyz), col_of_atom_dev:
  * int [n], sc_info_dev: int [n_superclusters][2] = {first cluster, number of
  * clusters} of each super-cluster.  nslots = n_clusters * C from nb_check.
+ * One-box contexts only.
  * Errors: NB_ERR_STATE, NB_ERR_CUDA. */
 nb_status nb_get_grid(nb_ctx* ctx, int* atom_of_slot_dev, int* slot_of_atom_dev,
                       int* col_clu_start_dev, float* xyzq_dev, int* type_slot_dev, float* bb_dev,
@@ -243,7 +270,7 @@ nb_status nb_get_grid(nb_ctx* ctx, int* atom_of_slot_dev, int* slot_of_atom_dev,
  * interaction).  Shift index s encodes (sx, sy, sz) in {-1,0,1}^3 as
  * (sx+1)*9 + (sy+1)*3 + (sz+1), applied to the i side.  Sizes from nb_check
  * (j-entries are indexed by the i-entries' ranges; for the pruned list use
- * the outer list's n_jentries as the array size).
+ * the outer list's n_jentries as the array size).  One-box contexts only.
  * Errors: NB_ERR_STATE, NB_ERR_CUDA. */
 nb_status nb_get_list(nb_ctx* ctx, int which, int* ient_dev, int* cj_dev, uint64_t* mask_dev,
                       nb_stream stream);

@@ -56,7 +56,7 @@ class nb_info(C.Structure):
                 ("jent_capacity", C.c_int64), ("n_pairs_rc", C.c_int64),
                 ("n_cluster_pairs", C.c_int64), ("n_cluster_pairs_pruned", C.c_int64),
                 ("n_superclusters", C.c_int), ("super_size", C.c_int), ("n_launches", C.c_int64),
-                ("flags", C.c_uint32)]
+                ("flags", C.c_uint32), ("n_boxes", C.c_int), ("atom_offset", C.c_int)]
 
 
 class NbError(RuntimeError):
@@ -85,6 +85,8 @@ def load():
             "nb_status_string": ([i], C.c_char_p),
             "nb_lj_combine": ([i, P, P, i, P], st),
             "nb_workspace_query": ([P, i, P, C.c_double, i, C.c_double, C.POINTER(C.c_size_t)], st),
+            "nb_workspace_query_boxes": ([P, i, P, P, C.c_double, i, C.c_double,
+                                          C.POINTER(C.c_size_t)], st),
             "nb_set_workspace": ([P, P, C.c_size_t], st),
             "nb_set_atoms": ([P, i, P, P, i, P, P], st),
             "nb_grid_put": ([P, P, P, P], st),
@@ -93,6 +95,7 @@ def load():
             "nb_prune": ([P, P, C.c_float, P], st),
             "nb_compute": ([P, C.POINTER(nb_params), P, P, P, P, P], st),
             "nb_check": ([P, P, C.POINTER(nb_info)], st),
+            "nb_box_info": ([P, i, C.POINTER(nb_info)], st),
             "nb_get_grid": ([P, P, P, P, P, P, P, P, P, P], st),
             "nb_get_list": ([P, i, P, P, P, P], st),
             "nb_profile": ([P, i], st),
@@ -179,6 +182,27 @@ def nb_workspace_query(ctx, n_atoms: int, box, rlist_max: float, ntypes: int,
     return nbytes.value
 
 
+def _boxes(boxes):
+    """double [nbox][3] host array from one box (3 numbers) or a list of boxes."""
+    import numpy as np
+    b = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+    return b
+
+
+def nb_workspace_query_boxes(ctx, n_atoms, boxes, rlist_max: float, ntypes: int,
+                             list_factor: float = 0.0) -> int:
+    import numpy as np
+    n = np.ascontiguousarray(n_atoms, dtype=np.int32).reshape(-1)
+    b = _boxes(boxes)
+    if b.shape[0] != n.shape[0]:
+        raise ValueError("one box per particle count")
+    nbytes = C.c_size_t()
+    _check(ctx, load().nb_workspace_query_boxes(ctx, int(n.shape[0]), n.ctypes.data, b.ctypes.data,
+                                                float(rlist_max), int(ntypes), float(list_factor),
+                                                C.byref(nbytes)))
+    return nbytes.value
+
+
 def nb_set_workspace(ctx, ws, nbytes: int):
     _check(ctx, load().nb_set_workspace(ctx, _ptr(ws), int(nbytes)))
 
@@ -188,9 +212,10 @@ def nb_set_atoms(ctx, n, q, types, ntypes, c6c12, stream=None):
                                     _stream(stream)))
 
 
-def nb_grid_put(ctx, xyz, box, stream=None):
-    b = (C.c_double * 3)(*[float(v) for v in box])
-    _check(ctx, load().nb_grid_put(ctx, _ptr(xyz), b, _stream(stream)))
+def nb_grid_put(ctx, xyz, boxes, stream=None):
+    """boxes: the edges of one box (3 numbers) or of every box ([nbox][3])."""
+    b = _boxes(boxes)
+    _check(ctx, load().nb_grid_put(ctx, _ptr(xyz), b.ctypes.data, _stream(stream)))
 
 
 def nb_pairlist_build(ctx, rlist, rbb=0.0, excl_off=None, excl_idx=None, stream=None):
@@ -223,6 +248,12 @@ def nb_check(ctx, stream=None, raise_on_error: bool = True) -> nb_info:
     if raise_on_error:
         _check(ctx, s)
     info.status = s
+    return info
+
+
+def nb_box_info(ctx, box: int) -> nb_info:
+    info = nb_info()
+    _check(ctx, load().nb_box_info(ctx, int(box), C.byref(info)))
     return info
 
 
@@ -263,22 +294,28 @@ def nb_grid_put_noalloc(n, xyz, q, types, ntypes, box, cluster_size, atom_of_slo
     _check(None, s)
 
 
-# --- convenience: one box with its torch-allocated workspace ---------------
+# --- convenience: boxes with their torch-allocated workspace ----------------
 
 class Context:
-    """A context bound to one box: allocates the workspace with torch and
-    keeps the per-particle inputs on the device."""
+    """A context for one box (n particles, box = 3 edges) or a batch of boxes
+    (n = particles per box, box = [nbox][3] edges; particle arrays are the
+    boxes' ranges concatenated): allocates the workspace with torch and keeps
+    the per-particle inputs on the device."""
 
     def __init__(self, n, box, rlist_max, q, types, c6c12, cluster_size=8, device=0,
                  list_factor=0.0, stream=None):
+        import numpy as np
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
-        self.n = int(n)
+        counts = np.atleast_1d(np.asarray(n, dtype=np.int64))
+        self.counts = counts
+        self.nbox = int(counts.shape[0])
+        self.n = int(counts.sum())
         self.C = cluster_size
         self.ctx = nb_create(cluster_size, device)
         nt = int(c6c12.shape[0])
-        self.ws_bytes = nb_workspace_query(self.ctx, self.n, box, rlist_max, nt, list_factor)
+        self.ws_bytes = nb_workspace_query_boxes(self.ctx, counts, box, rlist_max, nt, list_factor)
         self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.dev)
         base = self.ws.data_ptr()
         aligned = (base + 255) // 256 * 256

@@ -1,38 +1,59 @@
 // C ABI of nbcluster (declared in include/nbcluster.h): context, workspace
-// carving, argument checks, and the stream-ordered launch sequence of the
-// hot path.  No device allocation happens here; all device data lives in the
-// caller's workspace.
+// planning and carving for one or many boxes, argument checks, and the
+// stream-ordered launch sequence of the hot path.  No device allocation
+// happens here; all device data lives in the caller's workspace.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
-#include "nb_internal.cuh"
 #include "nb_ewald_fit.h"
+#include "nb_internal.cuh"
 
 using namespace nbc;
+
+namespace {
+
+struct BoxPlan {
+    int n, ncol_cap, nclu_cap, nsc_cap;
+    long long ient_cap, jent_cap;
+};
+
+constexpr int kGeoRing = 8;  // pinned staging buffers for box geometry uploads
+
+}  // namespace
 
 struct nb_ctx {
     int C = 8;
     int device = 0;
     int n_sm = 0;
-    // workspace sizes
+    // plan (fixed by nb_workspace_query*)
+    int nbox = 0;
+    std::vector<BoxPlan> plan;
+    std::vector<int> atom_off, col_off, clu_off, sc_off;
+    std::vector<long long> ient_off, jent_off;
+    int ntypes_cap = 0;
+    // workspace
     char* ws_base = nullptr;
     size_t ws_bytes = 0;
-    int n_cap = 0;
-    int ncol_cap = 0;
-    long long nslot_cap = 0, nclu_cap = 0, nsc_cap = 0, ient_cap = 0, jent_cap = 0;
-    int ntypes_cap = 0;
     Workspace ws{};
-    DevState* st_host = nullptr;  // pinned read-back buffer
+    // geometry mirror and upload ring
+    std::vector<BoxGeom> geo_host;
+    bool geo_uploaded = false;
+    BoxGeom* geo_pinned[kGeoRing] = {};
+    cudaEvent_t geo_ev[kGeoRing] = {};
+    bool geo_ev_used[kGeoRing] = {};
+    int geo_slot = 0;
+    // read-back
+    DevState* st_host = nullptr;  // pinned [nbox]
+    std::vector<DevState> last;
+    bool last_valid = false;
     // state
     int n = 0, ntypes = 0;
     bool have_atoms = false, have_grid = false, have_list = false, have_pruned = false;
-    GridGeom geom{};
     float rlist = 0.f, r_prune = 0.f;
-    DevState last{};
-    bool last_valid = false;
     long long n_launches = 0;
     // timing spans (nb_profile)
     static constexpr int kMaxSpans = 256;
@@ -43,7 +64,6 @@ struct nb_ctx {
     char err[512] = {0};
 };
 
-// Record the start of a timed span (returns its slot or -1).
 static int span_begin(nb_ctx* c, int kind, cudaStream_t s) {
     if (!c->prof || c->ev_n >= nb_ctx::kMaxSpans) return -1;
     const int k = c->ev_n++;
@@ -70,9 +90,9 @@ static nb_status cuda_fail(nb_ctx* c, cudaError_t e, const char* where) {
     return fail(c, NB_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-#define NB_CUDA(ctx, call)                                   \
-    do {                                                     \
-        cudaError_t e_ = (call);                             \
+#define NB_CUDA(ctx, call)                                       \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
     } while (0)
 
@@ -108,13 +128,40 @@ static float dummy_spacing(const float L[3]) {
     return g;
 }
 
-struct Sizes {
-    int n, ncol, ntypes, S;
-    long long nslot, nclu, nsc, ient, jent;
-};
+// Capacities of one box holding n particles in box L with lists up to rlist.
+// The number of j-entries is estimated from the density: j-clusters whose
+// bounding box is within rlist of a super-cluster's box (half of them,
+// Newton's third law) -- the cluster density times the volume of the rounded
+// box of side (super-cluster extent + cluster extent) dilated by rlist --
+// scaled by factor.
+static BoxPlan plan_box(int n, const float L[3], int C, double rlist, double factor) {
+    BoxPlan z{};
+    int nx, ny;
+    grid_dims(n, L, C, &nx, &ny);
+    const int S = super_size(C);
+    z.n = n;
+    z.ncol_cap = nx * ny;
+    const long long nslot = (long long)n + (long long)z.ncol_cap * (C - 1);
+    z.nclu_cap = (int)(nslot / C + 1);
+    z.nsc_cap = z.nclu_cap / S + z.ncol_cap + 1;
+    const double V = (double)L[0] * L[1] * L[2];
+    const double wx = (double)L[0] / nx, wy = (double)L[1] / ny;
+    const double rho = n > 0 ? n / V : 1.0;
+    const double hz = C / (rho * wx * wy);
+    const double a = 2 * wx, b = 2 * wy, c = (S + 1) * hz, r = rlist;
+    const double vm = a * b * c + 2 * r * (a * b + b * c + c * a) + M_PI * r * r * (a + b + c) +
+                      4.0 / 3.0 * M_PI * r * r * r;
+    const double rho_c = (double)z.nclu_cap / V;
+    double per = 0.5 * rho_c * vm + S;
+    const double maxper = 0.5 * 27.0 * (double)z.nclu_cap + 1.0;
+    if (per > maxper) per = maxper;
+    z.jent_cap = (long long)std::ceil(factor * per * (double)z.nsc_cap) + 64;
+    z.ient_cap = (long long)z.nsc_cap * 27 + z.jent_cap / kJChunk + 64;
+    return z;
+}
 
 // Lay the workspace out from base (nullptr: only count bytes).
-static size_t carve(const Sizes& z, char* base, Workspace* ws) {
+static size_t carve(const nb_ctx* c, char* base, Workspace* ws) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         off = (off + 255) & ~(size_t)255;
@@ -122,69 +169,159 @@ static size_t carve(const Sizes& z, char* base, Workspace* ws) {
         off += bytes;
         return p;
     };
+    const int nb = c->nbox, C = c->C, S = super_size(C);
     Workspace w{};
-    w.st = (DevState*)take(sizeof(DevState));
-    w.acc = (Accum*)take(sizeof(Accum));
-    w.xw = (float4*)take(sizeof(float4) * z.n);
-    w.woff = (float4*)take(sizeof(float4) * z.n);
-    w.col_of_atom = (int*)take(sizeof(int) * z.n);
-    w.rank_in_col = (int*)take(sizeof(int) * z.n);
-    w.slot_of_atom = (int*)take(sizeof(int) * z.n);
-    w.q = (float*)take(sizeof(float) * z.n);
-    w.type = (int*)take(sizeof(int) * z.n);
-    w.col_count = (int*)take(sizeof(int) * z.ncol);
-    w.col_atom_start = (int*)take(sizeof(int) * z.ncol);
-    w.col_clu_start = (int*)take(sizeof(int) * (z.ncol + 1));
-    w.col_sc_start = (int*)take(sizeof(int) * (z.ncol + 1));
-    w.sc_info = (int2*)take(sizeof(int2) * z.nsc);
-    w.keys = (unsigned long long*)take(sizeof(unsigned long long) * z.n);
-    w.xyzq = (float4*)take(sizeof(float4) * z.nslot);
-    w.atom_of_slot = (int*)take(sizeof(int) * z.nslot);
-    w.type_slot = (int*)take(sizeof(int) * z.nslot);
-    w.fslot = (float4*)take(sizeof(float4) * z.nslot);
-    w.bb = (float4*)take(sizeof(float4) * 2 * z.nclu);
-    w.ient = (int4*)take(sizeof(int4) * z.ient);
-    w.cj = (int*)take(sizeof(int) * z.jent);
-    w.mask = (unsigned long long*)take(sizeof(unsigned long long) * z.jent * z.S);
-    w.ient_p = (int4*)take(sizeof(int4) * z.ient);
-    w.cj_p = (int*)take(sizeof(int) * z.jent);
-    w.mask_p = (unsigned long long*)take(sizeof(unsigned long long) * z.jent * z.S);
-    w.jstride = z.jent;
-    w.c6c12 = (float2*)take(sizeof(float2) * z.ntypes * z.ntypes);
+    w.nbox = nb;
+    w.atom_total = c->atom_off[nb];
+    w.col_total = c->col_off[nb];
+    w.clu_total = c->clu_off[nb];
+    w.sc_total = c->sc_off[nb];
+    w.ient_total = c->ient_off[nb];
+    w.jstride = c->jent_off[nb];
+    const size_t na = w.atom_total > 0 ? w.atom_total : 1;
+    w.st = (DevState*)take(sizeof(DevState) * nb);
+    w.acc = (Accum*)take(sizeof(Accum) * nb);
+    w.geo = (BoxGeom*)take(sizeof(BoxGeom) * nb);
+    w.lay.atom_off = (int*)take(sizeof(int) * (nb + 1));
+    w.lay.col_off = (int*)take(sizeof(int) * (nb + 1));
+    w.lay.clu_off = (int*)take(sizeof(int) * (nb + 1));
+    w.lay.sc_off = (int*)take(sizeof(int) * (nb + 1));
+    w.lay.ient_off = (long long*)take(sizeof(long long) * (nb + 1));
+    w.lay.jent_off = (long long*)take(sizeof(long long) * (nb + 1));
+    w.xw = (float4*)take(sizeof(float4) * na);
+    w.woff = (float4*)take(sizeof(float4) * na);
+    w.col_of_atom = (int*)take(sizeof(int) * na);
+    w.rank_in_col = (int*)take(sizeof(int) * na);
+    w.slot_of_atom = (int*)take(sizeof(int) * na);
+    w.q = (float*)take(sizeof(float) * na);
+    w.type = (int*)take(sizeof(int) * na);
+    w.col_count = (int*)take(sizeof(int) * w.col_total);
+    w.col_atom_start = (int*)take(sizeof(int) * w.col_total);
+    w.col_clu_start = (int*)take(sizeof(int) * w.col_total);
+    w.col_sc_start = (int*)take(sizeof(int) * w.col_total);
+    w.sc_info = (int2*)take(sizeof(int2) * w.sc_total);
+    w.keys = (unsigned long long*)take(sizeof(unsigned long long) * na);
+    const size_t ns = (size_t)w.clu_total * C;
+    w.xyzq = (float4*)take(sizeof(float4) * ns);
+    w.atom_of_slot = (int*)take(sizeof(int) * ns);
+    w.type_slot = (int*)take(sizeof(int) * ns);
+    w.fslot = (float4*)take(sizeof(float4) * ns);
+    w.bb = (float4*)take(sizeof(float4) * 2 * (size_t)w.clu_total);
+    w.ient = (int4*)take(sizeof(int4) * w.ient_total);
+    w.cj = (int*)take(sizeof(int) * w.jstride);
+    w.mask = (unsigned long long*)take(sizeof(unsigned long long) * w.jstride * S);
+    w.ient_p = (int4*)take(sizeof(int4) * w.ient_total);
+    w.cj_p = (int*)take(sizeof(int) * w.jstride);
+    w.mask_p = (unsigned long long*)take(sizeof(unsigned long long) * w.jstride * S);
+    w.c6c12 = (float2*)take(sizeof(float2) * kMaxTypes * kMaxTypes);
     if (ws) *ws = w;
     return (off + 255) & ~(size_t)255;
 }
 
-// Sizes for n particles in box L with lists up to rlist.  The number of
-// j-entries is estimated from the density: j-clusters whose bounding box is
-// within rlist of a super-cluster's box (half of them, Newton's third law),
-// i.e. the cluster density times the volume of the rounded box of side
-// (super-cluster extent + cluster extent) dilated by rlist, scaled by factor.
-static Sizes plan(int n, const float L[3], int C, double rlist, int ntypes, double factor) {
-    Sizes z{};
-    int nx, ny;
-    grid_dims(n, L, C, &nx, &ny);
-    z.n = n > 0 ? n : 1;
-    z.ncol = nx * ny;
-    z.ntypes = ntypes;
-    z.S = super_size(C);
-    z.nslot = (long long)n + (long long)z.ncol * (C - 1);
-    z.nclu = z.nslot / C + 1;
-    z.nsc = z.nclu / z.S + z.ncol + 1;
-    const double V = (double)L[0] * L[1] * L[2];
-    const double wx = (double)L[0] / nx, wy = (double)L[1] / ny;
-    const double rho = n > 0 ? n / V : 1.0;
-    const double hz = C / (rho * wx * wy);
-    const double a = 2 * wx, b = 2 * wy, c = (z.S + 1) * hz, r = rlist;
-    const double vm = a * b * c + 2 * r * (a * b + b * c + c * a) + M_PI * r * r * (a + b + c) +
-                      4.0 / 3.0 * M_PI * r * r * r;
-    const double rho_c = (double)z.nclu / V;
-    double per = 0.5 * rho_c * vm + z.S;
-    const double maxper = 0.5 * 27.0 * (double)z.nclu + 1.0;
-    if (per > maxper) per = maxper;
-    z.jent = (long long)std::ceil(factor * per * (double)z.nsc) + 1024;
-    z.ient = z.nsc * 27 + z.jent / kJChunk + 1024;
-    return z;
+static void set_plan(nb_ctx* c, const std::vector<BoxPlan>& plans) {
+    const int nb = (int)plans.size();
+    c->nbox = nb;
+    c->plan = plans;
+    c->atom_off.assign(nb + 1, 0);
+    c->col_off.assign(nb + 1, 0);
+    c->clu_off.assign(nb + 1, 0);
+    c->sc_off.assign(nb + 1, 0);
+    c->ient_off.assign(nb + 1, 0);
+    c->jent_off.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+        c->atom_off[b + 1] = c->atom_off[b] + plans[b].n;
+        c->col_off[b + 1] = c->col_off[b] + plans[b].ncol_cap + 1;
+        c->clu_off[b + 1] = c->clu_off[b] + plans[b].nclu_cap;
+        c->sc_off[b + 1] = c->sc_off[b] + plans[b].nsc_cap;
+        c->ient_off[b + 1] = c->ient_off[b] + plans[b].ient_cap;
+        c->jent_off[b + 1] = c->jent_off[b] + plans[b].jent_cap;
+    }
+    c->ntypes_cap = kMaxTypes;
+    c->ws_base = nullptr;
+    c->have_atoms = c->have_grid = c->have_list = c->have_pruned = false;
+    c->geo_uploaded = false;
+    c->last_valid = false;
+}
+
+// Upload the boxes' geometry if it changed (pinned ring, each slot reused
+// only after its previous copy has completed).
+static nb_status upload_geometry(nb_ctx* c, const std::vector<BoxGeom>& geo, cudaStream_t s) {
+    if (c->geo_uploaded && memcmp(geo.data(), c->geo_host.data(), sizeof(BoxGeom) * c->nbox) == 0)
+        return NB_OK;
+    const int k = c->geo_slot;
+    c->geo_slot = (k + 1) % kGeoRing;
+    if (c->geo_ev_used[k]) NB_CUDA(c, cudaEventSynchronize(c->geo_ev[k]));
+    memcpy(c->geo_pinned[k], geo.data(), sizeof(BoxGeom) * c->nbox);
+    NB_CUDA(c, cudaMemcpyAsync(c->ws.geo, c->geo_pinned[k], sizeof(BoxGeom) * c->nbox,
+                               cudaMemcpyHostToDevice, s));
+    NB_CUDA(c, cudaEventRecord(c->geo_ev[k], s));
+    c->geo_ev_used[k] = true;
+    c->geo_host = geo;
+    c->geo_uploaded = true;
+    return NB_OK;
+}
+
+static void release_host(nb_ctx* c) {
+    for (int k = 0; k < kGeoRing; ++k) {
+        if (c->geo_pinned[k]) cudaFreeHost(c->geo_pinned[k]);
+        if (c->geo_ev[k]) cudaEventDestroy(c->geo_ev[k]);
+        c->geo_pinned[k] = nullptr;
+        c->geo_ev[k] = nullptr;
+        c->geo_ev_used[k] = false;
+    }
+    if (c->st_host) cudaFreeHost(c->st_host);
+    c->st_host = nullptr;
+}
+
+// Reset every box's list counters.
+static __global__ void k_list_reset(Workspace ws) {
+    for (int b = threadIdx.x; b < ws.nbox; b += blockDim.x) {
+        ws.st[b].n_ient = 0;
+        ws.st[b].n_jent = 0;
+        ws.st[b].n_keys = 0;
+    }
+}
+
+static float min_edge(const nb_ctx* c) {
+    float m = INFINITY;
+    for (int b = 0; b < c->nbox; ++b)
+        for (int k = 0; k < 3; ++k) m = fminf(m, c->geo_host[b].L[k]);
+    return m;
+}
+
+static void fill_info(const nb_ctx* c, int b0, int b1, nb_info* info, unsigned flags) {
+    memset(info, 0, sizeof(*info));
+    info->n_jentries_pruned = c->have_pruned ? 0 : -1;
+    info->n_cluster_pairs_pruned = c->have_pruned ? 0 : -1;
+    for (int b = b0; b < b1; ++b) {
+        const DevState& d = c->last[b];
+        info->n_atoms += c->plan[b].n;
+        if (c->have_grid) {
+            info->n_clusters += d.nclu;
+            info->n_superclusters += d.nsc;
+        }
+        if (c->have_list) {
+            info->n_ientries += (int64_t)d.n_ient;
+            info->n_jentries += (int64_t)d.n_jent;
+            info->n_cluster_pairs += (int64_t)d.n_keys;
+        }
+        if (c->have_pruned) {
+            info->n_jentries_pruned += (int64_t)d.n_jent_pruned;
+            info->n_cluster_pairs_pruned += (int64_t)d.n_keys_pruned;
+        }
+        info->n_pairs_rc += (int64_t)d.n_pairs_rc;
+        info->ient_capacity += c->plan[b].ient_cap;
+        info->jent_capacity += c->plan[b].jent_cap;
+    }
+    if (b1 - b0 == 1 && c->geo_uploaded) {
+        info->nx = c->geo_host[b0].nx;
+        info->ny = c->geo_host[b0].ny;
+    }
+    info->super_size = super_size(c->C);
+    info->n_launches = c->n_launches;
+    info->n_boxes = b1 - b0;
+    info->atom_offset = c->atom_off[b0];
+    info->flags = flags;
 }
 
 extern "C" {
@@ -215,7 +352,6 @@ nb_status nb_create(nb_ctx** out, const nb_options* opt) {
     c->device = dev;
     cudaError_t e = cudaSetDevice(dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->st_host, sizeof(DevState));
     if (e != cudaSuccess) {
         delete c;
         return NB_ERR_CUDA;
@@ -226,7 +362,7 @@ nb_status nb_create(nb_ctx** out, const nb_options* opt) {
 
 nb_status nb_destroy(nb_ctx* c) {
     if (!c) return NB_ERR_ARG;
-    if (c->st_host) cudaFreeHost(c->st_host);
+    release_host(c);
     for (int k = 0; k < 2 * nb_ctx::kMaxSpans; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
@@ -259,53 +395,72 @@ nb_status nb_lj_combine(int ntypes, const double* sigma, const double* eps, int 
     return NB_OK;
 }
 
-nb_status nb_workspace_query(nb_ctx* c, int n, const double* box, double rlist_max, int ntypes,
-                             double list_factor, size_t* bytes) {
-    if (!c || !bytes || n < 0 || ntypes <= 0) return fail(c, NB_ERR_ARG, "workspace_query: bad argument");
+nb_status nb_workspace_query_boxes(nb_ctx* c, int nbox, const int* n_atoms, const double* boxes,
+                                   double rlist_max, int ntypes, double list_factor, size_t* bytes) {
+    if (!c || !bytes || nbox <= 0 || !n_atoms || !boxes || ntypes <= 0)
+        return fail(c, NB_ERR_ARG, "workspace_query: bad argument");
+    if (nbox > kMaxBoxes) return fail(c, NB_ERR_ARG, "at most %d boxes", kMaxBoxes);
     if (ntypes > kMaxTypes) return fail(c, NB_ERR_ARG, "at most %d LJ types", kMaxTypes);
-    if (!box_ok(box)) return fail(c, NB_ERR_BOX, "box edges must be positive");
     if (!(rlist_max > 0.0)) return fail(c, NB_ERR_ARG, "rlist_max must be positive");
     if (list_factor == 0.0) list_factor = 1.5;
     if (list_factor < 1.0) return fail(c, NB_ERR_ARG, "list_factor must be >= 1");
-    const float L[3] = {(float)box[0], (float)box[1], (float)box[2]};
-    const Sizes z = plan(n, L, c->C, rlist_max, kMaxTypes, list_factor);
-    *bytes = carve(z, nullptr, nullptr);
-    // remember the plan for nb_set_workspace
-    c->n_cap = z.n;
-    c->ncol_cap = z.ncol;
-    c->nslot_cap = z.nslot;
-    c->nclu_cap = z.nclu;
-    c->nsc_cap = z.nsc;
-    c->ient_cap = z.ient;
-    c->jent_cap = z.jent;
-    c->ntypes_cap = kMaxTypes;
-    (void)ntypes;
+    std::vector<BoxPlan> plans(nbox);
+    long long total = 0;
+    for (int b = 0; b < nbox; ++b) {
+        if (n_atoms[b] < 0) return fail(c, NB_ERR_ARG, "negative particle count");
+        if (!box_ok(boxes + 3 * b)) return fail(c, NB_ERR_BOX, "box %d: edges must be positive", b);
+        const float L[3] = {(float)boxes[3 * b], (float)boxes[3 * b + 1], (float)boxes[3 * b + 2]};
+        plans[b] = plan_box(n_atoms[b], L, c->C, rlist_max, list_factor);
+        total += n_atoms[b];
+    }
+    if (total > 0x7fffffffLL) return fail(c, NB_ERR_ARG, "too many particles");
+    set_plan(c, plans);
+    *bytes = carve(c, nullptr, nullptr);
     return NB_OK;
+}
+
+nb_status nb_workspace_query(nb_ctx* c, int n, const double* box, double rlist_max, int ntypes,
+                             double list_factor, size_t* bytes) {
+    if (!c) return NB_ERR_ARG;
+    if (!box_ok(box)) return fail(c, NB_ERR_BOX, "box edges must be positive");
+    return nb_workspace_query_boxes(c, 1, &n, box, rlist_max, ntypes, list_factor, bytes);
 }
 
 nb_status nb_set_workspace(nb_ctx* c, void* ws, size_t bytes) {
     if (!c || !ws) return fail(c, NB_ERR_ARG, "set_workspace: null");
     if (((uintptr_t)ws & 255) != 0) return fail(c, NB_ERR_ARG, "workspace must be 256-byte aligned");
-    if (c->n_cap == 0) return fail(c, NB_ERR_STATE, "call nb_workspace_query first");
-    Sizes z{};
-    z.n = c->n_cap;
-    z.ncol = c->ncol_cap;
-    z.ntypes = c->ntypes_cap;
-    z.nslot = c->nslot_cap;
-    z.nclu = c->nclu_cap;
-    z.nsc = c->nsc_cap;
-    z.S = super_size(c->C);
-    z.ient = c->ient_cap;
-    z.jent = c->jent_cap;
-    const size_t need = carve(z, nullptr, nullptr);
+    if (c->nbox == 0) return fail(c, NB_ERR_STATE, "call nb_workspace_query first");
+    const size_t need = carve(c, nullptr, nullptr);
     if (bytes < need) return fail(c, NB_ERR_CAPACITY, "workspace has %zu bytes, needs %zu", bytes, need);
     NB_CUDA(c, cudaSetDevice(c->device));
-    carve(z, (char*)ws, &c->ws);
+    carve(c, (char*)ws, &c->ws);
     c->ws_base = (char*)ws;
     c->ws_bytes = bytes;
     c->have_atoms = c->have_grid = c->have_list = c->have_pruned = false;
     c->last_valid = false;
-    NB_CUDA(c, cudaMemset(c->ws.st, 0, sizeof(DevState)));
+    c->geo_uploaded = false;
+    release_host(c);
+    for (int k = 0; k < kGeoRing; ++k) {
+        NB_CUDA(c, cudaMallocHost((void**)&c->geo_pinned[k], sizeof(BoxGeom) * c->nbox));
+        NB_CUDA(c, cudaEventCreateWithFlags(&c->geo_ev[k], cudaEventDisableTiming));
+    }
+    NB_CUDA(c, cudaMallocHost((void**)&c->st_host, sizeof(DevState) * c->nbox));
+    c->last.assign(c->nbox, DevState{});
+    const int nb = c->nbox;
+    NB_CUDA(c, cudaMemset(c->ws.st, 0, sizeof(DevState) * nb));
+    NB_CUDA(c, cudaMemset(c->ws.geo, 0, sizeof(BoxGeom) * nb));
+    NB_CUDA(c, cudaMemcpy((void*)c->ws.lay.atom_off, c->atom_off.data(), sizeof(int) * (nb + 1),
+                          cudaMemcpyHostToDevice));
+    NB_CUDA(c, cudaMemcpy((void*)c->ws.lay.col_off, c->col_off.data(), sizeof(int) * (nb + 1),
+                          cudaMemcpyHostToDevice));
+    NB_CUDA(c, cudaMemcpy((void*)c->ws.lay.clu_off, c->clu_off.data(), sizeof(int) * (nb + 1),
+                          cudaMemcpyHostToDevice));
+    NB_CUDA(c, cudaMemcpy((void*)c->ws.lay.sc_off, c->sc_off.data(), sizeof(int) * (nb + 1),
+                          cudaMemcpyHostToDevice));
+    NB_CUDA(c, cudaMemcpy((void*)c->ws.lay.ient_off, c->ient_off.data(), sizeof(long long) * (nb + 1),
+                          cudaMemcpyHostToDevice));
+    NB_CUDA(c, cudaMemcpy((void*)c->ws.lay.jent_off, c->jent_off.data(), sizeof(long long) * (nb + 1),
+                          cudaMemcpyHostToDevice));
     return NB_OK;
 }
 
@@ -315,7 +470,8 @@ nb_status nb_set_atoms(nb_ctx* c, int n, const float* q, const int* type, int nt
     if (!c->ws_base) return fail(c, NB_ERR_STATE, "no workspace");
     if (n < 0 || (n > 0 && (!q || !type)) || ntypes <= 0 || !c6c12)
         return fail(c, NB_ERR_ARG, "set_atoms: bad argument");
-    if (n > c->n_cap) return fail(c, NB_ERR_CAPACITY, "%d particles, workspace holds %d", n, c->n_cap);
+    if (n != c->atom_off[c->nbox])
+        return fail(c, NB_ERR_CAPACITY, "%d particles, the workspace is planned for %d", n, c->atom_off[c->nbox]);
     if (ntypes > c->ntypes_cap) return fail(c, NB_ERR_CAPACITY, "too many LJ types");
     cudaStream_t s = (cudaStream_t)stream;
     if (n > 0) {
@@ -331,27 +487,38 @@ nb_status nb_set_atoms(nb_ctx* c, int n, const float* q, const int* type, int nt
     return NB_OK;
 }
 
-nb_status nb_grid_put(nb_ctx* c, const float* xyz, const double* box, nb_stream stream) {
+nb_status nb_grid_put(nb_ctx* c, const float* xyz, const double* boxes, nb_stream stream) {
     if (!c) return NB_ERR_ARG;
     if (!c->have_atoms) return fail(c, NB_ERR_STATE, "nb_set_atoms first");
     if (c->n > 0 && !xyz) return fail(c, NB_ERR_ARG, "xyz is null");
-    if (!box_ok(box)) return fail(c, NB_ERR_BOX, "box edges must be positive");
-    GridGeom g{};
-    for (int k = 0; k < 3; ++k) g.L[k] = (float)box[k];
-    grid_dims(c->n, g.L, c->C, &g.nx, &g.ny);
-    if (g.nx * g.ny > c->ncol_cap) return fail(c, NB_ERR_CAPACITY, "grid has more columns than the workspace");
-    if ((long long)c->n + (long long)g.nx * g.ny * (c->C - 1) > c->nslot_cap)
-        return fail(c, NB_ERR_CAPACITY, "grid may need more slots than the workspace");
-    g.inv_x = (float)((double)g.nx / (double)g.L[0]);
-    g.inv_y = (float)((double)g.ny / (double)g.L[1]);
-    g.dummy_g = dummy_spacing(g.L);
+    if (!boxes) return fail(c, NB_ERR_BOX, "box is null");
+    std::vector<BoxGeom> geo(c->nbox);
+    for (int b = 0; b < c->nbox; ++b) {
+        if (!box_ok(boxes + 3 * b)) return fail(c, NB_ERR_BOX, "box %d: edges must be positive", b);
+        BoxGeom& g = geo[b];
+        memset(&g, 0, sizeof(g));
+        for (int k = 0; k < 3; ++k) g.L[k] = (float)boxes[3 * b + k];
+        const int nb_atoms = c->plan[b].n;
+        grid_dims(nb_atoms, g.L, c->C, &g.nx, &g.ny);
+        if (g.nx * g.ny > c->plan[b].ncol_cap)
+            return fail(c, NB_ERR_CAPACITY, "box %d: grid has more columns than the workspace", b);
+        if ((long long)nb_atoms + (long long)g.nx * g.ny * (c->C - 1) > (long long)c->plan[b].nclu_cap * c->C)
+            return fail(c, NB_ERR_CAPACITY, "box %d: grid may need more slots than the workspace", b);
+        g.inv_x = (float)((double)g.nx / (double)g.L[0]);
+        g.inv_y = (float)((double)g.ny / (double)g.L[1]);
+        g.inv_cx = (float)g.nx / g.L[0];
+        g.inv_cy = (float)g.ny / g.L[1];
+        g.dummy_g = dummy_spacing(g.L);
+    }
     NB_CUDA(c, cudaSetDevice(c->device));
-    const int sp = span_begin(c, NB_KERNEL_GRID, (cudaStream_t)stream);
-    cudaError_t e = launch_grid(c->ws, g, c->n, c->C, c->ntypes, xyz, c->n_sm, (cudaStream_t)stream);
-    span_end(c, sp, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    nb_status st = upload_geometry(c, geo, s);
+    if (st != NB_OK) return st;
+    const int sp = span_begin(c, NB_KERNEL_GRID, s);
+    cudaError_t e = launch_grid(c->ws, c->C, c->ntypes, xyz, s);
+    span_end(c, sp, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "grid kernels");
     c->n_launches += kLaunchesGrid;
-    c->geom = g;
     c->have_grid = true;
     c->have_list = c->have_pruned = false;
     c->last_valid = false;
@@ -364,18 +531,15 @@ nb_status nb_pairlist_build(nb_ctx* c, float rlist, float rbb, const int* excl_o
     if (!c->have_grid) return fail(c, NB_ERR_STATE, "nb_grid_put first");
     if (!(rlist > 0.f) || !(rbb >= 0.f) || ((excl_off == nullptr) != (excl_idx == nullptr)))
         return fail(c, NB_ERR_ARG, "pairlist_build: bad argument");
-    for (int k = 0; k < 3; ++k)
-        if (!(rlist < 0.5f * c->geom.L[k])) return fail(c, NB_ERR_BOX, "rlist must be below half the box");
+    if (!(rlist < 0.5f * min_edge(c))) return fail(c, NB_ERR_BOX, "rlist must be below half the box");
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(c, cudaSetDevice(c->device));
-    NB_CUDA(c, cudaMemsetAsync(c->ws.st, 0, 2 * sizeof(unsigned long long), s));
-    NB_CUDA(c, cudaMemsetAsync(&c->ws.st->n_keys, 0, sizeof(unsigned long long), s));
+    k_list_reset<<<1, 256, 0, s>>>(c->ws);
     const int sp = span_begin(c, NB_KERNEL_SEARCH, s);
-    cudaError_t e = launch_search(c->ws, c->geom, c->C, c->nclu_cap, rlist, rbb, excl_off, excl_idx,
-                                  c->ient_cap, c->jent_cap, c->n, c->n_sm, s);
+    cudaError_t e = launch_search(c->ws, c->C, rlist, rbb, excl_off, excl_idx, c->n_sm, s);
     span_end(c, sp, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "search kernel");
-    c->n_launches += kLaunchesSearch;
+    c->n_launches += kLaunchesSearch + 1;
     c->rlist = rlist;
     c->have_list = true;
     c->have_pruned = false;
@@ -388,7 +552,7 @@ nb_status nb_set_coords(nb_ctx* c, const float* xyz, nb_stream stream) {
     if (!c->have_grid) return fail(c, NB_ERR_STATE, "nb_grid_put first");
     if (!xyz && c->n > 0) return fail(c, NB_ERR_ARG, "xyz is null");
     NB_CUDA(c, cudaSetDevice(c->device));
-    cudaError_t e = launch_set_coords(c->ws, (int)c->nslot_cap, c->C, xyz, (cudaStream_t)stream);
+    cudaError_t e = launch_set_coords(c->ws, c->C, xyz, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_coords kernel");
     c->n_launches += kLaunchesSetCoords;
     return NB_OK;
@@ -398,14 +562,13 @@ nb_status nb_prune(nb_ctx* c, const float* xyz, float r_prune, nb_stream stream)
     if (!c) return NB_ERR_ARG;
     if (!c->have_list) return fail(c, NB_ERR_STATE, "nb_pairlist_build first");
     if (!(r_prune > 0.f)) return fail(c, NB_ERR_ARG, "r_prune must be positive");
-    for (int k = 0; k < 3; ++k)
-        if (!(r_prune < 0.5f * c->geom.L[k])) return fail(c, NB_ERR_BOX, "r_prune must be below half the box");
+    if (!(r_prune < 0.5f * min_edge(c))) return fail(c, NB_ERR_BOX, "r_prune must be below half the box");
     if (xyz) {
         nb_status st = nb_set_coords(c, xyz, stream);
         if (st != NB_OK) return st;
     }
     const int sp = span_begin(c, NB_KERNEL_PRUNE, (cudaStream_t)stream);
-    cudaError_t e = launch_prune(c->ws, c->geom, c->C, r_prune, c->ient_cap, c->n_sm, (cudaStream_t)stream);
+    cudaError_t e = launch_prune(c->ws, c->C, r_prune, c->n_sm, (cudaStream_t)stream);
     span_end(c, sp, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "prune kernel");
     c->n_launches += kLaunchesPrune;
@@ -422,8 +585,7 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     if (!c->have_list) return fail(c, NB_ERR_STATE, "nb_pairlist_build first");
     if (p->elec != NB_ELEC_RF && p->elec != NB_ELEC_EWALD) return fail(c, NB_ERR_ARG, "unknown electrostatics");
     if (!(p->rc > 0.f)) return fail(c, NB_ERR_ARG, "rc must be positive");
-    for (int k = 0; k < 3; ++k)
-        if (!(p->rc < 0.5f * c->geom.L[k])) return fail(c, NB_ERR_BOX, "rc must be below half the box");
+    if (!(p->rc < 0.5f * min_edge(c))) return fail(c, NB_ERR_BOX, "rc must be below half the box");
     const float rlive = c->have_pruned ? c->r_prune : c->rlist;
     if (p->rc > rlive) return fail(c, NB_ERR_BOX, "rc above the list radius");
     if (p->elec == NB_ELEC_EWALD && !(p->beta >= 0.f)) return fail(c, NB_ERR_ARG, "beta must be >= 0");
@@ -449,16 +611,14 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     fp.beta3 = (float)((double)p->beta * p->beta * p->beta);
     fp.use_fit = ((double)p->beta * p->beta * rc * rc <= (double)kEwaldFitWMax) ? 1 : 0;
     fp.ntypes = c->ntypes;
-    for (int d = 0; d < 3; ++d) fp.L[d] = c->geom.L[d];
     fp.use_pruned = c->have_pruned ? 1 : 0;
-    fp.ient_cap = c->ient_cap;
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(c, cudaSetDevice(c->device));
     const int sp = span_begin(c, NB_KERNEL_FORCE, s);
-    cudaError_t e = launch_force(c->ws, fp, c->C, c->n_sm, c->nslot_cap, s);
+    cudaError_t e = launch_force(c->ws, fp, c->C, c->n_sm, s);
     span_end(c, sp, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "force kernel");
-    e = launch_finalize(c->ws, fp, c->n, f, e_out, vir_out, s);
+    e = launch_finalize(c->ws, fp, f, e_out, vir_out, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
     c->n_launches += 2 + (fp.want_energy ? 1 : 0);
     return NB_OK;
@@ -469,39 +629,39 @@ nb_status nb_check(nb_ctx* c, nb_stream stream, nb_info* info) {
     if (!c->ws_base) return fail(c, NB_ERR_STATE, "no workspace");
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(c, cudaSetDevice(c->device));
-    NB_CUDA(c, cudaMemcpyAsync(c->st_host, c->ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(c, cudaMemcpyAsync(c->st_host, c->ws.st, sizeof(DevState) * c->nbox, cudaMemcpyDeviceToHost, s));
     NB_CUDA(c, cudaStreamSynchronize(s));
-    c->last = *c->st_host;
+    unsigned flags = 0;
+    int worst = -1;
+    for (int b = 0; b < c->nbox; ++b) {
+        c->last[b] = c->st_host[b];
+        if (c->last[b].flags && worst < 0) worst = b;
+        flags |= c->last[b].flags;
+    }
     c->last_valid = true;
-    const unsigned flags = c->last.flags;
     if (flags) {
-        NB_CUDA(c, cudaMemsetAsync(&c->ws.st->flags, 0, sizeof(unsigned), s));
+        for (int b = 0; b < c->nbox; ++b)
+            if (c->last[b].flags) NB_CUDA(c, cudaMemsetAsync(&c->ws.st[b].flags, 0, sizeof(unsigned), s));
         NB_CUDA(c, cudaStreamSynchronize(s));
     }
-    if (info) {
-        info->n_atoms = c->n;
-        info->nx = c->geom.nx;
-        info->ny = c->geom.ny;
-        info->n_clusters = c->have_grid ? c->last.nclu : 0;
-        info->n_ientries = c->have_list ? (int64_t)c->last.n_ient : 0;
-        info->n_jentries = c->have_list ? (int64_t)c->last.n_jent : 0;
-        info->n_jentries_pruned = c->have_pruned ? (int64_t)c->last.n_jent_pruned : -1;
-        info->ient_capacity = c->ient_cap;
-        info->jent_capacity = c->jent_cap;
-        info->n_pairs_rc = (int64_t)c->last.n_pairs_rc;
-        info->n_superclusters = c->have_grid ? c->last.nsc : 0;
-        info->n_cluster_pairs = c->have_list ? (int64_t)c->last.n_keys : 0;
-        info->n_cluster_pairs_pruned = c->have_pruned ? (int64_t)c->last.n_keys_pruned : -1;
-        info->super_size = super_size(c->C);
-        info->n_launches = c->n_launches;
-        info->flags = flags;
-    }
-    if (flags & (1u << NB_ERR_COORD)) return fail(c, NB_ERR_COORD, "a coordinate was outside [-L, 2L)");
+    if (info) fill_info(c, 0, c->nbox, info, flags);
+    if (flags & (1u << NB_ERR_COORD))
+        return fail(c, NB_ERR_COORD, "box %d: a coordinate was outside [-L, 2L)", worst);
     if (flags & (1u << NB_ERR_CAPACITY))
-        return fail(c, NB_ERR_CAPACITY, "device capacity exceeded (list %llu/%lld j-entries, longest column %d)",
-                    (unsigned long long)c->last.n_jent, c->jent_cap, c->last.max_col);
+        return fail(c, NB_ERR_CAPACITY, "box %d: device capacity exceeded (list %llu/%lld j-entries, longest column %d)",
+                    worst, (unsigned long long)c->last[worst].n_jent, c->plan[worst].jent_cap,
+                    c->last[worst].max_col);
+    if (flags & (1u << NB_ERR_ARG)) return fail(c, NB_ERR_ARG, "box %d: a type or exclusion index out of range", worst);
     if (flags & (1u << NB_ERR_TIMEOUT)) return fail(c, NB_ERR_TIMEOUT, "a bounded device wait expired");
     if (flags) return fail(c, NB_ERR_CUDA, "device flags 0x%x", flags);
+    return NB_OK;
+}
+
+nb_status nb_box_info(nb_ctx* c, int box, nb_info* info) {
+    if (!c || !info) return NB_ERR_ARG;
+    if (box < 0 || box >= c->nbox) return fail(c, NB_ERR_ARG, "box index out of range");
+    if (!c->last_valid) return fail(c, NB_ERR_STATE, "call nb_check first");
+    fill_info(c, box, box + 1, info, c->last[box].flags);
     return NB_OK;
 }
 
@@ -516,7 +676,8 @@ nb_status nb_profile(nb_ctx* c, int enable) {
 }
 
 nb_status nb_profile_read(nb_ctx* c, int* kinds, float* ms, int max, int* count) {
-    if (!c || !count || max < 0 || (max > 0 && (!kinds || !ms))) return fail(c, NB_ERR_ARG, "profile_read: bad argument");
+    if (!c || !count || max < 0 || (max > 0 && (!kinds || !ms)))
+        return fail(c, NB_ERR_ARG, "profile_read: bad argument");
     const int n = c->ev_n < max ? c->ev_n : max;
     for (int k = 0; k < n; ++k) {
         NB_CUDA(c, cudaEventSynchronize(c->ev[2 * k + 1]));
@@ -532,10 +693,11 @@ nb_status nb_get_grid(nb_ctx* c, int* atom_of_slot, int* slot_of_atom, int* col_
                       int* type_slot, float* bb, int* col_of_atom, int* sc_info, nb_stream stream) {
     if (!c) return NB_ERR_ARG;
     if (!c->have_grid || !c->last_valid) return fail(c, NB_ERR_STATE, "need a grid and nb_check");
+    if (c->nbox != 1) return fail(c, NB_ERR_STATE, "grid copies are for single-box contexts");
     cudaStream_t s = (cudaStream_t)stream;
-    const long long nclu = c->last.nclu;
+    const long long nclu = c->last[0].nclu;
     const long long ns = nclu * c->C;
-    const int ncol = c->geom.nx * c->geom.ny;
+    const int ncol = c->geo_host[0].nx * c->geo_host[0].ny;
     auto cp = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
         if (!dst || bytes == 0) return cudaSuccess;
         return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
@@ -546,7 +708,7 @@ nb_status nb_get_grid(nb_ctx* c, int* atom_of_slot, int* slot_of_atom, int* col_
     NB_CUDA(c, cp(xyzq, c->ws.xyzq, sizeof(float4) * ns));
     NB_CUDA(c, cp(type_slot, c->ws.type_slot, sizeof(int) * ns));
     NB_CUDA(c, cp(col_of_atom, c->ws.col_of_atom, sizeof(int) * c->n));
-    NB_CUDA(c, cp(sc_info, c->ws.sc_info, sizeof(int2) * (size_t)c->last.nsc));
+    NB_CUDA(c, cp(sc_info, c->ws.sc_info, sizeof(int2) * (size_t)c->last[0].nsc));
     if (bb && nclu > 0) {
         // float4 pairs -> float [nclu][6]
         NB_CUDA(c, cudaMemcpy2DAsync(bb, 6 * sizeof(float), c->ws.bb, 8 * sizeof(float), 3 * sizeof(float),
@@ -562,9 +724,10 @@ nb_status nb_get_list(nb_ctx* c, int which, int* ient, int* cj, uint64_t* mask, 
     if (which != 0 && which != 1) return fail(c, NB_ERR_ARG, "which must be 0 or 1");
     if (!c->have_list || !c->last_valid || (which == 1 && !c->have_pruned))
         return fail(c, NB_ERR_STATE, "need a list and nb_check");
+    if (c->nbox != 1) return fail(c, NB_ERR_STATE, "list copies are for single-box contexts");
     cudaStream_t s = (cudaStream_t)stream;
-    const long long ni = (long long)c->last.n_ient, nj = (long long)c->last.n_jent;
-    if (ni > c->ient_cap || nj > c->jent_cap) return fail(c, NB_ERR_CAPACITY, "list overflowed");
+    const long long ni = (long long)c->last[0].n_ient, nj = (long long)c->last[0].n_jent;
+    if (ni > c->plan[0].ient_cap || nj > c->plan[0].jent_cap) return fail(c, NB_ERR_CAPACITY, "list overflowed");
     const int4* si = which ? c->ws.ient_p : c->ws.ient;
     const int* sc = which ? c->ws.cj_p : c->ws.cj;
     const unsigned long long* sm = which ? c->ws.mask_p : c->ws.mask;

@@ -25,17 +25,10 @@
 namespace nbc {
 
 struct ForceArgs {
-    const DevState* st;
-    const float4* xyzq;
-    const int* type_slot;
-    const float2* c6c12;
-    const int4* ient;
+    Workspace ws;
+    const int4* ient;                 // outer or pruned list
     const int* cj;
     const unsigned long long* mask;
-    float4* fslot;
-    Accum* acc;
-    const int2* sc_info;
-    long long jstride;
     ForceParams p;
 };
 
@@ -215,6 +208,23 @@ __device__ __forceinline__ float2 pair_force2(const ForceParams& P, float2 r2, b
     return make_float2(inc0 ? flj0 + fc0 : 0.0f, inc1 ? flj1 + fc1 : 0.0f);
 }
 
+// Add a warp's energy partial sums to box b's FP64 totals and clear them.
+__device__ __forceinline__ void flush_energy(Accum* acc, int b, float& e_lj, float& e_c, unsigned& n_inc) {
+    const unsigned full = 0xffffffffu;
+    for (int o = 16; o > 0; o >>= 1) {
+        e_lj += __shfl_xor_sync(full, e_lj, o);
+        e_c += __shfl_xor_sync(full, e_c, o);
+        n_inc += __shfl_xor_sync(full, n_inc, o);
+    }
+    if ((threadIdx.x & 31) == 0 && b >= 0) {
+        atomicAdd(&acc[b].energy[0], (double)e_lj);
+        atomicAdd(&acc[b].energy[1], (double)e_c);
+        atomicAdd(&acc[b].n_inc, (unsigned long long)n_inc);
+    }
+    e_lj = e_c = 0.0f;
+    n_inc = 0;
+}
+
 // The pairs of i-cluster k (of the super-cluster) with one j-cluster.
 // Returns (warp-uniformly) whether any pair was inside rc.
 template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, bool FULL>
@@ -274,11 +284,11 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
     if (lane < nt) {
         W.w[lane] = A.cj[jb + lane];
 #pragma unroll
-        for (int k = 0; k < kSuper8; ++k) W.m[k][lane] = A.mask[k * A.jstride + jb + lane];
+        for (int k = 0; k < kSuper8; ++k) W.m[k][lane] = A.mask[k * A.ws.jstride + jb + lane];
     }
     __syncwarp();
-    const float4* xyzq_j = A.xyzq + L.j;
-    const int* type_j = A.type_slot + L.j;
+    const float4* xyzq_j = A.ws.xyzq + L.j;
+    const int* type_j = A.ws.type_slot + L.j;
     int cjn = W.w[0] & kCjMask;
     float4 xjn = xyzq_j[cjn * 8];
     int tjn = type_j[cjn * 8];
@@ -315,7 +325,7 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
         fjx += __shfl_xor_sync(full, fjx, 16);
         fjy += __shfl_xor_sync(full, fjy, 16);
         fjz += __shfl_xor_sync(full, fjz, 16);
-        if (L.ih == 0) atomicAdd(&A.fslot[cjt * 8 + L.j], make_float4(fjx, fjy, fjz, 0.0f));
+        if (L.ih == 0) atomicAdd(&A.ws.fslot[cjt * 8 + L.j], make_float4(fjx, fjy, fjz, 0.0f));
     }
     __syncwarp();
 }
@@ -327,7 +337,7 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 5 : 6) k_force8(For
     const unsigned full = 0xffffffffu;
     const int nt2 = A.p.ntypes * A.p.ntypes;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
-        const float2 v = A.c6c12[k];
+        const float2 v = A.ws.c6c12[k];
         s_lj[k] = make_float2(-6.0f * v.x, 12.0f * v.y);
     }
     __syncthreads();
@@ -339,21 +349,28 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 5 : 6) k_force8(For
     L.lower0 = L.j <= L.ih;
     L.lower1 = L.j <= L.ih + 4;
     L.sel = 1u << (L.ih * 8 + L.j);
-    const long long nient = min((long long)A.st->n_ient, A.p.ient_cap);
     float e_lj = 0.0f, e_c = 0.0f;
     unsigned n_inc = 0;
-    for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < nient;
+    int b = 0, b_acc = -1;
+    for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < A.ws.ient_total;
          e += (long long)gridDim.x * kForceWarps) {
+        b = advance_box(A.ws.lay.ient_off, A.ws.nbox, b, e);
+        const long long ient_base = A.ws.lay.ient_off[b];
+        if (e - ient_base >= min((long long)A.ws.st[b].n_ient, A.ws.lay.ient_off[b + 1] - ient_base)) continue;
+        if (ENERGY && b != b_acc) {
+            flush_energy(A.ws.acc, b_acc, e_lj, e_c, n_inc);
+            b_acc = b;
+        }
         const int4 ie = A.ient[e];
         const int q = ie.x, s = ie.y, jb = ie.z, je = ie.w;
         if (jb >= je) continue;
-        const int2 info = A.sc_info[q];
+        const int2 info = A.ws.sc_info[q];
         const int g0 = info.x, n = info.y;
-        const float sh[3] = {(float)(s / 9 - 1) * A.p.L[0], (float)((s / 3) % 3 - 1) * A.p.L[1],
-                             (float)(s % 3 - 1) * A.p.L[2]};
+        float sh[3];
+        shift_vector(s, A.ws.geo[b].L, sh);
         // stage the super-cluster's i particles: shifted coordinates as hi + lo
         if (lane < n * 8) {
-            const float4 x = A.xyzq[g0 * 8 + lane];
+            const float4 x = A.ws.xyzq[g0 * 8 + lane];
             float4 h, l;
             two_sum(x.x, sh[0], h.x, l.x);
             two_sum(x.y, sh[1], h.y, l.y);
@@ -362,7 +379,7 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 5 : 6) k_force8(For
             l.w = 0.0f;
             W.xi[lane] = h;
             W.xl[lane] = l;
-            W.row[lane] = A.type_slot[g0 * 8 + lane] * A.p.ntypes;
+            W.row[lane] = A.ws.type_slot[g0 * 8 + lane] * A.p.ntypes;
         }
         __syncwarp();
         const bool center = (s == kShiftCenter);
@@ -394,8 +411,8 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 5 : 6) k_force8(For
                 tsum[d] += f0[d] + f1[d];
             }
             if (L.j == 0) {
-                atomicAdd(&A.fslot[(g0 + k) * 8 + L.ih], make_float4(f0[0], f0[1], f0[2], 0.0f));
-                atomicAdd(&A.fslot[(g0 + k) * 8 + L.ih + 4], make_float4(f1[0], f1[1], f1[2], 0.0f));
+                atomicAdd(&A.ws.fslot[(g0 + k) * 8 + L.ih], make_float4(f0[0], f0[1], f0[2], 0.0f));
+                atomicAdd(&A.ws.fslot[(g0 + k) * 8 + L.ih + 4], make_float4(f1[0], f1[1], f1[2], 0.0f));
             }
         }
         if (ENERGY && !center) {
@@ -406,22 +423,11 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 5 : 6) k_force8(For
                 tsum[d] += __shfl_xor_sync(full, tsum[d], 16);
             }
             if (lane == 0)
-                for (int d = 0; d < 3; ++d) atomicAdd(&A.acc->fshift[s][d], (double)tsum[d]);
+                for (int d = 0; d < 3; ++d) atomicAdd(&A.ws.acc[b].fshift[s][d], (double)tsum[d]);
         }
         __syncwarp();
     }
-    if (ENERGY) {
-        for (int o = 16; o > 0; o >>= 1) {
-            e_lj += __shfl_xor_sync(full, e_lj, o);
-            e_c += __shfl_xor_sync(full, e_c, o);
-            n_inc += __shfl_xor_sync(full, n_inc, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&A.acc->energy[0], (double)e_lj);
-            atomicAdd(&A.acc->energy[1], (double)e_c);
-            atomicAdd(&A.acc->n_inc, (unsigned long long)n_inc);
-        }
-    }
+    if (ENERGY) flush_energy(A.ws.acc, b_acc, e_lj, e_c, n_inc);
 }
 
 // Generic C = 4 kernel (super-clusters of one cluster): one warp per
@@ -433,29 +439,36 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
     const unsigned full = 0xffffffffu;
     const int nt2 = A.p.ntypes * A.p.ntypes;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
-        const float2 v = A.c6c12[k];
+        const float2 v = A.ws.c6c12[k];
         s_lj[k] = make_float2(6.0f * v.x, 12.0f * v.y);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int half = lane >> 4, i = (lane >> 2) & 3, j = lane & 3;
-    const long long nient = min((long long)A.st->n_ient, A.p.ient_cap);
     float e_lj = 0.0f, e_c = 0.0f;
     unsigned n_inc = 0;
-    for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < nient;
+    int b = 0, b_acc = -1;
+    for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < A.ws.ient_total;
          e += (long long)gridDim.x * kForceWarps) {
+        b = advance_box(A.ws.lay.ient_off, A.ws.nbox, b, e);
+        const long long ient_base = A.ws.lay.ient_off[b];
+        if (e - ient_base >= min((long long)A.ws.st[b].n_ient, A.ws.lay.ient_off[b + 1] - ient_base)) continue;
+        if (ENERGY && b != b_acc) {
+            flush_energy(A.ws.acc, b_acc, e_lj, e_c, n_inc);
+            b_acc = b;
+        }
         const int4 ie = A.ient[e];
-        const int ci = A.sc_info[ie.x].x, s = ie.y, jb = ie.z, je = ie.w;
+        const int ci = A.ws.sc_info[ie.x].x, s = ie.y, jb = ie.z, je = ie.w;
         if (jb >= je) continue;
-        const float sh[3] = {(float)(s / 9 - 1) * A.p.L[0], (float)((s / 3) % 3 - 1) * A.p.L[1],
-                             (float)(s % 3 - 1) * A.p.L[2]};
-        const float4 x0 = A.xyzq[ci * 4 + i];
+        float sh[3];
+        shift_vector(s, A.ws.geo[b].L, sh);
+        const float4 x0 = A.ws.xyzq[ci * 4 + i];
         float xh[3], xl[3];
         two_sum(x0.x, sh[0], xh[0], xl[0]);
         two_sum(x0.y, sh[1], xh[1], xl[1]);
         two_sum(x0.z, sh[2], xh[2], xl[2]);
         const float qi = x0.w * A.p.fcoul;
-        const int ti = A.type_slot[ci * 4 + i] * A.p.ntypes;
+        const int ti = A.ws.type_slot[ci * 4 + i] * A.p.ntypes;
         const bool center = (s == kShiftCenter);
         float fi[3] = {0.f, 0.f, 0.f};
         for (int k = jb; k < je; k += 2) {
@@ -463,8 +476,8 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
             const bool live = kk < je;
             const int cjt = live ? (A.cj[kk] & kCjMask) : ci;
             const unsigned long long m = live ? A.mask[kk] : 0ull;
-            const float4 xj = A.xyzq[cjt * 4 + j];
-            const int tj = A.type_slot[cjt * 4 + j];
+            const float4 xj = A.ws.xyzq[cjt * 4 + j];
+            const int tj = A.ws.type_slot[cjt * 4 + j];
             const bool diag = center && (cjt == ci);
             const float b = (float)((m >> (i * 4 + j)) & 1ull);
             const float dx = (xh[0] - xj.x) + xl[0];
@@ -489,7 +502,7 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
                 fjy += __shfl_xor_sync(full, fjy, o);
                 fjz += __shfl_xor_sync(full, fjz, o);
             }
-            if (i == 0 && live) atomicAdd(&A.fslot[cjt * 4 + j], make_float4(fjx, fjy, fjz, 0.0f));
+            if (i == 0 && live) atomicAdd(&A.ws.fslot[cjt * 4 + j], make_float4(fjx, fjy, fjz, 0.0f));
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -497,7 +510,7 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
             fi[d] += __shfl_xor_sync(full, fi[d], 2);
             fi[d] += __shfl_xor_sync(full, fi[d], 16);
         }
-        if (j == 0 && half == 0) atomicAdd(&A.fslot[ci * 4 + i], make_float4(fi[0], fi[1], fi[2], 0.0f));
+        if (j == 0 && half == 0) atomicAdd(&A.ws.fslot[ci * 4 + i], make_float4(fi[0], fi[1], fi[2], 0.0f));
         if (ENERGY && !center) {
             float t[3] = {fi[0], fi[1], fi[2]};
 #pragma unroll
@@ -506,21 +519,10 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
                 t[d] += __shfl_xor_sync(full, t[d], 8);
             }
             if (lane == 0)
-                for (int d = 0; d < 3; ++d) atomicAdd(&A.acc->fshift[s][d], (double)t[d]);
+                for (int d = 0; d < 3; ++d) atomicAdd(&A.ws.acc[b].fshift[s][d], (double)t[d]);
         }
     }
-    if (ENERGY) {
-        for (int o = 16; o > 0; o >>= 1) {
-            e_lj += __shfl_xor_sync(full, e_lj, o);
-            e_c += __shfl_xor_sync(full, e_c, o);
-            n_inc += __shfl_xor_sync(full, n_inc, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&A.acc->energy[0], (double)e_lj);
-            atomicAdd(&A.acc->energy[1], (double)e_c);
-            atomicAdd(&A.acc->n_inc, (unsigned long long)n_inc);
-        }
-    }
+    if (ENERGY) flush_energy(A.ws.acc, b_acc, e_lj, e_c, n_inc);
 }
 
 template <int ELEC, bool ENERGY, bool FIT>
@@ -541,23 +543,14 @@ static cudaError_t launch_force_e(const ForceArgs& A, int C, int n_sm, cudaStrea
     return launch_force_t<ELEC, ENERGY, false>(A, C, n_sm, s);
 }
 
-cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n_sm,
-                         long long n_slots_cap, cudaStream_t s) {
-    (void)n_slots_cap;
+cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n_sm, cudaStream_t s) {
     ForceArgs A;
-    A.st = ws.st;
-    A.xyzq = ws.xyzq;
-    A.type_slot = ws.type_slot;
-    A.c6c12 = ws.c6c12;
+    A.ws = ws;
     A.ient = p.use_pruned ? ws.ient_p : ws.ient;
     A.cj = p.use_pruned ? ws.cj_p : ws.cj;
     A.mask = p.use_pruned ? ws.mask_p : ws.mask;
-    A.fslot = ws.fslot;
-    A.acc = ws.acc;
-    A.sc_info = ws.sc_info;
-    A.jstride = ws.jstride;
     A.p = p;
-    cudaError_t e = cudaMemsetAsync(ws.acc, 0, sizeof(Accum), s);
+    cudaError_t e = cudaMemsetAsync(ws.acc, 0, sizeof(Accum) * ws.nbox, s);
     if (e != cudaSuccess) return e;
     if (p.elec == NB_ELEC_RF)
         return p.want_energy ? launch_force_e<NB_ELEC_RF, true>(A, C, n_sm, s)
@@ -567,74 +560,82 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
 }
 
 // Forces back to the caller's order (and zeroed for the next evaluation);
-// with energies, the FP64 sum over slots of x (x) f for the virial.
-__global__ void k_finalize(int n, const int* __restrict__ slot_of_atom, float4* __restrict__ fslot,
-                           const float4* __restrict__ xyzq, float* __restrict__ f_out, int want_vir,
-                           Accum* acc) {
-    double w[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int s = slot_of_atom[p];
-        const float4 f = fslot[s];
-        fslot[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        f_out[3 * p] = f.x;
-        f_out[3 * p + 1] = f.y;
-        f_out[3 * p + 2] = f.z;
-        if (want_vir) {
-            const float4 x = xyzq[s];
-            const double xa[3] = {x.x, x.y, x.z}, fb[3] = {f.x, f.y, f.z};
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = 0; b < 3; ++b) w[3 * a + b] += xa[a] * fb[b];
-        }
-    }
-    if (!want_vir) return;
-    __shared__ double s_w[9][8];
+// with energies, the FP64 sum per box over slots of x (x) f for the virial.
+__global__ void k_finalize(Workspace ws, float* __restrict__ f_out, int want_vir) {
     const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int n = ws.atom_total;
+    // whole warps step through the particles so that box boundaries are seen warp-wide
+    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) - lane; base < n;
+         base += gridDim.x * blockDim.x) {
+        const int p = base + lane;
+        const bool live = p < n;
+        int b = 0;
+        double w[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (live) {
+            const int s = ws.slot_of_atom[p];
+            const float4 f = ws.fslot[s];
+            ws.fslot[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+            f_out[3 * p] = f.x;
+            f_out[3 * p + 1] = f.y;
+            f_out[3 * p + 2] = f.z;
+            if (want_vir) {
+                b = find_box(ws.lay.atom_off, ws.nbox, p);
+                const float4 x = ws.xyzq[s];
+                const double xa[3] = {x.x, x.y, x.z}, fb[3] = {f.x, f.y, f.z};
 #pragma unroll
-    for (int k = 0; k < 9; ++k)
-        for (int o = 16; o > 0; o >>= 1) w[k] += __shfl_xor_sync(full, w[k], o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0)
-        for (int k = 0; k < 9; ++k) s_w[k][warp] = w[k];
-    __syncthreads();
-    if (threadIdx.x < 9) {
-        double v = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += s_w[threadIdx.x][q];
-        atomicAdd(&acc->vir_xf[threadIdx.x], v);
-    }
-}
-
-__global__ void k_finalize_small(const Accum* acc, DevState* st, float Lx, float Ly, float Lz,
-                                 double* e_out, double* vir_out) {
-    if (threadIdx.x != 0) return;
-    st->n_pairs_rc = acc->n_inc;
-    if (e_out) {
-        e_out[0] = acc->energy[0];
-        e_out[1] = acc->energy[1];
-    }
-    if (vir_out) {
-        double w[9];
-        for (int k = 0; k < 9; ++k) w[k] = acc->vir_xf[k];
-        for (int s = 0; s < 27; ++s) {
-            const double sv[3] = {(double)(s / 9 - 1) * Lx, (double)((s / 3) % 3 - 1) * Ly,
-                                  (double)(s % 3 - 1) * Lz};
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) w[3 * a + b] += sv[a] * acc->fshift[s][b];
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) w[3 * a + c] = xa[a] * fb[c];
+            }
         }
-        for (int k = 0; k < 9; ++k) vir_out[k] = w[k];
+        if (!want_vir) continue;
+        const int b0 = __shfl_sync(full, b, 0);
+        if (__all_sync(full, !live || b == b0)) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                for (int o = 16; o > 0; o >>= 1) w[k] += __shfl_xor_sync(full, w[k], o);
+            }
+            if (lane == 0)
+                for (int k = 0; k < 9; ++k) atomicAdd(&ws.acc[b0].vir_xf[k], w[k]);
+        } else if (live) {
+            for (int k = 0; k < 9; ++k) atomicAdd(&ws.acc[b].vir_xf[k], w[k]);
+        }
     }
 }
 
-cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int n, float* f_out,
-                            double* e_out, double* vir_out, cudaStream_t s) {
+// Per box: energies out, and W = sum x (x) f + sum_s (s L) (x) f_shift.
+__global__ void k_finalize_small(Workspace ws, double* e_out, double* vir_out) {
+    for (int b = threadIdx.x; b < ws.nbox; b += blockDim.x) {
+        const Accum* acc = &ws.acc[b];
+        ws.st[b].n_pairs_rc = acc->n_inc;
+        if (e_out) {
+            e_out[2 * b] = acc->energy[0];
+            e_out[2 * b + 1] = acc->energy[1];
+        }
+        if (vir_out) {
+            const float* L = ws.geo[b].L;
+            double w[9];
+            for (int k = 0; k < 9; ++k) w[k] = acc->vir_xf[k];
+            for (int s = 0; s < 27; ++s) {
+                const double sv[3] = {(double)(s / 9 - 1) * L[0], (double)((s / 3) % 3 - 1) * L[1],
+                                      (double)(s % 3 - 1) * L[2]};
+                for (int a = 0; a < 3; ++a)
+                    for (int c = 0; c < 3; ++c) w[3 * a + c] += sv[a] * acc->fshift[s][c];
+            }
+            for (int k = 0; k < 9; ++k) vir_out[9 * b + k] = w[k];
+        }
+    }
+}
+
+cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, float* f_out, double* e_out,
+                            double* vir_out, cudaStream_t s) {
     const int want_vir = (p.want_energy && vir_out) ? 1 : 0;
-    int blocks = (n + 255) / 256;
+    int blocks = (ws.atom_total + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    k_finalize<<<blocks, 256, 0, s>>>(n, ws.slot_of_atom, ws.fslot, ws.xyzq, f_out, want_vir, ws.acc);
-    if (p.want_energy)
-        k_finalize_small<<<1, 32, 0, s>>>(ws.acc, ws.st, p.L[0], p.L[1], p.L[2], e_out, vir_out);
+    k_finalize<<<blocks, 256, 0, s>>>(ws, f_out, want_vir);
+    if (p.want_energy) k_finalize_small<<<1, 256, 0, s>>>(ws, e_out, vir_out);
     return cudaGetLastError();
 }
 

@@ -1,9 +1,19 @@
 // Internal declarations shared by the nbcluster CUDA sources (not part of the
-// C ABI).  Layouts of the workspace-resident data:
+// C ABI).
+//
+// A context holds one or more independent periodic boxes in one workspace.
+// Every per-particle, per-column, per-cluster, per-super-cluster and list
+// array is one batch array in which box b owns a region [off[b], off[b+1])
+// fixed when the workspace is planned (capacity bounds); cluster, slot and
+// list indices stored anywhere are batch-global.  Kernels find the box of a
+// work item by binary search over the region offsets, so a single box is the
+// batch of one and many small boxes share one launch per step.
+// Layouts:
 //   slots      : cluster g holds slots g*C .. g*C+C-1 (Sec. 2.3 clusters)
 //   xyzq       : float4 per slot, wrapped coordinates + charge (dummies far away)
 //   bb         : two float4 per cluster {xmin, ymin, zmin, 0}, {xmax, ymax, zmax, 0}
-//   i-entry    : int4 {ci, shift, j_begin, j_end}; j-entry: cj (int) + mask (u64)
+//   i-entry    : int4 {super-cluster, shift, j_begin, j_end}
+//   j-entry    : word cj | (interaction bits << kSuperShift); masks [S][jstride]
 //   fslot      : float4 per slot, force accumulators (w unused)
 #pragma once
 
@@ -16,18 +26,19 @@ namespace nbc {
 
 constexpr int kMaxTypes = 64;          // LJ types (type table staged in shared memory)
 constexpr int kMaxColumn = 8192;       // particles per grid column sorted on-chip
+constexpr int kMaxBoxes = 4096;        // boxes per context
 constexpr int kShiftCenter = 13;       // shift index of (0, 0, 0)
 constexpr int kJChunk = 32;            // j-entries per i-entry at most (load balance)
-constexpr int kMaxExclPerCluster = 256;
 // Super-clusters (Sec. 3.1, Fig. 6: several i-clusters share one j-list):
-// up to kSuper consecutive clusters of one grid column.  A j-entry's word
-// holds the j-cluster index in its low kSuperShift bits and one interaction
-// bit per i-cluster of the super-cluster above them.
+// up to super_size(C) consecutive clusters of one grid column.  A j-entry's
+// word holds the j-cluster index in its low kSuperShift bits and one
+// interaction bit per i-cluster of the super-cluster above them.
 constexpr int kSuperShift = 27;
 constexpr int kCjMask = (1 << kSuperShift) - 1;
 __host__ __device__ constexpr int super_size(int C) { return C == 8 ? 2 : 1; }
 
-// Device-resident state: counters written by kernels, read back by nb_check.
+// Device-resident state of one box: counters written by kernels, read back
+// by nb_check.  Counts are box-local.
 struct DevState {
     unsigned long long n_ient;          // outer list i-entries
     unsigned long long n_jent;          // outer list j-entries
@@ -41,7 +52,7 @@ struct DevState {
     unsigned long long n_keys_pruned;   // cluster pairs kept by the last prune
 };
 
-// FP64 accumulators of one force evaluation.
+// FP64 accumulators of one force evaluation of one box.
 struct Accum {
     double fshift[27][3];   // i-side force per periodic shift (virial bookkeeping)
     double energy[2];       // E_LJ, E_Coulomb
@@ -49,63 +60,74 @@ struct Accum {
     unsigned long long n_inc;  // pairs inside the cut-off (energy kernels only)
 };
 
+// Geometry of one box, rewritten by each nb_grid_put.
+struct BoxGeom {
+    float L[3];
+    float inv_x, inv_y;     // FP32 n_x / L_x, n_y / L_y of the cell decision
+    float inv_cx, inv_cy;   // the same, for the search's column ranges
+    float dummy_g;          // dummy spacing (power of two >= 4 max L)
+    int nx, ny;
+};
+
+// Region offsets of the boxes (device arrays of nbox + 1 entries, fixed by
+// the workspace plan).  Column regions hold n_cols + 1 entries per box.
+struct Layout {
+    const int* atom_off;
+    const int* col_off;
+    const int* clu_off;
+    const int* sc_off;
+    const long long* ient_off;
+    const long long* jent_off;
+};
+
 struct Workspace {
-    DevState* st;
-    Accum* acc;
-    // per particle (caller order)
+    int nbox;
+    DevState* st;        // [nbox]
+    Accum* acc;          // [nbox]
+    BoxGeom* geo;        // [nbox]
+    Layout lay;
+    int atom_total, col_total, clu_total, sc_total;
+    long long ient_total;
+    // per particle (caller order, all boxes concatenated)
     float4* xw;          // wrapped coordinates + charge
     float4* woff;        // wrap offset (wrapped - input), per particle
-    int* col_of_atom;
+    int* col_of_atom;    // batch column index
     int* rank_in_col;
-    int* slot_of_atom;
+    int* slot_of_atom;   // batch slot index
     float* q;
     int* type;
-    // per column
+    // per column (box regions of n_cols + 1)
     int* col_count;
-    int* col_atom_start;
-    int* col_clu_start;  // [ncol + 1]
-    int* col_sc_start;   // [ncol + 1] first super-cluster of each column
-    int2* sc_info;       // per super-cluster {first cluster, number of clusters}
-    // sort keys (column order)
-    unsigned long long* keys;
+    int* col_atom_start; // position of the column's first key in keys
+    int* col_clu_start;  // first (batch) cluster of each column, end entry after the last
+    int* col_sc_start;   // first (batch) super-cluster of each column
+    int2* sc_info;       // per super-cluster {first batch cluster, number of clusters}
+    unsigned long long* keys;  // sort keys in column order
     // per slot
     float4* xyzq;
-    int* atom_of_slot;
+    int* atom_of_slot;   // batch particle index, -1 for dummies
     int* type_slot;
     float4* fslot;
     // per cluster
-    float4* bb;          // [2 * nclu]
-    // lists: i-entry {super-cluster, shift, j_begin, j_end}; j-entry word
-    // = cj | (interaction bits << kSuperShift); masks [S][jent capacity]
+    float4* bb;          // [2 * clusters]
+    // lists
     int4* ient;
     int* cj;
     unsigned long long* mask;
     int4* ient_p;
     int* cj_p;
     unsigned long long* mask_p;
-    long long jstride;   // j-entry capacity: stride between the S mask arrays
+    long long jstride;   // total j-entry capacity: stride between the S mask arrays
     // LJ table {C6, C12} [ntypes][ntypes]
     float2* c6c12;
 };
 
-struct GridGeom {
-    float L[3];
-    float inv_x, inv_y;
-    int nx, ny;
-    float dummy_g;
-};
-
 // Kernel launchers (defined in the .cu files).
-cudaError_t launch_grid(const Workspace& ws, const GridGeom& g, int n, int C, int ntypes,
-                        const float* xyz, int n_sm, cudaStream_t s);
-cudaError_t launch_set_coords(const Workspace& ws, int n_slots_cap, int C, const float* xyz,
-                              cudaStream_t s);
-cudaError_t launch_search(const Workspace& ws, const GridGeom& g, int C, long long nclu_cap,
-                          float rlist, float rbb, const int* excl_off, const int* excl_idx,
-                          long long ient_cap, long long jent_cap, int n_atoms, int n_sm,
-                          cudaStream_t s);
-cudaError_t launch_prune(const Workspace& ws, const GridGeom& g, int C, float r_prune,
-                         long long ient_cap, int n_sm, cudaStream_t s);
+cudaError_t launch_grid(const Workspace& ws, int C, int ntypes, const float* xyz, cudaStream_t s);
+cudaError_t launch_set_coords(const Workspace& ws, int C, const float* xyz, cudaStream_t s);
+cudaError_t launch_search(const Workspace& ws, int C, float rlist, float rbb, const int* excl_off,
+                          const int* excl_idx, int n_sm, cudaStream_t s);
+cudaError_t launch_prune(const Workspace& ws, int C, float r_prune, int n_sm, cudaStream_t s);
 
 struct ForceParams {
     int elec;
@@ -119,24 +141,39 @@ struct ForceParams {
     float beta2, beta3;   // beta^2, beta^3 for the fitted correction
     int use_fit;          // (beta rc)^2 within the fitted range
     int ntypes;
-    float L[3];
     int use_pruned;
-    long long ient_cap;
 };
 
-cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n_sm,
-                         long long n_slots_cap, cudaStream_t s);
-cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int n, float* f_out,
-                            double* e_out, double* vir_out, cudaStream_t s);
+cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n_sm, cudaStream_t s);
+cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, float* f_out, double* e_out,
+                            double* vir_out, cudaStream_t s);
 
 // Kernels each launcher issues (for launch accounting).
-constexpr int kLaunchesGrid = 4, kLaunchesSearch = 1, kLaunchesPrune = 1, kLaunchesSetCoords = 1;
+constexpr int kLaunchesGrid = 4, kLaunchesSearch = 1, kLaunchesPrune = 2, kLaunchesSetCoords = 1;
 
 // ---------------------------------------------------------------------------
 // Device helpers
 
 __device__ __forceinline__ void set_flag(DevState* st, int code) {
     atomicOr(&st->flags, 1u << code);
+}
+
+// Box b with off[b] <= x < off[b+1] (off ascending, nbox + 1 entries).
+template <typename T>
+__device__ __forceinline__ int find_box(const T* off, int nbox, T x) {
+    int lo = 0, hi = nbox;
+    while (hi - lo > 1) {
+        const int m = (lo + hi) >> 1;
+        if (off[m] <= x) lo = m; else hi = m;
+    }
+    return lo;
+}
+
+// Advance box b (ascending walk) until off[b] <= x < off[b+1].
+template <typename T>
+__device__ __forceinline__ int advance_box(const T* off, int nbox, int b, T x) {
+    while (b + 1 < nbox && off[b + 1] <= x) ++b;
+    return b;
 }
 
 // Error-free sum a + b = s + e (Knuth TwoSum), every operation rounded once.
@@ -146,8 +183,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__device__ __forceinline__ int shift_comp(int s, int k) {
-    return k == 0 ? s / 9 - 1 : (k == 1 ? (s / 3) % 3 - 1 : s % 3 - 1);
+__device__ __forceinline__ void shift_vector(int s, const float L[3], float sh[3]) {
+    sh[0] = (float)(s / 9 - 1) * L[0];
+    sh[1] = (float)((s / 3) % 3 - 1) * L[1];
+    sh[2] = (float)(s % 3 - 1) * L[2];
 }
 
 }  // namespace nbc

@@ -28,17 +28,19 @@ constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Scratch layout (byte offsets).
 constexpr size_t kOffState = 0;
-constexpr size_t kOffXw = align256(kOffState + sizeof(DevState));
+constexpr size_t kOffGeo = align256(kOffState + sizeof(DevState));
+constexpr size_t kOffLayout = align256(kOffGeo + sizeof(BoxGeom));
+constexpr size_t kOffXw = align256(kOffLayout + 4 * 2 * sizeof(int) + 2 * 2 * sizeof(long long));
 constexpr size_t kOffWoff = align256(kOffXw + sizeof(float4) * kNoallocMaxAtoms);
 constexpr size_t kOffColOfAtom = align256(kOffWoff + sizeof(float4) * kNoallocMaxAtoms);
 constexpr size_t kOffRank = align256(kOffColOfAtom + sizeof(int) * kNoallocMaxAtoms);
 constexpr size_t kOffSlotOfAtom = align256(kOffRank + sizeof(int) * kNoallocMaxAtoms);
 constexpr size_t kOffKeys = align256(kOffSlotOfAtom + sizeof(int) * kNoallocMaxAtoms);
 constexpr size_t kOffColCount = align256(kOffKeys + sizeof(unsigned long long) * kNoallocMaxAtoms);
-constexpr size_t kOffColAtomStart = align256(kOffColCount + sizeof(int) * kNoallocMaxColumns);
-constexpr size_t kOffColScStart = align256(kOffColAtomStart + sizeof(int) * kNoallocMaxColumns);
+constexpr size_t kOffColAtomStart = align256(kOffColCount + sizeof(int) * (kNoallocMaxColumns + 1));
+constexpr size_t kOffColScStart = align256(kOffColAtomStart + sizeof(int) * (kNoallocMaxColumns + 1));
 constexpr size_t kOffScInfo = align256(kOffColScStart + sizeof(int) * (kNoallocMaxColumns + 1));
-constexpr size_t kOffFslot = align256(kOffScInfo + sizeof(int2) * (kNoallocMaxSlots / 4 + kNoallocMaxColumns));
+constexpr size_t kOffFslot = align256(kOffScInfo + sizeof(int2) * (kNoallocMaxSlots / 4 + kNoallocMaxColumns + 1));
 constexpr size_t kNoallocScratchBytes = align256(kOffFslot + sizeof(float4) * kNoallocMaxSlots);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
@@ -60,6 +62,28 @@ static cudaError_t noalloc_scratch(int dev, unsigned char** out) {
     return cudaSuccess;
 }
 
+// Box geometry, the one-box region offsets and a cleared state, written into
+// the scratch on the stream (the values travel as kernel arguments, so no host
+// staging buffer is involved).
+__global__ void k_noalloc_setup(Workspace ws, BoxGeom g, int n, int ncol, int nclu_cap, int nsc_cap) {
+    if (threadIdx.x != 0) return;
+    *ws.geo = g;
+    int* a = const_cast<int*>(ws.lay.atom_off);
+    int* c = const_cast<int*>(ws.lay.col_off);
+    int* u = const_cast<int*>(ws.lay.clu_off);
+    int* q = const_cast<int*>(ws.lay.sc_off);
+    long long* ie = const_cast<long long*>(ws.lay.ient_off);
+    long long* je = const_cast<long long*>(ws.lay.jent_off);
+    a[0] = c[0] = u[0] = q[0] = 0;
+    a[1] = n;
+    c[1] = ncol + 1;
+    u[1] = nclu_cap;
+    q[1] = nsc_cap;
+    ie[0] = ie[1] = je[0] = je[1] = 0;
+    DevState z{};
+    *ws.st = z;
+}
+
 }  // namespace nbc
 
 using namespace nbc;
@@ -76,7 +100,7 @@ extern "C" nb_status nb_grid_put_noalloc(int n, const float* xyz, const float* q
         return NB_ERR_ARG;
     if (((uintptr_t)xyzq & 15) || ((uintptr_t)bb & 15)) return NB_ERR_ARG;
     if (!box) return NB_ERR_BOX;
-    GridGeom g{};
+    BoxGeom g{};
     for (int k = 0; k < 3; ++k) {
         if (!(box[k] > 0.0) || !(box[k] < 1e30)) return NB_ERR_BOX;
         g.L[k] = (float)box[k];
@@ -84,9 +108,9 @@ extern "C" nb_status nb_grid_put_noalloc(int n, const float* xyz, const float* q
     // grid dimensions: spacing (C / rho)^(1/3) along x and y
     {
         const double Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
-        const double s = std::cbrt((double)C / ((double)n / (Lx * Ly * Lz)));
-        g.nx = (int)std::floor(Lx / s);
-        g.ny = (int)std::floor(Ly / s);
+        const double sp = std::cbrt((double)C / ((double)n / (Lx * Ly * Lz)));
+        g.nx = (int)std::floor(Lx / sp);
+        g.ny = (int)std::floor(Ly / sp);
         if (g.nx < 1) g.nx = 1;
         if (g.ny < 1) g.ny = 1;
     }
@@ -97,6 +121,8 @@ extern "C" nb_status nb_grid_put_noalloc(int n, const float* xyz, const float* q
     if (nslot_bound > max_slots || ncol > max_columns) return NB_ERR_CAPACITY;
     g.inv_x = (float)((double)g.nx / (double)g.L[0]);
     g.inv_y = (float)((double)g.ny / (double)g.L[1]);
+    g.inv_cx = (float)g.nx / g.L[0];
+    g.inv_cy = (float)g.ny / g.L[1];
     {
         float m = g.L[0];
         if (g.L[1] > m) m = g.L[1];
@@ -110,8 +136,27 @@ extern "C" nb_status nb_grid_put_noalloc(int n, const float* xyz, const float* q
     unsigned char* base = nullptr;
     if (noalloc_scratch(dev, &base) != cudaSuccess) return NB_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    const int S = super_size(C);
+    const int nclu_cap = (int)(nslot_bound / C + 1);
+    const int nsc_cap = nclu_cap / S + (int)ncol + 1;
     Workspace ws{};
+    ws.nbox = 1;
     ws.st = (DevState*)(base + kOffState);
+    ws.geo = (BoxGeom*)(base + kOffGeo);
+    {
+        int* li = (int*)(base + kOffLayout);
+        ws.lay.atom_off = li;
+        ws.lay.col_off = li + 2;
+        ws.lay.clu_off = li + 4;
+        ws.lay.sc_off = li + 6;
+        long long* ll = (long long*)(li + 8);
+        ws.lay.ient_off = ll;
+        ws.lay.jent_off = ll + 2;
+    }
+    ws.atom_total = n;
+    ws.col_total = (int)ncol + 1;
+    ws.clu_total = nclu_cap;
+    ws.sc_total = nsc_cap;
     ws.xw = (float4*)(base + kOffXw);
     ws.woff = (float4*)(base + kOffWoff);
     ws.col_of_atom = (int*)(base + kOffColOfAtom);
@@ -130,9 +175,10 @@ extern "C" nb_status nb_grid_put_noalloc(int n, const float* xyz, const float* q
     ws.atom_of_slot = atom_of_slot;
     ws.type_slot = type_slot;
     ws.bb = (float4*)bb;
-    // the device state keeps the previous call's flags and counts: clear it
-    if (cudaMemsetAsync(ws.st, 0, sizeof(DevState), s) != cudaSuccess) return NB_ERR_CUDA;
-    if (launch_grid(ws, g, n, C, ntypes, xyz, 0, s) != cudaSuccess) return NB_ERR_CUDA;
+    // geometry, offsets and a cleared state (the previous call's flags and counts)
+    k_noalloc_setup<<<1, 32, 0, s>>>(ws, g, n, (int)ncol, nclu_cap, nsc_cap);
+    if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
+    if (launch_grid(ws, C, ntypes, xyz, s) != cudaSuccess) return NB_ERR_CUDA;
     if (cudaMemcpyAsync(&info[0], &ws.st->nclu, sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(&info[1], &ws.st->flags, sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return NB_ERR_CUDA;

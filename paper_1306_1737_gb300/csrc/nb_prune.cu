@@ -14,19 +14,8 @@
 namespace nbc {
 
 struct PruneArgs {
-    DevState* st;
-    const float4* xyzq;
-    const int2* sc_info;
-    const int4* ient;
-    const int* cj;
-    const unsigned long long* mask;
-    int4* ient_p;
-    int* cj_p;
-    unsigned long long* mask_p;
-    long long jstride;
-    float L[3];
+    Workspace ws;
     float rp2;
-    long long ient_cap;
 };
 
 constexpr int kPruneWarps = 4;
@@ -41,8 +30,10 @@ __global__ void __launch_bounds__(32 * kPruneWarps) k_prune(PruneArgs A) {
     // shifted i particles of the current super-cluster: hi and lo parts
     __shared__ float4 s_h[kPruneWarps][NA];
     __shared__ float4 s_l[kPruneWarps][NA];
-    const long long nient = min((long long)A.st->n_ient, A.ient_cap);
+    const Workspace& W = A.ws;
+    int b = 0;
     unsigned long long kept_total = 0, keys_total = 0;
+    int b_acc = -1;  // box whose totals are being accumulated
     int pi[PPL], pj[PPL];
     bool pv[PPL];
 #pragma unroll
@@ -52,16 +43,28 @@ __global__ void __launch_bounds__(32 * kPruneWarps) k_prune(PruneArgs A) {
         pi[k] = pv[k] ? p / C : 0;
         pj[k] = pv[k] ? p % C : 0;
     }
-    for (long long e = (long long)blockIdx.x * kPruneWarps + wib; e < nient;
+    for (long long e = (long long)blockIdx.x * kPruneWarps + wib; e < W.ient_total;
          e += (long long)gridDim.x * kPruneWarps) {
-        const int4 ie = A.ient[e];
+        b = advance_box(W.lay.ient_off, W.nbox, b, e);
+        const long long ient_base = W.lay.ient_off[b];
+        const long long nvalid = min((long long)W.st[b].n_ient, W.lay.ient_off[b + 1] - ient_base);
+        if (e - ient_base >= nvalid) continue;
+        if (b != b_acc) {
+            if (lane == 0 && b_acc >= 0 && kept_total) {
+                atomicAdd(&W.st[b_acc].n_jent_pruned, kept_total);
+                atomicAdd(&W.st[b_acc].n_keys_pruned, keys_total);
+            }
+            kept_total = keys_total = 0;
+            b_acc = b;
+        }
+        const int4 ie = W.ient[e];
         const int q = ie.x, s = ie.y, jb = ie.z, je = ie.w;
-        const int2 info = A.sc_info[q];
+        const int2 info = W.sc_info[q];
         const int g0 = info.x;
-        const float sh[3] = {(float)(s / 9 - 1) * A.L[0], (float)((s / 3) % 3 - 1) * A.L[1],
-                             (float)(s % 3 - 1) * A.L[2]};
+        float sh[3];
+        shift_vector(s, W.geo[b].L, sh);
         if (lane < info.y * C) {
-            const float4 x = A.xyzq[g0 * C + lane];
+            const float4 x = W.xyzq[g0 * C + lane];
             float4 h, l;
             two_sum(x.x, sh[0], h.x, l.x);
             two_sum(x.y, sh[1], h.y, l.y);
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(32 * kPruneWarps) k_prune(PruneArgs A) {
         for (int base = jb; base < je; base += 32) {
             const int nt = min(32, je - base);
             int my_w = 0;
-            if (lane < nt) my_w = A.cj[base + lane];
+            if (lane < nt) my_w = W.cj[base + lane];
             unsigned my_keep = 0;
             for (int t = 0; t < nt; ++t) {
                 const int w = __shfl_sync(full, my_w, t);
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(32 * kPruneWarps) k_prune(PruneArgs A) {
                 unsigned bits = (unsigned)w >> kSuperShift;
                 float4 xj[PPL];
 #pragma unroll
-                for (int kk = 0; kk < PPL; ++kk) xj[kk] = A.xyzq[cjt * C + pj[kk]];
+                for (int kk = 0; kk < PPL; ++kk) xj[kk] = W.xyzq[cjt * C + pj[kk]];
                 unsigned keep = 0;
                 while (bits) {
                     const int k = __ffs(bits) - 1;
@@ -109,45 +112,39 @@ __global__ void __launch_bounds__(32 * kPruneWarps) k_prune(PruneArgs A) {
             const int pos = __popc(kb & ((1u << lane) - 1u));
             if (my_keep) {
                 const long long o = jb + kept + pos;
-                A.cj_p[o] = (my_w & kCjMask) | (int)(my_keep << kSuperShift);
+                W.cj_p[o] = (my_w & kCjMask) | (int)(my_keep << kSuperShift);
 #pragma unroll
                 for (int k = 0; k < S; ++k)
-                    A.mask_p[k * A.jstride + o] = ((my_keep >> k) & 1u) ? A.mask[k * A.jstride + base + lane] : 0ull;
+                    W.mask_p[k * W.jstride + o] = ((my_keep >> k) & 1u) ? W.mask[k * W.jstride + base + lane] : 0ull;
             }
             kept += __popc(kb);
             unsigned nk = __popc(my_keep);
             for (int o = 16; o > 0; o >>= 1) nk += __shfl_xor_sync(full, nk, o);
             keys_total += nk;
         }
-        if (lane == 0) A.ient_p[e] = make_int4(q, s, jb, jb + kept);
+        if (lane == 0) W.ient_p[e] = make_int4(q, s, jb, jb + kept);
         kept_total += kept;
         __syncwarp();
     }
-    if (lane == 0 && kept_total) {
-        atomicAdd(&A.st->n_jent_pruned, kept_total);
-        atomicAdd(&A.st->n_keys_pruned, keys_total);
+    if (lane == 0 && b_acc >= 0 && kept_total) {
+        atomicAdd(&W.st[b_acc].n_jent_pruned, kept_total);
+        atomicAdd(&W.st[b_acc].n_keys_pruned, keys_total);
     }
 }
 
-cudaError_t launch_prune(const Workspace& ws, const GridGeom& g, int C, float r_prune,
-                         long long ient_cap, int n_sm, cudaStream_t s) {
+// Zero every box's pruned counters.
+__global__ void k_prune_reset(Workspace ws) {
+    for (int b = threadIdx.x; b < ws.nbox; b += blockDim.x) {
+        ws.st[b].n_jent_pruned = 0;
+        ws.st[b].n_keys_pruned = 0;
+    }
+}
+
+cudaError_t launch_prune(const Workspace& ws, int C, float r_prune, int n_sm, cudaStream_t s) {
     PruneArgs A;
-    A.st = ws.st;
-    A.xyzq = ws.xyzq;
-    A.sc_info = ws.sc_info;
-    A.ient = ws.ient;
-    A.cj = ws.cj;
-    A.mask = ws.mask;
-    A.ient_p = ws.ient_p;
-    A.cj_p = ws.cj_p;
-    A.mask_p = ws.mask_p;
-    A.jstride = ws.jstride;
-    for (int k = 0; k < 3; ++k) A.L[k] = g.L[k];
+    A.ws = ws;
     A.rp2 = r_prune * r_prune;
-    A.ient_cap = ient_cap;
-    cudaError_t e = cudaMemsetAsync(&ws.st->n_jent_pruned, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&ws.st->n_keys_pruned, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
+    k_prune_reset<<<1, 256, 0, s>>>(ws);
     const int blocks = n_sm * 16;
     if (C == 8)
         k_prune<8, super_size(8)><<<blocks, 32 * kPruneWarps, 0, s>>>(A);

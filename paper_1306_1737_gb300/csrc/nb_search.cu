@@ -19,25 +19,10 @@
 namespace nbc {
 
 struct SearchArgs {
-    DevState* st;
-    const float4* bb;
-    const float4* xyzq;
-    const int* atom_of_slot;
-    const int* slot_of_atom;
-    const int* col_clu_start;
-    const int2* sc_info;
+    Workspace ws;
     const int* excl_off;
     const int* excl_idx;
-    float L[3];
-    float inv_cx, inv_cy;
-    int nx, ny;
     float rl, rl2, rbb2;
-    int4* ient;
-    int* cj;
-    unsigned long long* mask;
-    long long jstride;
-    long long ient_cap, jent_cap;
-    int n_atoms;
 };
 
 template <int C>
@@ -59,7 +44,7 @@ constexpr int kSearchWarps = 4;
 constexpr int kMaxExclPerSuper = 512;
 
 template <int C, int S>
-__global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
+__global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
     constexpr int PPL = (C * C + 31) / 32;  // particle pairs per lane in an atom test
     constexpr int NA = S * C;               // i particles of a super-cluster (<= 32)
     static_assert(NA <= 32, "a super-cluster's particles must fit one warp");
@@ -73,19 +58,27 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
     __shared__ int s_buf_w[kSearchWarps][kJChunk];
     __shared__ unsigned long long s_buf_m[kSearchWarps][S][kJChunk];
 
-    const int nsc = A.st->nsc;
+    const Workspace& W = A.ws;
     const float eps = 1e-4f;
-    for (int q = blockIdx.x * kSearchWarps + wib; q < nsc; q += gridDim.x * kSearchWarps) {
-        const int2 info = A.sc_info[q];
+    int b = 0;
+    for (int q = blockIdx.x * kSearchWarps + wib; q < W.sc_total; q += gridDim.x * kSearchWarps) {
+        b = advance_box(W.lay.sc_off, W.nbox, b, q);
+        if (q - W.lay.sc_off[b] >= W.st[b].nsc) continue;
+        DevState* st = &W.st[b];
+        const BoxGeom G = W.geo[b];
+        const int col_base = W.lay.col_off[b];
+        const long long ient_base = W.lay.ient_off[b], ient_cap = W.lay.ient_off[b + 1] - ient_base;
+        const long long jent_base = W.lay.jent_off[b], jent_cap = W.lay.jent_off[b + 1] - jent_base;
+        const int2 info = W.sc_info[q];
         const int g0 = info.x, n = info.y;
         // i particles of the super-cluster, real-slot bits per i-cluster
-        const int aos = lane < n * C ? A.atom_of_slot[g0 * C + lane] : -1;
-        if (lane < NA) s_xi[wib][lane] = lane < n * C ? A.xyzq[g0 * C + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int aos = lane < n * C ? W.atom_of_slot[g0 * C + lane] : -1;
+        if (lane < NA) s_xi[wib][lane] = lane < n * C ? W.xyzq[g0 * C + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         const unsigned realAll = __ballot_sync(full, aos >= 0);
         // union bounding box
         float ulo[3] = {INFINITY, INFINITY, INFINITY}, uhi[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int k = 0; k < n; ++k) {
-            const float4 lo = A.bb[2 * (g0 + k)], hi = A.bb[2 * (g0 + k) + 1];
+            const float4 lo = W.bb[2 * (g0 + k)], hi = W.bb[2 * (g0 + k) + 1];
             ulo[0] = fminf(ulo[0], lo.x); ulo[1] = fminf(ulo[1], lo.y); ulo[2] = fminf(ulo[2], lo.z);
             uhi[0] = fmaxf(uhi[0], hi.x); uhi[1] = fmaxf(uhi[1], hi.y); uhi[2] = fmaxf(uhi[2], hi.z);
         }
@@ -103,15 +96,15 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
                 if (lane >= o) incl += v;
             }
             const int total = __shfl_sync(full, incl, 31);
-            if (total > kMaxExclPerSuper && lane == 0) set_flag(A.st, NB_ERR_CAPACITY);
+            if (total > kMaxExclPerSuper && lane == 0) set_flag(st, NB_ERR_CAPACITY);
             for (int k = 0; k < cnt; ++k) {
                 const int idx = incl - cnt + k;
                 if (idx < kMaxExclPerSuper) {
                     const int qa = A.excl_idx[off + k];
-                    const bool ok = qa >= 0 && qa < A.n_atoms;
-                    if (!ok) set_flag(A.st, NB_ERR_ARG);
+                    const bool ok = qa >= 0 && qa < W.atom_total;
+                    if (!ok) set_flag(st, NB_ERR_ARG);
                     s_ex_r[wib][idx] = lane;
-                    s_ex_s[wib][idx] = ok ? A.slot_of_atom[qa] : -1;
+                    s_ex_s[wib][idx] = ok ? W.slot_of_atom[qa] : -1;
                 }
             }
             nex = min(total, kMaxExclPerSuper);
@@ -119,61 +112,63 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
         __syncwarp();
 
         for (int s = 0; s < 27; ++s) {
-            const float sh[3] = {(float)(s / 9 - 1) * A.L[0], (float)((s / 3) % 3 - 1) * A.L[1],
-                                 (float)(s % 3 - 1) * A.L[2]};
+            const float sh[3] = {(float)(s / 9 - 1) * G.L[0], (float)((s / 3) % 3 - 1) * G.L[1],
+                                 (float)(s % 3 - 1) * G.L[2]};
             // candidate columns from the shifted union box (plain FP32 with a margin)
-            int ix0 = (int)floorf((ulo[0] + sh[0] - A.rl - eps) * A.inv_cx);
-            int ix1 = (int)floorf((uhi[0] + sh[0] + A.rl + eps) * A.inv_cx);
-            int iy0 = (int)floorf((ulo[1] + sh[1] - A.rl - eps) * A.inv_cy);
-            int iy1 = (int)floorf((uhi[1] + sh[1] + A.rl + eps) * A.inv_cy);
-            if (ix1 < 0 || ix0 > A.nx - 1 || iy1 < 0 || iy0 > A.ny - 1) continue;
+            int ix0 = (int)floorf((ulo[0] + sh[0] - A.rl - eps) * G.inv_cx);
+            int ix1 = (int)floorf((uhi[0] + sh[0] + A.rl + eps) * G.inv_cx);
+            int iy0 = (int)floorf((ulo[1] + sh[1] - A.rl - eps) * G.inv_cy);
+            int iy1 = (int)floorf((uhi[1] + sh[1] + A.rl + eps) * G.inv_cy);
+            if (ix1 < 0 || ix0 > G.nx - 1 || iy1 < 0 || iy0 > G.ny - 1) continue;
             const float zlo = ulo[2] + sh[2] - A.rl - eps, zhi = uhi[2] + sh[2] + A.rl + eps;
-            if (zhi < 0.0f || zlo >= A.L[2]) continue;
+            if (zhi < 0.0f || zlo >= G.L[2]) continue;
             ix0 = max(ix0, 0);
-            ix1 = min(ix1, A.nx - 1);
+            ix1 = min(ix1, G.nx - 1);
             iy0 = max(iy0, 0);
-            iy1 = min(iy1, A.ny - 1);
+            iy1 = min(iy1, G.ny - 1);
             const int ncy = iy1 - iy0 + 1;
             const int ncols = (ix1 - ix0 + 1) * ncy;
             // exact shifted boxes of the i-clusters as hi + lo
             if (lane < n * 6) {
                 const int k = lane / 6, c = lane % 6, d = c % 3;
-                const float4 b = c < 3 ? A.bb[2 * (g0 + k)] : A.bb[2 * (g0 + k) + 1];
-                const float v = d == 0 ? b.x : (d == 1 ? b.y : b.z);
+                const float4 bx = c < 3 ? W.bb[2 * (g0 + k)] : W.bb[2 * (g0 + k) + 1];
+                const float v = d == 0 ? bx.x : (d == 1 ? bx.y : bx.z);
+                const float shd = d == 0 ? sh[0] : (d == 1 ? sh[1] : sh[2]);
                 float h, l;
-                two_sum(v, sh[d], h, l);
+                two_sum(v, shd, h, l);
                 s_bb[wib][k][2 * c] = h;
                 s_bb[wib][k][2 * c + 1] = l;
             }
             __syncwarp();
 
             int nbuf = 0;
-            auto flush = [&]() {
+            auto flush = [&]() __attribute__((always_inline)) {
                 __syncwarp();
                 unsigned long long jb = 0, ie = 0;
                 unsigned nk = 0;
                 for (int t = lane; t < nbuf; t += 32) nk += __popc((unsigned)s_buf_w[wib][t] >> kSuperShift);
                 for (int o = 16; o > 0; o >>= 1) nk += __shfl_xor_sync(full, nk, o);
                 if (lane == 0) {
-                    jb = atomicAdd(&A.st->n_jent, (unsigned long long)nbuf);
-                    ie = atomicAdd(&A.st->n_ient, 1ull);
-                    atomicAdd(&A.st->n_keys, (unsigned long long)nk);
+                    jb = atomicAdd(&st->n_jent, (unsigned long long)nbuf);
+                    ie = atomicAdd(&st->n_ient, 1ull);
+                    atomicAdd(&st->n_keys, (unsigned long long)nk);
                 }
                 jb = __shfl_sync(full, jb, 0);
                 ie = __shfl_sync(full, ie, 0);
-                if ((long long)(jb + nbuf) > A.jent_cap || (long long)ie >= A.ient_cap) {
+                if ((long long)(jb + nbuf) > jent_cap || (long long)ie >= ient_cap) {
                     // keep every stored i-entry valid: an empty range on overflow
                     if (lane == 0) {
-                        set_flag(A.st, NB_ERR_CAPACITY);
-                        if ((long long)ie < A.ient_cap) A.ient[ie] = make_int4(q, s, 0, 0);
+                        set_flag(st, NB_ERR_CAPACITY);
+                        if ((long long)ie < ient_cap) W.ient[ient_base + ie] = make_int4(q, s, 0, 0);
                     }
                 } else {
+                    const long long j0 = jent_base + (long long)jb;
                     for (int t = lane; t < nbuf; t += 32) {
-                        A.cj[jb + t] = s_buf_w[wib][t];
+                        W.cj[j0 + t] = s_buf_w[wib][t];
 #pragma unroll
-                        for (int k = 0; k < S; ++k) A.mask[k * A.jstride + jb + t] = s_buf_m[wib][k][t];
+                        for (int k = 0; k < S; ++k) W.mask[k * W.jstride + j0 + t] = s_buf_m[wib][k][t];
                     }
-                    if (lane == 0) A.ient[ie] = make_int4(q, s, (int)jb, (int)(jb + nbuf));
+                    if (lane == 0) W.ient[ient_base + ie] = make_int4(q, s, (int)j0, (int)(j0 + nbuf));
                 }
                 nbuf = 0;
                 __syncwarp();
@@ -183,18 +178,18 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
                 const int cidx = cb + lane;
                 int k0 = 0, cnt = 0;
                 if (cidx < ncols) {
-                    const int col = (ix0 + cidx / ncy) * A.ny + (iy0 + cidx % ncy);
-                    const int c0 = A.col_clu_start[col], c1 = A.col_clu_start[col + 1];
+                    const int col = col_base + (ix0 + cidx / ncy) * G.ny + (iy0 + cidx % ncy);
+                    const int c0 = W.col_clu_start[col], c1 = W.col_clu_start[col + 1];
                     int lo = c0, hi = c1;
                     while (lo < hi) {  // first cluster with zmax >= zlo
                         const int m = (lo + hi) >> 1;
-                        if (A.bb[2 * m + 1].z < zlo) lo = m + 1; else hi = m;
+                        if (W.bb[2 * m + 1].z < zlo) lo = m + 1; else hi = m;
                     }
                     const int f = lo;
                     hi = c1;
                     while (lo < hi) {  // first cluster with zmin > zhi
                         const int m = (lo + hi) >> 1;
-                        if (A.bb[2 * m].z <= zhi) lo = m + 1; else hi = m;
+                        if (W.bb[2 * m].z <= zhi) lo = m + 1; else hi = m;
                     }
                     const int f2 = max(f, g0);
                     if (lo > f2) {
@@ -219,14 +214,14 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
                     const int ok0 = __shfl_sync(full, k0, owner);
                     const int oex = __shfl_sync(full, excl, owner);
                     const bool valid = idx < total;
-                    const int b = ok0 + (idx - oex);
+                    const int cb_ = ok0 + (idx - oex);
                     unsigned need = 0, acc = 0;  // per candidate: i-clusters to test / accepted
                     if (valid) {
-                        const float4 jlo = A.bb[2 * b], jhi = A.bb[2 * b + 1];
+                        const float4 jlo = W.bb[2 * cb_], jhi = W.bb[2 * cb_ + 1];
                         const float jl[3] = {jlo.x, jlo.y, jlo.z}, jh[3] = {jhi.x, jhi.y, jhi.z};
                         for (int k = 0; k < n; ++k) {
                             const int ck = g0 + k;
-                            if (b < ck || (b == ck && s < kShiftCenter)) continue;
+                            if (cb_ < ck || (cb_ == ck && s < kShiftCenter)) continue;
                             float d2 = 0.0f;
 #pragma unroll
                             for (int d = 0; d < 3; ++d) {
@@ -247,7 +242,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
                     while (pending) {
                         const int t = __ffs(pending) - 1;
                         pending &= pending - 1;
-                        const int bt = __shfl_sync(full, b, t);
+                        const int bt = __shfl_sync(full, cb_, t);
                         unsigned nk = __shfl_sync(full, need, t);
                         while (nk) {
                             const int k = __ffs(nk) - 1;
@@ -258,7 +253,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
                                 const int p = lane + 32 * kk;
                                 if (p >= C * C) continue;
                                 const float4 xi = s_xi[wib][k * C + p / C];
-                                const float4 xj = A.xyzq[bt * C + p % C];
+                                const float4 xj = W.xyzq[bt * C + p % C];
                                 float h, l;
                                 two_sum(xi.x, sh[0], h, l);
                                 const float dx = (h - xj.x) + l;
@@ -275,9 +270,9 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
                     while (accepted) {
                         const int t = __ffs(accepted) - 1;
                         accepted &= accepted - 1;
-                        const int bt = __shfl_sync(full, b, t);
+                        const int bt = __shfl_sync(full, cb_, t);
                         const unsigned at = __shfl_sync(full, acc, t);
-                        const int bos = lane < C ? A.atom_of_slot[bt * C + lane] : -1;
+                        const int bos = lane < C ? W.atom_of_slot[bt * C + lane] : -1;
                         const unsigned realB = __ballot_sync(full, bos >= 0);
 #pragma unroll
                         for (int k = 0; k < S; ++k) {
@@ -319,36 +314,16 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(SearchArgs A) {
     }
 }
 
-cudaError_t launch_search(const Workspace& ws, const GridGeom& g, int C, long long nclu_cap,
-                          float rlist, float rbb, const int* excl_off, const int* excl_idx,
-                          long long ient_cap, long long jent_cap, int n_atoms, int n_sm,
-                          cudaStream_t s) {
+cudaError_t launch_search(const Workspace& ws, int C, float rlist, float rbb, const int* excl_off,
+                          const int* excl_idx, int n_sm, cudaStream_t s) {
     SearchArgs A;
-    A.st = ws.st;
-    A.bb = ws.bb;
-    A.xyzq = ws.xyzq;
-    A.atom_of_slot = ws.atom_of_slot;
-    A.slot_of_atom = ws.slot_of_atom;
-    A.col_clu_start = ws.col_clu_start;
-    A.sc_info = ws.sc_info;
+    A.ws = ws;
     A.excl_off = excl_off;
     A.excl_idx = excl_idx;
-    for (int k = 0; k < 3; ++k) A.L[k] = g.L[k];
-    A.inv_cx = (float)g.nx / g.L[0];
-    A.inv_cy = (float)g.ny / g.L[1];
-    A.nx = g.nx;
-    A.ny = g.ny;
     A.rl = rlist;
     A.rl2 = rlist * rlist;
     A.rbb2 = rbb * rbb;
-    A.ient = ws.ient;
-    A.cj = ws.cj;
-    A.mask = ws.mask;
-    A.jstride = ws.jstride;
-    A.ient_cap = ient_cap;
-    A.jent_cap = jent_cap;
-    A.n_atoms = n_atoms;
-    long long want = (nclu_cap + kSearchWarps - 1) / kSearchWarps;
+    long long want = ((long long)ws.sc_total + kSearchWarps - 1) / kSearchWarps;
     long long blocks = (long long)n_sm * 16;
     if (blocks > want) blocks = want;
     if (blocks < 1) blocks = 1;

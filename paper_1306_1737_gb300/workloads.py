@@ -357,3 +357,68 @@ def prune_radius(rc: float, rlist: float, nstprune: int, T: float = 300.0,
     rlist.  The paper prunes close to the cut-off without giving the radius."""
     s_pair = math.sqrt(2.0) * math.sqrt(KB_KJ_PER_MOL_K * T / m_fast) * dt * math.sqrt(nstprune)
     return rc + max(0.0, min(rlist - rc, 6.0 * s_pair))
+
+
+@dataclass
+class Batch:
+    """Independent periodic boxes handled together.  Particle arrays are the
+    boxes' arrays concatenated in box order; exclusion partner indices are
+    shifted to batch-global indices.  All boxes share one LJ type table."""
+
+    xyz: np.ndarray          # float32 [n, 3]
+    q: np.ndarray            # float32 [n]
+    types: np.ndarray        # int32 [n]
+    sigma: np.ndarray        # float64 [ntypes]
+    eps: np.ndarray          # float64 [ntypes]
+    mass: np.ndarray         # float64 [n]
+    excl_off: np.ndarray     # int32 [n + 1]
+    excl_idx: np.ndarray     # int32 [nexcl], batch-global
+    counts: np.ndarray       # int64 [nbox] particles per box
+    boxes: np.ndarray        # float64 [nbox, 3] edge lengths
+    members: list = field(default_factory=list)  # the Box of each box
+
+    @property
+    def n(self) -> int:
+        return int(self.xyz.shape[0])
+
+    @property
+    def nbox(self) -> int:
+        return int(self.counts.shape[0])
+
+    @property
+    def offsets(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum(self.counts)]).astype(np.int64)
+
+
+def concat(boxes: list) -> Batch:
+    """Concatenate boxes that share one LJ type table into a Batch."""
+    if not boxes:
+        raise ValueError("no boxes")
+    s0, e0 = boxes[0].sigma, boxes[0].eps
+    for b in boxes:
+        if b.sigma.shape != s0.shape or not (np.array_equal(b.sigma, s0) and np.array_equal(b.eps, e0)):
+            raise ValueError("boxes of a batch must share the LJ type table")
+    counts = np.array([b.n for b in boxes], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    eo, ei = [np.zeros(1, np.int64)], []
+    base_e = 0
+    for k, b in enumerate(boxes):
+        eo.append(b.excl_off[1:].astype(np.int64) + base_e)
+        ei.append(b.excl_idx.astype(np.int64) + off[k])
+        base_e += int(b.excl_off[-1])
+    return Batch(xyz=np.concatenate([b.xyz for b in boxes]).astype(np.float32),
+                 q=np.concatenate([b.q for b in boxes]).astype(np.float32),
+                 types=np.concatenate([b.types for b in boxes]).astype(np.int32),
+                 sigma=s0.copy(), eps=e0.copy(),
+                 mass=np.concatenate([b.mass for b in boxes]),
+                 excl_off=np.concatenate(eo).astype(np.int32),
+                 excl_idx=(np.concatenate(ei) if ei else np.zeros(0)).astype(np.int32),
+                 counts=counts, boxes=np.stack([b.box for b in boxes]), members=list(boxes))
+
+
+def batch_boxes(n_boxes: int = 256, seed: int = 1004) -> Batch:
+    """The batch of uneven water boxes: box k holds batch_sizes()[k] atoms
+    (a whole number of molecules) at water density, drawn with seed
+    seed * 1000 + k."""
+    sizes = batch_sizes(n_boxes, seed)
+    return concat([water_box(int(n) // 3, None, seed=seed * 1000 + k) for k, n in enumerate(sizes)])
