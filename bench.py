@@ -214,10 +214,32 @@ def cpu_baseline(box, p, budget_s=15.0):
             "sample": f"{n} x ({what}), FP64 OpenMP, after one untimed repetition"}
 
 
+def run_reference_batch(args):
+    """The oracle on the batch workload: each step is the seeded sample of
+    batch_cpu_baseline, scaled to batch evaluations."""
+    import oracle
+    B, p = batch_workload()
+    vals = [batch_cpu_baseline(B, p, budget_s=4.0) for _ in range(args.warmup + args.steps)][args.warmup:]
+    value = len(vals) / sum(1.0 / v["value"] for v in vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": BATCH_UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "batch256", "n_boxes": B.nbox, "n_atoms": int(B.n)},
+        "cpu_baseline": {"value": value, "unit": BATCH_UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": "each step: " + vals[0]["sample"]},
+        "e2e": {"value": value, "unit": BATCH_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload == "batch256":
+        return run_reference_batch(args)
     desc, fn = workloads()[args.workload]
     box, p = fn()
     import oracle
@@ -457,18 +479,255 @@ def run_ours(args):
     return 0
 
 
+BATCH_H = 40          # frames per batch step (a multiple of every tuned nstlist)
+BATCH_UNIT = "batch force evals/s"
+
+
+def batch_workload():
+    from paper_1306_1737_gb300 import workloads as w
+    B = w.batch_boxes(256, seed=1004)
+    p = {"elec": "ewald", "rc": 1.0, "rlist": 1.1, "beta": 3.12, "nstlist": 20, "nstprune": 5}
+    return B, p
+
+
+def batch_frames(B, dev):
+    """Device tensor [BATCH_H, n, 3]: a random walk of every box from its
+    initial coordinates (seeded), drawn one frame at a time."""
+    import torch
+    from paper_1306_1737_gb300 import workloads as w
+    fr = torch.empty((BATCH_H, B.n, 3), dtype=torch.float32, device=dev)
+    for f, x in enumerate(w.frame_walk(B.xyz, B.mass, BATCH_H, seed=3004)):
+        fr[f].copy_(torch.from_numpy(x))
+    return fr
+
+
+def batch_cpu_baseline(B, p, budget_s=15.0):
+    """The oracle on a seeded sample: for 8 boxes, the forces of a seeded
+    subset of particles against all particles of their box; scaled by the
+    pair work of one evaluation of the whole batch."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(11)
+    picks = rng.choice(B.nbox, 8, replace=False)
+    total_work = float((B.counts.astype(np.float64) ** 2).sum())
+    # size the subset from one probe
+    b0 = B.members[int(picks[0])]
+    t0 = time.perf_counter()
+    oracle_eval(b0, p, sel=rng.choice(b0.n, 32, replace=False))
+    per_pair = (time.perf_counter() - t0) / (32 * b0.n)
+    m = int(max(32, min(4096, budget_s / 8 / max(per_pair, 1e-12) / float(B.counts[picks].mean()))))
+    sels = [(B.members[int(k)], rng.choice(B.members[int(k)].n, min(m, B.members[int(k)].n), replace=False))
+            for k in picks]
+    work = sum(float(len(sel) * b.n) for b, sel in sels)
+    t0 = time.perf_counter()
+    for b, sel in sels:
+        oracle_eval(b, p, sel=sel)
+    dt = time.perf_counter() - t0
+    frac = work / total_work
+    return {"value": frac / dt, "unit": BATCH_UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"forces of {m} seeded particles in each of 8 seeded boxes against all particles of "
+                      f"their box (brute force FP64) = {frac:.2e} of the pair work of one batch evaluation"}
+
+
+def run_batch(args):
+    """The batch of 256 uneven boxes: tuned groups stepped in a CUDA graph,
+    against one context for all boxes (graph) and one context per box
+    (plain launches, one box after another)."""
+    import numpy as np
+    import torch
+
+    import paper_1306_1737_gb300 as nb
+    from paper_1306_1737_gb300 import tuner
+    from paper_1306_1737_gb300.batch import BatchRunner, GroupSpec
+
+    ws_n, rank, local = dist_env()
+    if ws_n > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nb.load()
+    B, p = batch_workload()
+    c6c12 = nb.nb_lj_combine(B.sigma, B.eps)
+    frames = batch_frames(B, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    common = (B.counts, B.boxes, B.q, B.types, c6c12, B.excl_off, B.excl_idx, frames)
+    rc, rl0, nst0, nstprune = p["rc"], p["rlist"], p["nstlist"], p["nstprune"]
+
+    def timed(fn, steps):
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms
+
+    def statuses(r):
+        return [nb.status_name(i.status) for i in r.check()]
+
+    # 1. autotuner (cached per GPU and batch)
+    cache = os.path.join(ROOT, "paper_1306_1737_gb300", "_build", "tune_cache.json")
+    t0 = time.perf_counter()
+    groups, table = tuner.tune(*common, p, nstprune, rl0, nst0, cache_path=cache, device=dev.index)
+    tune_s = time.perf_counter() - t0
+
+    # 2. tuned groups, graph
+    tuned = BatchRunner(*common, groups, p, nstprune, device=dev.index)
+    l0 = tuned.launches()
+    tuned.step()
+    torch.cuda.synchronize()
+    launches_per_step = tuned.launches() - l0
+    st_tuned = statuses(tuned)
+    tuned.capture()
+    for _ in range(args.warmup):
+        tuned.replay()
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ms_tuned = timed(tuned.replay, args.steps)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    total_s = sum(ms_tuned) / 1000.0
+    if dist is not None:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = ws_n * args.steps * BATCH_H / total_s
+
+    out = None
+    if rank == 0:
+        # 3. e2e through the API with host buffers (tuned groups, eager launches)
+        host = []
+        fr_cpu = frames.cpu()
+        for g in tuned.groups:
+            at = torch.as_tensor(g.atoms)
+            hx = fr_cpu.index_select(1, at).contiguous().pin_memory()
+            hf = torch.empty_like(hx).pin_memory()
+            host.append((hx, hf, torch.empty((g.n, 3), dtype=torch.float32, device=dev)))
+        del fr_cpu
+        tuned.step(host=host)
+        torch.cuda.synchronize()
+        e2e_ms = []
+        for _ in range(max(1, min(args.steps, 5))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            tuned.step(host=host)
+            torch.cuda.synchronize()
+            e2e_ms.append(1000 * (time.perf_counter() - t1))
+        e2e_value = len(e2e_ms) * BATCH_H / (sum(e2e_ms) / 1000.0)
+        del host
+    groups_info = [{"C": g.spec.C, "nstlist": g.spec.nstlist, "rlist_nm": round(g.spec.rlist, 4),
+                    "boxes": len(g.spec.boxes), "atoms": int(g.n)} for g in tuned.groups]
+    per_box = {int(k): f"{g.spec.C}/{g.spec.nstlist}" for g in tuned.groups for k in g.spec.boxes}
+    tuned.close()
+
+    # 4. one context for all boxes (C = 8, nstlist 20, rlist 1.1), graph; its
+    #    eager step gives the force kernel's launch times for the roofline
+    one = BatchRunner(*common, [GroupSpec(8, nst0, rl0, list(range(B.nbox)))], p, nstprune, device=dev.index)
+    g1 = one.groups[0]
+    nb.nb_profile(g1.cx.ctx, True)
+    nb.nb_profile_read(g1.cx.ctx)
+    one.step(concurrent=False)
+    spans = nb.nb_profile_read(g1.cx.ctx)
+    nb.nb_profile(g1.cx.ctx, False)
+    info1 = nb.nb_check(g1.cx.ctx)
+    one.capture(concurrent=False)
+    for _ in range(args.warmup):
+        one.replay()
+    ms_one = timed(one.replay, args.steps)
+    v_one = args.steps * BATCH_H / (sum(ms_one) / 1000.0)
+    one.close()
+
+    # 5. plain: one context per box, launches one box after another
+    plain = BatchRunner(*common, [GroupSpec(8, nst0, rl0, [k]) for k in range(B.nbox)], p, nstprune,
+                        device=dev.index)
+    plain.step(concurrent=False)
+    torch.cuda.synchronize()
+    ms_plain = timed(lambda: plain.step(concurrent=False), max(1, min(args.steps, 3)))
+    v_plain = len(ms_plain) * BATCH_H / (sum(ms_plain) / 1000.0)
+    plain.close()
+
+    if rank == 0:
+        force_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_FORCE]
+        # frames 0 and 20 use the outer list, the others the pruned one
+        # (nb_check after the step reports the last list and prune)
+        n_rc = int(info1.n_pairs_rc)
+        outer = int(info1.n_cluster_pairs) * 64
+        pruned = int(info1.n_cluster_pairs_pruned) * 64
+        listed = (2 * outer + (BATCH_H - 2) * pruned) / BATCH_H if pruned > 0 else outer
+        flops = FLOPS_DIST * listed + (FLOPS_PAIR["ewald"] - FLOPS_DIST) * n_rc
+        t_force = statistics.mean(force_ms) / 1000.0
+        pk = peaks()
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp32_peak = n_sm * 128 * 2 * pk["sm_max_mhz"] * 1e6
+        cpu = batch_cpu_baseline(B, p) if ws_n == 1 else None
+        h2d = BATCH_H * B.n * 12
+        out = {
+            "metric": METRIC, "value": value, "unit": BATCH_UNIT, "n_gpus": ws_n, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_s * 1000 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch256",
+                       "description": "256 water boxes, 1.5k-60k atoms log-uniform, Ewald rc 1.0, rlist 1.1 "
+                                      "(scaled with nstlist), prune/5; a step = 40 frames of every box",
+                       "n_boxes": B.nbox, "n_atoms": int(B.n), "frames_per_step": BATCH_H, "elec": "ewald",
+                       "rc_nm": rc, "rlist_nm": rl0, "beta_nm-1": p["beta"], "nstlist": nst0, "nstprune": nstprune,
+                       "l2": "flushed between timed steps (512 MiB write); inputs 2 GB > L2",
+                       "parallelism": f"replicas x{ws_n}", "seed": 1004},
+            "box_force_evals_per_s": value * B.nbox,
+            "atom_force_evals_per_s": value * B.n,
+            "batch": {"tuned_graph": value, "one_context_graph": v_one, "plain_per_box": v_plain,
+                      "speedup_vs_plain": value / v_plain, "one_context_vs_plain": v_one / v_plain,
+                      "groups": groups_info, "tuner_classes": table, "tuner_s": tune_s,
+                      "per_box_choice": per_box},
+            "roofline": {"bound": "alu", "kernel": "k_force8 (Ewald), one context for all 256 boxes",
+                         "achieved": flops / t_force / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                         "frac": flops / t_force / fp32_peak, "traffic": None,
+                         "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {pk['sm_max_mhz']:.0f} MHz "
+                                        f"(max SM clock, {pk['source']})",
+                         "algorithmic_flops_per_launch": flops, "launch_ms": t_force * 1e3},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": BATCH_UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "clocks": clocks,
+            "status": st_tuned[0] if len(set(st_tuned)) == 1 else st_tuned,
+        }
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="water24k", choices=["water24k", "water3m", "water1536", "water1m"])
+    ap.add_argument("--workload", default="water24k",
+                    choices=["water24k", "water3m", "water1536", "water1m", "batch256"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch256":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -171,7 +171,10 @@ nb_status nb_set_atoms(nb_ctx* ctx, int n, const float* q_dev, const int* type_d
  * coordinate in [-L, 2L) of its own box) into its box, grid x/y into columns
  * of spacing (C/rho)^(1/3), sort each column on z, cut clusters of C with
  * dummy padding, compute bounding boxes.  boxes_host: double [nbox][3] edge
- * lengths (nm) of every box, used as FP32.  Invalidates the lists.
+ * lengths (nm) of every box, used as FP32.  Invalidates the lists.  Inside
+ * a stream capture the edges must equal those of the previous call (new
+ * edges are staged through host memory, which a captured graph would re-read
+ * at every replay): NB_ERR_STATE otherwise.
  * Errors: NB_ERR_ARG, NB_ERR_BOX, NB_ERR_STATE (no atoms set),
  * NB_ERR_CAPACITY (more columns/slots than the workspace holds), NB_ERR_CUDA;
  * device flags NB_ERR_COORD, NB_ERR_CAPACITY (column > 8192 particles). */
@@ -237,7 +240,8 @@ nb_status nb_box_info(nb_ctx* ctx, int box, nb_info* info);
 
 /* enable != 0: from now on record a pair of CUDA events on the launching
  * stream around each hot-path kernel (kinds above; at most 256 spans are kept
- * until read).  enable == 0 stops recording.  Errors: NB_ERR_CUDA. */
+ * until read; launches into a capturing stream are not recorded).  enable
+ * == 0 stops recording.  Errors: NB_ERR_CUDA. */
 nb_status nb_profile(nb_ctx* ctx, int enable);
 
 /* Wait for the recorded spans and return them in launch order: kinds[k] and

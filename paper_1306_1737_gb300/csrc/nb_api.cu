@@ -66,6 +66,8 @@ struct nb_ctx {
 
 static int span_begin(nb_ctx* c, int kind, cudaStream_t s) {
     if (!c->prof || c->ev_n >= nb_ctx::kMaxSpans) return -1;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return -1;
     const int k = c->ev_n++;
     c->ev_kind[k] = kind;
     cudaEventRecord(c->ev[2 * k], s);
@@ -248,6 +250,12 @@ static void set_plan(nb_ctx* c, const std::vector<BoxPlan>& plans) {
 static nb_status upload_geometry(nb_ctx* c, const std::vector<BoxGeom>& geo, cudaStream_t s) {
     if (c->geo_uploaded && memcmp(geo.data(), c->geo_host.data(), sizeof(BoxGeom) * c->nbox) == 0)
         return NB_OK;
+    // a captured copy would read the staging buffer at every replay, after
+    // later calls may have reused it: new geometry needs an uncaptured call
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NB_CUDA(c, cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(c, NB_ERR_STATE, "box edges changed during stream capture: call nb_grid_put with them once before capturing");
     const int k = c->geo_slot;
     c->geo_slot = (k + 1) % kGeoRing;
     if (c->geo_ev_used[k]) NB_CUDA(c, cudaEventSynchronize(c->geo_ev[k]));
@@ -414,6 +422,15 @@ nb_status nb_workspace_query_boxes(nb_ctx* c, int nbox, const int* n_atoms, cons
         total += n_atoms[b];
     }
     if (total > 0x7fffffffLL) return fail(c, NB_ERR_ARG, "too many particles");
+    long long ient_sum = 0, jent_sum = 0, slot_sum = 0;
+    for (const BoxPlan& z : plans) {
+        ient_sum += z.ient_cap;
+        jent_sum += z.jent_cap;
+        slot_sum += (long long)z.nclu_cap * c->C;
+    }
+    // list and slot indices are stored as 32-bit integers
+    if (ient_sum > 0x7fffffffLL || jent_sum > 0x7fffffffLL || slot_sum > 0x7fffffffLL)
+        return fail(c, NB_ERR_CAPACITY, "list or slot capacity above 2^31 entries");
     set_plan(c, plans);
     *bytes = carve(c, nullptr, nullptr);
     return NB_OK;

@@ -352,11 +352,11 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 5 : 6) k_force8(For
     float e_lj = 0.0f, e_c = 0.0f;
     unsigned n_inc = 0;
     int b = 0, b_acc = -1;
-    for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < A.ws.ient_total;
-         e += (long long)gridDim.x * kForceWarps) {
-        b = advance_box(A.ws.lay.ient_off, A.ws.nbox, b, e);
-        const long long ient_base = A.ws.lay.ient_off[b];
-        if (e - ient_base >= min((long long)A.ws.st[b].n_ient, A.ws.lay.ient_off[b + 1] - ient_base)) continue;
+    const int ient_total = (int)A.ws.ient_total;  // below 2^31 (checked when the workspace is planned)
+    for (int e = blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < ient_total; e += gridDim.x * kForceWarps) {
+        b = advance_box(A.ws.lay.ient_off, A.ws.nbox, b, (long long)e);
+        const int ient_base = (int)A.ws.lay.ient_off[b];
+        if (e - ient_base >= (int)min((long long)A.ws.st[b].n_ient, A.ws.lay.ient_off[b + 1] - ient_base)) continue;
         if (ENERGY && b != b_acc) {
             flush_energy(A.ws.acc, b_acc, e_lj, e_c, n_inc);
             b_acc = b;
@@ -448,11 +448,11 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
     float e_lj = 0.0f, e_c = 0.0f;
     unsigned n_inc = 0;
     int b = 0, b_acc = -1;
-    for (long long e = (long long)blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < A.ws.ient_total;
-         e += (long long)gridDim.x * kForceWarps) {
-        b = advance_box(A.ws.lay.ient_off, A.ws.nbox, b, e);
-        const long long ient_base = A.ws.lay.ient_off[b];
-        if (e - ient_base >= min((long long)A.ws.st[b].n_ient, A.ws.lay.ient_off[b + 1] - ient_base)) continue;
+    const int ient_total = (int)A.ws.ient_total;  // below 2^31 (checked when the workspace is planned)
+    for (int e = blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < ient_total; e += gridDim.x * kForceWarps) {
+        b = advance_box(A.ws.lay.ient_off, A.ws.nbox, b, (long long)e);
+        const int ient_base = (int)A.ws.lay.ient_off[b];
+        if (e - ient_base >= (int)min((long long)A.ws.st[b].n_ient, A.ws.lay.ient_off[b + 1] - ient_base)) continue;
         if (ENERGY && b != b_acc) {
             flush_energy(A.ws.acc, b_acc, e_lj, e_c, n_inc);
             b_acc = b;

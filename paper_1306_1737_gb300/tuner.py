@@ -1,0 +1,117 @@
+"""Autotuner for batches of boxes.
+
+The boxes are split into size classes (equal numbers of boxes, by particle
+count).  For every class and every candidate (cluster size C in {8, 4}, list
+lifetime nstlist with its scaled list radius) the class's boxes are run
+alone as one group for one horizon, captured in a CUDA graph, and timed with
+CUDA events; the candidate with the least device time per frame wins the
+class.  Winners are cached in a JSON file keyed by the GPU, the class's
+sizes and the interaction parameters, so a later run with the same batch
+skips the timing.  Classes that chose the same candidate are merged into one
+group (one context).
+
+The paper picks the cluster shape per architecture (Sec. 2.2, Table 1) and
+the list lifetime from a buffer estimate (Sec. 2.3, Appendix); here both are
+measured on the GPU at hand.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import numpy as np
+
+from paper_1306_1737_gb300.batch import BatchRunner, GroupSpec, scaled_rlist
+
+CLUSTER_SIZES = (8, 4)
+NSTLISTS = (10, 20, 40)
+
+
+def _classes(counts, n_classes):
+    order = np.argsort(counts, kind="stable")
+    return [list(map(int, part)) for part in np.array_split(order, n_classes) if part.size]
+
+
+def _key(gpu, counts, boxes, params, rlist0, nstlist0, nstprune, H):
+    d = {"gpu": gpu, "counts": [int(c) for c in counts], "boxes": np.round(boxes, 6).tolist(),
+         "elec": params["elec"], "rc": params["rc"], "beta": params.get("beta"), "rlist0": rlist0,
+         "nstlist0": nstlist0, "nstprune": nstprune, "H": H,
+         "candidates": [list(CLUSTER_SIZES), list(NSTLISTS)]}
+    return hashlib.sha1(json.dumps(d, sort_keys=True).encode()).hexdigest()[:16]
+
+
+def time_group(spec, counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nstprune,
+               device, reps):
+    """Device ms per frame of one group run alone (graph replays)."""
+    import torch
+    r = BatchRunner(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, [spec], params, nstprune,
+                    device=device)
+    try:
+        r.capture()
+        r.replay()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            r.replay()
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        for info in r.check():
+            if info.status != 0:
+                return float("inf")
+        return float(np.median(ms)) / frames.shape[0]
+    finally:
+        r.close()
+
+
+def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nstprune, rlist0, nstlist0,
+         n_classes=4, reps=3, cache_path=None, device=0, log=None):
+    """Returns (groups: list of GroupSpec, table: list of per-class results)."""
+    import torch
+    counts = np.asarray(counts, dtype=np.int64)
+    boxes = np.asarray(boxes, dtype=np.float64).reshape(-1, 3)
+    H = int(frames.shape[0])
+    gpu = torch.cuda.get_device_name(device)
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            cache = json.load(open(cache_path))
+        except Exception:
+            cache = {}
+    table = []
+    choice = {}
+    for cls in _classes(counts, n_classes):
+        key = _key(gpu, counts[cls], boxes[cls], params, rlist0, nstlist0, nstprune, H)
+        if key in cache:
+            ent = cache[key]
+            ent["cached"] = True
+        else:
+            times = {}
+            for C in CLUSTER_SIZES:
+                for nst in NSTLISTS:
+                    if H % nst:
+                        continue
+                    spec = GroupSpec(C, nst, scaled_rlist(params["rc"], rlist0, nstlist0, nst), list(cls))
+                    t = time_group(spec, counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params,
+                                   nstprune, device, reps)
+                    times[f"{C}/{nst}"] = t
+                    if log:
+                        log(f"class {len(cls)} boxes {int(counts[cls].min())}-{int(counts[cls].max())} atoms: "
+                            f"C={C} nstlist={nst}: {t:.4f} ms/frame")
+            best = min(times, key=times.get)
+            ent = {"best": best, "ms_per_frame": times, "cached": False}
+            cache[key] = {k: v for k, v in ent.items() if k != "cached"}
+        C, nst = map(int, ent["best"].split("/"))
+        choice.setdefault((C, nst), []).extend(cls)
+        table.append({"boxes": len(cls), "atoms_min": int(counts[cls].min()), "atoms_max": int(counts[cls].max()),
+                      "best": ent["best"], "ms_per_frame": ent["ms_per_frame"], "cached": ent["cached"]})
+    if cache_path:
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        json.dump(cache, open(cache_path, "w"), indent=1, sort_keys=True)
+    groups = [GroupSpec(C, nst, scaled_rlist(params["rc"], rlist0, nstlist0, nst), sorted(b))
+              for (C, nst), b in sorted(choice.items())]
+    return groups, table

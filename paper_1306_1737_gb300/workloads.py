@@ -422,3 +422,18 @@ def batch_boxes(n_boxes: int = 256, seed: int = 1004) -> Batch:
     seed * 1000 + k."""
     sizes = batch_sizes(n_boxes, seed)
     return concat([water_box(int(n) // 3, None, seed=seed * 1000 + k) for k, n in enumerate(sizes)])
+
+
+def frame_walk(xyz: np.ndarray, mass: np.ndarray, n_frames: int, seed: int,
+               T: float = 300.0, dt: float = 0.002):
+    """Yield n_frames coordinate frames (float32 [n, 3]): frame 0 is xyz and
+    each later frame adds one Gaussian increment per coordinate with sigma
+    sqrt(kT/m) dt to the previous one (the random walk of frame_displacements,
+    drawn one frame at a time to bound host memory)."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    s = thermal_sigma(mass, T, dt).astype(np.float32)[:, None]
+    x = np.array(xyz, dtype=np.float32, copy=True)
+    yield x.copy()
+    for _ in range(n_frames - 1):
+        x += rng.standard_normal(x.shape, dtype=np.float32) * s
+        yield x.copy()
