@@ -12,6 +12,9 @@ Functions (each follows the paper passage cited in ``oracle.c``):
   pairlist       -- cluster-pair search by brute force over all cluster
                     pairs and shifts, with exclusion masks (Sec. 2.3, 2.4)
   prune          -- particle-pair distance pruning (Sec. 2.3)
+  ewald_factor   -- the Ewald real-space force factor c(r) (Sec. 3.2)
+  mlp_forward    -- the 1-32-32-1 SiLU network that may stand in for c(r)
+  mlp_loss_grad  -- its weighted squared-error loss and parameter gradient
 """
 from __future__ import annotations
 
@@ -94,6 +97,10 @@ def lib():
             L.or_key_distances.argtypes = [C.c_int, P, P, P, P, i64, P, P, P, P, P]
             L.or_prune.argtypes = [C.c_int, P, P, P, C.c_double, i64, P, P, P, P, P]
             L.or_pair_cover.argtypes = [C.c_int, P, P, C.c_double, C.c_int, P, P, i64, P, P, P, P]
+            L.or_ewald_factor.argtypes = [i64, P, C.c_double, P]
+            L.or_mlp_forward.argtypes = [P, C.c_double, C.c_double, i64, P, P]
+            L.or_mlp_loss_grad.argtypes = [P, C.c_double, C.c_double, i64, P, P, P, P]
+            L.or_mlp_loss_grad.restype = C.c_double
             _lib = L
     return _lib
 
@@ -327,3 +334,36 @@ def pair_cover(g: Grid, pl: PairList, r: float):
 
 def shift_index_to_vec(s: int):
     return (s // 9 - 1, (s // 3) % 3 - 1, s % 3 - 1)
+
+
+MLP_HIDDEN = 32
+MLP_NPARAMS = 32 + 32 + 32 * 32 + 32 + 32 + 1
+
+
+def ewald_factor(r, beta: float) -> np.ndarray:
+    """c(r) = erfc(beta r) + 2 beta r / sqrt(pi) exp(-beta^2 r^2), FP64."""
+    r = _f64(r).reshape(-1)
+    out = np.empty_like(r)
+    lib().or_ewald_factor(r.size, _p(r), float(beta), _p(out))
+    return out
+
+
+def mlp_forward(params, r_min: float, r_max: float, r) -> np.ndarray:
+    p = _f64(params).reshape(-1)
+    assert p.size == MLP_NPARAMS
+    r = _f64(r).reshape(-1)
+    y = np.empty_like(r)
+    lib().or_mlp_forward(_p(p), float(r_min), float(r_max), r.size, _p(r), _p(y))
+    return y
+
+
+def mlp_loss_grad(params, r_min: float, r_max: float, r, t, w=None):
+    """(loss, gradient [1153]) of (1/n) sum w (y(r) - t)^2."""
+    p = _f64(params).reshape(-1)
+    assert p.size == MLP_NPARAMS
+    r = _f64(r).reshape(-1)
+    t = _f64(t).reshape(-1)
+    wv = None if w is None else _f64(w).reshape(-1)
+    g = np.empty(MLP_NPARAMS)
+    loss = lib().or_mlp_loss_grad(_p(p), float(r_min), float(r_max), r.size, _p(r), _p(t), _p(wv), _p(g))
+    return float(loss), g

@@ -676,3 +676,113 @@ void or_pair_cover(int n, const float* xyz_wrapped, const float* box, double r, 
     cover[2] = many;
     free(hits);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Ewald real-space force factor (Sec. 3.2) and the small network that may
+ * stand in for it.
+ *
+ * c(r) = erfc(beta r) + (2 beta r / sqrt(pi)) exp(-beta^2 r^2): the force of
+ * a non-excluded Ewald real-space pair is f qq c(r) / r^2 (g(r) = d/dr
+ * [erf(beta r)/r] added to the plain 1/r^2).  Parity: pinned by erfc values
+ * and the beta -> 0 limit c = 1.
+ */
+void or_ewald_factor(int64_t n, const double* r, double beta, double* out) {
+    for (int64_t i = 0; i < n; ++i) {
+        const double br = beta * r[i];
+        out[i] = erfc(br) + 2.0 * br / sqrt(M_PI) * exp(-br * br);
+    }
+}
+
+#define OR_MLP_H 32
+#define OR_MLP_NP (OR_MLP_H + OR_MLP_H + OR_MLP_H * OR_MLP_H + OR_MLP_H + OR_MLP_H + 1)
+
+static double or_silu(double z) { return z / (1.0 + exp(-z)); }
+
+/* d/dz [z s(z)] with s the logistic function: s + z s (1 - s). */
+static double or_silu_d(double z) {
+    const double s = 1.0 / (1.0 + exp(-z));
+    return s + z * s * (1.0 - s);
+}
+
+/* One sample through the network, keeping the pre-activations. */
+static double or_mlp_one(const double* p, double x, double* z1, double* h1, double* z2, double* h2) {
+    const double* W1 = p;
+    const double* b1 = p + OR_MLP_H;
+    const double* W2 = p + 2 * OR_MLP_H;
+    const double* b2 = W2 + OR_MLP_H * OR_MLP_H;
+    const double* W3 = b2 + OR_MLP_H;
+    const double b3 = W3[OR_MLP_H];
+    for (int j = 0; j < OR_MLP_H; ++j) {
+        z1[j] = W1[j] * x + b1[j];
+        h1[j] = or_silu(z1[j]);
+    }
+    double y = b3;
+    for (int k = 0; k < OR_MLP_H; ++k) {
+        double s = b2[k];
+        for (int j = 0; j < OR_MLP_H; ++j) s += W2[k * OR_MLP_H + j] * h1[j];
+        z2[k] = s;
+        h2[k] = or_silu(s);
+        y += W3[k] * h2[k];
+    }
+    return y;
+}
+
+/* Multilayer perceptron 1 -> 32 -> 32 -> 1 with SiLU hidden layers (the
+ * learned stand-in for c(r)).  Input x = (r - (r_min + r_max) / 2) * 2 /
+ * (r_max - r_min); h1 = SiLU(W1 x + b1), h2 = SiLU(W2 h1 + b2),
+ * y = W3 . h2 + b3.  Parameters (1153): W1[32], b1[32], W2[32][32] (row =
+ * output unit), b2[32], W3[32], b3.
+ * Parity: pinned by a closed form (weights reducing the network to
+ * SiLU(SiLU(ln 3)) = (3/4) SiLU(ln 3) ... at chosen inputs) and by its
+ * linearity in the last layer. */
+void or_mlp_forward(const double* p, double rmin, double rmax, int64_t n, const double* r, double* y) {
+    const double c0 = 0.5 * (rmin + rmax), c1 = 2.0 / (rmax - rmin);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double z1[OR_MLP_H], h1[OR_MLP_H], z2[OR_MLP_H], h2[OR_MLP_H];
+        y[i] = or_mlp_one(p, (r[i] - c0) * c1, z1, h1, z2, h2);
+    }
+}
+
+/* Loss L = (1/n) sum_i w_i (y(r_i) - t_i)^2 (w may be NULL: all ones) and its
+ * gradient with respect to the 1153 parameters, by the chain rule layer by
+ * layer from the output back.  Parity: pinned by central finite differences
+ * of the loss (forward pinned separately). */
+double or_mlp_loss_grad(const double* p, double rmin, double rmax, int64_t n, const double* r,
+                        const double* t, const double* w, double* grad) {
+    const double c0 = 0.5 * (rmin + rmax), c1 = 2.0 / (rmax - rmin);
+    const double* W2 = p + 2 * OR_MLP_H;
+    const double* W3 = W2 + OR_MLP_H * OR_MLP_H + OR_MLP_H;
+    double* gW1 = grad;
+    double* gb1 = grad + OR_MLP_H;
+    double* gW2 = grad + 2 * OR_MLP_H;
+    double* gb2 = gW2 + OR_MLP_H * OR_MLP_H;
+    double* gW3 = gb2 + OR_MLP_H;
+    double* gb3 = gW3 + OR_MLP_H;
+    memset(grad, 0, sizeof(double) * OR_MLP_NP);
+    double loss = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double z1[OR_MLP_H], h1[OR_MLP_H], z2[OR_MLP_H], h2[OR_MLP_H], dz2[OR_MLP_H];
+        const double x = (r[i] - c0) * c1;
+        const double y = or_mlp_one(p, x, z1, h1, z2, h2);
+        const double wi = w ? w[i] : 1.0;
+        const double e = y - t[i];
+        loss += wi * e * e / (double)n;
+        const double dy = 2.0 * wi * e / (double)n;   /* dL/dy */
+        *gb3 += dy;
+        for (int k = 0; k < OR_MLP_H; ++k) {
+            gW3[k] += dy * h2[k];
+            dz2[k] = dy * W3[k] * or_silu_d(z2[k]);
+            gb2[k] += dz2[k];
+            for (int j = 0; j < OR_MLP_H; ++j) gW2[k * OR_MLP_H + j] += dz2[k] * h1[j];
+        }
+        for (int j = 0; j < OR_MLP_H; ++j) {
+            double dh = 0.0;
+            for (int k = 0; k < OR_MLP_H; ++k) dh += W2[k * OR_MLP_H + j] * dz2[k];
+            const double dz1 = dh * or_silu_d(z1[j]);
+            gW1[j] += dz1 * x;
+            gb1[j] += dz1;
+        }
+    }
+    return loss;
+}
