@@ -52,7 +52,9 @@ enum nb_status_code {
 
 enum nb_elec {
     NB_ELEC_RF = 0,    /* reaction field, g(r) = -2 k r (Sec. 3.2) */
-    NB_ELEC_EWALD = 1  /* Ewald real space, g(r) = d/dr[erf(beta r)/r] (Sec. 3.2) */
+    NB_ELEC_EWALD = 1, /* Ewald real space, g(r) = d/dr[erf(beta r)/r] (Sec. 3.2) */
+    NB_ELEC_EWALD_MLP = 2  /* Ewald real space with the force factor c(r) of unmasked pairs
+                              taken from a trained network (nb_set_surrogate); forces only */
 };
 
 enum nb_comb {
@@ -221,8 +223,14 @@ nb_status nb_prune(nb_ctx* ctx, const float* xyz_dev, float r_prune, nb_stream s
  * vir_dev: double [nbox][9], per box W = sum over pairs r_ij (x) F_ij
  * (row-major), with r_ij = x_i - x_j and F_ij the force on i; overwritten;
  * may be NULL.
+ * With p->elec == NB_ELEC_EWALD_MLP (C = 8 contexts with a network set by
+ * nb_set_surrogate), the Coulomb force of every unmasked pair inside rc with
+ * r >= r_min is f qq c_net(r) / r^2, c_net evaluated per 8 x 8 tile on the
+ * tensor cores; excluded pairs keep the analytic correction.  That mode
+ * computes forces only: with want_energy set, the analytic Ewald kernel runs
+ * instead (forces, energies and virial all analytic).
  * Errors: NB_ERR_ARG, NB_ERR_BOX (rc >= L/2 or rc > rlist), NB_ERR_STATE (no
- * list), NB_ERR_CUDA. */
+ * list; no network for NB_ELEC_EWALD_MLP), NB_ERR_CUDA. */
 nb_status nb_compute(nb_ctx* ctx, const nb_params* p, const float* xyz_dev, float* f_dev,
                      double* e_dev, double* vir_dev, nb_stream stream);
 
@@ -278,6 +286,69 @@ nb_status nb_get_grid(nb_ctx* ctx, int* atom_of_slot_dev, int* slot_of_atom_dev,
  * Errors: NB_ERR_STATE, NB_ERR_CUDA. */
 nb_status nb_get_list(nb_ctx* ctx, int which, int* ient_dev, int* cj_dev, uint64_t* mask_dev,
                       nb_stream stream);
+
+/* --- learned Ewald force factor --------------------------------------------- */
+
+/* The network: a multilayer perceptron 1 -> 32 -> 32 -> 1 with SiLU hidden
+ * layers that stands in for the Ewald real-space force factor
+ * c(r) = erfc(beta r) + 2 beta r / sqrt(pi) exp(-beta^2 r^2) (Sec. 3.2: the
+ * non-excluded real-space Coulomb force is f qq c(r) / r^2).  Input
+ * x = (r - (r_min + r_max)/2) * 2 / (r_max - r_min).  Parameters: float
+ * [NB_MLP_NPARAMS] = W1[32], b1[32], W2[32][32] (row = output unit), b2[32],
+ * W3[32], b3.  All pointers are device pointers; all calls are asynchronous
+ * on the stream.  The paper has no network; it is an alternative to the
+ * paper's analytic approximation of the same factor. */
+#define NB_MLP_NPARAMS 1153
+
+/* FP64 c(r) for n distances (the training targets).  Errors: NB_ERR_ARG,
+ * NB_ERR_CUDA. */
+nb_status nb_ewald_factor(const double* r_dev, int64_t n, double beta, double* out_dev, nb_stream stream);
+
+/* y = network(r) for n distances on the CUDA cores in FP32.
+ * Errors: NB_ERR_ARG (r_max <= r_min, null pointers), NB_ERR_CUDA. */
+nb_status nb_mlp_forward(const float* params_dev, float r_min, float r_max, const float* r_dev, int64_t n,
+                         float* y_dev, nb_stream stream);
+
+/* Bytes of the tensor-core form of a network (per-lane fragments of W2 as
+ * BF16 hi + lo parts and the lane's FP32 layer-1/3 parameters). */
+size_t nb_mlp_packed_bytes(void);
+
+/* Write the tensor-core form of params into packed_dev (16-byte aligned, at
+ * least nb_mlp_packed_bytes()).  Errors: NB_ERR_ARG, NB_ERR_CUDA. */
+nb_status nb_mlp_pack(const float* params_dev, float r_min, float r_max, void* packed_dev, nb_stream stream);
+
+/* y = network(r) through the tensor-core tile evaluator of the force kernel
+ * (64 distances per warp; layer 2 as BF16 mma.sync with hi/lo splitting and
+ * FP32 accumulation).  Errors: NB_ERR_ARG, NB_ERR_CUDA. */
+nb_status nb_mlp_forward_tc(const void* packed_dev, const float* r_dev, int64_t n, float* y_dev,
+                            nb_stream stream);
+
+/* Loss L = (1/n) sum_i w_i (y(r_i) - t_i)^2 (w_dev may be NULL: weights 1)
+ * into *loss_dev (may be NULL) and dL/dparams into grad_dev
+ * [NB_MLP_NPARAMS], FP32.  Errors: NB_ERR_ARG, NB_ERR_CUDA. */
+nb_status nb_mlp_loss_grad(const float* params_dev, float r_min, float r_max, const float* r_dev,
+                           const float* t_dev, const float* w_dev, int64_t n, float* grad_dev,
+                           float* loss_dev, nb_stream stream);
+
+/* steps Adam updates (beta1 0.9, beta2 0.999, eps 1e-8) of params_dev on
+ * minibatches of `batch` consecutive samples of (r, t, w) (wrapping around
+ * the n samples; step k of the schedule starts at sample k * batch mod n),
+ * learning rate lr_min + (lr_max - lr_min) (1 + cos(pi k / total_steps)) / 2
+ * for schedule steps k = step0 .. step0 + steps - 1.  state_dev: float
+ * [3 * NB_MLP_NPARAMS] = Adam first and second moments and a gradient
+ * buffer; zero it before step 0.  loss_dev: float [steps] minibatch losses,
+ * or NULL.  Errors: NB_ERR_ARG, NB_ERR_CUDA. */
+nb_status nb_mlp_train(float* params_dev, float* state_dev, float r_min, float r_max, const float* r_dev,
+                       const float* t_dev, const float* w_dev, int64_t n, int batch, int steps, int step0,
+                       int total_steps, float lr_max, float lr_min, float* loss_dev, nb_stream stream);
+
+/* Give the context a network for NB_ELEC_EWALD_MLP (copied into the
+ * workspace in tensor-core form on the stream; params_dev may be freed once
+ * the stream reaches this call).  The network is used for unmasked pairs
+ * with r_min <= r < rc, so r_max must be >= the rc of later nb_compute calls.
+ * Errors: NB_ERR_ARG (C != 8, bad range), NB_ERR_STATE (no workspace),
+ * NB_ERR_CUDA. */
+nb_status nb_set_surrogate(nb_ctx* ctx, const float* params_dev, float r_min, float r_max, nb_stream stream);
 
 /* --- gridding without device allocation ------------------------------------ */
 

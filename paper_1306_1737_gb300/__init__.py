@@ -28,6 +28,8 @@ NB_ERR_COORD = 7
 
 NB_ELEC_RF = 0
 NB_ELEC_EWALD = 1
+NB_ELEC_EWALD_MLP = 2
+NB_MLP_NPARAMS = 1153
 NB_COMB_LB = 0
 NB_COMB_GEOM = 1
 
@@ -101,6 +103,15 @@ def load():
             "nb_profile": ([P, i], st),
             "nb_profile_read": ([P, P, P, i, C.POINTER(C.c_int)], st),
             "nb_grid_put_noalloc": ([i, P, P, P, i, P, i, P, P, P, P, P, P, i, i, P], st),
+            "nb_ewald_factor": ([P, C.c_int64, C.c_double, P, P], st),
+            "nb_mlp_forward": ([P, C.c_float, C.c_float, P, C.c_int64, P, P], st),
+            "nb_mlp_packed_bytes": ([], C.c_size_t),
+            "nb_mlp_pack": ([P, C.c_float, C.c_float, P, P], st),
+            "nb_mlp_forward_tc": ([P, P, C.c_int64, P, P], st),
+            "nb_mlp_loss_grad": ([P, C.c_float, C.c_float, P, P, P, C.c_int64, P, P, P], st),
+            "nb_mlp_train": ([P, P, C.c_float, C.c_float, P, P, P, C.c_int64, i, i, i, i, C.c_float,
+                              C.c_float, P, P], st),
+            "nb_set_surrogate": ([P, P, C.c_float, C.c_float, P], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -114,7 +125,7 @@ def exported_symbols():
     """Names declared in include/nbcluster.h (for the ABI test)."""
     import re
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:nb_status|const char\*)\s+(nb_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:nb_status|const char\*|size_t)\s+(nb_\w+)\s*\(", txt, re.M)))
 
 
 def status_name(s: int) -> str:
@@ -233,8 +244,9 @@ def nb_prune(ctx, xyz, r_prune, stream=None):
 
 def make_params(elec: str, rc: float, eps_rf: float = float("inf"), beta: float = 0.0,
                 want_energy: bool = True) -> nb_params:
-    return nb_params(NB_ELEC_RF if elec == "rf" else NB_ELEC_EWALD, int(bool(want_energy)),
-                     float(rc), float(eps_rf), float(beta))
+    """elec: "rf", "ewald" or "ewald_mlp" (the network from nb_set_surrogate)."""
+    code = {"rf": NB_ELEC_RF, "ewald": NB_ELEC_EWALD, "ewald_mlp": NB_ELEC_EWALD_MLP}[elec]
+    return nb_params(code, int(bool(want_energy)), float(rc), float(eps_rf), float(beta))
 
 
 def nb_compute(ctx, params: nb_params, xyz, f, e=None, vir=None, stream=None):
@@ -292,6 +304,51 @@ def nb_grid_put_noalloc(n, xyz, q, types, ntypes, box, cluster_size, atom_of_slo
                                    _ptr(bb), _ptr(col_clu_start), _ptr(info), int(max_slots),
                                    int(max_columns), _stream(stream))
     _check(None, s)
+
+
+def _status(s, what):
+    if s != NB_OK:
+        raise NbError(s, what)
+
+
+def nb_ewald_factor(r, beta, out, stream=None):
+    _status(load().nb_ewald_factor(_ptr(r), int(r.numel()), float(beta), _ptr(out), _stream(stream)),
+            "nb_ewald_factor")
+
+
+def nb_mlp_forward(params, r_min, r_max, r, y, stream=None):
+    _status(load().nb_mlp_forward(_ptr(params), float(r_min), float(r_max), _ptr(r), int(r.numel()), _ptr(y),
+                                  _stream(stream)), "nb_mlp_forward")
+
+
+def nb_mlp_packed_bytes() -> int:
+    return int(load().nb_mlp_packed_bytes())
+
+
+def nb_mlp_pack(params, r_min, r_max, packed, stream=None):
+    _status(load().nb_mlp_pack(_ptr(params), float(r_min), float(r_max), _ptr(packed), _stream(stream)),
+            "nb_mlp_pack")
+
+
+def nb_mlp_forward_tc(packed, r, y, stream=None):
+    _status(load().nb_mlp_forward_tc(_ptr(packed), _ptr(r), int(r.numel()), _ptr(y), _stream(stream)),
+            "nb_mlp_forward_tc")
+
+
+def nb_mlp_loss_grad(params, r_min, r_max, r, t, w, grad, loss=None, stream=None):
+    _status(load().nb_mlp_loss_grad(_ptr(params), float(r_min), float(r_max), _ptr(r), _ptr(t), _ptr(w),
+                                    int(r.numel()), _ptr(grad), _ptr(loss), _stream(stream)), "nb_mlp_loss_grad")
+
+
+def nb_mlp_train(params, state, r_min, r_max, r, t, w, batch, steps, step0, total_steps, lr_max, lr_min,
+                 loss=None, stream=None):
+    _status(load().nb_mlp_train(_ptr(params), _ptr(state), float(r_min), float(r_max), _ptr(r), _ptr(t), _ptr(w),
+                                int(r.numel()), int(batch), int(steps), int(step0), int(total_steps),
+                                float(lr_max), float(lr_min), _ptr(loss), _stream(stream)), "nb_mlp_train")
+
+
+def nb_set_surrogate(ctx, params, r_min, r_max, stream=None):
+    _check(ctx, load().nb_set_surrogate(ctx, _ptr(params), float(r_min), float(r_max), _stream(stream)))
 
 
 # --- convenience: boxes with their torch-allocated workspace ----------------

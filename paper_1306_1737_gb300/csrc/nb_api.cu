@@ -11,6 +11,7 @@
 
 #include "nb_ewald_fit.h"
 #include "nb_internal.cuh"
+#include "nb_mlp.cuh"
 
 using namespace nbc;
 
@@ -53,6 +54,8 @@ struct nb_ctx {
     // state
     int n = 0, ntypes = 0;
     bool have_atoms = false, have_grid = false, have_list = false, have_pruned = false;
+    bool have_mlp = false;
+    float mlp_rmin = 0.f, mlp_rmax = 0.f;
     float rlist = 0.f, r_prune = 0.f;
     long long n_launches = 0;
     // timing spans (nb_profile)
@@ -216,6 +219,7 @@ static size_t carve(const nb_ctx* c, char* base, Workspace* ws) {
     w.cj_p = (int*)take(sizeof(int) * w.jstride);
     w.mask_p = (unsigned long long*)take(sizeof(unsigned long long) * w.jstride * S);
     w.c6c12 = (float2*)take(sizeof(float2) * kMaxTypes * kMaxTypes);
+    w.mlp = (MlpTC*)take(sizeof(MlpTC));
     if (ws) *ws = w;
     return (off + 255) & ~(size_t)255;
 }
@@ -454,6 +458,7 @@ nb_status nb_set_workspace(nb_ctx* c, void* ws, size_t bytes) {
     c->ws_base = (char*)ws;
     c->ws_bytes = bytes;
     c->have_atoms = c->have_grid = c->have_list = c->have_pruned = false;
+    c->have_mlp = false;
     c->last_valid = false;
     c->geo_uploaded = false;
     release_host(c);
@@ -600,18 +605,25 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     if (!c) return NB_ERR_ARG;
     if (!p || (!f && c->n > 0)) return fail(c, NB_ERR_ARG, "compute: null argument");
     if (!c->have_list) return fail(c, NB_ERR_STATE, "nb_pairlist_build first");
-    if (p->elec != NB_ELEC_RF && p->elec != NB_ELEC_EWALD) return fail(c, NB_ERR_ARG, "unknown electrostatics");
+    if (p->elec != NB_ELEC_RF && p->elec != NB_ELEC_EWALD && p->elec != NB_ELEC_EWALD_MLP)
+        return fail(c, NB_ERR_ARG, "unknown electrostatics");
+    if (p->elec == NB_ELEC_EWALD_MLP) {
+        if (!c->have_mlp) return fail(c, NB_ERR_STATE, "no network: call nb_set_surrogate first");
+        if (p->rc > c->mlp_rmax) return fail(c, NB_ERR_ARG, "rc above the network's input range");
+    }
     if (!(p->rc > 0.f)) return fail(c, NB_ERR_ARG, "rc must be positive");
     if (!(p->rc < 0.5f * min_edge(c))) return fail(c, NB_ERR_BOX, "rc must be below half the box");
     const float rlive = c->have_pruned ? c->r_prune : c->rlist;
     if (p->rc > rlive) return fail(c, NB_ERR_BOX, "rc above the list radius");
-    if (p->elec == NB_ELEC_EWALD && !(p->beta >= 0.f)) return fail(c, NB_ERR_ARG, "beta must be >= 0");
+    if (p->elec != NB_ELEC_RF && !(p->beta >= 0.f)) return fail(c, NB_ERR_ARG, "beta must be >= 0");
     if (xyz) {
         nb_status st = nb_set_coords(c, xyz, stream);
         if (st != NB_OK) return st;
     }
     ForceParams fp{};
-    fp.elec = p->elec;
+    // the surrogate kernel computes forces only; energy evaluations are analytic
+    fp.elec = (p->elec == NB_ELEC_EWALD_MLP && p->want_energy) ? NB_ELEC_EWALD : p->elec;
+    fp.mlp_rmin = c->mlp_rmin;
     fp.want_energy = p->want_energy ? 1 : 0;
     fp.rc2 = p->rc * p->rc;
     fp.fcoul = 138.935458f;
@@ -627,6 +639,8 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     fp.beta2 = (float)((double)p->beta * p->beta);
     fp.beta3 = (float)((double)p->beta * p->beta * p->beta);
     fp.use_fit = ((double)p->beta * p->beta * rc * rc <= (double)kEwaldFitWMax) ? 1 : 0;
+    if (fp.elec == NB_ELEC_EWALD_MLP && !fp.use_fit)
+        return fail(c, NB_ERR_ARG, "the surrogate kernel needs (beta rc)^2 <= %g", (double)kEwaldFitWMax);
     fp.ntypes = c->ntypes;
     fp.use_pruned = c->have_pruned ? 1 : 0;
     cudaStream_t s = (cudaStream_t)stream;
@@ -638,6 +652,22 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     e = launch_finalize(c->ws, fp, f, e_out, vir_out, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
     c->n_launches += 2 + (fp.want_energy ? 1 : 0);
+    return NB_OK;
+}
+
+nb_status nb_set_surrogate(nb_ctx* c, const float* params, float r_min, float r_max, nb_stream stream) {
+    if (!c) return NB_ERR_ARG;
+    if (!c->ws_base) return fail(c, NB_ERR_STATE, "no workspace");
+    if (c->C != 8) return fail(c, NB_ERR_ARG, "the surrogate kernel needs 8-particle clusters");
+    if (!params || !(r_min >= 0.f) || !(r_max > r_min) || !std::isfinite(r_max))
+        return fail(c, NB_ERR_ARG, "set_surrogate: bad argument");
+    NB_CUDA(c, cudaSetDevice(c->device));
+    const nb_status st = nb_mlp_pack(params, r_min, r_max, c->ws.mlp, stream);
+    if (st != NB_OK) return fail(c, st, "packing the network failed");
+    c->n_launches += 1;
+    c->have_mlp = true;
+    c->mlp_rmin = r_min;
+    c->mlp_rmax = r_max;
     return NB_OK;
 }
 

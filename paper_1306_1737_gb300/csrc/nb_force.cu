@@ -21,6 +21,7 @@
 //           V = qq (erfc(br) - (1-e)) r^-1
 #include "nb_internal.cuh"
 #include "nb_ewald_fit.h"
+#include "nb_mlp.cuh"
 
 namespace nbc {
 
@@ -271,13 +272,106 @@ __device__ __forceinline__ bool icluster8(const ForceParams& P, const float2* s_
     return true;
 }
 
+// The surrogate form of icluster8 (forces only): unmasked pairs inside rc
+// with r >= r_min take the Coulomb factor c(r) from the network, evaluated
+// for the whole 8 x 8 tile at once on the tensor cores; force-field-excluded
+// pairs (and any unmasked pair below r_min) keep the fitted analytic
+// correction.
+template <bool SHIFTED, bool FULL>
+__device__ __forceinline__ bool icluster8_mlp(const ForceParams& P, const float2* s_lj, const WarpSmem& W,
+                                              const Lane8& L, int k, bool diag, unsigned long long m,
+                                              float4 xj, int tj, float2& fx, float2& fy, float2& fz,
+                                              float& fjx, float& fjy, float& fjz, const MlpTC& M, float* mo) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const float4 a0 = W.xi[k * 8 + L.ih], a1 = W.xi[k * 8 + L.ih + 4];
+    float d0x = a0.x - xj.x, d1x = a1.x - xj.x;
+    float d0y = a0.y - xj.y, d1y = a1.y - xj.y;
+    float d0z = a0.z - xj.z, d1z = a1.z - xj.z;
+    if (SHIFTED) {
+        const float4 b0 = W.xl[k * 8 + L.ih], b1 = W.xl[k * 8 + L.ih + 4];
+        d0x += b0.x; d1x += b1.x;
+        d0y += b0.y; d1y += b1.y;
+        d0z += b0.z; d1z += b1.z;
+    }
+    const float2 dx = make_float2(d0x, d1x), dy = make_float2(d0y, d1y), dz = make_float2(d0z, d1z);
+    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    bool u0 = true, u1 = true;
+    if (!FULL) {
+        u0 = ((unsigned)m & L.sel) != 0u;
+        u1 = ((unsigned)(m >> 32) & L.sel) != 0u;
+    }
+    bool inc0 = r2.x < P.rc2;
+    bool inc1 = r2.y < P.rc2;
+    if (!FULL && diag) {
+        inc0 = inc0 && (u0 || !L.lower0);
+        inc1 = inc1 && (u1 || !L.lower1);
+    }
+    if (!__any_sync(full, inc0 || inc1)) return false;
+    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 rinv2 = mul2(rinv, rinv);
+    const float2 rinv3 = mul2(rinv, rinv2);
+    const float2 rinv6 = mul2(rinv3, rinv3);
+    const float rr0 = r2.x * rinv.x, rr1 = r2.y * rinv.y;
+    const bool n0 = inc0 && u0 && rr0 >= P.mlp_rmin, n1 = inc1 && u1 && rr1 >= P.mlp_rmin;
+    float c0 = 0.0f, c1 = 0.0f;
+    if (__any_sync(full, n0 || n1)) {
+        // tile row p is the lane's first pair (p = lane) or its second
+        // (p = lane + 32); m-tile t holds rows 16 t + g and 16 t + 8 + g
+        const float ra = n0 ? rr0 : P.mlp_rmin, rb = n1 ? rr1 : P.mlp_rmin;
+        const int g = lane >> 2;
+#pragma unroll 1
+        for (int t = 0; t < 4; ++t) {
+            const float src = t < 2 ? ra : rb;
+            const int base = g + 16 * (t & 1);
+            const float x0 = (__shfl_sync(full, src, base) - M.c0) * M.c1;
+            const float x1 = (__shfl_sync(full, src, base + 8) - M.c0) * M.c1;
+            float o0, o1;
+            mlp_mtile(M, lane, x0, x1, o0, o1);
+            if ((lane & 3) == 0) {
+                mo[16 * t + g] = o0;
+                mo[16 * t + 8 + g] = o1;
+            }
+        }
+        __syncwarp();
+        c0 = mo[lane];
+        c1 = mo[lane + 32];
+        __syncwarp();
+    }
+    const bool a0f = inc0 && !n0, a1f = inc1 && !n1;   // analytic correction
+    float g0 = 0.0f, g1 = 0.0f;
+    if (__any_sync(full, a0f || a1f)) {
+        g0 = a0f ? ewald_fit_g(P.beta2 * r2.x) : 0.0f;
+        g1 = a1f ? ewald_fit_g(P.beta2 * r2.y) : 0.0f;
+    }
+    const float2 lj0 = s_lj[W.row[k * 8 + L.ih] + tj], lj1 = s_lj[W.row[k * 8 + L.ih + 4] + tj];
+    const float qq0 = a0.w * xj.w, qq1 = a1.w * xj.w;
+    float flj0 = fmaf(lj0.y, rinv6.x, lj0.x) * rinv6.x * rinv2.x;
+    float flj1 = fmaf(lj1.y, rinv6.y, lj1.x) * rinv6.y * rinv2.y;
+    if (!FULL) {
+        flj0 = u0 ? flj0 : 0.0f;
+        flj1 = u1 ? flj1 : 0.0f;
+    }
+    const float fc0 = n0 ? qq0 * c0 * rinv3.x : qq0 * fmaf(-P.beta3, g0, u0 ? rinv3.x : 0.0f);
+    const float fc1 = n1 ? qq1 * c1 * rinv3.y : qq1 * fmaf(-P.beta3, g1, u1 ? rinv3.y : 0.0f);
+    const float2 fs = make_float2(inc0 ? flj0 + fc0 : 0.0f, inc1 ? flj1 + fc1 : 0.0f);
+    const float2 px = mul2(fs, dx), py = mul2(fs, dy), pz = mul2(fs, dz);
+    fx = add2(fx, px);
+    fy = add2(fy, py);
+    fz = add2(fz, pz);
+    fjx -= px.x + px.y;
+    fjy -= py.x + py.y;
+    fjz -= pz.x + pz.y;
+    return true;
+}
+
 // All j-entries [jb, je) (at most 32) of one super-cluster i-entry.
 template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED>
 __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s_lj, WarpSmem& W,
                                              const Lane8& L, int g0, bool center, int jb, int je,
                                              float2 (&fx)[kSuper8], float2 (&fy)[kSuper8],
                                              float2 (&fz)[kSuper8], float& e_lj, float& e_c,
-                                             unsigned& n_inc) {
+                                             unsigned& n_inc, const MlpTC* M, float* mo) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int nt = je - jb;
@@ -308,14 +402,22 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
             if ((bits >> k) & 1u) {
                 const bool diag = center && (cjt == g0 + k);
                 const unsigned long long m = W.m[k][t];
-                if (!diag && m == ~0ull)
+                if constexpr (ELEC == NB_ELEC_EWALD_MLP) {
+                    if (!diag && m == ~0ull)
+                        any |= icluster8_mlp<SHIFTED, true>(A.p, s_lj, W, L, k, false, m, xj, tj, fx[k], fy[k],
+                                                            fz[k], fjx, fjy, fjz, *M, mo);
+                    else
+                        any |= icluster8_mlp<SHIFTED, false>(A.p, s_lj, W, L, k, diag, m, xj, tj, fx[k], fy[k],
+                                                             fz[k], fjx, fjy, fjz, *M, mo);
+                } else if (!diag && m == ~0ull) {
                     any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true>(A.p, s_lj, W, L, k, false, m, xj, tj,
                                                                        fx[k], fy[k], fz[k], fjx, fjy, fjz,
                                                                        e_lj, e_c, n_inc);
-                else
+                } else {
                     any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, false>(A.p, s_lj, W, L, k, diag, m, xj, tj,
                                                                         fx[k], fy[k], fz[k], fjx, fjy, fjz,
                                                                         e_lj, e_c, n_inc);
+                }
             }
         }
         if (!any) continue;
@@ -331,7 +433,8 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
 }
 
 template <int ELEC, bool ENERGY, bool FIT>
-__global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 5 : 6) k_force8(ForceArgs A) {
+__global__ void __launch_bounds__(32 * kForceWarps, ELEC == NB_ELEC_EWALD_MLP ? 4 : (ENERGY ? 5 : 6))
+k_force8(ForceArgs A) {
     extern __shared__ float2 s_lj[];
     __shared__ WarpSmem s_w[kForceWarps];
     const unsigned full = 0xffffffffu;
@@ -339,6 +442,18 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 5 : 6) k_force8(For
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
         const float2 v = A.ws.c6c12[k];
         s_lj[k] = make_float2(-6.0f * v.x, 12.0f * v.y);
+    }
+    const MlpTC* M = nullptr;
+    float* mo = nullptr;
+    if constexpr (ELEC == NB_ELEC_EWALD_MLP) {
+        // the network in per-lane layout, and a 64-value exchange row per warp
+        __shared__ MlpTC s_mlp;
+        __shared__ float s_mo[kForceWarps][64];
+        const uint4* src = reinterpret_cast<const uint4*>(A.ws.mlp);
+        uint4* dst = reinterpret_cast<uint4*>(&s_mlp);
+        for (int k = threadIdx.x; k < (int)(sizeof(MlpTC) / 16); k += blockDim.x) dst[k] = src[k];
+        M = &s_mlp;
+        mo = s_mo[threadIdx.x >> 5];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -390,10 +505,10 @@ __global__ void __launch_bounds__(32 * kForceWarps, ENERGY ? 5 : 6) k_force8(For
             const int bend = min(je, base + 32);
             if (center)
                 force_entry8<ELEC, ENERGY, FIT, false>(A, s_lj, W, L, g0, true, base, bend, fx, fy, fz, e_lj,
-                                                       e_c, n_inc);
+                                                       e_c, n_inc, M, mo);
             else
                 force_entry8<ELEC, ENERGY, FIT, true>(A, s_lj, W, L, g0, false, base, bend, fx, fy, fz, e_lj,
-                                                      e_c, n_inc);
+                                                      e_c, n_inc, M, mo);
         }
         // i-forces: per i-cluster, sum over the 8 lanes of each i row
         float tsum[3] = {0.f, 0.f, 0.f};
@@ -552,6 +667,17 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
     A.p = p;
     cudaError_t e = cudaMemsetAsync(ws.acc, 0, sizeof(Accum) * ws.nbox, s);
     if (e != cudaSuccess) return e;
+    if (p.elec == NB_ELEC_EWALD_MLP) {
+        // forces only, 8-particle clusters (checked by the caller)
+        auto kern = k_force8<NB_ELEC_EWALD_MLP, false, true>;
+        const size_t smem = sizeof(float2) * A.p.ntypes * A.p.ntypes;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kForceWarps, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        kern<<<n_sm * per_sm, 32 * kForceWarps, smem, s>>>(A);
+        return cudaGetLastError();
+    }
     if (p.elec == NB_ELEC_RF)
         return p.want_energy ? launch_force_e<NB_ELEC_RF, true>(A, C, n_sm, s)
                              : launch_force_e<NB_ELEC_RF, false>(A, C, n_sm, s);

@@ -24,6 +24,8 @@
 
 namespace nbc {
 
+struct MlpTC;   // tensor-core form of the Ewald-factor network (nb_mlp.cuh)
+
 constexpr int kMaxTypes = 64;          // LJ types (type table staged in shared memory)
 constexpr int kMaxColumn = 8192;       // particles per grid column sorted on-chip
 constexpr int kMaxBoxes = 4096;        // boxes per context
@@ -120,6 +122,8 @@ struct Workspace {
     long long jstride;   // total j-entry capacity: stride between the S mask arrays
     // LJ table {C6, C12} [ntypes][ntypes]
     float2* c6c12;
+    // the Ewald-factor network in tensor-core form (nb_set_surrogate)
+    MlpTC* mlp;
 };
 
 // Kernel launchers (defined in the .cu files).
@@ -140,6 +144,7 @@ struct ForceParams {
     float beta, two_beta_sqrtpi;
     float beta2, beta3;   // beta^2, beta^3 for the fitted correction
     int use_fit;          // (beta rc)^2 within the fitted range
+    float mlp_rmin;       // network input range starts here (surrogate kernel)
     int ntypes;
     int use_pruned;
 };

@@ -437,3 +437,11 @@ def frame_walk(xyz: np.ndarray, mass: np.ndarray, n_frames: int, seed: int,
     for _ in range(n_frames - 1):
         x += rng.standard_normal(x.shape, dtype=np.float32) * s
         yield x.copy()
+
+
+def surrogate_samples(n: int = 1 << 20, r_min: float = 0.05, r_max: float = 1.0,
+                      seed: int = 1005) -> np.ndarray:
+    """Training distances for the Ewald-factor network: n draws of
+    U[r_min, r_max] nm (FP64, seeded)."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    return rng.uniform(r_min, r_max, size=n)
