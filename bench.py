@@ -9,8 +9,9 @@ first and last frame).  The headline value is force evaluations per second
 over the whole job.  Default workload: 24,000-atom water box, Ewald real
 space rc 1.0 nm, beta 3.12 nm^-1, rlist 1.1 nm, nstlist 20, prune every 5.
 
---impl reference times the FP64 CPU oracle (brute-force minimum-image pair
-loop) on the same workload and metric: one force+energy evaluation per step.
+--impl reference times the FP64 CPU oracle (its cell-list tier, the same
+pairs as the brute-force minimum-image loop) on the same workload and metric:
+one force+energy evaluation per step.
 
 Under torchrun each rank runs an independent replica of the workload on its
 own GPU (the boxes share nothing); value = evaluations of all ranks / the
@@ -176,29 +177,30 @@ def oracle_eval(box, p, sel=None):
     import oracle
     prm = oracle.make_params(p["elec"], float(np.float32(p["rc"])), eps_rf=p.get("eps_rf", math.inf),
                              beta=p.get("beta", 0.0), comb=p.get("comb", "lb"))
-    return oracle.forces_brute(box.xyz, box.q, box.types, box.sigma, box.eps, box.excl_off,
+    return oracle.forces_cells(box.xyz, box.q, box.types, box.sigma, box.eps, box.excl_off,
                                box.excl_idx, box.box, prm, sel=sel)
 
 
 def oracle_unit(box, p, budget_s):
-    """One timed unit of oracle work sized to about budget_s: a whole brute-force
-    evaluation for small boxes, else the forces of a seeded particle sample
-    (each against all particles).  Returns (fraction of one evaluation, text)."""
+    """One timed unit of oracle work sized to about budget_s: a whole
+    evaluation by the oracle's FP64 cell-list tier for small boxes, else the
+    forces of a seeded particle sample (each against its cell neighbourhood).
+    Returns (selection, fraction of one evaluation, text)."""
     import numpy as np
     if box.n <= SAMPLE_ABOVE:
-        return None, 1.0, f"one brute-force O(N^2) force+energy evaluation of the {box.n}-particle box"
+        return None, 1.0, f"one FP64 cell-list force+energy evaluation of the {box.n}-particle box"
     rng = np.random.default_rng(7)
     t0 = time.perf_counter()
     oracle_eval(box, p, sel=rng.choice(box.n, 64, replace=False))
     per_atom = (time.perf_counter() - t0) / 64
     k = int(max(64, min(box.n, budget_s / max(per_atom, 1e-9))))
     sel = rng.choice(box.n, k, replace=False)
-    return sel, k / box.n, (f"brute-force forces of {k} seeded particles, each against all {box.n} "
-                            f"particles = {k / box.n:.2e} of one evaluation")
+    return sel, k / box.n, (f"FP64 cell-list forces of {k} seeded particles of the {box.n}-particle box "
+                            f"= {k / box.n:.2e} of one evaluation")
 
 
 def cpu_baseline(box, p, budget_s=15.0):
-    """The oracle (brute-force FP64 pair loop) on a bounded sample of the same
+    """The oracle (its FP64 cell-list tier) on a bounded sample of the same
     workload, scaled to force evaluations per second."""
     import oracle
     sel, frac, what = oracle_unit(box, p, budget_s / 3)
@@ -271,6 +273,48 @@ def config_dict(args, box, p, desc):
             "nstprune": p.get("nstprune", 0), "cluster": "8x8 cluster pairs (two 8x4 halves per warp), super-clusters of 2 i-clusters sharing a j-list",
             "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}",
             "seed": int(box.seed)}
+
+
+def surrogate_ab(nb, ctx, box, p, xs, F, stream, dev, steps=60000, reps=20):
+    """The learned Ewald factor against the analytic kernel on the same list
+    and GPU: train the network on the GPU (FP64 targets from the library),
+    install it, and time force evaluations (forces only) of both kernels on
+    the last frame; the surrogate's force error is taken against the
+    analytic kernel's forces."""
+    import numpy as np
+    import torch
+    from paper_1306_1737_gb300 import surrogate
+    from paper_1306_1737_gb300 import workloads as w
+    r = w.surrogate_samples(1 << 20, surrogate.R_MIN, surrogate.R_MAX, seed=1005)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    params, losses = surrogate.train(r, p["beta"], steps=steps, device=dev.index)
+    train_s = time.perf_counter() - t0
+    nb.nb_set_surrogate(ctx, params, surrogate.R_MIN, surrogate.R_MAX, stream)
+    x = xs[-1]
+    res = {}
+    forces = {}
+    for mode in ("ewald", "ewald_mlp"):
+        prm = nb.make_params(mode, p["rc"], beta=p["beta"], want_energy=False)
+        nb.nb_compute(ctx, prm, x, F, None, None, stream)
+        torch.cuda.synchronize()
+        forces[mode] = F.double().cpu().numpy()
+        nb.nb_profile(ctx, True)
+        nb.nb_profile_read(ctx)
+        for _ in range(reps):
+            nb.nb_compute(ctx, prm, None, F, None, None, stream)
+        spans = [ms for kind, ms in nb.nb_profile_read(ctx) if kind == nb.NB_KERNEL_FORCE]
+        nb.nb_profile(ctx, False)
+        res[mode] = statistics.mean(spans)
+    fa, fm = forces["ewald"], forces["ewald_mlp"]
+    rms = float(np.sqrt((fa ** 2).sum(1).mean()))
+    d = np.sqrt(((fm - fa) ** 2).sum(1))
+    return {"network": "MLP 1-32-32-1 SiLU, layer 2 on BF16 mma.sync m16n8k16 (hi/lo split), FP32 accumulate",
+            "train_steps": steps, "train_s": train_s, "final_minibatch_loss": float(losses[-1]),
+            "force_ms_analytic": res["ewald"], "force_ms_surrogate": res["ewald_mlp"],
+            "surrogate_over_analytic_time": res["ewald_mlp"] / res["ewald"],
+            "max_dF_over_rms_vs_analytic": float(d.max() / rms), "rms_dF_over_rms_vs_analytic":
+                float(np.sqrt((d ** 2).mean()) / rms)}
 
 
 def run_ours(args):
@@ -444,6 +488,7 @@ def run_ours(args):
         h2d = nstlist * box.n * 12
         d2h = nstlist * box.n * 12 + 16
         cpu = cpu_baseline(box, p) if ws_n == 1 else None
+        surr = surrogate_ab(nb, ctx, box, p, xs, F, stream, dev) if elec == "ewald" and args.surrogate else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1000 / args.steps,
@@ -466,6 +511,7 @@ def run_ours(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "surrogate": surr,
             "gpu_launches": int(launches),
             "clocks": clocks,
             "status": nb.status_name(info0.status),
@@ -502,31 +548,30 @@ def batch_frames(B, dev):
 
 
 def batch_cpu_baseline(B, p, budget_s=15.0):
-    """The oracle on a seeded sample: for 8 boxes, the forces of a seeded
-    subset of particles against all particles of their box; scaled by the
-    pair work of one evaluation of the whole batch."""
+    """The oracle (FP64 cell-list tier) on a seeded sample: the forces of a
+    seeded subset of particles in each of 8 seeded boxes; its cost per
+    particle does not depend on the box size, so the sample is the fraction
+    (sampled particles / all particles) of one batch evaluation."""
     import numpy as np
     import oracle
     rng = np.random.default_rng(11)
     picks = rng.choice(B.nbox, 8, replace=False)
-    total_work = float((B.counts.astype(np.float64) ** 2).sum())
-    # size the subset from one probe
     b0 = B.members[int(picks[0])]
     t0 = time.perf_counter()
-    oracle_eval(b0, p, sel=rng.choice(b0.n, 32, replace=False))
-    per_pair = (time.perf_counter() - t0) / (32 * b0.n)
-    m = int(max(32, min(4096, budget_s / 8 / max(per_pair, 1e-12) / float(B.counts[picks].mean()))))
+    oracle_eval(b0, p, sel=rng.choice(b0.n, min(256, b0.n), replace=False))
+    per_atom = (time.perf_counter() - t0) / min(256, b0.n)
+    m = int(max(64, budget_s / 8 / max(per_atom, 1e-9)))
     sels = [(B.members[int(k)], rng.choice(B.members[int(k)].n, min(m, B.members[int(k)].n), replace=False))
             for k in picks]
-    work = sum(float(len(sel) * b.n) for b, sel in sels)
+    work = sum(len(sel) for _, sel in sels)
     t0 = time.perf_counter()
     for b, sel in sels:
         oracle_eval(b, p, sel=sel)
     dt = time.perf_counter() - t0
-    frac = work / total_work
+    frac = work / B.n
     return {"value": frac / dt, "unit": BATCH_UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"forces of {m} seeded particles in each of 8 seeded boxes against all particles of "
-                      f"their box (brute force FP64) = {frac:.2e} of the pair work of one batch evaluation"}
+            "sample": f"FP64 cell-list forces of {work} seeded particles in 8 seeded boxes "
+                      f"= {frac:.2e} of one batch evaluation"}
 
 
 def run_batch(args):
@@ -719,6 +764,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",
+                    help="skip the learned Ewald factor A/B (Ewald workloads)")
     ap.add_argument("--workload", default="water24k",
                     choices=["water24k", "water3m", "water1536", "water1m", "batch256"])
     args = ap.parse_args()

@@ -6,7 +6,8 @@ leg may import this package.  It builds ``oracle.c`` with gcc into
 with the CUDA library and never imports it.
 
 Functions (each follows the paper passage cited in ``oracle.c``):
-  forces_brute   -- O(N^2) minimum-image pair loop (Sec. 3.2 interactions)
+  forces_brute   -- Tier A: O(N^2) minimum-image pair loop (Sec. 3.2 interactions)
+  forces_cells   -- Tier B: the same through a cell list (linear cost)
   pair           -- one pair interaction (Sec. 3.2)
   grid           -- spatial clustering into columns and clusters (Sec. 2.3)
   pairlist       -- cluster-pair search by brute force over all cluster
@@ -77,6 +78,8 @@ def lib():
             L.or_forces_brute.argtypes = [C.c_int, P, P, P, C.c_int, P, P, P, P, P,
                                           C.POINTER(Params), C.c_int, P, P, P, P]
             L.or_forces_brute.restype = C.c_int
+            L.or_forces_cells.argtypes = L.or_forces_brute.argtypes
+            L.or_forces_cells.restype = C.c_int
             L.or_count_pairs_within.argtypes = [C.c_int, P, P, C.c_double]
             L.or_count_pairs_within.restype = i64
             L.or_grid_dims.argtypes = [C.c_int, P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -147,14 +150,7 @@ def lj_pair_params(comb: str, si: float, ei: float, sj: float, ej: float):
     return c6.value, c12.value
 
 
-def forces_brute(xyz, q, types, sigma, eps, excl_off, excl_idx, box, params: Params,
-                 sel=None, exact: bool = False):
-    """Brute-force FP64 forces [n or len(sel), 3], energies [2], virial [3, 3].
-
-    By default xyz and box are rounded to FP32 first (the precision the
-    kernels receive) and promoted to FP64; exact=True passes FP64 values
-    through unchanged (finite-difference checks).
-    """
+def _forces(fn, xyz, q, types, sigma, eps, excl_off, excl_idx, box, params, sel, exact):
     if exact:
         xyz = _f64(xyz)
         box64 = _f64(box)
@@ -172,20 +168,39 @@ def forces_brute(xyz, q, types, sigma, eps, excl_off, excl_idx, box, params: Par
         f = np.zeros((n, 3))
         e = np.zeros(2)
         vir = np.zeros(9)
-        rc = lib().or_forces_brute(n, _p(xyz), _p(q), _p(types), sigma.shape[0], _p(sigma), _p(eps),
-                                   _p(eo), _p(ei), _p(box64), C.byref(params), 0, None,
-                                   _p(f), _p(e), _p(vir))
+        rc = fn(n, _p(xyz), _p(q), _p(types), sigma.shape[0], _p(sigma), _p(eps), _p(eo), _p(ei), _p(box64),
+                C.byref(params), 0, None, _p(f), _p(e), _p(vir))
         if rc != 0:
             raise ValueError("cut-off must be below half the box")
         return f, e, vir.reshape(3, 3)
     sel = _i32(sel)
     f = np.zeros((sel.shape[0], 3))
-    rc = lib().or_forces_brute(n, _p(xyz), _p(q), _p(types), sigma.shape[0], _p(sigma), _p(eps),
-                               _p(eo), _p(ei), _p(box64), C.byref(params), sel.shape[0], _p(sel),
-                               _p(f), None, None)
+    rc = fn(n, _p(xyz), _p(q), _p(types), sigma.shape[0], _p(sigma), _p(eps), _p(eo), _p(ei), _p(box64),
+            C.byref(params), sel.shape[0], _p(sel), _p(f), None, None)
     if rc != 0:
         raise ValueError("cut-off must be below half the box")
     return f, None, None
+
+
+def forces_brute(xyz, q, types, sigma, eps, excl_off, excl_idx, box, params: Params,
+                 sel=None, exact: bool = False):
+    """Tier A: brute-force FP64 forces [n or len(sel), 3], energies [2],
+    virial [3, 3] (with sel: the selected particles' forces only).
+
+    By default xyz and box are rounded to FP32 first (the precision the
+    kernels receive) and promoted to FP64; exact=True passes FP64 values
+    through unchanged (finite-difference checks).
+    """
+    return _forces(lib().or_forces_brute, xyz, q, types, sigma, eps, excl_off, excl_idx, box, params, sel,
+                   exact)
+
+
+def forces_cells(xyz, q, types, sigma, eps, excl_off, excl_idx, box, params: Params,
+                 sel=None, exact: bool = False):
+    """Tier B: the same quantities through an FP64 cell list (cost linear in
+    the number of particles)."""
+    return _forces(lib().or_forces_cells, xyz, q, types, sigma, eps, excl_off, excl_idx, box, params, sel,
+                   exact)
 
 
 def count_pairs_within(xyz, box, r: float) -> int:

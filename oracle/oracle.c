@@ -786,3 +786,123 @@ double or_mlp_loss_grad(const double* p, double rmin, double rmax, int64_t n, co
     }
     return loss;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Tier B: the same forces, energies and virial as or_forces_brute through a
+ * cell list (cells of edge >= rc along each axis; every particle meets the
+ * particles of its own and its neighbouring cells, each neighbouring cell
+ * counted once even where fewer than three cells span an axis), so its cost
+ * grows linearly with n.  Pairs use the same pair function and minimum
+ * image as Tier A, so the two agree to rounding; the cell enumeration is
+ * independent code and is pinned against Tier A on small boxes.
+ * Arguments and outputs as or_forces_brute (sel: forces of the selected
+ * particles only).  Returns 0, or -1 when rc >= L/2.
+ */
+int or_forces_cells(int n, const double* xyz, const float* q, const int* type,
+                    int ntypes, const double* sigma, const double* eps,
+                    const int* excl_off, const int* excl_idx, const double* box,
+                    const or_params* p, int n_sel, const int* sel,
+                    double* f, double* e, double* vir) {
+    const double L[3] = {box[0], box[1], box[2]};
+    for (int k = 0; k < 3; ++k)
+        if (!(p->rc < 0.5 * L[k])) return -1;
+    int nc[3];
+    for (int k = 0; k < 3; ++k) {
+        nc[k] = (int)floor(L[k] / p->rc);
+        if (nc[k] < 1) nc[k] = 1;
+    }
+    const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    int* cell_of = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    int64_t* start = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+    int* members = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        int c[3];
+        for (int k = 0; k < 3; ++k) {
+            double x = xyz[3 * i + k] - L[k] * floor(xyz[3 * i + k] / L[k]);
+            int v = (int)(x / L[k] * nc[k]);
+            if (v < 0) v = 0;
+            if (v >= nc[k]) v = nc[k] - 1;
+            c[k] = v;
+        }
+        cell_of[i] = (c[0] * nc[1] + c[1]) * nc[2] + c[2];
+        start[cell_of[i] + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+    {
+        int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ncell > 0 ? ncell : 1));
+        memcpy(fill, start, sizeof(int64_t) * (size_t)ncell);
+        for (int i = 0; i < n; ++i) members[fill[cell_of[i]]++] = i;
+        free(fill);
+    }
+    double* c6t = (double*)malloc(sizeof(double) * ntypes * ntypes);
+    double* c12t = (double*)malloc(sizeof(double) * ntypes * ntypes);
+    for (int a = 0; a < ntypes; ++a)
+        for (int b = 0; b < ntypes; ++b)
+            or_lj_pair_params(p->comb, sigma[a], eps[a], sigma[b], eps[b],
+                              &c6t[a * ntypes + b], &c12t[a * ntypes + b]);
+    const int full = (n_sel <= 0);
+    const int ni = full ? n : n_sel;
+    const double rc2 = p->rc * p->rc;
+    double elj = 0.0, ec = 0.0;
+    double w[9] = {0};
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : elj, ec) reduction(+ : w[:9])
+    for (int ii = 0; ii < ni; ++ii) {
+        const int i = full ? ii : sel[ii];
+        const int ci = cell_of[i];
+        const int cz = ci % nc[2], cy = (ci / nc[2]) % nc[1], cx = ci / (nc[2] * nc[1]);
+        /* distinct neighbouring cells along each axis */
+        int nb[3][3], nn[3];
+        const int cc[3] = {cx, cy, cz};
+        for (int k = 0; k < 3; ++k) {
+            nn[k] = 0;
+            for (int o = -1; o <= 1; ++o) {
+                const int v = ((cc[k] + o) % nc[k] + nc[k]) % nc[k];
+                int seen = 0;
+                for (int m = 0; m < nn[k]; ++m) seen |= (nb[k][m] == v);
+                if (!seen) nb[k][nn[k]++] = v;
+            }
+        }
+        double fi[3] = {0, 0, 0};
+        for (int a = 0; a < nn[0]; ++a)
+            for (int b = 0; b < nn[1]; ++b)
+                for (int c = 0; c < nn[2]; ++c) {
+                    const int64_t cell = ((int64_t)nb[0][a] * nc[1] + nb[1][b]) * nc[2] + nb[2][c];
+                    for (int64_t m = start[cell]; m < start[cell + 1]; ++m) {
+                        const int j = members[m];
+                        if (j == i) continue;
+                        double d[3];
+                        for (int k = 0; k < 3; ++k) {
+                            double v = xyz[3 * i + k] - xyz[3 * j + k];
+                            v -= L[k] * nearbyint(v / L[k]);
+                            d[k] = v;
+                        }
+                        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (!(r2 < rc2)) continue;
+                        int ex = 0;
+                        if (excl_off)
+                            for (int k = excl_off[i]; k < excl_off[i + 1]; ++k) ex |= (excl_idx[k] == j);
+                        const int tt = type[i] * ntypes + type[j];
+                        double fs, vlj, vc;
+                        or_pair(p, sqrt(r2), (double)q[i] * (double)q[j], c6t[tt], c12t[tt], ex, &fs, &vlj, &vc);
+                        for (int k = 0; k < 3; ++k) fi[k] += fs * d[k];
+                        if (full) {
+                            elj += 0.5 * vlj;
+                            ec += 0.5 * vc;
+                            for (int x = 0; x < 3; ++x)
+                                for (int y = 0; y < 3; ++y) w[3 * x + y] += 0.5 * d[x] * fs * d[y];
+                        }
+                    }
+                }
+        for (int k = 0; k < 3; ++k) f[3 * ii + k] = fi[k];
+    }
+    if (full) {
+        if (e) { e[0] = elj; e[1] = ec; }
+        if (vir) memcpy(vir, w, sizeof(w));
+    }
+    free(c6t);
+    free(c12t);
+    free(cell_of);
+    free(start);
+    free(members);
+    return 0;
+}

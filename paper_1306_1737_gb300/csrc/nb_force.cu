@@ -466,10 +466,11 @@ k_force8(ForceArgs A) {
     L.sel = 1u << (L.ih * 8 + L.j);
     float e_lj = 0.0f, e_c = 0.0f;
     unsigned n_inc = 0;
-    int b = 0, b_acc = -1;
+    int b_acc = -1;
     const int ient_total = (int)A.ws.ient_total;  // below 2^31 (checked when the workspace is planned)
     for (int e = blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < ient_total; e += gridDim.x * kForceWarps) {
-        b = advance_box(A.ws.lay.ient_off, A.ws.nbox, b, (long long)e);
+        // box of this entry by binary search (no state carried across entries)
+        const int b = find_box(A.ws.lay.ient_off, A.ws.nbox, (long long)e);
         const int ient_base = (int)A.ws.lay.ient_off[b];
         if (e - ient_base >= (int)min((long long)A.ws.st[b].n_ient, A.ws.lay.ient_off[b + 1] - ient_base)) continue;
         if (ENERGY && b != b_acc) {
@@ -562,10 +563,11 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
     const int half = lane >> 4, i = (lane >> 2) & 3, j = lane & 3;
     float e_lj = 0.0f, e_c = 0.0f;
     unsigned n_inc = 0;
-    int b = 0, b_acc = -1;
+    int b_acc = -1;
     const int ient_total = (int)A.ws.ient_total;  // below 2^31 (checked when the workspace is planned)
     for (int e = blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < ient_total; e += gridDim.x * kForceWarps) {
-        b = advance_box(A.ws.lay.ient_off, A.ws.nbox, b, (long long)e);
+        // box of this entry by binary search (no state carried across entries)
+        const int b = find_box(A.ws.lay.ient_off, A.ws.nbox, (long long)e);
         const int ient_base = (int)A.ws.lay.ient_off[b];
         if (e - ient_base >= (int)min((long long)A.ws.st[b].n_ient, A.ws.lay.ient_off[b + 1] - ient_base)) continue;
         if (ENERGY && b != b_acc) {

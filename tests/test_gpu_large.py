@@ -2,8 +2,10 @@
 10% re-typed among 8 LJ types combined by Lorentz-Berthelot), in the
 configuration bench.py times: the full grid bit-exact against the oracle,
 the cluster-pair list and the pruned list compared key by key for sampled
-clusters, and the forces of sampled particles (each against all 3M particles
-in the oracle) within 1e-4 of their RMS."""
+clusters, the forces of sampled particles (each against all 3M particles
+in the brute-force oracle) and of every particle (the oracle's cell-list
+tier) within 1e-4 of their RMS, and the FP64 energies and virial of the
+whole box within 1e-5 relative."""
 import numpy as np
 import pytest
 
@@ -87,6 +89,13 @@ def test_config3_grid_list_prune_forces(env):
         assert emax < FORCE_TOL, (emax, erms)
         # Newton's third law over the whole box (FP32 accumulation)
         assert np.abs(f.sum(0)).max() < 1e-3 * rms * np.sqrt(b.n)
+        # every particle, energies and virial against the cell-list tier
+        fc, ec, vc = oracle.forces_cells(b.xyz, b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx,
+                                         b.box, oprm)
+        emax_all, erms_all, _ = gp.force_errors(f, fc)
+        assert emax_all < FORCE_TOL, (emax_all, erms_all)
+        assert np.abs(e - ec).max() / np.abs(ec).max() < 1e-5, (e, ec)
+        assert np.abs(vir - vc).max() / np.abs(vc).max() < 1e-5
         # after 5 frames of displacements: prune and forces again
         disp = w.frame_displacements(b.mass, 5, seed=3003).sum(0)
         x5 = b.xyz + disp

@@ -223,3 +223,63 @@ def test_error_paths(gp, cfg1):
         assert ei.value.status == nb.NB_ERR_BOX
     finally:
         gb.close()
+
+
+def test_config2_every_frame(gp, cfg2):
+    """The benchmark's list lifetime on the 24,000-atom box: grid and list at
+    frame 0, prune every 5 frames, forces and energies at each of the 20
+    frames against the oracle's cell-list tier."""
+    import paper_1306_1737_gb300 as nb
+    b, p = cfg2
+    gb = gp.GpuBox(b, p["rlist"])
+    frames = list(w.frame_walk(b.xyz, b.mass, p["nstlist"], seed=2200))
+    rp = float(np.float32(w.prune_radius(p["rc"], p["rlist"], p["nstprune"])))
+    prm = nb.make_params("ewald", p["rc"], beta=p["beta"])
+    oprm = oracle.make_params("ewald", float(np.float32(p["rc"])), beta=p["beta"])
+    worst = 0.0
+    try:
+        gb.grid(frames[0])
+        gb.build(float(np.float32(p["rlist"])))
+        for f, x in enumerate(frames):
+            if f > 0 and f % p["nstprune"] == 0:
+                gb.prune(rp, x)
+                fg, eg, vg = gb.compute(prm)
+            else:
+                fg, eg, vg = gb.compute(prm, x if f > 0 else None)
+            fo, eo, vo = oracle.forces_cells(x, b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx, b.box, oprm)
+            emax, erms, _ = gp.force_errors(fg, fo)
+            worst = max(worst, emax)
+            assert emax < FORCE_TOL, (f, emax, erms)
+            assert np.abs(eg - eo).max() / np.abs(eo).max() < E_TOL, (f, eg, eo)
+            assert np.abs(vg - vo).max() / np.abs(vo).max() < E_TOL, f
+    finally:
+        gb.close()
+    print(f"\nworst frame max|dF|/rms {worst:.2e}")
+
+
+def test_no_missed_pairs_over_frames(gp):
+    """Every particle pair inside rc is covered exactly once by the list in
+    use (outer list, then the pruned lists) at every frame of a 20-frame
+    lifetime: no missed pair anywhere (3,000 particles, all pairs checked)."""
+    b = w.water_box(1000, None, seed=2300)
+    rc, rl, nstprune = 1.0, 1.1, 5
+    gb = gp.GpuBox(b, rl)
+    frames = list(w.frame_walk(b.xyz, b.mass, 20, seed=2301))
+    rp = float(np.float32(w.prune_radius(rc, rl, nstprune)))
+    try:
+        gb.grid(frames[0])
+        g_or = oracle.grid(frames[0], b.q, b.types, b.box, 8)
+        gb.build(float(np.float32(rl)))
+        woff = (g_or.wrapped - frames[0]).astype(np.float32)
+        which = 0
+        for f, x in enumerate(frames):
+            if f > 0 and f % nstprune == 0:
+                gb.prune(rp, x)
+                which = 1
+            _, ient, cj, masks, sci = gb.list_arrays(which)
+            a, bb, s, _ = __import__("gpu_path").expand_keys(ient, cj, masks, sci)
+            g_f = oracle.Grid(**{**g_or.__dict__, "wrapped": (x + woff).astype(np.float32)})
+            once, none, many = oracle.pair_cover(g_f, oracle.PairList(a, bb, s, np.zeros(a.size, np.uint64)), rc)
+            assert none == 0 and many == 0 and once > 0, (f, once, none, many)
+    finally:
+        gb.close()
