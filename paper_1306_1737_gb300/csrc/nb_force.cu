@@ -667,8 +667,13 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
     A.cj = p.use_pruned ? ws.cj_p : ws.cj;
     A.mask = p.use_pruned ? ws.mask_p : ws.mask;
     A.p = p;
-    cudaError_t e = cudaMemsetAsync(ws.acc, 0, sizeof(Accum) * ws.nbox, s);
-    if (e != cudaSuccess) return e;
+    // the accumulators hold energies, pair counts and shift forces, which
+    // only energy evaluations produce and read
+    cudaError_t e = cudaSuccess;
+    if (p.want_energy) {
+        e = cudaMemsetAsync(ws.acc, 0, sizeof(Accum) * ws.nbox, s);
+        if (e != cudaSuccess) return e;
+    }
     if (p.elec == NB_ELEC_EWALD_MLP) {
         // forces only, 8-particle clusters (checked by the caller)
         auto kern = k_force8<NB_ELEC_EWALD_MLP, false, true>;
