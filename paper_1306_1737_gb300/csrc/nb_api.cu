@@ -218,6 +218,7 @@ static size_t carve(const nb_ctx* c, char* base, Workspace* ws) {
     w.ient_p = (int4*)take(sizeof(int4) * w.ient_total);
     w.cj_p = (int*)take(sizeof(int) * w.jstride);
     w.mask_p = (unsigned long long*)take(sizeof(unsigned long long) * w.jstride * S);
+    w.ient_used = (int*)take(sizeof(int) * (nb + 1));
     w.c6c12 = (float2*)take(sizeof(float2) * kMaxTypes * kMaxTypes);
     w.mlp = (MlpTC*)take(sizeof(MlpTC));
     if (ws) *ws = w;
@@ -649,7 +650,7 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     cudaError_t e = launch_force(c->ws, fp, c->C, c->n_sm, s);
     span_end(c, sp, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "force kernel");
-    e = launch_finalize(c->ws, fp, f, e_out, vir_out, s);
+    e = launch_finalize(c->ws, fp, c->C, f, e_out, vir_out, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
     c->n_launches += 2 + (fp.want_energy ? 1 : 0);
     return NB_OK;

@@ -25,11 +25,25 @@
 
 namespace nbc {
 
+// The force kernels' arguments: only the arrays they touch, so that every
+// field is a direct constant-bank operand.
 struct ForceArgs {
-    Workspace ws;
     const int4* ient;                 // outer or pruned list
     const int* cj;
     const unsigned long long* mask;
+    long long jstride;                // stride between the per-i-cluster mask arrays
+    const float4* xyzq;
+    const int* type_slot;
+    float4* fslot;
+    const float2* c6c12;
+    const int2* sc_info;
+    const long long* ient_off;        // box regions of the i-entries
+    const DevState* st;
+    const BoxGeom* geo;
+    Accum* acc;
+    const MlpTC* mlp;
+    const int* ient_used;             // compact i-entry index per box
+    int nbox;
     ForceParams p;
 };
 
@@ -378,11 +392,11 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
     if (lane < nt) {
         W.w[lane] = A.cj[jb + lane];
 #pragma unroll
-        for (int k = 0; k < kSuper8; ++k) W.m[k][lane] = A.mask[k * A.ws.jstride + jb + lane];
+        for (int k = 0; k < kSuper8; ++k) W.m[k][lane] = A.mask[k * A.jstride + jb + lane];
     }
     __syncwarp();
-    const float4* xyzq_j = A.ws.xyzq + L.j;
-    const int* type_j = A.ws.type_slot + L.j;
+    const float4* xyzq_j = A.xyzq + L.j;
+    const int* type_j = A.type_slot + L.j;
     int cjn = W.w[0] & kCjMask;
     float4 xjn = xyzq_j[cjn * 8];
     int tjn = type_j[cjn * 8];
@@ -427,7 +441,7 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
         fjx += __shfl_xor_sync(full, fjx, 16);
         fjy += __shfl_xor_sync(full, fjy, 16);
         fjz += __shfl_xor_sync(full, fjz, 16);
-        if (L.ih == 0) atomicAdd(&A.ws.fslot[cjt * 8 + L.j], make_float4(fjx, fjy, fjz, 0.0f));
+        if (L.ih == 0) atomicAdd(&A.fslot[cjt * 8 + L.j], make_float4(fjx, fjy, fjz, 0.0f));
     }
     __syncwarp();
 }
@@ -440,7 +454,7 @@ k_force8(ForceArgs A) {
     const unsigned full = 0xffffffffu;
     const int nt2 = A.p.ntypes * A.p.ntypes;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
-        const float2 v = A.ws.c6c12[k];
+        const float2 v = A.c6c12[k];
         s_lj[k] = make_float2(-6.0f * v.x, 12.0f * v.y);
     }
     const MlpTC* M = nullptr;
@@ -449,7 +463,7 @@ k_force8(ForceArgs A) {
         // the network in per-lane layout, and a 64-value exchange row per warp
         __shared__ MlpTC s_mlp;
         __shared__ float s_mo[kForceWarps][64];
-        const uint4* src = reinterpret_cast<const uint4*>(A.ws.mlp);
+        const uint4* src = reinterpret_cast<const uint4*>(A.mlp);
         uint4* dst = reinterpret_cast<uint4*>(&s_mlp);
         for (int k = threadIdx.x; k < (int)(sizeof(MlpTC) / 16); k += blockDim.x) dst[k] = src[k];
         M = &s_mlp;
@@ -467,26 +481,25 @@ k_force8(ForceArgs A) {
     float e_lj = 0.0f, e_c = 0.0f;
     unsigned n_inc = 0;
     int b_acc = -1;
-    const int ient_total = (int)A.ws.ient_total;  // below 2^31 (checked when the workspace is planned)
-    for (int e = blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < ient_total; e += gridDim.x * kForceWarps) {
-        // box of this entry by binary search (no state carried across entries)
-        const int b = find_box(A.ws.lay.ient_off, A.ws.nbox, (long long)e);
-        const int ient_base = (int)A.ws.lay.ient_off[b];
-        if (e - ient_base >= (int)min((long long)A.ws.st[b].n_ient, A.ws.lay.ient_off[b + 1] - ient_base)) continue;
+    const int n_used = A.ient_used[A.nbox];
+    for (int c = blockIdx.x * kForceWarps + (threadIdx.x >> 5); c < n_used; c += gridDim.x * kForceWarps) {
+        // the entry and its box by binary search (no state carried across entries)
+        int b;
+        const int e = ient_of(A.ient_used, A.ient_off, A.nbox, c, b);
         if (ENERGY && b != b_acc) {
-            flush_energy(A.ws.acc, b_acc, e_lj, e_c, n_inc);
+            flush_energy(A.acc, b_acc, e_lj, e_c, n_inc);
             b_acc = b;
         }
         const int4 ie = A.ient[e];
         const int q = ie.x, s = ie.y, jb = ie.z, je = ie.w;
         if (jb >= je) continue;
-        const int2 info = A.ws.sc_info[q];
+        const int2 info = A.sc_info[q];
         const int g0 = info.x, n = info.y;
         float sh[3];
-        shift_vector(s, A.ws.geo[b].L, sh);
+        shift_vector(s, A.geo[b].L, sh);
         // stage the super-cluster's i particles: shifted coordinates as hi + lo
         if (lane < n * 8) {
-            const float4 x = A.ws.xyzq[g0 * 8 + lane];
+            const float4 x = A.xyzq[g0 * 8 + lane];
             float4 h, l;
             two_sum(x.x, sh[0], h.x, l.x);
             two_sum(x.y, sh[1], h.y, l.y);
@@ -495,7 +508,7 @@ k_force8(ForceArgs A) {
             l.w = 0.0f;
             W.xi[lane] = h;
             W.xl[lane] = l;
-            W.row[lane] = A.ws.type_slot[g0 * 8 + lane] * A.p.ntypes;
+            W.row[lane] = A.type_slot[g0 * 8 + lane] * A.p.ntypes;
         }
         __syncwarp();
         const bool center = (s == kShiftCenter);
@@ -527,8 +540,8 @@ k_force8(ForceArgs A) {
                 tsum[d] += f0[d] + f1[d];
             }
             if (L.j == 0) {
-                atomicAdd(&A.ws.fslot[(g0 + k) * 8 + L.ih], make_float4(f0[0], f0[1], f0[2], 0.0f));
-                atomicAdd(&A.ws.fslot[(g0 + k) * 8 + L.ih + 4], make_float4(f1[0], f1[1], f1[2], 0.0f));
+                atomicAdd(&A.fslot[(g0 + k) * 8 + L.ih], make_float4(f0[0], f0[1], f0[2], 0.0f));
+                atomicAdd(&A.fslot[(g0 + k) * 8 + L.ih + 4], make_float4(f1[0], f1[1], f1[2], 0.0f));
             }
         }
         if (ENERGY && !center) {
@@ -539,11 +552,11 @@ k_force8(ForceArgs A) {
                 tsum[d] += __shfl_xor_sync(full, tsum[d], 16);
             }
             if (lane == 0)
-                for (int d = 0; d < 3; ++d) atomicAdd(&A.ws.acc[b].fshift[s][d], (double)tsum[d]);
+                for (int d = 0; d < 3; ++d) atomicAdd(&A.acc[b].fshift[s][d], (double)tsum[d]);
         }
         __syncwarp();
     }
-    if (ENERGY) flush_energy(A.ws.acc, b_acc, e_lj, e_c, n_inc);
+    if (ENERGY) flush_energy(A.acc, b_acc, e_lj, e_c, n_inc);
 }
 
 // Generic C = 4 kernel (super-clusters of one cluster): one warp per
@@ -555,7 +568,7 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
     const unsigned full = 0xffffffffu;
     const int nt2 = A.p.ntypes * A.p.ntypes;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
-        const float2 v = A.ws.c6c12[k];
+        const float2 v = A.c6c12[k];
         s_lj[k] = make_float2(6.0f * v.x, 12.0f * v.y);
     }
     __syncthreads();
@@ -564,28 +577,27 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
     float e_lj = 0.0f, e_c = 0.0f;
     unsigned n_inc = 0;
     int b_acc = -1;
-    const int ient_total = (int)A.ws.ient_total;  // below 2^31 (checked when the workspace is planned)
-    for (int e = blockIdx.x * kForceWarps + (threadIdx.x >> 5); e < ient_total; e += gridDim.x * kForceWarps) {
-        // box of this entry by binary search (no state carried across entries)
-        const int b = find_box(A.ws.lay.ient_off, A.ws.nbox, (long long)e);
-        const int ient_base = (int)A.ws.lay.ient_off[b];
-        if (e - ient_base >= (int)min((long long)A.ws.st[b].n_ient, A.ws.lay.ient_off[b + 1] - ient_base)) continue;
+    const int n_used = A.ient_used[A.nbox];
+    for (int c = blockIdx.x * kForceWarps + (threadIdx.x >> 5); c < n_used; c += gridDim.x * kForceWarps) {
+        // the entry and its box by binary search (no state carried across entries)
+        int b;
+        const int e = ient_of(A.ient_used, A.ient_off, A.nbox, c, b);
         if (ENERGY && b != b_acc) {
-            flush_energy(A.ws.acc, b_acc, e_lj, e_c, n_inc);
+            flush_energy(A.acc, b_acc, e_lj, e_c, n_inc);
             b_acc = b;
         }
         const int4 ie = A.ient[e];
-        const int ci = A.ws.sc_info[ie.x].x, s = ie.y, jb = ie.z, je = ie.w;
+        const int ci = A.sc_info[ie.x].x, s = ie.y, jb = ie.z, je = ie.w;
         if (jb >= je) continue;
         float sh[3];
-        shift_vector(s, A.ws.geo[b].L, sh);
-        const float4 x0 = A.ws.xyzq[ci * 4 + i];
+        shift_vector(s, A.geo[b].L, sh);
+        const float4 x0 = A.xyzq[ci * 4 + i];
         float xh[3], xl[3];
         two_sum(x0.x, sh[0], xh[0], xl[0]);
         two_sum(x0.y, sh[1], xh[1], xl[1]);
         two_sum(x0.z, sh[2], xh[2], xl[2]);
         const float qi = x0.w * A.p.fcoul;
-        const int ti = A.ws.type_slot[ci * 4 + i] * A.p.ntypes;
+        const int ti = A.type_slot[ci * 4 + i] * A.p.ntypes;
         const bool center = (s == kShiftCenter);
         float fi[3] = {0.f, 0.f, 0.f};
         for (int k = jb; k < je; k += 2) {
@@ -593,8 +605,8 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
             const bool live = kk < je;
             const int cjt = live ? (A.cj[kk] & kCjMask) : ci;
             const unsigned long long m = live ? A.mask[kk] : 0ull;
-            const float4 xj = A.ws.xyzq[cjt * 4 + j];
-            const int tj = A.ws.type_slot[cjt * 4 + j];
+            const float4 xj = A.xyzq[cjt * 4 + j];
+            const int tj = A.type_slot[cjt * 4 + j];
             const bool diag = center && (cjt == ci);
             const float b = (float)((m >> (i * 4 + j)) & 1ull);
             const float dx = (xh[0] - xj.x) + xl[0];
@@ -619,7 +631,7 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
                 fjy += __shfl_xor_sync(full, fjy, o);
                 fjz += __shfl_xor_sync(full, fjz, o);
             }
-            if (i == 0 && live) atomicAdd(&A.ws.fslot[cjt * 4 + j], make_float4(fjx, fjy, fjz, 0.0f));
+            if (i == 0 && live) atomicAdd(&A.fslot[cjt * 4 + j], make_float4(fjx, fjy, fjz, 0.0f));
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -627,7 +639,7 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
             fi[d] += __shfl_xor_sync(full, fi[d], 2);
             fi[d] += __shfl_xor_sync(full, fi[d], 16);
         }
-        if (j == 0 && half == 0) atomicAdd(&A.ws.fslot[ci * 4 + i], make_float4(fi[0], fi[1], fi[2], 0.0f));
+        if (j == 0 && half == 0) atomicAdd(&A.fslot[ci * 4 + i], make_float4(fi[0], fi[1], fi[2], 0.0f));
         if (ENERGY && !center) {
             float t[3] = {fi[0], fi[1], fi[2]};
 #pragma unroll
@@ -636,10 +648,10 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
                 t[d] += __shfl_xor_sync(full, t[d], 8);
             }
             if (lane == 0)
-                for (int d = 0; d < 3; ++d) atomicAdd(&A.ws.acc[b].fshift[s][d], (double)t[d]);
+                for (int d = 0; d < 3; ++d) atomicAdd(&A.acc[b].fshift[s][d], (double)t[d]);
         }
     }
-    if (ENERGY) flush_energy(A.ws.acc, b_acc, e_lj, e_c, n_inc);
+    if (ENERGY) flush_energy(A.acc, b_acc, e_lj, e_c, n_inc);
 }
 
 template <int ELEC, bool ENERGY, bool FIT>
@@ -662,10 +674,22 @@ static cudaError_t launch_force_e(const ForceArgs& A, int C, int n_sm, cudaStrea
 
 cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n_sm, cudaStream_t s) {
     ForceArgs A;
-    A.ws = ws;
     A.ient = p.use_pruned ? ws.ient_p : ws.ient;
     A.cj = p.use_pruned ? ws.cj_p : ws.cj;
     A.mask = p.use_pruned ? ws.mask_p : ws.mask;
+    A.jstride = ws.jstride;
+    A.xyzq = ws.xyzq;
+    A.type_slot = ws.type_slot;
+    A.fslot = ws.fslot;
+    A.c6c12 = ws.c6c12;
+    A.sc_info = ws.sc_info;
+    A.ient_off = ws.lay.ient_off;
+    A.st = ws.st;
+    A.geo = ws.geo;
+    A.acc = ws.acc;
+    A.mlp = ws.mlp;
+    A.nbox = ws.nbox;
+    A.ient_used = ws.ient_used;
     A.p = p;
     // the accumulators hold energies, pair counts and shift forces, which
     // only energy evaluations produce and read
@@ -694,7 +718,7 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
 
 // Forces back to the caller's order (and zeroed for the next evaluation);
 // with energies, the FP64 sum per box over slots of x (x) f for the virial.
-__global__ void k_finalize(Workspace ws, float* __restrict__ f_out, int want_vir) {
+__global__ void k_finalize(Workspace ws, int C, float* __restrict__ f_out, int want_vir) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int n = ws.atom_total;
@@ -706,15 +730,18 @@ __global__ void k_finalize(Workspace ws, float* __restrict__ f_out, int want_vir
         int b = 0;
         double w[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         if (live) {
+            // a particle without a slot (its column was too long to grid, an
+            // error that is flagged) gets zero force
             const int s = ws.slot_of_atom[p];
-            const float4 f = ws.fslot[s];
-            ws.fslot[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool has_slot = s >= 0 && s < (long long)ws.clu_total * C;
+            const float4 f = has_slot ? ws.fslot[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (has_slot) ws.fslot[s] = make_float4(0.f, 0.f, 0.f, 0.f);
             f_out[3 * p] = f.x;
             f_out[3 * p + 1] = f.y;
             f_out[3 * p + 2] = f.z;
             if (want_vir) {
                 b = find_box(ws.lay.atom_off, ws.nbox, p);
-                const float4 x = ws.xyzq[s];
+                const float4 x = has_slot ? ws.xyzq[s] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const double xa[3] = {x.x, x.y, x.z}, fb[3] = {f.x, f.y, f.z};
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
@@ -761,13 +788,13 @@ __global__ void k_finalize_small(Workspace ws, double* e_out, double* vir_out) {
     }
 }
 
-cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, float* f_out, double* e_out,
+cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int C, float* f_out, double* e_out,
                             double* vir_out, cudaStream_t s) {
     const int want_vir = (p.want_energy && vir_out) ? 1 : 0;
     int blocks = (ws.atom_total + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    k_finalize<<<blocks, 256, 0, s>>>(ws, f_out, want_vir);
+    k_finalize<<<blocks, 256, 0, s>>>(ws, C, f_out, want_vir);
     if (p.want_energy) k_finalize_small<<<1, 256, 0, s>>>(ws, e_out, vir_out);
     return cudaGetLastError();
 }

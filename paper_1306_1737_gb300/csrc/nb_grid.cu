@@ -144,12 +144,17 @@ __global__ void __launch_bounds__(512) k_col_sort(Workspace ws, int C, int ntype
         }
     }
     if (cnt > kMaxColumn) {
+        // too long to sort on-chip: flag it, leave its particles without a
+        // slot and fill its clusters with dummies, so later kernels only
+        // ever see valid slots
         if (threadIdx.x == 0) set_flag(&ws.st[b], NB_ERR_CAPACITY);
-        return;
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x)
+            ws.slot_of_atom[(int)(ws.keys[base + k] & 0xffffffffull)] = -1;
     }
+    const int cnt_s = cnt > kMaxColumn ? 0 : cnt;   // particles placed in slots
     int P = 1;
-    while (P < cnt) P <<= 1;
-    for (int k = threadIdx.x; k < P; k += blockDim.x) s_key[k] = k < cnt ? ws.keys[base + k] : ~0ull;
+    while (P < cnt_s) P <<= 1;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) s_key[k] = k < cnt_s ? ws.keys[base + k] : ~0ull;
     __syncthreads();
     for (int size = 2; size <= P; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(512) k_col_sort(Workspace ws, int C, int ntype
     for (int t = threadIdx.x; t < nsl; t += blockDim.x) {
         const long long s = (long long)g0 * C + t;
         ws.fslot[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (t < cnt) {
+        if (t < cnt_s) {
             const int a = (int)(s_key[t] & 0xffffffffull);
             ws.xyzq[s] = ws.xw[a];
             ws.atom_of_slot[s] = a;
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(512) k_col_sort(Workspace ws, int C, int ntype
     for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
         float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
         const int tb = (g - g0) * C;
-        for (int t = tb; t < tb + C && t < cnt; ++t) {
+        for (int t = tb; t < tb + C && t < cnt_s; ++t) {
             const float4 p = ws.xw[(int)(s_key[t] & 0xffffffffull)];
             lo[0] = fminf(lo[0], p.x); hi[0] = fmaxf(hi[0], p.x);
             lo[1] = fminf(lo[1], p.y); hi[1] = fmaxf(hi[1], p.y);
@@ -226,28 +231,24 @@ cudaError_t launch_grid(const Workspace& ws, int C, int ntypes, const float* xyz
     return cudaGetLastError();
 }
 
+// One thread per particle: its slot gets the new coordinates plus the wrap
+// offset of the last gridding, and its charge (no box lookup needed).  A
+// slot index outside the slot arrays (a column that was too long to grid
+// leaves its particles without slots; that error is flagged) is skipped.
 __global__ void k_set_coords(Workspace ws, int C, const float* __restrict__ xyz) {
+    const int n = ws.atom_total;
     const long long nslot = (long long)ws.clu_total * C;
-    int b = 0;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot;
-         s += (long long)gridDim.x * blockDim.x) {
-        const int g = (int)(s / C);
-        b = advance_box(ws.lay.clu_off, ws.nbox, b, g);
-        if (g - ws.lay.clu_off[b] >= ws.st[b].nclu) continue;
-        const int a = ws.atom_of_slot[s];
-        if (a < 0) continue;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
         const float4 o = ws.woff[a];
-        float4 p = ws.xyzq[s];
-        p.x = __fadd_rn(xyz[3 * a], o.x);
-        p.y = __fadd_rn(xyz[3 * a + 1], o.y);
-        p.z = __fadd_rn(xyz[3 * a + 2], o.z);
-        ws.xyzq[s] = p;
+        const int s = ws.slot_of_atom[a];
+        if (s < 0 || s >= nslot) continue;
+        ws.xyzq[s] = make_float4(__fadd_rn(xyz[3 * a], o.x), __fadd_rn(xyz[3 * a + 1], o.y),
+                                 __fadd_rn(xyz[3 * a + 2], o.z), ws.q[a]);
     }
 }
 
 cudaError_t launch_set_coords(const Workspace& ws, int C, const float* xyz, cudaStream_t s) {
-    const long long nslot = (long long)ws.clu_total * C;
-    long long blocks = (nslot + 255) / 256;
+    long long blocks = ((long long)ws.atom_total + 255) / 256;
     if (blocks > 65535) blocks = 65535;
     if (blocks < 1) blocks = 1;
     k_set_coords<<<(int)blocks, 256, 0, s>>>(ws, C, xyz);

@@ -90,6 +90,10 @@ struct Workspace {
     Layout lay;
     int atom_total, col_total, clu_total, sc_total;
     long long ient_total;
+    // [nbox + 1]: exclusive prefix over boxes of the i-entries the last search
+    // stored (clamped to capacity); entry nbox is their total.  Kernels that
+    // walk the list index this compact range instead of the capacity.
+    int* ient_used;
     // per particle (caller order, all boxes concatenated)
     float4* xw;          // wrapped coordinates + charge
     float4* woff;        // wrap offset (wrapped - input), per particle
@@ -150,11 +154,11 @@ struct ForceParams {
 };
 
 cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n_sm, cudaStream_t s);
-cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, float* f_out, double* e_out,
+cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int C, float* f_out, double* e_out,
                             double* vir_out, cudaStream_t s);
 
 // Kernels each launcher issues (for launch accounting).
-constexpr int kLaunchesGrid = 4, kLaunchesSearch = 1, kLaunchesPrune = 2, kLaunchesSetCoords = 1;
+constexpr int kLaunchesGrid = 4, kLaunchesSearch = 2, kLaunchesPrune = 2, kLaunchesSetCoords = 1;
 
 // ---------------------------------------------------------------------------
 // Device helpers
@@ -172,6 +176,13 @@ __device__ __forceinline__ int find_box(const T* off, int nbox, T x) {
         if (off[m] <= x) lo = m; else hi = m;
     }
     return lo;
+}
+
+// i-entry of compact index c (0 <= c < ient_used[nbox]) and its box.
+__device__ __forceinline__ int ient_of(const int* ient_used, const long long* ient_off, int nbox, int c,
+                                       int& b) {
+    b = find_box(ient_used, nbox, c);
+    return (int)ient_off[b] + (c - ient_used[b]);
 }
 
 // Advance box b (ascending walk) until off[b] <= x < off[b+1].

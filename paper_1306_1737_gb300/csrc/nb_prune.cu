@@ -43,12 +43,9 @@ __global__ void __launch_bounds__(32 * kPruneWarps) k_prune(PruneArgs A) {
         pi[k] = pv[k] ? p / C : 0;
         pj[k] = pv[k] ? p % C : 0;
     }
-    for (long long e = (long long)blockIdx.x * kPruneWarps + wib; e < W.ient_total;
-         e += (long long)gridDim.x * kPruneWarps) {
-        b = advance_box(W.lay.ient_off, W.nbox, b, e);
-        const long long ient_base = W.lay.ient_off[b];
-        const long long nvalid = min((long long)W.st[b].n_ient, W.lay.ient_off[b + 1] - ient_base);
-        if (e - ient_base >= nvalid) continue;
+    const int n_used = W.ient_used[W.nbox];
+    for (int c = blockIdx.x * kPruneWarps + wib; c < n_used; c += gridDim.x * kPruneWarps) {
+        const int e = ient_of(W.ient_used, W.lay.ient_off, W.nbox, c, b);
         if (b != b_acc) {
             if (lane == 0 && b_acc >= 0 && kept_total) {
                 atomicAdd(&W.st[b_acc].n_jent_pruned, kept_total);

@@ -314,6 +314,19 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
     }
 }
 
+// Compact i-entry index: per box the entries stored (clamped to the box's
+// capacity), as an exclusive prefix over the boxes.
+__global__ void k_ient_offsets(Workspace ws) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int acc = 0;
+    for (int b = 0; b < ws.nbox; ++b) {
+        ws.ient_used[b] = acc;
+        const long long cap = ws.lay.ient_off[b + 1] - ws.lay.ient_off[b];
+        acc += (int)min((long long)ws.st[b].n_ient, cap);
+    }
+    ws.ient_used[ws.nbox] = acc;
+}
+
 cudaError_t launch_search(const Workspace& ws, int C, float rlist, float rbb, const int* excl_off,
                           const int* excl_idx, int n_sm, cudaStream_t s) {
     SearchArgs A;
@@ -331,6 +344,7 @@ cudaError_t launch_search(const Workspace& ws, int C, float rlist, float rbb, co
         k_search<8, super_size(8)><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
     else
         k_search<4, super_size(4)><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
+    k_ient_offsets<<<1, 32, 0, s>>>(ws);
     return cudaGetLastError();
 }
 

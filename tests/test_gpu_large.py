@@ -89,11 +89,23 @@ def test_config3_grid_list_prune_forces(env):
         assert emax < FORCE_TOL, (emax, erms)
         # Newton's third law over the whole box (FP32 accumulation)
         assert np.abs(f.sum(0)).max() < 1e-3 * rms * np.sqrt(b.n)
-        # every particle, energies and virial against the cell-list tier
+        # every particle, energies and virial against the cell-list tier.
+        # Re-typed molecules carry LJ on all three sites at water contacts
+        # (sites 0.1 nm apart, sigma up to 0.4 nm), so a few particles feel
+        # forces of 1e9 kJ/mol/nm, 100 x the RMS; FP32 rounds such a force
+        # at about 1e-6 of itself, above 1e-4 of the RMS.  Per particle the
+        # bound is 1e-4 RMS + 4e-6 |F_i| (FP32 accumulation of ~200 terms).
         fc, ec, vc = oracle.forces_cells(b.xyz, b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx,
                                          b.box, oprm)
-        emax_all, erms_all, _ = gp.force_errors(f, fc)
-        assert emax_all < FORCE_TOL, (emax_all, erms_all)
+        rms_all = np.sqrt((fc ** 2).sum(1).mean())
+        err = np.sqrt(((f - fc) ** 2).sum(1))
+        fmag = np.sqrt((fc ** 2).sum(1))
+        bad = err > FORCE_TOL * rms_all + 4e-6 * fmag
+        assert not bad.any(), (int(bad.sum()), float((err / (FORCE_TOL * rms_all + 4e-6 * fmag)).max()))
+        # particles with forces below 100 x the median: the plain bound on their own RMS
+        typical = fmag < 100 * np.median(fmag)
+        rms_t = np.sqrt((fc[typical] ** 2).sum(1).mean())
+        assert err[typical].max() < FORCE_TOL * rms_t, (err[typical].max() / rms_t, typical.mean())
         assert np.abs(e - ec).max() / np.abs(ec).max() < 1e-5, (e, ec)
         assert np.abs(vir - vc).max() / np.abs(vc).max() < 1e-5
         # after 5 frames of displacements: prune and forces again
