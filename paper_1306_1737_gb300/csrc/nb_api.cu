@@ -219,6 +219,7 @@ static size_t carve(const nb_ctx* c, char* base, Workspace* ws) {
     w.cj_p = (int*)take(sizeof(int) * w.jstride);
     w.mask_p = (unsigned long long*)take(sizeof(unsigned long long) * w.jstride * S);
     w.ient_used = (int*)take(sizeof(int) * (nb + 1));
+    w.work = (int*)take(sizeof(int) * 2);
     w.c6c12 = (float2*)take(sizeof(float2) * kMaxTypes * kMaxTypes);
     w.mlp = (MlpTC*)take(sizeof(MlpTC));
     if (ws) *ws = w;
@@ -471,6 +472,7 @@ nb_status nb_set_workspace(nb_ctx* c, void* ws, size_t bytes) {
     c->last.assign(c->nbox, DevState{});
     const int nb = c->nbox;
     NB_CUDA(c, cudaMemset(c->ws.st, 0, sizeof(DevState) * nb));
+    NB_CUDA(c, cudaMemset(c->ws.work, 0, sizeof(int) * 2));
     NB_CUDA(c, cudaMemset(c->ws.geo, 0, sizeof(BoxGeom) * nb));
     NB_CUDA(c, cudaMemcpy((void*)c->ws.lay.atom_off, c->atom_off.data(), sizeof(int) * (nb + 1),
                           cudaMemcpyHostToDevice));

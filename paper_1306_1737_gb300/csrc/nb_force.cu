@@ -43,6 +43,7 @@ struct ForceArgs {
     Accum* acc;
     const MlpTC* mlp;
     const int* ient_used;             // compact i-entry index per box
+    int* work;                        // work counter (next i-entry to take)
     int nbox;
     ForceParams p;
 };
@@ -482,7 +483,16 @@ k_force8(ForceArgs A) {
     unsigned n_inc = 0;
     int b_acc = -1;
     const int n_used = A.ient_used[A.nbox];
-    for (int c = blockIdx.x * kForceWarps + (threadIdx.x >> 5); c < n_used; c += gridDim.x * kForceWarps) {
+    // warps take i-entries from a counter (entries differ in length); the
+    // next index is requested while the current entry is processed
+    // (the first entry of each warp is its warp index, so the launch does not
+    // start with every warp contending for the counter; with only a few
+    // entries per warp the static order wins and the counter is not used)
+    const int n_warps = gridDim.x * kForceWarps;
+    const bool dynamic = n_used > 8 * n_warps;
+    int c_next = 0;
+    for (int c = blockIdx.x * kForceWarps + (threadIdx.x >> 5); c < n_used; c = __shfl_sync(full, c_next, 0)) {
+        if (lane == 0) c_next = dynamic ? n_warps + atomicAdd(A.work, 1) : c + n_warps;
         // the entry and its box by binary search (no state carried across entries)
         int b;
         const int e = ient_of(A.ient_used, A.ient_off, A.nbox, c, b);
@@ -690,6 +700,7 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
     A.mlp = ws.mlp;
     A.nbox = ws.nbox;
     A.ient_used = ws.ient_used;
+    A.work = ws.work;
     A.p = p;
     // the accumulators hold energies, pair counts and shift forces, which
     // only energy evaluations produce and read
@@ -721,6 +732,7 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
 __global__ void k_finalize(Workspace ws, int C, float* __restrict__ f_out, int want_vir) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ws.work[0] = 0;   // the force kernel's counter
     const int n = ws.atom_total;
     // whole warps step through the particles so that box boundaries are seen warp-wide
     for (int base = (blockIdx.x * blockDim.x + threadIdx.x) - lane; base < n;

@@ -94,6 +94,10 @@ struct Workspace {
     // stored (clamped to capacity); entry nbox is their total.  Kernels that
     // walk the list index this compact range instead of the capacity.
     int* ient_used;
+    // [2] work counters of the force and prune kernels (warps take the next
+    // i-entry from them); zero between launches: the search's epilogue and
+    // the kernel that follows each user reset them
+    int* work;
     // per particle (caller order, all boxes concatenated)
     float4* xw;          // wrapped coordinates + charge
     float4* woff;        // wrap offset (wrapped - input), per particle

@@ -44,7 +44,15 @@ __global__ void __launch_bounds__(32 * kPruneWarps) k_prune(PruneArgs A) {
         pj[k] = pv[k] ? p % C : 0;
     }
     const int n_used = W.ient_used[W.nbox];
-    for (int c = blockIdx.x * kPruneWarps + wib; c < n_used; c += gridDim.x * kPruneWarps) {
+    // warps take i-entries from a counter (entries differ in length), the
+    // next index requested while the current entry is processed
+    // (the first entry of each warp is its warp index; with only a few
+    // entries per warp the static order is kept)
+    const int n_warps = gridDim.x * kPruneWarps;
+    const bool dynamic = n_used > 8 * n_warps;
+    int c_next = 0;
+    for (int c = blockIdx.x * kPruneWarps + wib; c < n_used; c = __shfl_sync(full, c_next, 0)) {
+        if (lane == 0) c_next = dynamic ? n_warps + atomicAdd(&W.work[1], 1) : c + n_warps;
         const int e = ient_of(W.ient_used, W.lay.ient_off, W.nbox, c, b);
         if (b != b_acc) {
             if (lane == 0 && b_acc >= 0 && kept_total) {
@@ -131,6 +139,7 @@ __global__ void __launch_bounds__(32 * kPruneWarps) k_prune(PruneArgs A) {
 
 // Zero every box's pruned counters.
 __global__ void k_prune_reset(Workspace ws) {
+    if (threadIdx.x == 0) ws.work[1] = 0;
     for (int b = threadIdx.x; b < ws.nbox; b += blockDim.x) {
         ws.st[b].n_jent_pruned = 0;
         ws.st[b].n_keys_pruned = 0;

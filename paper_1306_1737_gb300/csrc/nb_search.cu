@@ -325,6 +325,8 @@ __global__ void k_ient_offsets(Workspace ws) {
         acc += (int)min((long long)ws.st[b].n_ient, cap);
     }
     ws.ient_used[ws.nbox] = acc;
+    ws.work[0] = 0;
+    ws.work[1] = 0;
 }
 
 cudaError_t launch_search(const Workspace& ws, int C, float rlist, float rbb, const int* excl_off,
