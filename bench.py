@@ -362,6 +362,7 @@ def run_ours(args):
     prm_e = nb.make_params(elec, rc, eps_rf=p.get("eps_rf", math.inf), beta=p.get("beta", 0.0), want_energy=True)
     prm_f = nb.make_params(elec, rc, eps_rf=p.get("eps_rf", math.inf), beta=p.get("beta", 0.0), want_energy=False)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rbb = rlist if args.rbb < 0 else args.rbb
 
     def energy_frame(f):
         return f == 0 or f == nstlist - 1
@@ -375,15 +376,15 @@ def run_ours(args):
         else:
             x0 = xdev[0]
         nb.nb_grid_put(ctx, x0, box.box, stream)
-        nb.nb_pairlist_build(ctx, rlist, 0.0, eo, ei, stream)
+        nb.nb_pairlist_build(ctx, rlist, rbb, eo, ei, stream)
         for f in range(nstlist):
             if host is not None and f > 0:
                 xbuf.copy_(hx[f], non_blocking=True)
                 xf = xbuf
             else:
                 xf = x0 if host is not None else xdev[f]
-            if nstprune and f > 0 and f % nstprune == 0:
-                nb.nb_prune(ctx, xf, rprune, stream)
+            if nstprune and f % nstprune == 0 and (f > 0 or args.prune0):
+                nb.nb_prune(ctx, xf if f > 0 else None, rprune, stream)
                 xarg = None
             else:
                 xarg = xf if f > 0 else None
@@ -444,7 +445,7 @@ def run_ours(args):
     pairs_outer = int(info.n_cluster_pairs) * 64
     pairs_pruned = int(info.n_cluster_pairs_pruned) * 64 if info.n_cluster_pairs_pruned >= 0 else pairs_outer
     # frames before the first prune use the outer list
-    n_outer = min(nstprune, nstlist) if nstprune else nstlist
+    n_outer = 0 if (nstprune and args.prune0) else (min(nstprune, nstlist) if nstprune else nstlist)
     listed = (n_outer * pairs_outer + (nstlist - n_outer) * pairs_pruned) / nstlist
     pairs_rc = int(info.n_pairs_rc)
     flops = FLOPS_DIST * listed + (FLOPS_PAIR[elec] - FLOPS_DIST) * pairs_rc
@@ -764,6 +765,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rbb", type=float, default=0.0,
+                    help="bounding-box distance below which the search skips the particle test (nm; <0: rlist)")
+    ap.add_argument("--prune0", action="store_true", help="also prune right after each list build")
     ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",
                     help="skip the learned Ewald factor A/B (Ewald workloads)")
     ap.add_argument("--workload", default="water24k",

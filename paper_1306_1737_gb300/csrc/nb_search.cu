@@ -52,6 +52,8 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     __shared__ float4 s_xi[kSearchWarps][NA];
+    __shared__ float4 s_h[kSearchWarps][NA];   // i particles shifted by the current shift: hi part
+    __shared__ float4 s_l[kSearchWarps][NA];   // and lo part (TwoSum)
     __shared__ float s_bb[kSearchWarps][S][12];  // shifted BB: lo hi/lo, hi hi/lo per dimension
     __shared__ int s_ex_r[kSearchWarps][kMaxExclPerSuper];
     __shared__ int s_ex_s[kSearchWarps][kMaxExclPerSuper];
@@ -139,6 +141,16 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                 s_bb[wib][k][2 * c] = h;
                 s_bb[wib][k][2 * c + 1] = l;
             }
+            if (lane < NA) {
+                const float4 xi = s_xi[wib][lane];
+                float4 h, l;
+                two_sum(xi.x, sh[0], h.x, l.x);
+                two_sum(xi.y, sh[1], h.y, l.y);
+                two_sum(xi.z, sh[2], h.z, l.z);
+                h.w = l.w = 0.0f;
+                s_h[wib][lane] = h;
+                s_l[wib][lane] = l;
+            }
             __syncwarp();
 
             int nbuf = 0;
@@ -216,7 +228,16 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                     const bool valid = idx < total;
                     const int cb_ = ok0 + (idx - oex);
                     unsigned need = 0, acc = 0;  // per candidate: i-clusters to test / accepted
+                    unsigned realB_mine = 0;     // per candidate: its real (non-dummy) slots
                     if (valid) {
+                        // the candidate's slot table, loaded beside its bounding box
+                        const int4* ap = reinterpret_cast<const int4*>(W.atom_of_slot + (long long)cb_ * C);
+#pragma unroll
+                        for (int v = 0; v < C / 4; ++v) {
+                            const int4 a = ap[v];
+                            realB_mine |= ((a.x >= 0) ? 1u : 0u) << (4 * v) | ((a.y >= 0) ? 2u : 0u) << (4 * v) |
+                                          ((a.z >= 0) ? 4u : 0u) << (4 * v) | ((a.w >= 0) ? 8u : 0u) << (4 * v);
+                        }
                         const float4 jlo = W.bb[2 * cb_], jhi = W.bb[2 * cb_ + 1];
                         const float jl[3] = {jlo.x, jlo.y, jlo.z}, jh[3] = {jhi.x, jhi.y, jhi.z};
                         for (int k = 0; k < n; ++k) {
@@ -237,33 +258,47 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                             }
                         }
                     }
-                    // particle-distance tests, one warp-wide test per (candidate, i-cluster)
+                    // particle-distance tests, one warp-wide test per (candidate,
+                    // i-cluster); two candidates per round so that their
+                    // particle loads are in flight together
                     unsigned pending = __ballot_sync(full, need != 0);
                     while (pending) {
-                        const int t = __ffs(pending) - 1;
+                        const int t1 = __ffs(pending) - 1;
                         pending &= pending - 1;
-                        const int bt = __shfl_sync(full, cb_, t);
-                        unsigned nk = __shfl_sync(full, need, t);
-                        while (nk) {
-                            const int k = __ffs(nk) - 1;
-                            nk &= nk - 1;
-                            bool hit = false;
+                        const int t2 = pending ? __ffs(pending) - 1 : -1;
+                        if (t2 >= 0) pending &= pending - 1;
+                        const int bt1 = __shfl_sync(full, cb_, t1);
+                        const int bt2 = __shfl_sync(full, cb_, t2 >= 0 ? t2 : t1);
+                        unsigned nk1 = __shfl_sync(full, need, t1);
+                        unsigned nk2 = __shfl_sync(full, need, t2 >= 0 ? t2 : t1);
+                        if (t2 < 0) nk2 = 0u;
+                        float4 xa[PPL], xb[PPL];
 #pragma unroll
-                            for (int kk = 0; kk < PPL; ++kk) {
-                                const int p = lane + 32 * kk;
-                                if (p >= C * C) continue;
-                                const float4 xi = s_xi[wib][k * C + p / C];
-                                const float4 xj = W.xyzq[bt * C + p % C];
-                                float h, l;
-                                two_sum(xi.x, sh[0], h, l);
-                                const float dx = (h - xj.x) + l;
-                                two_sum(xi.y, sh[1], h, l);
-                                const float dy = (h - xj.y) + l;
-                                two_sum(xi.z, sh[2], h, l);
-                                const float dz = (h - xj.z) + l;
-                                hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < A.rl2;
+                        for (int kk = 0; kk < PPL; ++kk) {
+                            const int jj = (lane + 32 * kk) % C;
+                            xa[kk] = W.xyzq[bt1 * C + jj];
+                            xb[kk] = W.xyzq[bt2 * C + jj];
+                        }
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            unsigned nk = u == 0 ? nk1 : nk2;
+                            while (nk) {
+                                const int k = __ffs(nk) - 1;
+                                nk &= nk - 1;
+                                bool hit = false;
+#pragma unroll
+                                for (int kk = 0; kk < PPL; ++kk) {
+                                    const int p = lane + 32 * kk;
+                                    if (p >= C * C) continue;
+                                    const float4 h = s_h[wib][k * C + p / C], l = s_l[wib][k * C + p / C];
+                                    const float4 xj = u == 0 ? xa[kk] : xb[kk];
+                                    const float dx = (h.x - xj.x) + l.x;
+                                    const float dy = (h.y - xj.y) + l.y;
+                                    const float dz = (h.z - xj.z) + l.z;
+                                    hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < A.rl2;
+                                }
+                                if (__any_sync(full, hit) && lane == (u == 0 ? t1 : t2)) acc |= 1u << k;
                             }
-                            if (__any_sync(full, hit) && lane == t) acc |= 1u << k;
                         }
                     }
                     unsigned accepted = __ballot_sync(full, acc != 0);
@@ -272,8 +307,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                         accepted &= accepted - 1;
                         const int bt = __shfl_sync(full, cb_, t);
                         const unsigned at = __shfl_sync(full, acc, t);
-                        const int bos = lane < C ? W.atom_of_slot[bt * C + lane] : -1;
-                        const unsigned realB = __ballot_sync(full, bos >= 0);
+                        const unsigned realB = __shfl_sync(full, realB_mine, t);
 #pragma unroll
                         for (int k = 0; k < S; ++k) {
                             unsigned long long m = 0;
