@@ -248,12 +248,16 @@ nb_status nb_box_info(nb_ctx* ctx, int box, nb_info* info);
 
 /* enable != 0: from now on record a pair of CUDA events on the launching
  * stream around each hot-path kernel (kinds above; at most 256 spans are kept
- * until read; launches into a capturing stream are not recorded).  enable
- * == 0 stops recording.  Errors: NB_ERR_CUDA. */
+ * until read).  Inside a stream capture the events become event-record nodes
+ * of the graph, recorded at every replay.  enable == 2 does the same and also
+ * keeps the spans across nb_profile_read calls, so that each replay of a
+ * captured graph can be read; enable == 0 stops recording.
+ * Errors: NB_ERR_CUDA. */
 nb_status nb_profile(nb_ctx* ctx, int enable);
 
 /* Wait for the recorded spans and return them in launch order: kinds[k] and
- * ms[k] for k < *count (at most max), then forget them.  Host arrays.
+ * ms[k] for k < *count (at most max), then forget them (unless recording was
+ * enabled with 2).  Host arrays.
  * Errors: NB_ERR_ARG, NB_ERR_CUDA. */
 nb_status nb_profile_read(nb_ctx* ctx, int* kinds_host, float* ms_host, int max, int* count);
 

@@ -281,8 +281,9 @@ def nb_get_list(ctx, which, ient=None, cj=None, mask=None, stream=None):
                                    _stream(stream)))
 
 
-def nb_profile(ctx, enable=True):
-    _check(ctx, load().nb_profile(ctx, int(bool(enable))))
+def nb_profile(ctx, enable=True, keep=False):
+    """enable: record spans; keep: spans survive reads (timing graph replays)."""
+    _check(ctx, load().nb_profile(ctx, 2 if (enable and keep) else int(bool(enable))))
 
 
 def nb_profile_read(ctx, max_spans=256):

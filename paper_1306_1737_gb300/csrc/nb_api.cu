@@ -61,24 +61,35 @@ struct nb_ctx {
     // timing spans (nb_profile)
     static constexpr int kMaxSpans = 256;
     bool prof = false;
+    bool prof_keep = false;   // spans survive reads (graph replays re-record them)
     cudaEvent_t ev[2 * kMaxSpans] = {};
     int ev_kind[kMaxSpans] = {};
     int ev_n = 0;
     char err[512] = {0};
 };
 
+// Timing spans: a pair of events around a kernel.  Inside a stream capture
+// the events become event-record nodes of the graph (recorded at every
+// replay), so a replayed graph can be timed span by span.
+static cudaError_t span_record(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
+    if (cap == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    return cudaEventRecord(ev, s);
+}
+
 static int span_begin(nb_ctx* c, int kind, cudaStream_t s) {
     if (!c->prof || c->ev_n >= nb_ctx::kMaxSpans) return -1;
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return -1;
-    const int k = c->ev_n++;
+    const int k = c->ev_n;
+    if (span_record(c->ev[2 * k], s) != cudaSuccess) return -1;
+    c->ev_n = k + 1;
     c->ev_kind[k] = kind;
-    cudaEventRecord(c->ev[2 * k], s);
     return k;
 }
 
 static void span_end(nb_ctx* c, int k, cudaStream_t s) {
-    if (k >= 0) cudaEventRecord(c->ev[2 * k + 1], s);
+    if (k >= 0) span_record(c->ev[2 * k + 1], s);
 }
 
 static nb_status fail(nb_ctx* c, nb_status s, const char* fmt, ...) {
@@ -722,6 +733,7 @@ nb_status nb_profile(nb_ctx* c, int enable) {
         for (int k = 0; k < 2 * nb_ctx::kMaxSpans; ++k) NB_CUDA(c, cudaEventCreate(&c->ev[k]));
     }
     c->prof = enable != 0;
+    c->prof_keep = enable == 2;
     return NB_OK;
 }
 
@@ -735,7 +747,7 @@ nb_status nb_profile_read(nb_ctx* c, int* kinds, float* ms, int max, int* count)
         kinds[k] = c->ev_kind[k];
     }
     *count = n;
-    c->ev_n = 0;
+    if (!c->prof_keep) c->ev_n = 0;
     return NB_OK;
 }
 
