@@ -162,6 +162,24 @@ class ClockSampler:
         return out
 
 
+def slowest_rank_seconds(seconds, dist=None, device=None):
+    """The timed region's length on the slowest rank (every rank runs the
+    same number of steps on its own replica; the job is done when the last
+    rank is)."""
+    if dist is None:
+        return float(seconds)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(n_ranks, units_per_rank, seconds):
+    """Units of all ranks per second of the slowest rank (weak scaling:
+    each rank processes the same units)."""
+    return n_ranks * units_per_rank / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -454,12 +472,8 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     info = nb.nb_check(ctx, stream)
     launches = launches_per_step * args.steps
-    total_s = sum(step_ms) / 1000.0
-    if dist is not None:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = ws_n * args.steps * nstlist / total_s
+    total_s = slowest_rank_seconds(sum(step_ms) / 1000.0, dist, dev)
+    value = whole_job_rate(ws_n, args.steps * nstlist, total_s)
 
     # per-kernel device times: event spans inside replays of the same step
     # graph right after the timed region (L2 flushed before each)
@@ -684,12 +698,8 @@ def run_batch(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
-    total_s = sum(ms_tuned) / 1000.0
-    if dist is not None:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = ws_n * args.steps * BATCH_H / total_s
+    total_s = slowest_rank_seconds(sum(ms_tuned) / 1000.0, dist, dev)
+    value = whole_job_rate(ws_n, args.steps * BATCH_H, total_s)
 
     out = None
     if rank == 0:

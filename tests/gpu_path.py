@@ -37,6 +37,7 @@ class GpuBox:
         return nb.nb_check(self.ctx)
 
     def build(self, rlist, rbb=0.0, excl=True):
+        excl = excl and self.b.excl_idx.size > 0      # an empty CSR is passed as no exclusions
         nb.nb_pairlist_build(self.ctx, rlist, rbb, self.excl_off if excl else None,
                              self.excl_idx if excl else None)
         return nb.nb_check(self.ctx)
