@@ -162,12 +162,40 @@ constexpr int kSuper8 = super_size(8);
 
 // Per-warp shared staging of the force kernel.
 struct WarpSmem {
-    float4 xi[kSuper8 * 8];   // shifted i coordinates (hi part) and f*q
-    float4 xl[kSuper8 * 8];   // low part of the shift
-    int row[kSuper8 * 8];     // LJ row offset (type * ntypes)
+    // i particles of the super-cluster, paired the way a lane uses them:
+    // [k][ih] holds i-particles ih and ih + 4 of i-cluster k side by side
+    float4 ixy[kSuper8][4];   // {x, x', y, y'} shifted coordinates, hi part
+    float4 izq[kSuper8][4];   // {z, z', f q, f q'}
+    float4 lxy[kSuper8][4];   // {x, x', y, y'} lo part of the shift
+    float2 lz[kSuper8][4];    // {z, z'} lo part
+    int2 row[kSuper8][4];     // LJ row offsets (type * ntypes)
     int w[32];                // j-entry words of the current chunk
     unsigned long long m[kSuper8][32];  // their masks per i-cluster
 };
+
+// -x_j in both halves of a packed pair, per coordinate.
+struct NegJ {
+    float2 nx, ny, nz;
+};
+
+// Distance vectors of the lane's two pairs with j-particle (xj) as packed
+// pairs, from the paired i layout: d = (x_i + shift) - x_j with the shift
+// as hi + lo, every operation rounded once (x_i^hi + (-x_j)) + x_i^lo.
+template <bool SHIFTED>
+__device__ __forceinline__ void pair_deltas(const WarpSmem& W, int k, int ih, float2 nx, float2 ny, float2 nz,
+                                            float2& dx, float2& dy, float2& dz, float2& fq) {
+    const float4 a = W.ixy[k][ih], b = W.izq[k][ih];
+    dx = add2(make_float2(a.x, a.y), nx);
+    dy = add2(make_float2(a.z, a.w), ny);
+    dz = add2(make_float2(b.x, b.y), nz);
+    fq = make_float2(b.z, b.w);
+    if (SHIFTED) {
+        const float4 l = W.lxy[k][ih];
+        dx = add2(dx, make_float2(l.x, l.y));
+        dy = add2(dy, make_float2(l.z, l.w));
+        dz = add2(dz, W.lz[k][ih]);
+    }
+}
 
 // Force/energy of the lane's two pairs (x and y components) given squared
 // distances; scalar arithmetic wherever a parameter enters (constant
@@ -246,20 +274,11 @@ __device__ __forceinline__ void flush_energy(Accum* acc, int b, float& e_lj, flo
 template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, bool FULL>
 __device__ __forceinline__ bool icluster8(const ForceParams& P, const float2* s_lj, const WarpSmem& W,
                                           const Lane8& L, int k, bool diag, unsigned long long m,
-                                          float4 xj, int tj, float2& fx, float2& fy, float2& fz,
+                                          float4 xj, const NegJ& nxj, int tj, float2& fx, float2& fy, float2& fz,
                                           float& fjx, float& fjy, float& fjz, float& e_lj, float& e_c,
                                           unsigned& n_inc) {
-    const float4 a0 = W.xi[k * 8 + L.ih], a1 = W.xi[k * 8 + L.ih + 4];
-    float d0x = a0.x - xj.x, d1x = a1.x - xj.x;
-    float d0y = a0.y - xj.y, d1y = a1.y - xj.y;
-    float d0z = a0.z - xj.z, d1z = a1.z - xj.z;
-    if (SHIFTED) {
-        const float4 b0 = W.xl[k * 8 + L.ih], b1 = W.xl[k * 8 + L.ih + 4];
-        d0x += b0.x; d1x += b1.x;
-        d0y += b0.y; d1y += b1.y;
-        d0z += b0.z; d1z += b1.z;
-    }
-    const float2 dx = make_float2(d0x, d1x), dy = make_float2(d0y, d1y), dz = make_float2(d0z, d1z);
+    float2 dx, dy, dz, fq;
+    pair_deltas<SHIFTED>(W, k, L.ih, nxj.nx, nxj.ny, nxj.nz, dx, dy, dz, fq);
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     bool u0 = true, u1 = true;
     if (!FULL) {
@@ -273,9 +292,10 @@ __device__ __forceinline__ bool icluster8(const ForceParams& P, const float2* s_
         inc1 = inc1 && (u1 || !L.lower1);
     }
     if (!__any_sync(0xffffffffu, inc0 || inc1)) return false;
-    const float2 lj0 = s_lj[W.row[k * 8 + L.ih] + tj], lj1 = s_lj[W.row[k * 8 + L.ih + 4] + tj];
-    const float2 fs = pair_force2<ELEC, ENERGY, FIT, FULL>(P, r2, inc0, inc1, u0, u1, a0.w * xj.w,
-                                                           a1.w * xj.w, lj0, lj1, e_lj, e_c);
+    const int2 rw = W.row[k][L.ih];
+    const float2 lj0 = s_lj[rw.x + tj], lj1 = s_lj[rw.y + tj];
+    const float2 fs = pair_force2<ELEC, ENERGY, FIT, FULL>(P, r2, inc0, inc1, u0, u1, fq.x * xj.w,
+                                                           fq.y * xj.w, lj0, lj1, e_lj, e_c);
     if (ENERGY) n_inc += (unsigned)inc0 + (unsigned)inc1;
     const float2 px = mul2(fs, dx), py = mul2(fs, dy), pz = mul2(fs, dz);
     fx = add2(fx, px);
@@ -295,21 +315,13 @@ __device__ __forceinline__ bool icluster8(const ForceParams& P, const float2* s_
 template <bool SHIFTED, bool FULL>
 __device__ __forceinline__ bool icluster8_mlp(const ForceParams& P, const float2* s_lj, const WarpSmem& W,
                                               const Lane8& L, int k, bool diag, unsigned long long m,
-                                              float4 xj, int tj, float2& fx, float2& fy, float2& fz,
+                                              float4 xj, const NegJ& nxj, int tj, float2& fx, float2& fy,
+                                              float2& fz,
                                               float& fjx, float& fjy, float& fjz, const MlpTC& M, float* mo) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const float4 a0 = W.xi[k * 8 + L.ih], a1 = W.xi[k * 8 + L.ih + 4];
-    float d0x = a0.x - xj.x, d1x = a1.x - xj.x;
-    float d0y = a0.y - xj.y, d1y = a1.y - xj.y;
-    float d0z = a0.z - xj.z, d1z = a1.z - xj.z;
-    if (SHIFTED) {
-        const float4 b0 = W.xl[k * 8 + L.ih], b1 = W.xl[k * 8 + L.ih + 4];
-        d0x += b0.x; d1x += b1.x;
-        d0y += b0.y; d1y += b1.y;
-        d0z += b0.z; d1z += b1.z;
-    }
-    const float2 dx = make_float2(d0x, d1x), dy = make_float2(d0y, d1y), dz = make_float2(d0z, d1z);
+    float2 dx, dy, dz, fq;
+    pair_deltas<SHIFTED>(W, k, L.ih, nxj.nx, nxj.ny, nxj.nz, dx, dy, dz, fq);
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     bool u0 = true, u1 = true;
     if (!FULL) {
@@ -359,8 +371,9 @@ __device__ __forceinline__ bool icluster8_mlp(const ForceParams& P, const float2
         g0 = a0f ? ewald_fit_g(P.beta2 * r2.x) : 0.0f;
         g1 = a1f ? ewald_fit_g(P.beta2 * r2.y) : 0.0f;
     }
-    const float2 lj0 = s_lj[W.row[k * 8 + L.ih] + tj], lj1 = s_lj[W.row[k * 8 + L.ih + 4] + tj];
-    const float qq0 = a0.w * xj.w, qq1 = a1.w * xj.w;
+    const int2 rw = W.row[k][L.ih];
+    const float2 lj0 = s_lj[rw.x + tj], lj1 = s_lj[rw.y + tj];
+    const float qq0 = fq.x * xj.w, qq1 = fq.y * xj.w;
     float flj0 = fmaf(lj0.y, rinv6.x, lj0.x) * rinv6.x * rinv2.x;
     float flj1 = fmaf(lj1.y, rinv6.y, lj1.x) * rinv6.y * rinv2.y;
     if (!FULL) {
@@ -406,6 +419,10 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
         const int cjt = (int)(w & kCjMask);
         const unsigned bits = w >> kSuperShift;
         const float4 xj = xjn;
+        NegJ nxj;
+        nxj.nx = make_float2(-xj.x, -xj.x);
+        nxj.ny = make_float2(-xj.y, -xj.y);
+        nxj.nz = make_float2(-xj.z, -xj.z);
         const int tj = tjn;
         cjn = W.w[min(t + 1, nt - 1)] & kCjMask;
         xjn = xyzq_j[cjn * 8];
@@ -419,17 +436,17 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
                 const unsigned long long m = W.m[k][t];
                 if constexpr (ELEC == NB_ELEC_EWALD_MLP) {
                     if (!diag && m == ~0ull)
-                        any |= icluster8_mlp<SHIFTED, true>(A.p, s_lj, W, L, k, false, m, xj, tj, fx[k], fy[k],
+                        any |= icluster8_mlp<SHIFTED, true>(A.p, s_lj, W, L, k, false, m, xj, nxj, tj, fx[k], fy[k],
                                                             fz[k], fjx, fjy, fjz, *M, mo);
                     else
-                        any |= icluster8_mlp<SHIFTED, false>(A.p, s_lj, W, L, k, diag, m, xj, tj, fx[k], fy[k],
+                        any |= icluster8_mlp<SHIFTED, false>(A.p, s_lj, W, L, k, diag, m, xj, nxj, tj, fx[k], fy[k],
                                                              fz[k], fjx, fjy, fjz, *M, mo);
                 } else if (!diag && m == ~0ull) {
-                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true>(A.p, s_lj, W, L, k, false, m, xj, tj,
+                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true>(A.p, s_lj, W, L, k, false, m, xj, nxj, tj,
                                                                        fx[k], fy[k], fz[k], fjx, fjy, fjz,
                                                                        e_lj, e_c, n_inc);
                 } else {
-                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, false>(A.p, s_lj, W, L, k, diag, m, xj, tj,
+                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, false>(A.p, s_lj, W, L, k, diag, m, xj, nxj, tj,
                                                                         fx[k], fy[k], fz[k], fjx, fjy, fjz,
                                                                         e_lj, e_c, n_inc);
                 }
@@ -516,9 +533,20 @@ k_force8(ForceArgs A) {
             two_sum(x.z, sh[2], h.z, l.z);
             h.w = x.w * A.p.fcoul;
             l.w = 0.0f;
-            W.xi[lane] = h;
-            W.xl[lane] = l;
-            W.row[lane] = A.type_slot[g0 * 8 + lane] * A.p.ntypes;
+            const int k = lane >> 3, ih = lane & 3, hh = (lane >> 2) & 1;
+            float* pxy = reinterpret_cast<float*>(&W.ixy[k][ih]);
+            float* pzq = reinterpret_cast<float*>(&W.izq[k][ih]);
+            float* qxy = reinterpret_cast<float*>(&W.lxy[k][ih]);
+            float* qz = reinterpret_cast<float*>(&W.lz[k][ih]);
+            int* pr = reinterpret_cast<int*>(&W.row[k][ih]);
+            pxy[hh] = h.x;
+            pxy[2 + hh] = h.y;
+            pzq[hh] = h.z;
+            pzq[2 + hh] = h.w;
+            qxy[hh] = l.x;
+            qxy[2 + hh] = l.y;
+            qz[hh] = l.z;
+            pr[hh] = A.type_slot[g0 * 8 + lane] * A.p.ntypes;
         }
         __syncwarp();
         const bool center = (s == kShiftCenter);
