@@ -66,7 +66,8 @@ def water1m():
 
 
 FORCE_SOURCES = ["paper_1306_1737_gb300/csrc/nb_force.cu", "paper_1306_1737_gb300/csrc/nb_internal.cuh",
-                 "paper_1306_1737_gb300/csrc/nb_ewald_fit.h"]
+                 "paper_1306_1737_gb300/csrc/nb_ewald_fit.h", "paper_1306_1737_gb300/csrc/nb_pair.cuh",
+                 "paper_1306_1737_gb300/csrc/nb_mlp.cuh"]
 
 
 def force_source_hash():
@@ -336,6 +337,57 @@ def surrogate_ab(nb, ctx, box, p, xs, F, stream, dev, steps=60000, reps=20):
                 float(np.sqrt((d ** 2).mean()) / rms)}
 
 
+def compare_1x1(nb, ctx, box, p, x0, F, rlist, rprune, stream, reps=10, max_nbr=768):
+    """The paper's comparison of cluster pairs with particle pairs (Table 3)
+    on this GPU: on frame 0, the cluster kernel on the outer (rlist) list and
+    on the pruned list, against a thread-per-particle kernel on the full 1 x 1
+    Verlet list of the same radius; device times from CUDA-event spans."""
+    import numpy as np
+    import torch
+    nb.nb_grid_put(ctx, x0, box.box, stream)
+    nb.nb_pairlist_build(ctx, rlist, 0.0, torch.as_tensor(box.excl_off, device=x0.device),
+                         torch.as_tensor(box.excl_idx, device=x0.device), stream)
+    nbr = torch.empty((box.n, max_nbr), dtype=torch.int32, device=x0.device)
+    cnt = torch.empty(box.n, dtype=torch.int32, device=x0.device)
+    nb.nb_pairlist_1x1(ctx, rlist, max_nbr, nbr, cnt, stream)
+    info_outer = nb.nb_check(ctx, stream)
+    listed_1x1 = int(cnt.sum().item())
+    prm = nb.make_params(p["elec"], p["rc"], eps_rf=p.get("eps_rf", math.inf), beta=p.get("beta", 0.0),
+                         want_energy=False)
+    prm_e = nb.make_params(p["elec"], p["rc"], eps_rf=p.get("eps_rf", math.inf), beta=p.get("beta", 0.0),
+                           want_energy=True)
+
+    def timed(fn, kind):
+        fn()
+        torch.cuda.synchronize()
+        nb.nb_profile(ctx, True)
+        nb.nb_profile_read(ctx)
+        for _ in range(reps):
+            fn()
+        ms = [m for k, m in nb.nb_profile_read(ctx) if k == kind]
+        nb.nb_profile(ctx, False)
+        return statistics.mean(ms)
+
+    t_1x1 = timed(lambda: nb.nb_compute_1x1(ctx, prm, None, nbr, cnt, max_nbr, F, stream), nb.NB_KERNEL_FORCE_1X1)
+    t_outer = timed(lambda: nb.nb_compute(ctx, prm, None, F, None, None, stream), nb.NB_KERNEL_FORCE)
+    nb.nb_compute(ctx, prm_e, None, F, None, None, stream)
+    pairs_rc = int(nb.nb_check(ctx, stream).n_pairs_rc)
+    nb.nb_prune(ctx, None, rprune, stream)
+    t_pruned = timed(lambda: nb.nb_compute(ctx, prm, None, F, None, None, stream), nb.NB_KERNEL_FORCE)
+    info_pruned = nb.nb_check(ctx, stream)
+    del nbr
+    return {"frame": 0, "rlist_nm": rlist, "r_prune_nm": rprune, "pairs_within_rc": pairs_rc,
+            "kernel_1x1": {"ms": t_1x1, "listed_pairs": listed_1x1,
+                           "effective_pairs_per_s": 2 * pairs_rc / (t_1x1 * 1e-3),
+                           "note": "full list: each pair computed for both particles"},
+            "kernel_cluster_outer": {"ms": t_outer, "listed_pairs": int(info_outer.n_cluster_pairs) * 64,
+                                     "effective_pairs_per_s": pairs_rc / (t_outer * 1e-3)},
+            "kernel_cluster_pruned": {"ms": t_pruned, "listed_pairs": int(info_pruned.n_cluster_pairs_pruned) * 64,
+                                      "effective_pairs_per_s": pairs_rc / (t_pruned * 1e-3)},
+            "cluster_outer_over_1x1_speed": t_1x1 / t_outer,
+            "cluster_pruned_over_1x1_speed": t_1x1 / t_pruned}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -542,6 +594,7 @@ def run_ours(args):
         d2h = nstlist * box.n * 12 + 16
         cpu = cpu_baseline(box, p) if ws_n == 1 else None
         surr = surrogate_ab(nb, ctx, box, p, xs, F, stream, dev) if elec == "ewald" and args.surrogate else None
+        cmp11 = compare_1x1(nb, ctx, box, p, xs[0], F, rlist, rprune, stream) if args.compare_1x1 else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1000 / args.steps,
@@ -565,6 +618,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "surrogate": surr,
+            "particle_pair_1x1": cmp11,
             "gpu_launches": int(launches),
             "clocks": clocks,
             "status": nb.status_name(info0.status),
@@ -816,6 +870,8 @@ def main():
     ap.add_argument("--rbb", type=float, default=0.0,
                     help="bounding-box distance below which the search skips the particle test (nm; <0: rlist)")
     ap.add_argument("--prune0", action="store_true", help="also prune right after each list build")
+    ap.add_argument("--no-1x1", dest="compare_1x1", action="store_false",
+                    help="skip the particle-pair (1 x 1) kernel comparison")
     ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",
                     help="skip the learned Ewald factor A/B (Ewald workloads)")
     ap.add_argument("--workload", default="water24k",

@@ -103,7 +103,8 @@ enum nb_kernel_kind {
     NB_KERNEL_GRID = 0,    /* the gridding kernels of nb_grid_put, as one span */
     NB_KERNEL_SEARCH = 1,  /* nb_pairlist_build's search kernel */
     NB_KERNEL_PRUNE = 2,   /* nb_prune's prune kernel */
-    NB_KERNEL_FORCE = 3    /* nb_compute's force/energy kernel */
+    NB_KERNEL_FORCE = 3,   /* nb_compute's force/energy kernel */
+    NB_KERNEL_FORCE_1X1 = 4 /* nb_compute_1x1's particle-pair force kernel */
 };
 
 /* --- context ------------------------------------------------------------ */
@@ -290,6 +291,29 @@ nb_status nb_get_grid(nb_ctx* ctx, int* atom_of_slot_dev, int* slot_of_atom_dev,
  * Errors: NB_ERR_STATE, NB_ERR_CUDA. */
 nb_status nb_get_list(nb_ctx* ctx, int which, int* ient_dev, int* cj_dev, uint64_t* mask_dev,
                       nb_stream stream);
+
+/* --- the particle-pair (1 x 1) comparison path -------------------------------- */
+
+/* A full particle-pair Verlet list (every pair within rlist stored for both
+ * particles) expanded from the current outer cluster-pair list, for the
+ * comparison the paper makes between cluster-pair (M x N) and particle-pair
+ * (1 x 1) setups (Sec. 4-5, Table 3).  rlist must not exceed the radius of
+ * the last nb_pairlist_build.  nbr_dev: int [n][max_nbr] entries, each
+ * (neighbour slot << 6) | (force-field excluded << 5) | shift index (the
+ * shift applied to the particle owning the row); count_dev: int [n] entries
+ * per particle (a row holds min(count, max_nbr); a count above max_nbr
+ * raises the NB_ERR_CAPACITY device flag).  Caller order, device memory.
+ * Errors: NB_ERR_ARG, NB_ERR_STATE (no list), NB_ERR_BOX, NB_ERR_CUDA. */
+nb_status nb_pairlist_1x1(nb_ctx* ctx, float rlist, int max_nbr, int* nbr_dev, int* count_dev,
+                          nb_stream stream);
+
+/* Forces over a 1 x 1 list from nb_pairlist_1x1: one thread per particle,
+ * the same pair interactions as nb_compute (RF or Ewald; forces only,
+ * p->want_energy must be 0).  xyz_dev may be NULL (current coordinates);
+ * f_dev: float [n][3], caller order, overwritten.
+ * Errors: NB_ERR_ARG, NB_ERR_STATE, NB_ERR_BOX, NB_ERR_CUDA. */
+nb_status nb_compute_1x1(nb_ctx* ctx, const nb_params* p, const float* xyz_dev, const int* nbr_dev,
+                         const int* count_dev, int max_nbr, float* f_dev, nb_stream stream);
 
 /* --- learned Ewald force factor --------------------------------------------- */
 

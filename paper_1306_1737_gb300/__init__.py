@@ -37,6 +37,7 @@ NB_KERNEL_GRID = 0
 NB_KERNEL_SEARCH = 1
 NB_KERNEL_PRUNE = 2
 NB_KERNEL_FORCE = 3
+NB_KERNEL_FORCE_1X1 = 4
 
 _lock = threading.Lock()
 _lib = None
@@ -112,6 +113,8 @@ def load():
             "nb_mlp_train": ([P, P, C.c_float, C.c_float, P, P, P, C.c_int64, i, i, i, i, C.c_float,
                               C.c_float, P, P], st),
             "nb_set_surrogate": ([P, P, C.c_float, C.c_float, P], st),
+            "nb_pairlist_1x1": ([P, C.c_float, i, P, P, P], st),
+            "nb_compute_1x1": ([P, C.POINTER(nb_params), P, P, P, i, P, P], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -346,6 +349,15 @@ def nb_mlp_train(params, state, r_min, r_max, r, t, w, batch, steps, step0, tota
     _status(load().nb_mlp_train(_ptr(params), _ptr(state), float(r_min), float(r_max), _ptr(r), _ptr(t), _ptr(w),
                                 int(r.numel()), int(batch), int(steps), int(step0), int(total_steps),
                                 float(lr_max), float(lr_min), _ptr(loss), _stream(stream)), "nb_mlp_train")
+
+
+def nb_pairlist_1x1(ctx, rlist, max_nbr, nbr, count, stream=None):
+    _check(ctx, load().nb_pairlist_1x1(ctx, float(rlist), int(max_nbr), _ptr(nbr), _ptr(count), _stream(stream)))
+
+
+def nb_compute_1x1(ctx, params, xyz, nbr, count, max_nbr, f, stream=None):
+    _check(ctx, load().nb_compute_1x1(ctx, C.byref(params), _ptr(xyz), _ptr(nbr), _ptr(count), int(max_nbr),
+                                      _ptr(f), _stream(stream)))
 
 
 def nb_set_surrogate(ctx, params, r_min, r_max, stream=None):

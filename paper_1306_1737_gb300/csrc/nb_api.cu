@@ -349,6 +349,34 @@ static void fill_info(const nb_ctx* c, int b0, int b1, nb_info* info, unsigned f
     info->flags = flags;
 }
 
+// Kernel constants of an interaction setup (Sec. 3.2).
+static nb_status force_params(nb_ctx* c, const nb_params* p, ForceParams* fp) {
+    *fp = ForceParams{};
+    // the surrogate kernel computes forces only; energy evaluations are analytic
+    fp->elec = (p->elec == NB_ELEC_EWALD_MLP && p->want_energy) ? NB_ELEC_EWALD : p->elec;
+    fp->mlp_rmin = c->mlp_rmin;
+    fp->want_energy = p->want_energy ? 1 : 0;
+    fp->rc2 = p->rc * p->rc;
+    fp->fcoul = 138.935458f;
+    const double rc = p->rc;
+    double k = 0.0;
+    if (!(p->eps_rf > 0.f) || std::isinf(p->eps_rf)) k = 1.0 / (2.0 * rc * rc * rc);
+    else k = ((double)p->eps_rf - 1.0) / ((2.0 * p->eps_rf + 1.0) * rc * rc * rc);
+    fp->k_rf = (float)k;
+    fp->two_k_rf = (float)(2.0 * k);
+    fp->c_rf = (float)(1.0 / rc + k * rc * rc);
+    fp->beta = p->beta;
+    fp->two_beta_sqrtpi = (float)(2.0 * (double)p->beta / std::sqrt(M_PI));
+    fp->beta2 = (float)((double)p->beta * p->beta);
+    fp->beta3 = (float)((double)p->beta * p->beta * p->beta);
+    fp->use_fit = ((double)p->beta * p->beta * rc * rc <= (double)kEwaldFitWMax) ? 1 : 0;
+    if (fp->elec == NB_ELEC_EWALD_MLP && !fp->use_fit)
+        return fail(c, NB_ERR_ARG, "the surrogate kernel needs (beta rc)^2 <= %g", (double)kEwaldFitWMax);
+    fp->ntypes = c->ntypes;
+    fp->use_pruned = c->have_pruned ? 1 : 0;
+    return NB_OK;
+}
+
 extern "C" {
 
 const char* nb_status_string(nb_status s) {
@@ -635,28 +663,8 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
         if (st != NB_OK) return st;
     }
     ForceParams fp{};
-    // the surrogate kernel computes forces only; energy evaluations are analytic
-    fp.elec = (p->elec == NB_ELEC_EWALD_MLP && p->want_energy) ? NB_ELEC_EWALD : p->elec;
-    fp.mlp_rmin = c->mlp_rmin;
-    fp.want_energy = p->want_energy ? 1 : 0;
-    fp.rc2 = p->rc * p->rc;
-    fp.fcoul = 138.935458f;
-    const double rc = p->rc;
-    double k = 0.0;
-    if (!(p->eps_rf > 0.f) || std::isinf(p->eps_rf)) k = 1.0 / (2.0 * rc * rc * rc);
-    else k = ((double)p->eps_rf - 1.0) / ((2.0 * p->eps_rf + 1.0) * rc * rc * rc);
-    fp.k_rf = (float)k;
-    fp.two_k_rf = (float)(2.0 * k);
-    fp.c_rf = (float)(1.0 / rc + k * rc * rc);
-    fp.beta = p->beta;
-    fp.two_beta_sqrtpi = (float)(2.0 * (double)p->beta / std::sqrt(M_PI));
-    fp.beta2 = (float)((double)p->beta * p->beta);
-    fp.beta3 = (float)((double)p->beta * p->beta * p->beta);
-    fp.use_fit = ((double)p->beta * p->beta * rc * rc <= (double)kEwaldFitWMax) ? 1 : 0;
-    if (fp.elec == NB_ELEC_EWALD_MLP && !fp.use_fit)
-        return fail(c, NB_ERR_ARG, "the surrogate kernel needs (beta rc)^2 <= %g", (double)kEwaldFitWMax);
-    fp.ntypes = c->ntypes;
-    fp.use_pruned = c->have_pruned ? 1 : 0;
+    const nb_status pst = force_params(c, p, &fp);
+    if (pst != NB_OK) return pst;
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(c, cudaSetDevice(c->device));
     const int sp = span_begin(c, NB_KERNEL_FORCE, s);
@@ -666,6 +674,48 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     e = launch_finalize(c->ws, fp, c->C, f, e_out, vir_out, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
     c->n_launches += 2 + (fp.want_energy ? 1 : 0);
+    return NB_OK;
+}
+
+nb_status nb_pairlist_1x1(nb_ctx* c, float rlist, int max_nbr, int* nbr, int* count, nb_stream stream) {
+    if (!c) return NB_ERR_ARG;
+    if (!c->have_list) return fail(c, NB_ERR_STATE, "nb_pairlist_build first");
+    if (!(rlist > 0.f) || max_nbr <= 0 || (c->n > 0 && (!nbr || !count)))
+        return fail(c, NB_ERR_ARG, "pairlist_1x1: bad argument");
+    if (rlist > c->rlist) return fail(c, NB_ERR_BOX, "rlist above the cluster list's radius");
+    NB_CUDA(c, cudaSetDevice(c->device));
+    cudaError_t e = launch_pairlist_1x1(c->ws, c->C, rlist, max_nbr, nbr, count, c->n_sm, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "1x1 list kernel");
+    c->n_launches += 1;
+    return NB_OK;
+}
+
+nb_status nb_compute_1x1(nb_ctx* c, const nb_params* p, const float* xyz, const int* nbr, const int* count,
+                         int max_nbr, float* f, nb_stream stream) {
+    if (!c) return NB_ERR_ARG;
+    if (!p || (c->n > 0 && (!f || !nbr || !count)) || max_nbr <= 0)
+        return fail(c, NB_ERR_ARG, "compute_1x1: null argument");
+    if (!c->have_grid) return fail(c, NB_ERR_STATE, "nb_grid_put first");
+    if (p->elec != NB_ELEC_RF && p->elec != NB_ELEC_EWALD)
+        return fail(c, NB_ERR_ARG, "the 1x1 kernel supports reaction field and Ewald");
+    if (p->want_energy) return fail(c, NB_ERR_ARG, "the 1x1 kernel computes forces only");
+    if (!(p->rc > 0.f) || !(p->rc < 0.5f * min_edge(c))) return fail(c, NB_ERR_BOX, "rc out of range");
+    if (xyz) {
+        nb_status st = nb_set_coords(c, xyz, stream);
+        if (st != NB_OK) return st;
+    }
+    ForceParams fp{};
+    const nb_status pst = force_params(c, p, &fp);
+    if (pst != NB_OK) return pst;
+    cudaStream_t s = (cudaStream_t)stream;
+    NB_CUDA(c, cudaSetDevice(c->device));
+    const int sp = span_begin(c, NB_KERNEL_FORCE_1X1, s);
+    cudaError_t e = launch_force_1x1(c->ws, fp, c->C, max_nbr, nbr, count, s);
+    span_end(c, sp, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "1x1 force kernel");
+    e = launch_finalize(c->ws, fp, c->C, f, nullptr, nullptr, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel");
+    c->n_launches += 2;
     return NB_OK;
 }
 

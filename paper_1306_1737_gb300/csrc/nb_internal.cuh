@@ -161,6 +161,11 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
 cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int C, float* f_out, double* e_out,
                             double* vir_out, cudaStream_t s);
 
+cudaError_t launch_pairlist_1x1(const Workspace& ws, int C, float rlist, int max_nbr, int* nbr, int* count,
+                                int n_sm, cudaStream_t s);
+cudaError_t launch_force_1x1(const Workspace& ws, const ForceParams& p, int C, int max_nbr, const int* nbr,
+                             const int* count, cudaStream_t s);
+
 // Kernels each launcher issues (for launch accounting).
 constexpr int kLaunchesGrid = 4, kLaunchesSearch = 2, kLaunchesPrune = 2, kLaunchesSetCoords = 1;
 

@@ -283,3 +283,40 @@ def test_no_missed_pairs_over_frames(gp):
             assert none == 0 and many == 0 and once > 0, (f, once, none, many)
     finally:
         gb.close()
+
+
+@pytest.mark.parametrize("cfg", ["cfg1", "cfg2"])
+def test_pair_1x1_list_and_forces(gp, cfg, request):
+    """The particle-pair comparison path: the full 1 x 1 list holds every pair
+    within rlist twice (against the oracle's pair count; pairs within 1e-6 nm
+    of rlist may differ), and its forces match the oracle."""
+    import paper_1306_1737_gb300 as nb
+    b, p = request.getfixturevalue(cfg)
+    gb = gp.GpuBox(b, p["rlist"])
+    torch = gb.torch
+    try:
+        gb.grid()
+        rl = float(np.float32(p["rlist"]))
+        gb.build(rl)
+        max_nbr = 768
+        nbr = torch.zeros((b.n, max_nbr), dtype=torch.int32, device=gb.dev)
+        cnt = torch.zeros(b.n, dtype=torch.int32, device=gb.dev)
+        nb.nb_pairlist_1x1(gb.ctx, rl, max_nbr, nbr, cnt)
+        nb.nb_check(gb.ctx)
+        counts = cnt.cpu().numpy()
+        assert counts.max() <= max_nbr
+        n_pairs = oracle.count_pairs_within(b.xyz, b.box, rl)
+        n_edge = oracle.count_pairs_within(b.xyz, b.box, rl + 1e-6) - oracle.count_pairs_within(b.xyz, b.box, rl - 1e-6)
+        assert abs(int(counts.sum()) - 2 * n_pairs) <= 2 * n_edge
+        elec = p["elec"]
+        prm = nb.make_params(elec, p["rc"], eps_rf=p.get("eps_rf", math.inf), beta=p.get("beta", 0.0),
+                             want_energy=False)
+        oprm = oracle.make_params(elec, float(np.float32(p["rc"])), beta=p.get("beta", 0.0))
+        f = torch.zeros((b.n, 3), dtype=torch.float32, device=gb.dev)
+        nb.nb_compute_1x1(gb.ctx, prm, None, nbr, cnt, max_nbr, f)
+        nb.nb_check(gb.ctx)
+        fo, _, _ = oracle.forces_brute(b.xyz, b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx, b.box, oprm)
+        emax, erms, _ = gp.force_errors(f.cpu().numpy().astype(np.float64), fo)
+        assert emax < FORCE_TOL, (emax, erms)
+    finally:
+        gb.close()
