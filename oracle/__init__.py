@@ -16,6 +16,7 @@ Functions (each follows the paper passage cited in ``oracle.c``):
   ewald_factor   -- the Ewald real-space force factor c(r) (Sec. 3.2)
   mlp_forward    -- the 1-32-32-1 SiLU network that may stand in for c(r)
   mlp_loss_grad  -- its weighted squared-error loss and parameter gradient
+  buffer_drift_integral -- the Appendix's Verlet-buffer drift integral, by quadrature
 """
 from __future__ import annotations
 
@@ -104,6 +105,8 @@ def lib():
             L.or_mlp_forward.argtypes = [P, C.c_double, C.c_double, i64, P, P]
             L.or_mlp_loss_grad.argtypes = [P, C.c_double, C.c_double, i64, P, P, P, P]
             L.or_mlp_loss_grad.restype = C.c_double
+            L.or_buffer_drift_integral.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
+            L.or_buffer_drift_integral.restype = C.c_double
             _lib = L
     return _lib
 
@@ -382,3 +385,9 @@ def mlp_loss_grad(params, r_min: float, r_max: float, r, t, w=None):
     g = np.empty(MLP_NPARAMS)
     loss = lib().or_mlp_loss_grad(_p(p), float(r_min), float(r_max), r.size, _p(r), _p(t), _p(wv), _p(g))
     return float(loss), g
+
+
+def buffer_drift_integral(v1: float, v2: float, rb: float, sigma: float) -> float:
+    """The Appendix's double integral of [V'(rc)(rt - rc) + V''(rc)(rt - rc)^2/2]
+    over rt < rc, r0 > rc + rb with a Gaussian of width sigma in rt - r0."""
+    return float(lib().or_buffer_drift_integral(float(v1), float(v2), float(rb), float(sigma)))

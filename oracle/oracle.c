@@ -906,3 +906,32 @@ int or_forces_cells(int n, const double* xyz, const float* q, const int* type,
     free(members);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Verlet-buffer energy drift (Appendix): for a pair whose distance moves
+ * from r0 > rl = rc + rb (outside the list) to rt < rc during a list
+ * lifetime, with the pair potential expanded to second order at rc,
+ *   I = int_{rt < rc} int_{r0 > rl} [V1 (rt - rc) + V2/2 (rt - rc)^2]
+ *           phi((rt - r0)/sigma)/sigma dr0 drt,
+ * phi the standard normal density.  Evaluated here by plain 2-D quadrature
+ * (midpoint rule on u = rt - rc in [-L, 0], w = r0 - rl in [0, L],
+ * L = rb + 12 sigma), with no use of the closed form.
+ * Parity: pinned by the exact value at rb = 0 and by symbolic integration. */
+double or_buffer_drift_integral(double V1, double V2, double rb, double sigma) {
+    const int n = 1500;
+    const double L = rb + 12.0 * sigma;
+    const double h = L / n;
+    double sum = 0.0;
+    for (int a = 0; a < n; ++a) {
+        const double u = -L + (a + 0.5) * h;           /* rt - rc <= 0 */
+        const double f = V1 * u + 0.5 * V2 * u * u;
+        double inner = 0.0;
+        for (int b = 0; b < n; ++b) {
+            const double w = (b + 0.5) * h;             /* r0 - rl >= 0 */
+            const double z = (u - w - rb) / sigma;      /* (rt - r0) / sigma */
+            inner += exp(-0.5 * z * z);
+        }
+        sum += f * inner;
+    }
+    return sum * h * h / (sigma * sqrt(2.0 * M_PI));
+}

@@ -107,3 +107,23 @@ def test_mlp_gradient_finite_differences():
         pm[i] -= h
         fd = (oracle.mlp_loss_grad(pp, 0.05, 1.0, r, t, w)[0] - oracle.mlp_loss_grad(pm, 0.05, 1.0, r, t, w)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+def test_buffer_drift_integral_pins():
+    """The Appendix's drift integral by quadrature: at rb = 0 the first-order
+    part is -sigma^2/4 and the second-order part sigma^3/(3 sqrt(2 pi))
+    (elementary Gaussian moments); for rb > 0 it matches the integrals
+    evaluated symbolically (sympy) -- a reference independent of the
+    closed form the library uses."""
+    s = 0.03
+    assert abs(oracle.buffer_drift_integral(1.0, 0.0, 0.0, s) - (-0.25 * s * s)) < 1e-6 * s * s
+    assert abs(oracle.buffer_drift_integral(0.0, 1.0, 0.0, s) - s ** 3 / (3 * math.sqrt(2 * math.pi))) < 1e-5 * s ** 3
+    sp = pytest.importorskip("sympy")
+    x = sp.symbols("x", positive=True)
+    for rb, sg in ((0.05, 0.03), (0.1, 0.05)):
+        E = sp.erfc(x / sp.sqrt(2)) / 2
+        # inner integral over r0 gives E((rb - u)/sigma); u = rb - sigma x
+        i1 = float(sg * sp.Integral((rb - sg * x) * E, (x, rb / sg, sp.oo)).evalf(30))
+        i2 = float(sg * sp.Integral(sp.Rational(1, 2) * (rb - sg * x) ** 2 * E, (x, rb / sg, sp.oo)).evalf(30))
+        assert abs(oracle.buffer_drift_integral(1.0, 0.0, rb, sg) - i1) < 1e-6 * abs(i1)
+        assert abs(oracle.buffer_drift_integral(0.0, 1.0, rb, sg) - i2) < 1e-5 * abs(i2)
