@@ -388,6 +388,25 @@ def compare_1x1(nb, ctx, box, p, x0, F, rlist, rprune, stream, reps=10, max_nbr=
             "cluster_pruned_over_1x1_speed": t_1x1 / t_pruned}
 
 
+def buffer_estimate(nb, box, p, nstlist, rlist, dt_ps=0.002, temperature=300.0):
+    """The Appendix's drift bound for this workload's buffer and lifetime,
+    and the buffer it asks for at the paper's 0.1 kB T/ns per particle."""
+    import numpy as np
+    from paper_1306_1737_gb300 import tuner
+    cls = tuner.particle_classes(box.q, box.types, box.mass)
+    table = nb.nb_lj_combine(box.sigma, box.eps)
+    vol = float(np.prod(box.box))
+    prm = nb.make_params(p["elec"], p["rc"], beta=p.get("beta", 0.0))
+    t = max(nstlist - 1, 1) * dt_ps
+    kt = 0.0083144626 * temperature
+    tol = 0.1 * kt / 1000.0
+    drift = nb.nb_buffer_drift(cls, table, vol, prm, rlist - p["rc"], t, temperature)
+    return {"lifetime_ps": t, "temperature_K": temperature, "buffer_nm": rlist - p["rc"],
+            "drift_bound_kT_per_ns_per_particle": drift / kt * 1000.0,
+            "buffer_for_0.1_kT_per_ns_nm": nb.nb_buffer_size(cls, table, vol, prm, t, temperature, tol),
+            "model": "free flight (sigma^2 = t^2 kB T (1/m1 + 1/m2)), an upper bound for rigid water"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -595,6 +614,7 @@ def run_ours(args):
         cpu = cpu_baseline(box, p) if ws_n == 1 else None
         surr = surrogate_ab(nb, ctx, box, p, xs, F, stream, dev) if elec == "ewald" and args.surrogate else None
         cmp11 = compare_1x1(nb, ctx, box, p, xs[0], F, rlist, rprune, stream) if args.compare_1x1 else None
+        buf = buffer_estimate(nb, box, p, nstlist, rlist) if elec == "ewald" else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1000 / args.steps,
@@ -619,6 +639,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "surrogate": surr,
             "particle_pair_1x1": cmp11,
+            "buffer_estimate": buf,
             "gpu_launches": int(launches),
             "clocks": clocks,
             "status": nb.status_name(info0.status),
@@ -728,7 +749,8 @@ def run_batch(args):
     # 1. autotuner (cached per GPU and batch)
     cache = os.path.join(ROOT, "paper_1306_1737_gb300", "_build", "tune_cache.json")
     t0 = time.perf_counter()
-    groups, table = tuner.tune(*common, p, nstprune, rl0, nst0, cache_path=cache, device=dev.index)
+    groups, table = tuner.tune(*common, p, nstprune, rl0, nst0, cache_path=cache, device=dev.index,
+                               rlist_rule=args.rlist_rule, mass=B.mass)
     tune_s = time.perf_counter() - t0
 
     # 2. tuned groups, graph
@@ -870,6 +892,8 @@ def main():
     ap.add_argument("--rbb", type=float, default=0.0,
                     help="bounding-box distance below which the search skips the particle test (nm; <0: rlist)")
     ap.add_argument("--prune0", action="store_true", help="also prune right after each list build")
+    ap.add_argument("--rlist-rule", default="sqrt", choices=["sqrt", "appendix"],
+                    help="batch tuner: list radius per lifetime by sqrt scaling or by the Appendix drift bound")
     ap.add_argument("--no-1x1", dest="compare_1x1", action="store_false",
                     help="skip the particle-pair (1 x 1) kernel comparison")
     ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",

@@ -292,6 +292,34 @@ nb_status nb_get_grid(nb_ctx* ctx, int* atom_of_slot_dev, int* slot_of_atom_dev,
 nb_status nb_get_list(nb_ctx* ctx, int which, int* ient_dev, int* cj_dev, uint64_t* mask_dev,
                       nb_stream stream);
 
+/* --- Verlet-buffer estimate (Appendix) ------------------------------------- */
+
+/* Particles sharing mass, charge and LJ type, for the buffer estimate. */
+typedef struct {
+    double count;   /* particles of the class in the volume */
+    double mass;    /* atomic mass units */
+    double charge;  /* e */
+    int type;       /* LJ type: row of the c6c12 table */
+} nb_particle_class;
+
+/* Upper bound on the energy drift (kJ mol^-1 ps^-1 per particle) caused by a
+ * Verlet buffer rb (nm) over a list lifetime t_ps at temperature T (K), for
+ * the classes in volume (nm^3) with interactions p (rc, electrostatics) and
+ * the LJ table c6c12_host (float [ntypes][ntypes][2] = {C6, C12}): the
+ * Appendix's estimate with free-flight displacements, sigma^2 = t^2 kB T
+ * (1/m1 + 1/m2), and the pair potential expanded to second order at rc
+ * (the second-order term integrated exactly: sigma (rb^2 + 2 sigma^2)).
+ * Host-only arithmetic.  Errors: NB_ERR_ARG. */
+nb_status nb_buffer_drift(int nclass, const nb_particle_class* classes_host, int ntypes,
+                          const float* c6c12_host, double volume, const nb_params* p, double rb, double t_ps,
+                          double temperature, double* drift_per_ps);
+
+/* The smallest buffer rb (nm, to 1e-6) whose drift bound is at most
+ * tolerance (kJ mol^-1 ps^-1 per particle).  Errors: NB_ERR_ARG. */
+nb_status nb_buffer_size(int nclass, const nb_particle_class* classes_host, int ntypes, const float* c6c12_host,
+                         double volume, const nb_params* p, double t_ps, double temperature, double tolerance,
+                         double* rb);
+
 /* --- the particle-pair (1 x 1) comparison path -------------------------------- */
 
 /* A full particle-pair Verlet list (every pair within rlist stored for both

@@ -62,6 +62,10 @@ class nb_info(C.Structure):
                 ("flags", C.c_uint32), ("n_boxes", C.c_int), ("atom_offset", C.c_int)]
 
 
+class nb_particle_class(C.Structure):
+    _fields_ = [("count", C.c_double), ("mass", C.c_double), ("charge", C.c_double), ("type", C.c_int)]
+
+
 class NbError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_name(status)}: {msg}")
@@ -114,6 +118,10 @@ def load():
                               C.c_float, P, P], st),
             "nb_set_surrogate": ([P, P, C.c_float, C.c_float, P], st),
             "nb_pairlist_1x1": ([P, C.c_float, i, P, P, P], st),
+            "nb_buffer_drift": ([i, P, i, P, C.c_double, C.POINTER(nb_params), C.c_double, C.c_double,
+                                 C.c_double, C.POINTER(C.c_double)], st),
+            "nb_buffer_size": ([i, P, i, P, C.c_double, C.POINTER(nb_params), C.c_double, C.c_double,
+                                C.c_double, C.POINTER(C.c_double)], st),
             "nb_compute_1x1": ([P, C.POINTER(nb_params), P, P, P, i, P, P], st),
         }
         for name, (args, res) in sig.items():
@@ -349,6 +357,39 @@ def nb_mlp_train(params, state, r_min, r_max, r, t, w, batch, steps, step0, tota
     _status(load().nb_mlp_train(_ptr(params), _ptr(state), float(r_min), float(r_max), _ptr(r), _ptr(t), _ptr(w),
                                 int(r.numel()), int(batch), int(steps), int(step0), int(total_steps),
                                 float(lr_max), float(lr_min), _ptr(loss), _stream(stream)), "nb_mlp_train")
+
+
+def _classes(classes):
+    """[(count, mass, charge, type), ...] -> ctypes array of nb_particle_class."""
+    arr = (nb_particle_class * len(classes))()
+    for k, (cnt, m, q, t) in enumerate(classes):
+        arr[k] = nb_particle_class(float(cnt), float(m), float(q), int(t))
+    return arr
+
+
+def nb_buffer_drift(classes, c6c12, volume, params, rb, t_ps, temperature):
+    """Drift bound (kJ/mol/ps per particle) of buffer rb; classes as
+    [(count, mass, charge, LJ type)], c6c12 host [nt, nt, 2]."""
+    import numpy as np
+    t = np.ascontiguousarray(c6c12, dtype=np.float32)
+    out = C.c_double()
+    arr = _classes(classes)
+    _status(load().nb_buffer_drift(len(classes), arr, int(t.shape[0]), t.ctypes.data, float(volume),
+                                   C.byref(params), float(rb), float(t_ps), float(temperature), C.byref(out)),
+            "nb_buffer_drift")
+    return out.value
+
+
+def nb_buffer_size(classes, c6c12, volume, params, t_ps, temperature, tolerance):
+    """Smallest buffer (nm) whose drift bound is at most tolerance."""
+    import numpy as np
+    t = np.ascontiguousarray(c6c12, dtype=np.float32)
+    out = C.c_double()
+    arr = _classes(classes)
+    _status(load().nb_buffer_size(len(classes), arr, int(t.shape[0]), t.ctypes.data, float(volume),
+                                  C.byref(params), float(t_ps), float(temperature), float(tolerance),
+                                  C.byref(out)), "nb_buffer_size")
+    return out.value
 
 
 def nb_pairlist_1x1(ctx, rlist, max_nbr, nbr, count, stream=None):

@@ -12,7 +12,9 @@ group (one context).
 
 The paper picks the cluster shape per architecture (Sec. 2.2, Table 1) and
 the list lifetime from a buffer estimate (Sec. 2.3, Appendix); here both are
-measured on the GPU at hand.
+measured on the GPU at hand.  Each lifetime's list radius comes either from
+scaling the configured buffer with sqrt(nstlist / nstlist0) or from the
+Appendix's drift bound (nb_buffer_size).
 """
 from __future__ import annotations
 
@@ -68,9 +70,34 @@ def time_group(spec, counts, boxes, q, types, c6c12, excl_off, excl_idx, frames,
         r.close()
 
 
+def particle_classes(q, types, mass):
+    """[(count, mass, charge, LJ type)] of the distinct particle kinds."""
+    keys = np.stack([np.asarray(types, np.float64), np.asarray(q, np.float64), np.asarray(mass, np.float64)], 1)
+    uniq, cnt = np.unique(keys, axis=0, return_counts=True)
+    return [(int(c), float(u[2]), float(u[1]), int(u[0])) for u, c in zip(uniq, cnt)]
+
+
+def appendix_rlist(classes, c6c12, volume, params, nstlist, dt_ps=0.002, temperature=300.0, tolerance=None):
+    """rc plus the buffer the Appendix's drift bound asks for over a list
+    lifetime of (nstlist - 1) time steps; tolerance in kJ/mol/ps per particle
+    (default 0.1 kB T per ns, the drift of the paper's Table 3)."""
+    import paper_1306_1737_gb300 as nb
+    if tolerance is None:
+        tolerance = 0.1 * 0.0083144626 * temperature / 1000.0
+    prm = nb.make_params(params["elec"], params["rc"], eps_rf=params.get("eps_rf", float("inf")),
+                         beta=params.get("beta", 0.0))
+    rb = nb.nb_buffer_size(classes, c6c12, volume, prm, max(nstlist - 1, 1) * dt_ps, temperature, tolerance)
+    return params["rc"] + rb
+
+
 def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nstprune, rlist0, nstlist0,
-         n_classes=4, reps=3, cache_path=None, device=0, log=None):
-    """Returns (groups: list of GroupSpec, table: list of per-class results)."""
+         n_classes=4, reps=3, cache_path=None, device=0, log=None, rlist_rule="sqrt", mass=None,
+         tolerance=None):
+    """Returns (groups: list of GroupSpec, table: list of per-class results).
+
+    rlist_rule: "sqrt" scales the configured buffer with sqrt(nstlist /
+    nstlist0); "appendix" sizes it with the Appendix's drift bound (needs
+    mass; candidates whose list radius reaches half a box edge are skipped)."""
     import torch
     counts = np.asarray(counts, dtype=np.int64)
     boxes = np.asarray(boxes, dtype=np.float64).reshape(-1, 3)
@@ -84,8 +111,17 @@ def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nst
             cache = {}
     table = []
     choice = {}
+    if rlist_rule == "appendix":
+        if mass is None:
+            raise ValueError("the appendix rule needs particle masses")
+        pcls = particle_classes(q, types, mass)
+        vol = float(np.prod(boxes, axis=1).sum())
+        rlist_of = {nst: appendix_rlist(pcls, np.asarray(c6c12), vol, params, nst, tolerance=tolerance)
+                    for nst in NSTLISTS}
+    else:
+        rlist_of = {nst: scaled_rlist(params["rc"], rlist0, nstlist0, nst) for nst in NSTLISTS}
     for cls in _classes(counts, n_classes):
-        key = _key(gpu, counts[cls], boxes[cls], params, rlist0, nstlist0, nstprune, H)
+        key = _key(gpu, counts[cls], boxes[cls], params, rlist0, nstlist0, nstprune, H) + rlist_rule
         if key in cache:
             ent = cache[key]
             ent["cached"] = True
@@ -95,7 +131,9 @@ def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nst
                 for nst in NSTLISTS:
                     if H % nst:
                         continue
-                    spec = GroupSpec(C, nst, scaled_rlist(params["rc"], rlist0, nstlist0, nst), list(cls))
+                    if rlist_of[nst] >= 0.5 * float(boxes[cls].min()):
+                        continue                    # list radius too large for these boxes
+                    spec = GroupSpec(C, nst, rlist_of[nst], list(cls))
                     t = time_group(spec, counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params,
                                    nstprune, device, reps)
                     times[f"{C}/{nst}"] = t
@@ -112,6 +150,5 @@ def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nst
     if cache_path:
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
         json.dump(cache, open(cache_path, "w"), indent=1, sort_keys=True)
-    groups = [GroupSpec(C, nst, scaled_rlist(params["rc"], rlist0, nstlist0, nst), sorted(b))
-              for (C, nst), b in sorted(choice.items())]
+    groups = [GroupSpec(C, nst, rlist_of[nst], sorted(b)) for (C, nst), b in sorted(choice.items())]
     return groups, table
