@@ -109,30 +109,91 @@ def peaks():
     return p
 
 
-class ClockSampler:
-    """nvidia-smi clock/throttle samples while the timed region runs."""
+def device_uuid(dev):
+    """'GPU-...' UUID of a torch CUDA device (None if torch does not expose it)."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
 
+
+class ClockSampler:
+    """SM clock and clock-event-reason samples of this GPU while the timed
+    region runs: NVML (read-only queries through libnvidia-ml) every 2 ms in
+    a thread, else nvidia-smi every 200 ms."""
+
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap"}
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
+    def __init__(self, dev):
+        self.uuid = device_uuid(dev)
         self.proc = None
         self.path = None
+        self.thread = None
+        self.samples = []
+        self.nvml = None
+        self.handle = None
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                ok = self.uuid is not None and lib.nvmlDeviceGetHandleByUUID(self.uuid.encode(), ctypes.byref(h)) == 0
+                if ok:
+                    self.nvml, self.handle = lib, h
+        except Exception:
+            self.nvml = None
+
+    def _loop(self):
+        import ctypes
+        mhz = ctypes.c_uint()
+        reasons = ctypes.c_ulonglong()
+        getr = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop_flag:
+            if self.nvml.nvmlDeviceGetClockInfo(self.handle, 1, ctypes.byref(mhz)) == 0 and \
+                    getr(self.handle, ctypes.byref(reasons)) == 0:
+                self.samples.append((mhz.value, reasons.value))
+            time.sleep(0.002)
 
     def start(self):
+        if self.nvml is not None:
+            import threading
+            self.stop_flag = False
+            self.thread = threading.Thread(target=self._loop, daemon=True)
+            self.thread.start()
+            return
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
+            sel = [f"--id={self.uuid}"] if self.uuid else []
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"] + sel,
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.thread is not None:
+            import ctypes
+            self.stop_flag = True
+            self.thread.join(timeout=5)
+            mx = ctypes.c_uint()
+            smax = mx.value if self.nvml.nvmlDeviceGetMaxClockInfo(self.handle, 1, ctypes.byref(mx)) == 0 else None
+            reasons = set()
+            for _, r in self.samples:
+                for bit, name in self.REASONS.items():
+                    if r & bit:
+                        reasons.add(name)
+            out.update(sm_mhz=statistics.median([m for m, _ in self.samples]) if self.samples else None,
+                       sm_max_mhz=smax, reasons=sorted(reasons), samples=len(self.samples), source="nvml")
+            return out
         if self.proc is None:
             return out
         self.proc.terminate()
@@ -143,12 +204,8 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
+            if len(parts) >= 9:
                 rows.append(parts)
-            except Exception:
-                pass
         os.unlink(self.path)
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
@@ -159,7 +216,7 @@ class ClockSampler:
                 if r[5 + k].lower() == "active":
                     reasons.add(nm)
         out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
-                   reasons=sorted(reasons), samples=len(rows))
+                   reasons=sorted(reasons), samples=len(rows), source="nvidia-smi")
         return out
 
 
@@ -526,7 +583,7 @@ def run_ours(args):
 
     # timed region: graph replays, device time per step with CUDA events
     step_ms = []
-    sampler = ClockSampler(dev.index) if rank == 0 else None
+    sampler = ClockSampler(dev) if rank == 0 else None
     barrier()
     if sampler:
         sampler.start()
@@ -763,7 +820,7 @@ def run_batch(args):
     tuned.capture()
     for _ in range(args.warmup):
         tuned.replay()
-    sampler = ClockSampler(dev.index) if rank == 0 else None
+    sampler = ClockSampler(dev) if rank == 0 else None
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
