@@ -445,6 +445,32 @@ def compare_1x1(nb, ctx, box, p, x0, F, rlist, rprune, stream, reps=10, max_nbr=
             "cluster_pruned_over_1x1_speed": t_1x1 / t_pruned}
 
 
+def tabulated_ab(nb, ctx, p, x, F, stream, reps=20):
+    """The tabulated Ewald force factor against the fitted rational on the same
+    list and frame: force-kernel times (CUDA-event spans) and the largest
+    force difference relative to the RMS force."""
+    import numpy as np
+    import torch
+    out, forces = {}, {}
+    for mode in ("ewald", "ewald_tab"):
+        prm = nb.make_params(mode, p["rc"], beta=p["beta"], want_energy=False)
+        nb.nb_compute(ctx, prm, x, F, None, None, stream)
+        torch.cuda.synchronize()
+        forces[mode] = F.double().cpu().numpy()
+        nb.nb_profile(ctx, True)
+        nb.nb_profile_read(ctx)
+        for _ in range(reps):
+            nb.nb_compute(ctx, prm, None, F, None, None, stream)
+        out[mode] = statistics.mean(m for k, m in nb.nb_profile_read(ctx) if k == nb.NB_KERNEL_FORCE)
+        nb.nb_profile(ctx, False)
+    fa, ft = forces["ewald"], forces["ewald_tab"]
+    rms = float(np.sqrt((fa ** 2).sum(1).mean()))
+    return {"force_ms_fitted": out["ewald"], "force_ms_tabulated": out["ewald_tab"],
+            "tabulated_over_fitted_time": out["ewald_tab"] / out["ewald"],
+            "max_dF_over_rms_vs_fitted": float(np.sqrt(((ft - fa) ** 2).sum(1)).max() / rms),
+            "table": "2,048 intervals in (beta r)^2 on [0, 10], linear interpolation, shared memory"}
+
+
 def buffer_estimate(nb, box, p, nstlist, rlist, dt_ps=0.002, temperature=300.0):
     """The Appendix's drift bound for this workload's buffer and lifetime,
     and the buffer it asks for at the paper's 0.1 kB T/ns per particle."""
@@ -672,6 +698,7 @@ def run_ours(args):
         surr = surrogate_ab(nb, ctx, box, p, xs, F, stream, dev) if elec == "ewald" and args.surrogate else None
         cmp11 = compare_1x1(nb, ctx, box, p, xs[0], F, rlist, rprune, stream) if args.compare_1x1 else None
         buf = buffer_estimate(nb, box, p, nstlist, rlist) if elec == "ewald" else None
+        tab = tabulated_ab(nb, ctx, p, xs[0], F, stream) if elec == "ewald" else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1000 / args.steps,
@@ -697,6 +724,7 @@ def run_ours(args):
             "surrogate": surr,
             "particle_pair_1x1": cmp11,
             "buffer_estimate": buf,
+            "tabulated_ewald": tab,
             "gpu_launches": int(launches),
             "clocks": clocks,
             "status": nb.status_name(info0.status),

@@ -53,8 +53,12 @@ enum nb_status_code {
 enum nb_elec {
     NB_ELEC_RF = 0,    /* reaction field, g(r) = -2 k r (Sec. 3.2) */
     NB_ELEC_EWALD = 1, /* Ewald real space, g(r) = d/dr[erf(beta r)/r] (Sec. 3.2) */
-    NB_ELEC_EWALD_MLP = 2  /* Ewald real space with the force factor c(r) of unmasked pairs
+    NB_ELEC_EWALD_MLP = 2, /* Ewald real space with the force factor c(r) of unmasked pairs
                               taken from a trained network (nb_set_surrogate); forces only */
+    NB_ELEC_EWALD_TAB = 3  /* Ewald real space with the correction factor from a table in
+                              (beta r)^2 with linear interpolation (Sec. 3.2, tabulated
+                              kernels; 2,048 intervals on [0, 10], relative error 1.3e-6);
+                              forces only, 8-particle clusters, (beta rc)^2 <= 10 */
 };
 
 enum nb_comb {
@@ -227,9 +231,10 @@ nb_status nb_prune(nb_ctx* ctx, const float* xyz_dev, float r_prune, nb_stream s
  * With p->elec == NB_ELEC_EWALD_MLP (C = 8 contexts with a network set by
  * nb_set_surrogate), the Coulomb force of every unmasked pair inside rc with
  * r >= r_min is f qq c_net(r) / r^2, c_net evaluated per 8 x 8 tile on the
- * tensor cores; excluded pairs keep the analytic correction.  That mode
- * computes forces only: with want_energy set, the analytic Ewald kernel runs
- * instead (forces, energies and virial all analytic).
+ * tensor cores; excluded pairs keep the analytic correction.  That mode, and
+ * NB_ELEC_EWALD_TAB (the correction factor from a table), compute forces
+ * only: with want_energy set, the analytic Ewald kernel runs instead (forces,
+ * energies and virial all analytic).
  * Errors: NB_ERR_ARG, NB_ERR_BOX (rc >= L/2 or rc > rlist), NB_ERR_STATE (no
  * list; no network for NB_ELEC_EWALD_MLP), NB_ERR_CUDA. */
 nb_status nb_compute(nb_ctx* ctx, const nb_params* p, const float* xyz_dev, float* f_dev,

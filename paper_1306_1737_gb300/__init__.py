@@ -29,6 +29,7 @@ NB_ERR_COORD = 7
 NB_ELEC_RF = 0
 NB_ELEC_EWALD = 1
 NB_ELEC_EWALD_MLP = 2
+NB_ELEC_EWALD_TAB = 3
 NB_MLP_NPARAMS = 1153
 NB_COMB_LB = 0
 NB_COMB_GEOM = 1
@@ -255,8 +256,10 @@ def nb_prune(ctx, xyz, r_prune, stream=None):
 
 def make_params(elec: str, rc: float, eps_rf: float = float("inf"), beta: float = 0.0,
                 want_energy: bool = True) -> nb_params:
-    """elec: "rf", "ewald" or "ewald_mlp" (the network from nb_set_surrogate)."""
-    code = {"rf": NB_ELEC_RF, "ewald": NB_ELEC_EWALD, "ewald_mlp": NB_ELEC_EWALD_MLP}[elec]
+    """elec: "rf", "ewald", "ewald_mlp" (the network from nb_set_surrogate) or
+    "ewald_tab" (tabulated force factor)."""
+    code = {"rf": NB_ELEC_RF, "ewald": NB_ELEC_EWALD, "ewald_mlp": NB_ELEC_EWALD_MLP,
+            "ewald_tab": NB_ELEC_EWALD_TAB}[elec]
     return nb_params(code, int(bool(want_energy)), float(rc), float(eps_rf), float(beta))
 
 

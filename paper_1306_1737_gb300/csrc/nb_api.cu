@@ -233,6 +233,7 @@ static size_t carve(const nb_ctx* c, char* base, Workspace* ws) {
     w.work = (int*)take(sizeof(int) * 2);
     w.c6c12 = (float2*)take(sizeof(float2) * kMaxTypes * kMaxTypes);
     w.mlp = (MlpTC*)take(sizeof(MlpTC));
+    w.ewald_tab = (float2*)take(sizeof(float2) * kEwaldTabN);
     if (ws) *ws = w;
     return (off + 255) & ~(size_t)255;
 }
@@ -352,8 +353,12 @@ static void fill_info(const nb_ctx* c, int b0, int b1, nb_info* info, unsigned f
 // Kernel constants of an interaction setup (Sec. 3.2).
 static nb_status force_params(nb_ctx* c, const nb_params* p, ForceParams* fp) {
     *fp = ForceParams{};
-    // the surrogate kernel computes forces only; energy evaluations are analytic
-    fp->elec = (p->elec == NB_ELEC_EWALD_MLP && p->want_energy) ? NB_ELEC_EWALD : p->elec;
+    // the surrogate and tabulated kernels compute forces only; energy
+    // evaluations are analytic
+    const bool forces_only = p->elec == NB_ELEC_EWALD_MLP || p->elec == NB_ELEC_EWALD_TAB;
+    fp->elec = (forces_only && p->want_energy) ? NB_ELEC_EWALD : p->elec;
+    fp->tab_n = kEwaldTabN;
+    fp->tab_scale = (float)((double)p->beta * p->beta * kEwaldTabN / (double)kEwaldFitWMax);
     fp->mlp_rmin = c->mlp_rmin;
     fp->want_energy = p->want_energy ? 1 : 0;
     fp->rc2 = p->rc * p->rc;
@@ -370,8 +375,11 @@ static nb_status force_params(nb_ctx* c, const nb_params* p, ForceParams* fp) {
     fp->beta2 = (float)((double)p->beta * p->beta);
     fp->beta3 = (float)((double)p->beta * p->beta * p->beta);
     fp->use_fit = ((double)p->beta * p->beta * rc * rc <= (double)kEwaldFitWMax) ? 1 : 0;
-    if (fp->elec == NB_ELEC_EWALD_MLP && !fp->use_fit)
-        return fail(c, NB_ERR_ARG, "the surrogate kernel needs (beta rc)^2 <= %g", (double)kEwaldFitWMax);
+    if ((fp->elec == NB_ELEC_EWALD_MLP || fp->elec == NB_ELEC_EWALD_TAB) && !fp->use_fit)
+        return fail(c, NB_ERR_ARG, "the surrogate and tabulated kernels need (beta rc)^2 <= %g",
+                    (double)kEwaldFitWMax);
+    if (fp->elec == NB_ELEC_EWALD_TAB && c->C != 8)
+        return fail(c, NB_ERR_ARG, "the tabulated kernel needs 8-particle clusters");
     fp->ntypes = c->ntypes;
     fp->use_pruned = c->have_pruned ? 1 : 0;
     return NB_OK;
@@ -512,6 +520,8 @@ nb_status nb_set_workspace(nb_ctx* c, void* ws, size_t bytes) {
     const int nb = c->nbox;
     NB_CUDA(c, cudaMemset(c->ws.st, 0, sizeof(DevState) * nb));
     NB_CUDA(c, cudaMemset(c->ws.work, 0, sizeof(int) * 2));
+    NB_CUDA(c, launch_ewald_table(c->ws.ewald_tab, kEwaldTabN, (double)kEwaldFitWMax, 0));
+    NB_CUDA(c, cudaDeviceSynchronize());
     NB_CUDA(c, cudaMemset(c->ws.geo, 0, sizeof(BoxGeom) * nb));
     NB_CUDA(c, cudaMemcpy((void*)c->ws.lay.atom_off, c->atom_off.data(), sizeof(int) * (nb + 1),
                           cudaMemcpyHostToDevice));
@@ -647,7 +657,8 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     if (!c) return NB_ERR_ARG;
     if (!p || (!f && c->n > 0)) return fail(c, NB_ERR_ARG, "compute: null argument");
     if (!c->have_list) return fail(c, NB_ERR_STATE, "nb_pairlist_build first");
-    if (p->elec != NB_ELEC_RF && p->elec != NB_ELEC_EWALD && p->elec != NB_ELEC_EWALD_MLP)
+    if (p->elec != NB_ELEC_RF && p->elec != NB_ELEC_EWALD && p->elec != NB_ELEC_EWALD_MLP &&
+        p->elec != NB_ELEC_EWALD_TAB)
         return fail(c, NB_ERR_ARG, "unknown electrostatics");
     if (p->elec == NB_ELEC_EWALD_MLP) {
         if (!c->have_mlp) return fail(c, NB_ERR_STATE, "no network: call nb_set_surrogate first");

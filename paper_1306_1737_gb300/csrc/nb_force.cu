@@ -43,6 +43,7 @@ struct ForceArgs {
     const BoxGeom* geo;
     Accum* acc;
     const MlpTC* mlp;
+    const float2* ewald_tab;          // tabulated Ewald force factor
     const int* ient_used;             // compact i-entry index per box
     int* work;                        // work counter (next i-entry to take)
     int nbox;
@@ -166,10 +167,19 @@ __device__ __forceinline__ void pair_deltas(const WarpSmem& W, int k, int ih, fl
 // distances; scalar arithmetic wherever a parameter enters (constant
 // operands need no registers), packed only where both operands are pairs.
 // FULL: every pair inside rc is a full interaction (all-ones mask, no diagonal).
+// The Ewald force factor G(w), w = (beta r)^2, from the table in shared
+// memory: entry k = {G(k h), G((k+1) h) - G(k h)}, h = w_max / n, linear
+// interpolation (Sec. 3.2: the tabulated kernels).  t = r^2 beta^2 / h.
+__device__ __forceinline__ float ewald_tab_g(const float2* tab, int n, float t) {
+    const int i = min((int)t, n - 1);
+    const float2 v = tab[i];
+    return fmaf(t - (float)i, v.y, v.x);
+}
+
 template <int ELEC, bool ENERGY, bool FIT, bool FULL>
 __device__ __forceinline__ float2 pair_force2(const ForceParams& P, float2 r2, bool inc0, bool inc1,
                                               bool u0, bool u1, float qq0, float qq1, float2 lj0,
-                                              float2 lj1, float& e_lj, float& e_c) {
+                                              float2 lj1, float& e_lj, float& e_c, const float2* s_tab) {
     const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
     const float2 rinv2 = mul2(rinv, rinv);
     float2 rinv3 = mul2(rinv, rinv2);
@@ -186,6 +196,9 @@ __device__ __forceinline__ float2 pair_force2(const ForceParams& P, float2 r2, b
     if (ELEC == NB_ELEC_RF) {
         fc0 = qq0 * (rinv3.x - P.two_k_rf);
         fc1 = qq1 * (rinv3.y - P.two_k_rf);
+    } else if (ELEC == NB_ELEC_EWALD_TAB) {
+        fc0 = qq0 * fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.x * P.tab_scale), rinv3.x);
+        fc1 = qq1 * fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.y * P.tab_scale), rinv3.y);
     } else if (FIT) {
         fc0 = qq0 * fmaf(-P.beta3, ewald_fit_g(P.beta2 * r2.x), rinv3.x);
         fc1 = qq1 * fmaf(-P.beta3, ewald_fit_g(P.beta2 * r2.y), rinv3.y);
@@ -260,7 +273,8 @@ __device__ __forceinline__ bool icluster8(const ForceParams& P, const float2* s_
     const int2 rw = W.row[k][L.ih];
     const float2 lj0 = s_lj[rw.x + tj], lj1 = s_lj[rw.y + tj];
     const float2 fs = pair_force2<ELEC, ENERGY, FIT, FULL>(P, r2, inc0, inc1, u0, u1, fq.x * xj.w,
-                                                           fq.y * xj.w, lj0, lj1, e_lj, e_c);
+                                                           fq.y * xj.w, lj0, lj1, e_lj, e_c,
+                                                           s_lj + P.ntypes * P.ntypes);
     if (ENERGY) n_inc += (unsigned)inc0 + (unsigned)inc1;
     const float2 px = mul2(fs, dx), py = mul2(fs, dy), pz = mul2(fs, dz);
     fx = add2(fx, px);
@@ -439,6 +453,10 @@ k_force8(ForceArgs A) {
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
         const float2 v = A.c6c12[k];
         s_lj[k] = make_float2(-6.0f * v.x, 12.0f * v.y);
+    }
+    if constexpr (ELEC == NB_ELEC_EWALD_TAB) {
+        // the force-factor table follows the LJ table
+        for (int k = threadIdx.x; k < A.p.tab_n; k += blockDim.x) s_lj[nt2 + k] = A.ewald_tab[k];
     }
     const MlpTC* M = nullptr;
     float* mo = nullptr;
@@ -675,6 +693,30 @@ static cudaError_t launch_force_e(const ForceArgs& A, int C, int n_sm, cudaStrea
     return launch_force_t<ELEC, ENERGY, false>(A, C, n_sm, s);
 }
 
+// The tabulated force factor G(w) = (erf(x) - 2x/sqrt(pi) exp(-x^2)) / x^3,
+// x = sqrt(w), on w = k w_max / n (FP64, series near w = 0), stored as
+// {G_k, G_{k+1} - G_k}.
+__global__ void k_ewald_table(float2* tab, int n, double wmax) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double g[2];
+        for (int d = 0; d < 2; ++d) {
+            const double w = (k + d) * wmax / n;
+            if (w < 1e-6) {
+                g[d] = 4.0 / (3.0 * sqrt(M_PI)) * (1.0 - 0.6 * w + 3.0 / 14.0 * w * w);
+            } else {
+                const double x = sqrt(w);
+                g[d] = (erf(x) - 2.0 * x / sqrt(M_PI) * exp(-w)) / (w * x);
+            }
+        }
+        tab[k] = make_float2((float)g[0], (float)(g[1] - g[0]));
+    }
+}
+
+cudaError_t launch_ewald_table(float2* tab, int n, double wmax, cudaStream_t s) {
+    k_ewald_table<<<(n + 255) / 256, 256, 0, s>>>(tab, n, wmax);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n_sm, cudaStream_t s) {
     ForceArgs A;
     A.ient = p.use_pruned ? ws.ient_p : ws.ient;
@@ -693,6 +735,7 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
     A.mlp = ws.mlp;
     A.nbox = ws.nbox;
     A.ient_used = ws.ient_used;
+    A.ewald_tab = ws.ewald_tab;
     A.work = ws.work;
     A.p = p;
     // the accumulators hold energies, pair counts and shift forces, which
@@ -701,6 +744,23 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
     if (p.want_energy) {
         e = cudaMemsetAsync(ws.acc, 0, sizeof(Accum) * ws.nbox, s);
         if (e != cudaSuccess) return e;
+    }
+    if (p.elec == NB_ELEC_EWALD_TAB) {
+        // forces only, 8-particle clusters (checked by the caller)
+        auto kern = k_force8<NB_ELEC_EWALD_TAB, false, true>;
+        const size_t smem = sizeof(float2) * (A.p.ntypes * A.p.ntypes + A.p.tab_n);
+        static bool attr_set = false;
+        if (!attr_set) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kForceWarps, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        kern<<<n_sm * per_sm, 32 * kForceWarps, smem, s>>>(A);
+        return cudaGetLastError();
     }
     if (p.elec == NB_ELEC_EWALD_MLP) {
         // forces only, 8-particle clusters (checked by the caller)

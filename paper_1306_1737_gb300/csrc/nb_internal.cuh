@@ -132,7 +132,11 @@ struct Workspace {
     float2* c6c12;
     // the Ewald-factor network in tensor-core form (nb_set_surrogate)
     MlpTC* mlp;
+    // the tabulated Ewald force factor [kEwaldTabN] (built with the workspace)
+    float2* ewald_tab;
 };
+
+constexpr int kEwaldTabN = 2048;   // table intervals on w = (beta r)^2 in [0, kEwaldFitWMax]
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_grid(const Workspace& ws, int C, int ntypes, const float* xyz, cudaStream_t s);
@@ -153,11 +157,14 @@ struct ForceParams {
     float beta2, beta3;   // beta^2, beta^3 for the fitted correction
     int use_fit;          // (beta rc)^2 within the fitted range
     float mlp_rmin;       // network input range starts here (surrogate kernel)
+    float tab_scale;      // beta^2 n / w_max: r^2 to table coordinate (tabulated kernel)
+    int tab_n;            // table intervals
     int ntypes;
     int use_pruned;
 };
 
 cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n_sm, cudaStream_t s);
+cudaError_t launch_ewald_table(float2* tab, int n, double wmax, cudaStream_t s);
 cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int C, float* f_out, double* e_out,
                             double* vir_out, cudaStream_t s);
 

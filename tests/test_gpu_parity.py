@@ -320,3 +320,29 @@ def test_pair_1x1_list_and_forces(gp, cfg, request):
         assert emax < FORCE_TOL, (emax, erms)
     finally:
         gb.close()
+
+
+def test_tabulated_ewald_forces(gp, cfg2):
+    """The tabulated force factor (linear interpolation in (beta r)^2) gives
+    forces within 1e-4 of the RMS force of the oracle on the 24,000-atom box,
+    before and after a prune."""
+    import paper_1306_1737_gb300 as nb
+    b, p = cfg2
+    gb = gp.GpuBox(b, p["rlist"])
+    try:
+        gb.grid()
+        gb.build(float(np.float32(p["rlist"])))
+        prm = nb.make_params("ewald_tab", p["rc"], beta=p["beta"], want_energy=False)
+        oprm = oracle.make_params("ewald", float(np.float32(p["rc"])), beta=p["beta"])
+        f, _, _ = gb.compute(prm)
+        fo, _, _ = oracle.forces_cells(b.xyz, b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx, b.box, oprm)
+        emax, erms, _ = gp.force_errors(f, fo)
+        assert emax < FORCE_TOL, (emax, erms)
+        x5 = list(w.frame_walk(b.xyz, b.mass, 6, seed=2400))[5]
+        gb.prune(float(np.float32(w.prune_radius(p["rc"], p["rlist"], 5))), x5)
+        f5, _, _ = gb.compute(prm)
+        fo5, _, _ = oracle.forces_cells(x5, b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx, b.box, oprm)
+        emax, erms, _ = gp.force_errors(f5, fo5)
+        assert emax < FORCE_TOL, (emax, erms)
+    finally:
+        gb.close()
