@@ -137,6 +137,130 @@ __global__ void __launch_bounds__(32 * kPruneWarps) k_prune(PruneArgs A) {
     }
 }
 
+// 16-byte asynchronous global -> shared copy (cp.async, bypassing registers).
+__device__ __forceinline__ void copy16_async(void* smem, const void* gmem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void copy_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// The 8-particle form: lane (ih, j) = (lane / 8, lane % 8) tests pairs
+// (ih, j) and (ih + 4, j) of every i-cluster, as in the force kernel.  The
+// lane's shifted i-particles stay in registers for the whole entry; the
+// j-particles of a chunk of 32 j-entries (8 x 32 float4) are copied to shared
+// memory with all copies in flight at once, so a chunk waits for one L2 round
+// trip instead of one per j-entry.
+template <int S>
+__global__ void __launch_bounds__(32 * kPruneWarps) k_prune8(PruneArgs A) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int j = lane & 7, ih = lane >> 3;
+    const bool lower0 = j <= ih, lower1 = j <= ih + 4;
+    __shared__ float4 s_xj[kPruneWarps][32][8];
+    const Workspace& W = A.ws;
+    int b = 0;
+    unsigned long long kept_total = 0, keys_total = 0;
+    int b_acc = -1;
+    const int n_used = W.ient_used[W.nbox];
+    const int n_warps = gridDim.x * kPruneWarps;
+    const bool dynamic = n_used > 8 * n_warps;
+    int c_next = 0;
+    for (int c = blockIdx.x * kPruneWarps + wib; c < n_used; c = __shfl_sync(full, c_next, 0)) {
+        if (lane == 0) c_next = dynamic ? n_warps + atomicAdd(&W.work[1], 1) : c + n_warps;
+        const int e = ient_of(W.ient_used, W.lay.ient_off, W.nbox, c, b);
+        if (b != b_acc) {
+            if (lane == 0 && b_acc >= 0 && kept_total) {
+                atomicAdd(&W.st[b_acc].n_jent_pruned, kept_total);
+                atomicAdd(&W.st[b_acc].n_keys_pruned, keys_total);
+            }
+            kept_total = keys_total = 0;
+            b_acc = b;
+        }
+        const int4 ie = W.ient[e];
+        const int q = ie.x, s = ie.y, jb = ie.z, je = ie.w;
+        const int2 info = W.sc_info[q];
+        const int g0 = info.x;
+        float sh[3];
+        shift_vector(s, W.geo[b].L, sh);
+        // shifted i-particles (ih) and (ih + 4) of each i-cluster: hi + lo
+        float h0[S][3], l0[S][3], h1[S][3], l1[S][3];
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            const int kk = k < info.y ? k : 0;
+            const float4 a = W.xyzq[(g0 + kk) * 8 + ih], a1 = W.xyzq[(g0 + kk) * 8 + ih + 4];
+            two_sum(a.x, sh[0], h0[k][0], l0[k][0]);
+            two_sum(a.y, sh[1], h0[k][1], l0[k][1]);
+            two_sum(a.z, sh[2], h0[k][2], l0[k][2]);
+            two_sum(a1.x, sh[0], h1[k][0], l1[k][0]);
+            two_sum(a1.y, sh[1], h1[k][1], l1[k][1]);
+            two_sum(a1.z, sh[2], h1[k][2], l1[k][2]);
+        }
+        const bool center = s == kShiftCenter;
+        int kept = 0;
+        for (int base = jb; base < je; base += 32) {
+            const int nt = min(32, je - base);
+            int my_w = 0;
+            if (lane < nt) my_w = W.cj[base + lane];
+            // copy r covers j-entry t = 4 r + ih, particle j (8 lanes read
+            // one cluster's 128 contiguous bytes)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int t = 4 * r + ih;
+                const int wt = __shfl_sync(full, my_w, t);
+                if (t < nt) copy16_async(&s_xj[wib][t][j], W.xyzq + (wt & kCjMask) * 8 + j);
+            }
+            copy_async_wait_all();
+            __syncwarp();
+            unsigned my_keep = 0;
+            for (int t = 0; t < nt; ++t) {
+                const int w = __shfl_sync(full, my_w, t);
+                const float4 xj = s_xj[wib][t][j];
+                const int cjt = w & kCjMask;
+                const unsigned bits = (unsigned)w >> kSuperShift;
+                unsigned keep = 0;
+#pragma unroll
+                for (int k = 0; k < S; ++k) {
+                    if ((bits >> k) & 1u) {
+                        const bool diag = center && (cjt == g0 + k);
+                        const float dx0 = (h0[k][0] - xj.x) + l0[k][0], dx1 = (h1[k][0] - xj.x) + l1[k][0];
+                        const float dy0 = (h0[k][1] - xj.y) + l0[k][1], dy1 = (h1[k][1] - xj.y) + l1[k][1];
+                        const float dz0 = (h0[k][2] - xj.z) + l0[k][2], dz1 = (h1[k][2] - xj.z) + l1[k][2];
+                        const float r20 = fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0));
+                        const float r21 = fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1));
+                        const bool hit = (r20 < A.rp2 && !(diag && lower0)) || (r21 < A.rp2 && !(diag && lower1));
+                        if (__any_sync(full, hit)) keep |= 1u << k;
+                    }
+                }
+                if (lane == t) my_keep = keep;
+            }
+            __syncwarp();   // s_xj is rewritten by the next chunk
+            const unsigned kb = __ballot_sync(full, my_keep != 0);
+            const int pos = __popc(kb & ((1u << lane) - 1u));
+            if (my_keep) {
+                const long long o = jb + kept + pos;
+                W.cj_p[o] = (my_w & kCjMask) | (int)(my_keep << kSuperShift);
+#pragma unroll
+                for (int k = 0; k < S; ++k)
+                    W.mask_p[k * W.jstride + o] = ((my_keep >> k) & 1u) ? W.mask[k * W.jstride + base + lane] : 0ull;
+            }
+            kept += __popc(kb);
+            unsigned nk = __popc(my_keep);
+            for (int o = 16; o > 0; o >>= 1) nk += __shfl_xor_sync(full, nk, o);
+            keys_total += nk;
+        }
+        if (lane == 0) W.ient_p[e] = make_int4(q, s, jb, jb + kept);
+        kept_total += kept;
+        __syncwarp();
+    }
+    if (lane == 0 && b_acc >= 0 && kept_total) {
+        atomicAdd(&W.st[b_acc].n_jent_pruned, kept_total);
+        atomicAdd(&W.st[b_acc].n_keys_pruned, keys_total);
+    }
+}
+
 // Zero every box's pruned counters.
 __global__ void k_prune_reset(Workspace ws) {
     if (threadIdx.x == 0) ws.work[1] = 0;
@@ -153,7 +277,7 @@ cudaError_t launch_prune(const Workspace& ws, int C, float r_prune, int n_sm, cu
     k_prune_reset<<<1, 256, 0, s>>>(ws);
     const int blocks = n_sm * 16;
     if (C == 8)
-        k_prune<8, super_size(8)><<<blocks, 32 * kPruneWarps, 0, s>>>(A);
+        k_prune8<super_size(8)><<<blocks, 32 * kPruneWarps, 0, s>>>(A);
     else
         k_prune<4, super_size(4)><<<blocks, 32 * kPruneWarps, 0, s>>>(A);
     return cudaGetLastError();
