@@ -17,6 +17,7 @@ Functions (each follows the paper passage cited in ``oracle.c``):
   mlp_forward    -- the 1-32-32-1 SiLU network that may stand in for c(r)
   mlp_loss_grad  -- its weighted squared-error loss and parameter gradient
   buffer_drift_integral -- the Appendix's Verlet-buffer drift integral, by quadrature
+  rdf            -- pair-distance histogram (pair correlation; Sec. 1, Sec. 2.3)
 """
 from __future__ import annotations
 
@@ -107,6 +108,8 @@ def lib():
             L.or_mlp_loss_grad.restype = C.c_double
             L.or_buffer_drift_integral.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
             L.or_buffer_drift_integral.restype = C.c_double
+            L.or_rdf.argtypes = [C.c_int, P, P, P, P, P, C.c_double, C.c_int, C.c_int, C.c_int, C.c_double,
+                                 C.c_int, P, P]
             _lib = L
     return _lib
 
@@ -391,3 +394,25 @@ def buffer_drift_integral(v1: float, v2: float, rb: float, sigma: float) -> floa
     """The Appendix's double integral of [V'(rc)(rt - rc) + V''(rc)(rt - rc)^2/2]
     over rt < rc, r0 > rc + rb with a Gaussian of width sigma in rt - r0."""
     return float(lib().or_buffer_drift_integral(float(v1), float(v2), float(rb), float(sigma)))
+
+
+def rdf(xyz, types, box, r_max: float, nbins: int, excl_off=None, excl_idx=None, type_a: int = -1,
+        type_b: int = -1, delta: float = 0.0, brute: bool = False):
+    """(hist int64 [nbins], near int64 [nbins + 1]): counts of selected
+    unordered pairs per distance bin of width r_max / nbins (FP64 minimum-image
+    distances of the FP32 coordinates), and per bin edge the selected pairs
+    within delta of it.  Force-field-excluded pairs are not counted."""
+    xyz = _f32(xyz).astype(np.float64).reshape(-1, 3)
+    t = _i32(types)
+    box64 = _f32(box).astype(np.float64)
+    eo = None if excl_off is None else _i32(excl_off)
+    ei = None if excl_idx is None else _i32(excl_idx)
+    if ei is not None and ei.size == 0:
+        ei = np.zeros(1, np.int32)
+    hist = np.zeros(int(nbins), np.int64)
+    near = np.zeros(int(nbins) + 1, np.int64)
+    rc = lib().or_rdf(xyz.shape[0], _p(xyz), _p(t), _p(eo), _p(ei), _p(box64), float(r_max), int(nbins),
+                      int(type_a), int(type_b), float(delta), 1 if brute else 0, _p(hist), _p(near))
+    if rc != 0:
+        raise ValueError("rdf: r_max + delta must be below half the box, nbins >= 1, delta < dr / 2")
+    return hist, near

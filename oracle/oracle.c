@@ -935,3 +935,130 @@ double or_buffer_drift_integral(double V1, double V2, double rb, double sigma) {
     }
     return sum * h * h / (sigma * sqrt(2.0 * M_PI));
 }
+
+/* ------------------------------------------------------------------------ */
+/* Pair-distance histogram: the pair correlation function, the analysis the
+ * paper lists beside force calculation as limited-range pair work (Sec. 1)
+ * and for which it advises a list rebuilt every time and no cut-off
+ * conditional in the kernel (Sec. 2.3).
+ *
+ * Every unordered pair {i, j} of distinct particles that is not force-field
+ * excluded, whose types match the selection (type_a < 0: every pair; else
+ * {type_i, type_j} = {type_a, type_b}) and whose minimum-image FP64 distance
+ * r is below r_max adds one to bin floor(r / dr), dr = r_max / nbins.
+ * near[k] (k = 0..nbins) counts the selected pairs with |r - k dr| < delta,
+ * the pairs whose bin a computation of r in lower precision may put on the
+ * other side of edge k (near[nbins] includes pairs just beyond r_max).
+ * brute != 0: the O(n^2) double loop; else a cell list (cells of edge >=
+ * r_max + delta, each distinct neighbouring cell visited once, a pair counted
+ * from its lower index).
+ * Returns 0, or -1 when r_max + delta >= L/2, nbins < 1 or delta >= dr/2.
+ * Parity: pinned by a cubic lattice's exact shell counts and by brute force. */
+static int rdf_selected(const int* type, int type_a, int type_b, int i, int j) {
+    if (type_a < 0) return 1;
+    return (type[i] == type_a && type[j] == type_b) || (type[i] == type_b && type[j] == type_a);
+}
+
+static void rdf_add(double r2, double r_max, double dr, double delta, int nbins, int64_t* hist,
+                    int64_t* near) {
+    const double r = sqrt(r2);
+    if (r < r_max) {
+        int k = (int)floor(r / dr);
+        if (k > nbins - 1) k = nbins - 1;
+        hist[k]++;
+    }
+    const int e = (int)nearbyint(r / dr);
+    if (e >= 0 && e <= nbins && fabs(r - e * dr) < delta) near[e]++;
+}
+
+int or_rdf(int n, const double* xyz, const int* type, const int* excl_off, const int* excl_idx,
+           const double* box, double r_max, int nbins, int type_a, int type_b, double delta, int brute,
+           int64_t* hist, int64_t* near) {
+    const double L[3] = {box[0], box[1], box[2]};
+    const double dr = r_max / nbins;
+    const double rr = r_max + delta;
+    if (nbins < 1 || !(r_max > 0.0) || !(delta >= 0.0) || !(delta < 0.5 * dr)) return -1;
+    for (int k = 0; k < 3; ++k)
+        if (!(rr < 0.5 * L[k])) return -1;
+    memset(hist, 0, sizeof(int64_t) * (size_t)nbins);
+    memset(near, 0, sizeof(int64_t) * (size_t)(nbins + 1));
+    if (brute) {
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : hist[:nbins], near[:nbins + 1])
+        for (int i = 0; i < n; ++i) {
+            const double xi[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
+            for (int j = i + 1; j < n; ++j) {
+                if (!rdf_selected(type, type_a, type_b, i, j) || is_excluded(excl_off, excl_idx, i, j)) continue;
+                const double xj[3] = {xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2]};
+                double d[3];
+                min_image(L, xi, xj, d);
+                const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (r2 < rr * rr) rdf_add(r2, r_max, dr, delta, nbins, hist, near);
+            }
+        }
+        return 0;
+    }
+    int nc[3];
+    for (int k = 0; k < 3; ++k) {
+        nc[k] = (int)floor(L[k] / rr);
+        if (nc[k] < 1) nc[k] = 1;
+    }
+    const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    int* cell_of = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    int64_t* start = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+    int* members = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        int c[3];
+        for (int k = 0; k < 3; ++k) {
+            const double x = xyz[3 * i + k] - L[k] * floor(xyz[3 * i + k] / L[k]);
+            int v = (int)(x / L[k] * nc[k]);
+            if (v < 0) v = 0;
+            if (v >= nc[k]) v = nc[k] - 1;
+            c[k] = v;
+        }
+        cell_of[i] = (c[0] * nc[1] + c[1]) * nc[2] + c[2];
+        start[cell_of[i] + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+    {
+        int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ncell > 0 ? ncell : 1));
+        memcpy(fill, start, sizeof(int64_t) * (size_t)ncell);
+        for (int i = 0; i < n; ++i) members[fill[cell_of[i]]++] = i;
+        free(fill);
+    }
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : hist[:nbins], near[:nbins + 1])
+    for (int i = 0; i < n; ++i) {
+        const int ci = cell_of[i];
+        const int cc[3] = {ci / (nc[2] * nc[1]), (ci / nc[2]) % nc[1], ci % nc[2]};
+        int nb[3][3], nn[3];
+        for (int k = 0; k < 3; ++k) {
+            nn[k] = 0;
+            for (int o = -1; o <= 1; ++o) {
+                const int v = ((cc[k] + o) % nc[k] + nc[k]) % nc[k];
+                int seen = 0;
+                for (int m = 0; m < nn[k]; ++m) seen |= (nb[k][m] == v);
+                if (!seen) nb[k][nn[k]++] = v;
+            }
+        }
+        const double xi[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
+        for (int a = 0; a < nn[0]; ++a)
+            for (int b = 0; b < nn[1]; ++b)
+                for (int c = 0; c < nn[2]; ++c) {
+                    const int64_t cell = ((int64_t)nb[0][a] * nc[1] + nb[1][b]) * nc[2] + nb[2][c];
+                    for (int64_t m = start[cell]; m < start[cell + 1]; ++m) {
+                        const int j = members[m];
+                        if (j <= i) continue;
+                        if (!rdf_selected(type, type_a, type_b, i, j) || is_excluded(excl_off, excl_idx, i, j))
+                            continue;
+                        const double xj[3] = {xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2]};
+                        double d[3];
+                        min_image(L, xi, xj, d);
+                        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (r2 < rr * rr) rdf_add(r2, r_max, dr, delta, nbins, hist, near);
+                    }
+                }
+    }
+    free(cell_of);
+    free(start);
+    free(members);
+    return 0;
+}
