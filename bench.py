@@ -471,6 +471,54 @@ def tabulated_ab(nb, ctx, p, x, F, stream, reps=20):
             "table": "2,048 intervals in (beta r)^2 on [0, 10], linear interpolation, shared memory"}
 
 
+def pair_correlation(nb, ctx, box, x0, eo, ei, stream, rbb, r_max=1.0, nbins=400, reps=10):
+    """The pair correlation analysis (Sec. 1, Sec. 2.3): per frame a fresh
+    list at r_max (gridding + search, no pruning) and the histogram kernel
+    with no cut-off conditional; device times from CUDA-event spans, the O-O
+    g(r) first peak as a sanity figure."""
+    import numpy as np
+    import torch
+    dev = x0.device
+    nbox = 1
+    h = torch.zeros((nbox, nbins + 1), dtype=torch.int64, device=dev)
+    rl = float(np.float32(r_max))
+
+    def frame(sel=(-1, -1)):
+        nb.nb_grid_put(ctx, x0, box.box, stream)
+        nb.nb_pairlist_build(ctx, rl, min(rbb, rl), eo, ei, stream)
+        nb.nb_rdf(ctx, rl, nbins, sel[0], sel[1], 0, h, stream)
+
+    frame()
+    torch.cuda.synchronize()
+    nb.nb_profile(ctx, True)
+    nb.nb_profile_read(ctx)
+    for _ in range(reps):
+        frame()
+    spans = nb.nb_profile_read(ctx)
+    nb.nb_profile(ctx, False)
+    ms = {k: statistics.mean(m for kind, m in spans if kind == v) for k, v in
+          (("grid", nb.NB_KERNEL_GRID), ("search", nb.NB_KERNEL_SEARCH), ("rdf", nb.NB_KERNEL_RDF))}
+    counts = h[0].cpu().numpy()
+    info = nb.nb_check(ctx, stream)
+    frame((0, 0))
+    oo = h[0].cpu().numpy()[:nbins].astype(np.float64)
+    n_o = int((box.types == 0).sum())
+    dr = r_max / nbins
+    shell = 4.0 * np.pi / 3.0 * dr ** 3 * ((np.arange(nbins) + 1) ** 3 - np.arange(nbins) ** 3)
+    g_oo = oo * float(np.prod(box.box)) / (0.5 * n_o * (n_o - 1) * shell)
+    binned = int(counts.sum())
+    within = int(counts[:nbins].sum())
+    frame_ms = ms["grid"] + ms["search"] + ms["rdf"]
+    return {"r_max_nm": r_max, "nbins": nbins, "rbb_nm": min(rbb, rl),
+            "list": "rebuilt every frame at r_max, no pruning; histogram kernel without a cut-off test",
+            "kernel_ms": ms, "frame_ms": frame_ms,
+            "listed_pairs_binned": binned, "pairs_within_r_max": within,
+            "listed_pairs_per_s_rdf_kernel": binned / (ms["rdf"] * 1e-3),
+            "pairs_within_r_max_per_s_frame": within / (frame_ms * 1e-3),
+            "cluster_pairs": int(info.n_cluster_pairs),
+            "oo_first_peak_nm": float((np.argmax(g_oo) + 0.5) * dr), "oo_first_peak_g": float(g_oo.max())}
+
+
 def buffer_estimate(nb, box, p, nstlist, rlist, dt_ps=0.002, temperature=300.0):
     """The Appendix's drift bound for this workload's buffer and lifetime,
     and the buffer it asks for at the paper's 0.1 kB T/ns per particle."""
@@ -699,6 +747,7 @@ def run_ours(args):
         cmp11 = compare_1x1(nb, ctx, box, p, xs[0], F, rlist, rprune, stream) if args.compare_1x1 else None
         buf = buffer_estimate(nb, box, p, nstlist, rlist) if elec == "ewald" else None
         tab = tabulated_ab(nb, ctx, p, xs[0], F, stream) if elec == "ewald" else None
+        pcf = pair_correlation(nb, ctx, box, xs[0], eo, ei, stream, rbb) if args.pair_correlation else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1000 / args.steps,
@@ -725,6 +774,7 @@ def run_ours(args):
             "particle_pair_1x1": cmp11,
             "buffer_estimate": buf,
             "tabulated_ewald": tab,
+            "pair_correlation": pcf,
             "gpu_launches": int(launches),
             "clocks": clocks,
             "status": nb.status_name(info0.status),
@@ -981,6 +1031,8 @@ def main():
                     help="batch tuner: list radius per lifetime by sqrt scaling or by the Appendix drift bound")
     ap.add_argument("--no-1x1", dest="compare_1x1", action="store_false",
                     help="skip the particle-pair (1 x 1) kernel comparison")
+    ap.add_argument("--no-rdf", dest="pair_correlation", action="store_false",
+                    help="skip the pair correlation (g(r) histogram) measurement")
     ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",
                     help="skip the learned Ewald factor A/B (Ewald workloads)")
     ap.add_argument("--workload", default="water24k",

@@ -108,7 +108,8 @@ enum nb_kernel_kind {
     NB_KERNEL_SEARCH = 1,  /* nb_pairlist_build's search kernel */
     NB_KERNEL_PRUNE = 2,   /* nb_prune's prune kernel */
     NB_KERNEL_FORCE = 3,   /* nb_compute's force/energy kernel */
-    NB_KERNEL_FORCE_1X1 = 4 /* nb_compute_1x1's particle-pair force kernel */
+    NB_KERNEL_FORCE_1X1 = 4, /* nb_compute_1x1's particle-pair force kernel */
+    NB_KERNEL_RDF = 5       /* nb_rdf's pair-distance histogram kernel */
 };
 
 /* --- context ------------------------------------------------------------ */
@@ -347,6 +348,36 @@ nb_status nb_pairlist_1x1(nb_ctx* ctx, float rlist, int max_nbr, int* nbr_dev, i
  * Errors: NB_ERR_ARG, NB_ERR_STATE, NB_ERR_BOX, NB_ERR_CUDA. */
 nb_status nb_compute_1x1(nb_ctx* ctx, const nb_params* p, const float* xyz_dev, const int* nbr_dev,
                          const int* count_dev, int max_nbr, float* f_dev, nb_stream stream);
+
+/* --- pair-distance histogram (pair correlation) ------------------------------ */
+
+#define NB_RDF_MAX_BINS 2048
+
+/* Histogram of particle-pair distances over the current outer cluster-pair
+ * list: the pair correlation analysis that the paper names as limited-range
+ * pair work (Sec. 1) and for which it rebuilds the list for every evaluation
+ * and uses neither pruning nor a cut-off conditional in the kernel (Sec. 2.3).
+ * Every listed pair whose mask bit is set (distinct real particles, not
+ * force-field excluded; each pair once) and whose types match the selection
+ * (type_a = type_b = -1: every pair; else {type_i, type_j} = {type_a, type_b})
+ * adds one to bin min(int(r / dr), nbins) of its box, dr = r_max / nbins, r
+ * from the FP32 distance vector (periodic shift as hi + lo): bins
+ * 0 .. nbins - 1 cover [0, r_max), bin nbins counts the listed pairs at
+ * r >= r_max.  hist_dev: uint64 [nbox][nbins + 1], device memory, zeroed
+ * first unless accumulate != 0 (to sum several frames).  The list must come
+ * from nb_pairlist_build on the current coordinates (no nb_set_coords,
+ * nb_prune or nb_compute with new coordinates since) with rlist >= r_max, so
+ * that it holds every pair closer than r_max.  For N_a and N_b particles of
+ * the selected types in volume V, g(r) in bin k is h_k V / (P dV_k) with
+ * dV_k = 4 pi / 3 ((k + 1)^3 - k^3) dr^3 and P = N_a N_b pairs (P =
+ * N_a (N_a - 1) / 2 for one type or every pair) less the force-field-excluded
+ * pairs among them.
+ * Errors: NB_ERR_ARG (nbins outside 1 .. NB_RDF_MAX_BINS, r_max <= 0, a type
+ * outside -1 .. ntypes - 1 or only one of them -1, null hist_dev),
+ * NB_ERR_STATE (no list, or coordinates changed since it was built),
+ * NB_ERR_BOX (r_max above the list radius), NB_ERR_CUDA. */
+nb_status nb_rdf(nb_ctx* ctx, float r_max, int nbins, int type_a, int type_b, int accumulate,
+                 uint64_t* hist_dev, nb_stream stream);
 
 /* --- learned Ewald force factor --------------------------------------------- */
 

@@ -39,6 +39,8 @@ NB_KERNEL_SEARCH = 1
 NB_KERNEL_PRUNE = 2
 NB_KERNEL_FORCE = 3
 NB_KERNEL_FORCE_1X1 = 4
+NB_KERNEL_RDF = 5
+NB_RDF_MAX_BINS = 2048
 
 _lock = threading.Lock()
 _lib = None
@@ -124,6 +126,7 @@ def load():
             "nb_buffer_size": ([i, P, i, P, C.c_double, C.POINTER(nb_params), C.c_double, C.c_double,
                                 C.c_double, C.POINTER(C.c_double)], st),
             "nb_compute_1x1": ([P, C.POINTER(nb_params), P, P, P, i, P, P], st),
+            "nb_rdf": ([P, C.c_float, i, i, i, i, P, P], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -402,6 +405,11 @@ def nb_pairlist_1x1(ctx, rlist, max_nbr, nbr, count, stream=None):
 def nb_compute_1x1(ctx, params, xyz, nbr, count, max_nbr, f, stream=None):
     _check(ctx, load().nb_compute_1x1(ctx, C.byref(params), _ptr(xyz), _ptr(nbr), _ptr(count), int(max_nbr),
                                       _ptr(f), _stream(stream)))
+
+
+def nb_rdf(ctx, r_max, nbins, type_a, type_b, accumulate, hist, stream=None):
+    _check(ctx, load().nb_rdf(ctx, float(r_max), int(nbins), int(type_a), int(type_b), int(accumulate),
+                              _ptr(hist), _stream(stream)))
 
 
 def nb_set_surrogate(ctx, params, r_min, r_max, stream=None):

@@ -54,6 +54,7 @@ struct nb_ctx {
     // state
     int n = 0, ntypes = 0;
     bool have_atoms = false, have_grid = false, have_list = false, have_pruned = false;
+    bool list_fresh = false;   // no new coordinates since the last list build
     bool have_mlp = false;
     float mlp_rmin = 0.f, mlp_rmax = 0.f;
     float rlist = 0.f, r_prune = 0.f;
@@ -616,6 +617,7 @@ nb_status nb_pairlist_build(nb_ctx* c, float rlist, float rbb, const int* excl_o
     c->n_launches += kLaunchesSearch + 1;
     c->rlist = rlist;
     c->have_list = true;
+    c->list_fresh = true;
     c->have_pruned = false;
     c->last_valid = false;
     return NB_OK;
@@ -629,6 +631,7 @@ nb_status nb_set_coords(nb_ctx* c, const float* xyz, nb_stream stream) {
     cudaError_t e = launch_set_coords(c->ws, c->C, xyz, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_coords kernel");
     c->n_launches += kLaunchesSetCoords;
+    c->list_fresh = false;
     return NB_OK;
 }
 
@@ -727,6 +730,31 @@ nb_status nb_compute_1x1(nb_ctx* c, const nb_params* p, const float* xyz, const 
     e = launch_finalize(c->ws, fp, c->C, f, nullptr, nullptr, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel");
     c->n_launches += 2;
+    return NB_OK;
+}
+
+nb_status nb_rdf(nb_ctx* c, float r_max, int nbins, int type_a, int type_b, int accumulate, uint64_t* hist,
+                 nb_stream stream) {
+    if (!c) return NB_ERR_ARG;
+    if (!hist || nbins < 1 || nbins > NB_RDF_MAX_BINS || !(r_max > 0.f))
+        return fail(c, NB_ERR_ARG, "rdf: bad argument");
+    if ((type_a < 0) != (type_b < 0) || type_a < -1 || type_b < -1 || type_a >= c->ntypes || type_b >= c->ntypes)
+        return fail(c, NB_ERR_ARG, "rdf: type selection must be two types in range or both -1");
+    if (!c->have_list) return fail(c, NB_ERR_STATE, "nb_pairlist_build first");
+    if (!c->list_fresh) return fail(c, NB_ERR_STATE, "rdf: coordinates changed since the list was built");
+    if (r_max > c->rlist) return fail(c, NB_ERR_BOX, "rdf: r_max above the list radius");
+    cudaStream_t s = (cudaStream_t)stream;
+    NB_CUDA(c, cudaSetDevice(c->device));
+    if (!accumulate) {
+        cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint64_t) * (size_t)c->nbox * (size_t)(nbins + 1), s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "rdf: clearing the histogram");
+    }
+    const int sp = span_begin(c, NB_KERNEL_RDF, s);
+    cudaError_t e = launch_rdf(c->ws, c->C, r_max, nbins, type_a, type_b,
+                               reinterpret_cast<unsigned long long*>(hist), c->n_sm, s);
+    span_end(c, sp, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rdf kernel");
+    c->n_launches += 1;
     return NB_OK;
 }
 

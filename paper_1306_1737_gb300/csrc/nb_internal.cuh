@@ -170,6 +170,8 @@ cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int C, fl
 
 cudaError_t launch_pairlist_1x1(const Workspace& ws, int C, float rlist, int max_nbr, int* nbr, int* count,
                                 int n_sm, cudaStream_t s);
+cudaError_t launch_rdf(const Workspace& ws, int C, float r_max, int nbins, int type_a, int type_b,
+                       unsigned long long* hist, int n_sm, cudaStream_t s);
 cudaError_t launch_force_1x1(const Workspace& ws, const ForceParams& p, int C, int max_nbr, const int* nbr,
                              const int* count, cudaStream_t s);
 
