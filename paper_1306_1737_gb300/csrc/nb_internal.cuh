@@ -211,6 +211,20 @@ __device__ __forceinline__ int advance_box(const T* off, int nbox, int b, T x) {
 }
 
 // Error-free sum a + b = s + e (Knuth TwoSum), every operation rounded once.
+// Asynchronous global -> shared copies (cp.async, bypassing registers) of
+// 16 or 4 bytes, and the wait for all of the thread's outstanding copies.
+__device__ __forceinline__ void copy16_async(void* smem, const void* gmem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void copy4_async(void* smem, const void* gmem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void copy_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);

@@ -137,15 +137,6 @@ __global__ void __launch_bounds__(32 * kPruneWarps) k_prune(PruneArgs A) {
     }
 }
 
-// 16-byte asynchronous global -> shared copy (cp.async, bypassing registers).
-__device__ __forceinline__ void copy16_async(void* smem, const void* gmem) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void copy_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
 // The 8-particle form: lane (ih, j) = (lane / 8, lane % 8) tests pairs
 // (ih, j) and (ih + 4, j) of every i-cluster, as in the force kernel.  The
 // lane's shifted i-particles stay in registers for the whole entry; the
