@@ -200,8 +200,11 @@ __device__ __forceinline__ float2 pair_force2(const ForceParams& P, float2 r2, b
         fc0 = qq0 * fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.x * P.tab_scale), rinv3.x);
         fc1 = qq1 * fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.y * P.tab_scale), rinv3.y);
     } else if (FIT) {
-        fc0 = qq0 * fmaf(-P.beta3, ewald_fit_g(P.beta2 * r2.x), rinv3.x);
-        fc1 = qq1 * fmaf(-P.beta3, ewald_fit_g(P.beta2 * r2.y), rinv3.y);
+        // the fitted factor for both pairs at once (packed FP32x2 Horner)
+        const float2 g2 = ewald_fit_g2(mul2(bc2(P.beta2), r2));
+        const float2 fc2 = mul2(make_float2(qq0, qq1), fma2(g2, bc2(-P.beta3), rinv3));
+        fc0 = fc2.x;
+        fc1 = fc2.y;
     } else {
         const float r0 = r2.x * rinv.x, r1 = r2.y * rinv.y;
         const float b0 = P.beta * r0, b1 = P.beta * r1;
@@ -218,8 +221,10 @@ __device__ __forceinline__ float2 pair_force2(const ForceParams& P, float2 r2, b
             vc0 = qq0 * (re0 + fmaf(P.k_rf, r2.x, -P.c_rf));
             vc1 = qq1 * (re1 + fmaf(P.k_rf, r2.y, -P.c_rf));
         } else if (FIT) {
-            vc0 = qq0 * fmaf(-P.beta, ewald_fit_h(P.beta2 * r2.x), re0);
-            vc1 = qq1 * fmaf(-P.beta, ewald_fit_h(P.beta2 * r2.y), re1);
+            const float2 h2 = ewald_fit_h2(mul2(bc2(P.beta2), r2));
+            const float2 v2 = mul2(make_float2(qq0, qq1), fma2(h2, bc2(-P.beta), make_float2(re0, re1)));
+            vc0 = v2.x;
+            vc1 = v2.y;
         } else {
             vc0 = qq0 * ((erfcf(P.beta * r2.x * rinv.x) - 1.0f) * rinv.x + re0);
             vc1 = qq1 * ((erfcf(P.beta * r2.y * rinv.y) - 1.0f) * rinv.y + re1);
