@@ -41,9 +41,17 @@ __host__ __device__ constexpr unsigned long long diag_mask() {
 }
 
 constexpr int kSearchWarps = 4;
+constexpr int kCoopSuperPerSm = 16;   // block-per-super-cluster mode up to this many per SM
 constexpr int kMaxExclPerSuper = 512;
 
-template <int C, int S>
+// COOP = false: one warp per super-cluster.  COOP = true (boxes with few
+// super-clusters, where one warp each would leave the SMs mostly idle): the
+// block's warps share one super-cluster and split its candidate columns
+// (warp w takes columns w, w + kSearchWarps, ...); each warp writes full
+// chunks of kJChunk j-entries as it goes, and at the end of each shift the
+// block merges the warps' remainders into full chunks, so the j-lists are
+// not fragmented by the split.
+template <int C, int S, bool COOP>
 __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
     constexpr int PPL = (C * C + 31) / 32;  // particle pairs per lane in an atom test
     constexpr int NA = S * C;               // i particles of a super-cluster (<= 32)
@@ -59,11 +67,17 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
     __shared__ int s_ex_s[kSearchWarps][kMaxExclPerSuper];
     __shared__ int s_buf_w[kSearchWarps][kJChunk];
     __shared__ unsigned long long s_buf_m[kSearchWarps][S][kJChunk];
+    __shared__ float4 s_xc[kSearchWarps][COOP ? 32 * C : 1];  // particles of a batch's candidates
+    __shared__ int s_nbuf[kSearchWarps];
 
     const Workspace& W = A.ws;
     const float eps = 1e-4f;
     int b = 0;
-    for (int q = blockIdx.x * kSearchWarps + wib; q < W.sc_total; q += gridDim.x * kSearchWarps) {
+    const int part = COOP ? wib : 0;
+    constexpr int P = COOP ? kSearchWarps : 1;
+    const int q0 = COOP ? blockIdx.x : blockIdx.x * kSearchWarps + wib;
+    const int qstep = COOP ? gridDim.x : gridDim.x * kSearchWarps;
+    for (int q = q0; q < W.sc_total; q += qstep) {
         b = advance_box(W.lay.sc_off, W.nbox, b, q);
         if (q - W.lay.sc_off[b] >= W.st[b].nsc) continue;
         DevState* st = &W.st[b];
@@ -186,8 +200,8 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                 __syncwarp();
             };
 
-            for (int cb = 0; cb < ncols; cb += 32) {
-                const int cidx = cb + lane;
+            for (int cb = 0; cb * P + part < ncols; cb += 32) {
+                const int cidx = (cb + lane) * P + part;
                 int k0 = 0, cnt = 0;
                 if (cidx < ncols) {
                     const int col = col_base + (ix0 + cidx / ncy) * G.ny + (iy0 + cidx % ncy);
@@ -259,29 +273,27 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                         }
                     }
                     // particle-distance tests, one warp-wide test per (candidate,
-                    // i-cluster); two candidates per round so that their
-                    // particle loads are in flight together
+                    // i-cluster)
                     unsigned pending = __ballot_sync(full, need != 0);
-                    while (pending) {
-                        const int t1 = __ffs(pending) - 1;
-                        pending &= pending - 1;
-                        const int t2 = pending ? __ffs(pending) - 1 : -1;
-                        if (t2 >= 0) pending &= pending - 1;
-                        const int bt1 = __shfl_sync(full, cb_, t1);
-                        const int bt2 = __shfl_sync(full, cb_, t2 >= 0 ? t2 : t1);
-                        unsigned nk1 = __shfl_sync(full, need, t1);
-                        unsigned nk2 = __shfl_sync(full, need, t2 >= 0 ? t2 : t1);
-                        if (t2 < 0) nk2 = 0u;
-                        float4 xa[PPL], xb[PPL];
+                    if constexpr (COOP) {
+                        // the particles of every candidate of the batch that needs a
+                        // test are first copied to shared memory, all copies in
+                        // flight at once (one L2 round trip per batch)
+                        if (pending) {
 #pragma unroll
-                        for (int kk = 0; kk < PPL; ++kk) {
-                            const int jj = (lane + 32 * kk) % C;
-                            xa[kk] = W.xyzq[bt1 * C + jj];
-                            xb[kk] = W.xyzq[bt2 * C + jj];
+                            for (int r = 0; r < C; ++r) {
+                                const int t = r * (32 / C) + lane / C, jj = lane % C;
+                                const int bt = __shfl_sync(full, cb_, t);
+                                if ((pending >> t) & 1u)
+                                    copy16_async(&s_xc[wib][t * C + jj], W.xyzq + (long long)bt * C + jj);
+                            }
+                            copy_async_wait_all();
+                            __syncwarp();
                         }
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            unsigned nk = u == 0 ? nk1 : nk2;
+                        while (pending) {
+                            const int t = __ffs(pending) - 1;
+                            pending &= pending - 1;
+                            unsigned nk = __shfl_sync(full, need, t);
                             while (nk) {
                                 const int k = __ffs(nk) - 1;
                                 nk &= nk - 1;
@@ -291,13 +303,56 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                                     const int p = lane + 32 * kk;
                                     if (p >= C * C) continue;
                                     const float4 h = s_h[wib][k * C + p / C], l = s_l[wib][k * C + p / C];
-                                    const float4 xj = u == 0 ? xa[kk] : xb[kk];
+                                    const float4 xj = s_xc[wib][t * C + p % C];
                                     const float dx = (h.x - xj.x) + l.x;
                                     const float dy = (h.y - xj.y) + l.y;
                                     const float dz = (h.z - xj.z) + l.z;
                                     hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < A.rl2;
                                 }
-                                if (__any_sync(full, hit) && lane == (u == 0 ? t1 : t2)) acc |= 1u << k;
+                                if (__any_sync(full, hit) && lane == t) acc |= 1u << k;
+                            }
+                        }
+                        __syncwarp();   // s_xc is rewritten by the next batch
+                    } else {
+                        // two candidates per round so that their particle loads
+                        // are in flight together
+                        while (pending) {
+                            const int t1 = __ffs(pending) - 1;
+                            pending &= pending - 1;
+                            const int t2 = pending ? __ffs(pending) - 1 : -1;
+                            if (t2 >= 0) pending &= pending - 1;
+                            const int bt1 = __shfl_sync(full, cb_, t1);
+                            const int bt2 = __shfl_sync(full, cb_, t2 >= 0 ? t2 : t1);
+                            unsigned nk1 = __shfl_sync(full, need, t1);
+                            unsigned nk2 = __shfl_sync(full, need, t2 >= 0 ? t2 : t1);
+                            if (t2 < 0) nk2 = 0u;
+                            float4 xa[PPL], xb[PPL];
+#pragma unroll
+                            for (int kk = 0; kk < PPL; ++kk) {
+                                const int jj = (lane + 32 * kk) % C;
+                                xa[kk] = W.xyzq[bt1 * C + jj];
+                                xb[kk] = W.xyzq[bt2 * C + jj];
+                            }
+#pragma unroll
+                            for (int u = 0; u < 2; ++u) {
+                                unsigned nk = u == 0 ? nk1 : nk2;
+                                while (nk) {
+                                    const int k = __ffs(nk) - 1;
+                                    nk &= nk - 1;
+                                    bool hit = false;
+#pragma unroll
+                                    for (int kk = 0; kk < PPL; ++kk) {
+                                        const int p = lane + 32 * kk;
+                                        if (p >= C * C) continue;
+                                        const float4 h = s_h[wib][k * C + p / C], l = s_l[wib][k * C + p / C];
+                                        const float4 xj = u == 0 ? xa[kk] : xb[kk];
+                                        const float dx = (h.x - xj.x) + l.x;
+                                        const float dy = (h.y - xj.y) + l.y;
+                                        const float dz = (h.z - xj.z) + l.z;
+                                        hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < A.rl2;
+                                    }
+                                    if (__any_sync(full, hit) && lane == (u == 0 ? t1 : t2)) acc |= 1u << k;
+                                }
                             }
                         }
                     }
@@ -342,7 +397,66 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                     }
                 }
             }
-            if (nbuf > 0) flush();
+            if constexpr (COOP) {
+                // merge the warps' remainders (< kJChunk each) into full chunks
+                if (lane == 0) s_nbuf[wib] = nbuf;
+                __syncthreads();
+                if (wib == 0) {
+                    const int cnt_w = lane < kSearchWarps ? s_nbuf[lane] : 0;
+                    int incl = cnt_w;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(full, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int T = __shfl_sync(full, incl, 31);
+                    const int e1 = __shfl_sync(full, incl, 0), e2 = __shfl_sync(full, incl, 1),
+                              e3 = __shfl_sync(full, incl, 2);
+                    static_assert(kSearchWarps == 4, "the merge below locates entries among 4 warps");
+                    auto locate = [&](int idx, int& w, int& pos) {
+                        w = (idx >= e1) + (idx >= e2) + (idx >= e3);
+                        pos = idx - (w == 0 ? 0 : (w == 1 ? e1 : (w == 2 ? e2 : e3)));
+                    };
+                    if (T > 0) {
+                        const int nch = (T + kJChunk - 1) / kJChunk;
+                        unsigned nk = 0;
+                        for (int idx = lane; idx < T; idx += 32) {
+                            int w, pos;
+                            locate(idx, w, pos);
+                            nk += __popc((unsigned)s_buf_w[w][pos] >> kSuperShift);
+                        }
+                        for (int o = 16; o > 0; o >>= 1) nk += __shfl_xor_sync(full, nk, o);
+                        unsigned long long jb = 0, ie = 0;
+                        if (lane == 0) {
+                            jb = atomicAdd(&st->n_jent, (unsigned long long)T);
+                            ie = atomicAdd(&st->n_ient, (unsigned long long)nch);
+                            atomicAdd(&st->n_keys, (unsigned long long)nk);
+                        }
+                        jb = __shfl_sync(full, jb, 0);
+                        ie = __shfl_sync(full, ie, 0);
+                        if ((long long)(jb + T) > jent_cap || (long long)(ie + nch) > ient_cap) {
+                            if (lane == 0) set_flag(st, NB_ERR_CAPACITY);
+                            for (int c = lane; c < nch; c += 32)
+                                if ((long long)(ie + c) < ient_cap) W.ient[ient_base + ie + c] = make_int4(q, s, 0, 0);
+                        } else {
+                            const long long j0 = jent_base + (long long)jb;
+                            for (int idx = lane; idx < T; idx += 32) {
+                                int w, pos;
+                                locate(idx, w, pos);
+                                W.cj[j0 + idx] = s_buf_w[w][pos];
+#pragma unroll
+                                for (int k = 0; k < S; ++k) W.mask[k * W.jstride + j0 + idx] = s_buf_m[w][k][pos];
+                            }
+                            for (int c = lane; c < nch; c += 32)
+                                W.ient[ient_base + ie + c] =
+                                    make_int4(q, s, (int)(j0 + c * kJChunk), (int)(j0 + min(T, (c + 1) * kJChunk)));
+                        }
+                    }
+                }
+                __syncthreads();
+                nbuf = 0;
+            } else {
+                if (nbuf > 0) flush();
+            }
         }
         __syncwarp();
     }
@@ -372,14 +486,20 @@ cudaError_t launch_search(const Workspace& ws, int C, float rlist, float rbb, co
     A.rl = rlist;
     A.rl2 = rlist * rlist;
     A.rbb2 = rbb * rbb;
-    long long want = ((long long)ws.sc_total + kSearchWarps - 1) / kSearchWarps;
+    // few super-clusters (fewer than about two per resident warp): a block per
+    // super-cluster; else a warp per super-cluster
+    const bool coop = (long long)ws.sc_total <= (long long)n_sm * kCoopSuperPerSm;
+    long long want = coop ? (long long)ws.sc_total : ((long long)ws.sc_total + kSearchWarps - 1) / kSearchWarps;
     long long blocks = (long long)n_sm * 16;
     if (blocks > want) blocks = want;
     if (blocks < 1) blocks = 1;
-    if (C == 8)
-        k_search<8, super_size(8)><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
-    else
-        k_search<4, super_size(4)><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
+    if (C == 8) {
+        if (coop) k_search<8, super_size(8), true><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
+        else k_search<8, super_size(8), false><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
+    } else {
+        if (coop) k_search<4, super_size(4), true><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
+        else k_search<4, super_size(4), false><<<(int)blocks, 32 * kSearchWarps, 0, s>>>(A);
+    }
     k_ient_offsets<<<1, 32, 0, s>>>(ws);
     return cudaGetLastError();
 }
