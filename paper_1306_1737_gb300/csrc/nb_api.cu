@@ -173,7 +173,7 @@ static BoxPlan plan_box(int n, const float L[3], int C, double rlist, double fac
     const double maxper = 0.5 * 27.0 * (double)z.nclu_cap + 1.0;
     if (per > maxper) per = maxper;
     z.jent_cap = (long long)std::ceil(factor * per * (double)z.nsc_cap) + 64;
-    z.ient_cap = (long long)z.nsc_cap * 27 + z.jent_cap / kJChunk + 64;
+    z.ient_cap = (long long)z.nsc_cap * 27 + z.jent_cap / kJChunkCoop + 64;
     return z;
 }
 

@@ -31,6 +31,7 @@ constexpr int kMaxColumn = 8192;       // particles per grid column sorted on-ch
 constexpr int kMaxBoxes = 4096;        // boxes per context
 constexpr int kShiftCenter = 13;       // shift index of (0, 0, 0)
 constexpr int kJChunk = 32;            // j-entries per i-entry at most (load balance)
+constexpr int kJChunkCoop = 12;        // the same for boxes searched a block per super-cluster
 // Super-clusters (Sec. 3.1, Fig. 6: several i-clusters share one j-list):
 // up to super_size(C) consecutive clusters of one grid column.  A j-entry's
 // word holds the j-cluster index in its low kSuperShift bits and one

@@ -48,9 +48,10 @@ constexpr int kMaxExclPerSuper = 512;
 // super-clusters, where one warp each would leave the SMs mostly idle): the
 // block's warps share one super-cluster and split its candidate columns
 // (warp w takes columns w, w + kSearchWarps, ...); each warp writes full
-// chunks of kJChunk j-entries as it goes, and at the end of each shift the
-// block merges the warps' remainders into full chunks, so the j-lists are
-// not fragmented by the split.
+// chunks of kJChunkCoop j-entries as it goes, and at the end of each shift
+// the block merges the warps' remainders into full chunks, so the j-lists are
+// not fragmented by the split.  The shorter chunks of this mode give a small
+// box's force and prune kernels more i-entries than warps to balance.
 template <int C, int S, bool COOP>
 __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
     constexpr int PPL = (C * C + 31) / 32;  // particle pairs per lane in an atom test
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
     int b = 0;
     const int part = COOP ? wib : 0;
     constexpr int P = COOP ? kSearchWarps : 1;
+    constexpr int JC = COOP ? kJChunkCoop : kJChunk;   // j-entries per i-entry at most
     const int q0 = COOP ? blockIdx.x : blockIdx.x * kSearchWarps + wib;
     const int qstep = COOP ? gridDim.x : gridDim.x * kSearchWarps;
     for (int q = q0; q < W.sc_total; q += qstep) {
@@ -393,12 +395,12 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                         }
                         if (lane == 0) s_buf_w[wib][nbuf] = bt | (int)(at << kSuperShift);
                         ++nbuf;
-                        if (nbuf == kJChunk) flush();
+                        if (nbuf == JC) flush();
                     }
                 }
             }
             if constexpr (COOP) {
-                // merge the warps' remainders (< kJChunk each) into full chunks
+                // merge the warps' remainders (< JC each) into full chunks
                 if (lane == 0) s_nbuf[wib] = nbuf;
                 __syncthreads();
                 if (wib == 0) {
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                         pos = idx - (w == 0 ? 0 : (w == 1 ? e1 : (w == 2 ? e2 : e3)));
                     };
                     if (T > 0) {
-                        const int nch = (T + kJChunk - 1) / kJChunk;
+                        const int nch = (T + JC - 1) / JC;
                         unsigned nk = 0;
                         for (int idx = lane; idx < T; idx += 32) {
                             int w, pos;
@@ -448,7 +450,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                             }
                             for (int c = lane; c < nch; c += 32)
                                 W.ient[ient_base + ie + c] =
-                                    make_int4(q, s, (int)(j0 + c * kJChunk), (int)(j0 + min(T, (c + 1) * kJChunk)));
+                                    make_int4(q, s, (int)(j0 + c * JC), (int)(j0 + min(T, (c + 1) * JC)));
                         }
                     }
                 }
