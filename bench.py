@@ -3,9 +3,9 @@
 
 A step is one pair-list lifetime of the workload: grid the box
 (nb_grid_put), build the buffered cluster-pair list (nb_pairlist_build), then
-nstlist frames, each with new coordinates (pruning every nstprune frames,
-nb_prune) and one force evaluation (nb_compute; energies and virial on the
-first and last frame).  The headline value is force evaluations per second
+nstlist frames, each with new coordinates and one force evaluation
+(nb_compute; energies and virial on the first and last frame; every nstprune
+frames nb_prune_compute, which prunes the list in the same pass).  The headline value is force evaluations per second
 over the whole job.  Default workload: 24,000-atom water box, Ewald real
 space rc 1.0 nm, beta 3.12 nm^-1, rlist 1.1 nm, nstlist 20, prune every 5.
 
@@ -606,13 +606,16 @@ def run_ours(args):
                 xf = xbuf
             else:
                 xf = x0 if host is not None else xdev[f]
-            if nstprune and f % nstprune == 0 and (f > 0 or args.prune0):
-                nb.nb_prune(ctx, xf if f > 0 else None, rprune, stream)
-                xarg = None
-            else:
-                xarg = xf if f > 0 else None
             prm = prm_e if energy_frame(f) else prm_f
-            nb.nb_compute(ctx, prm, xarg, F, E, V, stream)
+            if nstprune and f % nstprune == 0 and (f > 0 or args.prune0):
+                if args.fused_prune:
+                    # prune while computing this frame's forces on the outer list
+                    nb.nb_prune_compute(ctx, prm, xf if f > 0 else None, rprune, F, E, V, stream)
+                else:
+                    nb.nb_prune(ctx, xf if f > 0 else None, rprune, stream)
+                    nb.nb_compute(ctx, prm, None, F, E, V, stream)
+            else:
+                nb.nb_compute(ctx, prm, xf if f > 0 else None, F, E, V, stream)
             if host is not None:
                 hF[f].copy_(F, non_blocking=True)
                 if energy_frame(f):
@@ -691,13 +694,22 @@ def run_ours(args):
     # force-kernel roofline (FP32 ALU): algorithmic flops per launch / duration
     force_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_FORCE]
     prune_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_PRUNE]
+    fprune_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_FORCE_PRUNE]
     search_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_SEARCH]
     grid_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_GRID]
     pairs_outer = int(info.n_cluster_pairs) * 64
     pairs_pruned = int(info.n_cluster_pairs_pruned) * 64 if info.n_cluster_pairs_pruned >= 0 else pairs_outer
-    # frames before the first prune use the outer list
-    n_outer = 0 if (nstprune and args.prune0) else (min(nstprune, nstlist) if nstprune else nstlist)
-    listed = (n_outer * pairs_outer + (nstlist - n_outer) * pairs_pruned) / nstlist
+    # frames before the first prune, and fused prune frames, use the outer list
+    prune_frames = [f for f in range(nstlist) if nstprune and f % nstprune == 0 and (f > 0 or args.prune0)]
+    first_prune = prune_frames[0] if prune_frames else nstlist
+
+    def listed_at(f):
+        outer = f < first_prune or (args.fused_prune and f in prune_frames)
+        return pairs_outer if outer else pairs_pruned
+    listed_all = sum(listed_at(f) for f in range(nstlist)) / nstlist
+    # the force-kernel spans: every frame but the fused prune frames (their own span kind)
+    force_frames = [f for f in range(nstlist) if not (args.fused_prune and f in prune_frames)]
+    listed = sum(listed_at(f) for f in force_frames) / len(force_frames)
     pairs_rc = int(info.n_pairs_rc)
     flops = FLOPS_DIST * listed + (FLOPS_PAIR[elec] - FLOPS_DIST) * pairs_rc
     t_force = statistics.mean(force_ms) / 1000.0 if force_ms else float("nan")
@@ -753,7 +765,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_s * 1000 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_dict(args, box, p, desc),
-            "pair_interactions_per_s": listed * nstlist * args.steps * ws_n / total_s,
+            "pair_interactions_per_s": listed_all * nstlist * args.steps * ws_n / total_s,
             "effective_pair_interactions_per_s": pairs_rc * nstlist * args.steps * ws_n / total_s,
             "force_kernel": {"ms": t_force * 1e3, "listed_pairs_per_s": listed / t_force,
                              "pairs_within_rc_per_s": pairs_rc / t_force,
@@ -761,6 +773,7 @@ def run_ours(args):
             "kernel_ms": {"grid": statistics.mean(grid_ms) if grid_ms else None,
                           "search": statistics.mean(search_ms) if search_ms else None,
                           "prune": statistics.mean(prune_ms) if prune_ms else None,
+                          "force_prune": statistics.mean(fprune_ms) if fprune_ms else None,
                           "force": t_force * 1e3},
             "list": {"clusters": int(info.n_clusters), "superclusters": int(info.n_superclusters),
                      "ientries": int(info.n_ientries), "jentries": int(info.n_jentries),
@@ -968,12 +981,16 @@ def run_batch(args):
 
     if rank == 0:
         force_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_FORCE]
-        # frames 0 and 20 use the outer list, the others the pruned one
+        # force-kernel spans: every frame of a list lifetime but the prune
+        # frames (fused force + prune, their own span kind); the frames before
+        # the first prune use the outer list, the later ones the pruned list
         # (nb_check after the step reports the last list and prune)
         n_rc = int(info1.n_pairs_rc)
         outer = int(info1.n_cluster_pairs) * 64
         pruned = int(info1.n_cluster_pairs_pruned) * 64
-        listed = (2 * outer + (BATCH_H - 2) * pruned) / BATCH_H if pruned > 0 else outer
+        lf_force = [f for f in range(nst0) if not (nstprune and f > 0 and f % nstprune == 0)]
+        n_out = sum(1 for f in lf_force if not nstprune or f < nstprune)
+        listed = ((n_out * outer + (len(lf_force) - n_out) * pruned) / len(lf_force)) if pruned > 0 else outer
         flops = FLOPS_DIST * listed + (FLOPS_PAIR["ewald"] - FLOPS_DIST) * n_rc
         t_force = statistics.mean(force_ms) / 1000.0
         pk = peaks()
@@ -1031,6 +1048,8 @@ def main():
                     help="batch tuner: list radius per lifetime by sqrt scaling or by the Appendix drift bound")
     ap.add_argument("--no-1x1", dest="compare_1x1", action="store_false",
                     help="skip the particle-pair (1 x 1) kernel comparison")
+    ap.add_argument("--separate-prune", dest="fused_prune", action="store_false",
+                    help="prune with the separate prune kernel instead of the fused force + prune pass")
     ap.add_argument("--no-rdf", dest="pair_correlation", action="store_false",
                     help="skip the pair correlation (g(r) histogram) measurement")
     ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",

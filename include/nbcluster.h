@@ -109,7 +109,8 @@ enum nb_kernel_kind {
     NB_KERNEL_PRUNE = 2,   /* nb_prune's prune kernel */
     NB_KERNEL_FORCE = 3,   /* nb_compute's force/energy kernel */
     NB_KERNEL_FORCE_1X1 = 4, /* nb_compute_1x1's particle-pair force kernel */
-    NB_KERNEL_RDF = 5       /* nb_rdf's pair-distance histogram kernel */
+    NB_KERNEL_RDF = 5,      /* nb_rdf's pair-distance histogram kernel */
+    NB_KERNEL_FORCE_PRUNE = 6 /* nb_prune_compute's fused force + prune kernel */
 };
 
 /* --- context ------------------------------------------------------------ */
@@ -325,6 +326,19 @@ nb_status nb_buffer_drift(int nclass, const nb_particle_class* classes_host, int
 nb_status nb_buffer_size(int nclass, const nb_particle_class* classes_host, int ntypes, const float* c6c12_host,
                          double volume, const nb_params* p, double t_ps, double temperature, double tolerance,
                          double* rb);
+
+/* Prune and compute in one pass (Sec. 2.3: pruning on the GPU).  With xyz_dev
+ * (may be NULL: current coordinates) the forces (and energies, virial as in
+ * nb_compute) are computed on the outer list of the last nb_pairlist_build,
+ * and the same pass writes the pruned list at r_prune that later nb_compute
+ * calls use; the pruned list equals the one nb_prune would write for these
+ * coordinates.  One fused kernel for 8-particle clusters computing forces
+ * with the analytic or tabulated factor; otherwise (4-particle clusters,
+ * energies, the surrogate factor) nb_prune's kernel followed by the force
+ * kernel on the pruned list.  rc must not exceed r_prune nor the list
+ * radius.  Errors: as nb_compute and nb_prune. */
+nb_status nb_prune_compute(nb_ctx* ctx, const nb_params* p, const float* xyz_dev, float r_prune, float* f_dev,
+                           double* e_dev, double* vir_dev, nb_stream stream);
 
 /* --- the particle-pair (1 x 1) comparison path -------------------------------- */
 

@@ -40,6 +40,7 @@ NB_KERNEL_PRUNE = 2
 NB_KERNEL_FORCE = 3
 NB_KERNEL_FORCE_1X1 = 4
 NB_KERNEL_RDF = 5
+NB_KERNEL_FORCE_PRUNE = 6
 NB_RDF_MAX_BINS = 2048
 
 _lock = threading.Lock()
@@ -127,6 +128,7 @@ def load():
                                 C.c_double, C.POINTER(C.c_double)], st),
             "nb_compute_1x1": ([P, C.POINTER(nb_params), P, P, P, i, P, P], st),
             "nb_rdf": ([P, C.c_float, i, i, i, i, P, P], st),
+            "nb_prune_compute": ([P, C.POINTER(nb_params), P, C.c_float, P, P, P, P], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -405,6 +407,11 @@ def nb_pairlist_1x1(ctx, rlist, max_nbr, nbr, count, stream=None):
 def nb_compute_1x1(ctx, params, xyz, nbr, count, max_nbr, f, stream=None):
     _check(ctx, load().nb_compute_1x1(ctx, C.byref(params), _ptr(xyz), _ptr(nbr), _ptr(count), int(max_nbr),
                                       _ptr(f), _stream(stream)))
+
+
+def nb_prune_compute(ctx, params, xyz, r_prune, f, e=None, vir=None, stream=None):
+    _check(ctx, load().nb_prune_compute(ctx, C.byref(params), _ptr(xyz), float(r_prune), _ptr(f), _ptr(e),
+                                        _ptr(vir), _stream(stream)))
 
 
 def nb_rdf(ctx, r_max, nbins, type_a, type_b, accumulate, hist, stream=None):

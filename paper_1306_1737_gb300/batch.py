@@ -125,8 +125,8 @@ class BatchRunner:
             nb.nb_pairlist_build(ctx, float(np.float32(g.spec.rlist)), 0.0, g.excl_off, g.excl_idx, stream)
             nb.nb_compute(ctx, prm, None, g.F, g.E, g.V, stream)
         elif self.nstprune and lf % self.nstprune == 0:
-            nb.nb_prune(ctx, x, float(np.float32(self.r_prune(g))), stream)
-            nb.nb_compute(ctx, prm, None, g.F, g.E, g.V, stream)
+            # prune while computing this frame's forces on the outer list
+            nb.nb_prune_compute(ctx, prm, x, float(np.float32(self.r_prune(g))), g.F, g.E, g.V, stream)
         else:
             nb.nb_compute(ctx, prm, x, g.F, g.E, g.V, stream)
 

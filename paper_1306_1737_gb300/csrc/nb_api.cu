@@ -691,6 +691,69 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     return NB_OK;
 }
 
+nb_status nb_prune_compute(nb_ctx* c, const nb_params* p, const float* xyz, float r_prune, float* f,
+                           double* e_out, double* vir_out, nb_stream stream) {
+    if (!c) return NB_ERR_ARG;
+    if (!p || (!f && c->n > 0)) return fail(c, NB_ERR_ARG, "prune_compute: null argument");
+    if (!c->have_list) return fail(c, NB_ERR_STATE, "nb_pairlist_build first");
+    if (p->elec != NB_ELEC_RF && p->elec != NB_ELEC_EWALD && p->elec != NB_ELEC_EWALD_MLP &&
+        p->elec != NB_ELEC_EWALD_TAB)
+        return fail(c, NB_ERR_ARG, "unknown electrostatics");
+    if (p->elec == NB_ELEC_EWALD_MLP) {
+        if (!c->have_mlp) return fail(c, NB_ERR_STATE, "no network: call nb_set_surrogate first");
+        if (p->rc > c->mlp_rmax) return fail(c, NB_ERR_ARG, "rc above the network's input range");
+    }
+    if (!(p->rc > 0.f) || !(r_prune > 0.f)) return fail(c, NB_ERR_ARG, "rc and r_prune must be positive");
+    if (!(r_prune < 0.5f * min_edge(c))) return fail(c, NB_ERR_BOX, "r_prune must be below half the box");
+    if (p->rc > r_prune || p->rc > c->rlist) return fail(c, NB_ERR_BOX, "rc above the prune or list radius");
+    if (p->elec != NB_ELEC_RF && !(p->beta >= 0.f)) return fail(c, NB_ERR_ARG, "beta must be >= 0");
+    if (xyz) {
+        nb_status st = nb_set_coords(c, xyz, stream);
+        if (st != NB_OK) return st;
+    }
+    ForceParams fp{};
+    const nb_status pst = force_params(c, p, &fp);
+    if (pst != NB_OK) return pst;
+    cudaStream_t s = (cudaStream_t)stream;
+    NB_CUDA(c, cudaSetDevice(c->device));
+    // one pass where the fused kernel exists (8-particle clusters, forces
+    // only, analytic or tabulated factor); else the prune kernel, then the
+    // force kernel on the pruned list
+    const bool fused = c->C == 8 && !fp.want_energy && fp.elec != NB_ELEC_EWALD_MLP;
+    cudaError_t e;
+    if (fused) {
+        e = launch_prune_reset(c->ws, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "prune reset");
+        fp.prune = 1;
+        fp.rp2 = r_prune * r_prune;
+        fp.use_pruned = 0;
+        const int sp = span_begin(c, NB_KERNEL_FORCE_PRUNE, s);
+        e = launch_force(c->ws, fp, c->C, c->n_sm, s);
+        span_end(c, sp, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "force + prune kernel");
+        c->n_launches += 2;
+    } else {
+        const int sp = span_begin(c, NB_KERNEL_PRUNE, s);
+        e = launch_prune(c->ws, c->C, r_prune, c->n_sm, s);
+        span_end(c, sp, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "prune kernel");
+        c->n_launches += kLaunchesPrune;
+        fp.use_pruned = 1;
+        const int sf = span_begin(c, NB_KERNEL_FORCE, s);
+        e = launch_force(c->ws, fp, c->C, c->n_sm, s);
+        span_end(c, sf, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "force kernel");
+        c->n_launches += 1;
+    }
+    c->r_prune = r_prune;
+    c->have_pruned = true;
+    c->last_valid = false;
+    e = launch_finalize(c->ws, fp, c->C, f, e_out, vir_out, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
+    c->n_launches += 1 + (fp.want_energy ? 1 : 0);
+    return NB_OK;
+}
+
 nb_status nb_pairlist_1x1(nb_ctx* c, float rlist, int max_nbr, int* nbr, int* count, nb_stream stream) {
     if (!c) return NB_ERR_ARG;
     if (!c->have_list) return fail(c, NB_ERR_STATE, "nb_pairlist_build first");

@@ -46,6 +46,11 @@ struct ForceArgs {
     const float2* ewald_tab;          // tabulated Ewald force factor
     const int* ient_used;             // compact i-entry index per box
     int* work;                        // work counter (next i-entry to take)
+    // pruned-list output of the fused force + prune kernel
+    int4* ient_p;
+    int* cj_p;
+    unsigned long long* mask_p;
+    DevState* stw;
     int nbox;
     ForceParams p;
 };
@@ -254,15 +259,22 @@ __device__ __forceinline__ void flush_energy(Accum* acc, int b, float& e_lj, flo
 
 // The pairs of i-cluster k (of the super-cluster) with one j-cluster.
 // Returns (warp-uniformly) whether any pair was inside rc.
-template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, bool FULL>
+// PRUNE: also sets bit k of keep when a counted pair (any pair but, on the
+// unshifted diagonal, j <= i) is closer than the prune radius (Sec. 2.3),
+// with the same FP32 distances as the separate prune kernel.
+template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, bool FULL, bool PRUNE>
 __device__ __forceinline__ bool icluster8(const ForceParams& P, const float2* s_lj, const WarpSmem& W,
                                           const Lane8& L, int k, bool diag, unsigned long long m,
                                           float4 xj, const NegJ& nxj, int tj, float2& fx, float2& fy, float2& fz,
                                           float& fjx, float& fjy, float& fjz, float& e_lj, float& e_c,
-                                          unsigned& n_inc) {
+                                          unsigned& n_inc, unsigned& keep) {
     float2 dx, dy, dz, fq;
     pair_deltas<SHIFTED>(W, k, L.ih, nxj.nx, nxj.ny, nxj.nz, dx, dy, dz, fq);
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    if constexpr (PRUNE) {
+        const bool c0 = FULL || !(diag && L.lower0), c1 = FULL || !(diag && L.lower1);
+        if (__any_sync(0xffffffffu, (c0 && r2.x < P.rp2) || (c1 && r2.y < P.rp2))) keep |= 1u << k;
+    }
     bool u0 = true, u1 = true;
     if (!FULL) {
         u0 = ((unsigned)m & L.sel) != 0u;
@@ -377,13 +389,17 @@ __device__ __forceinline__ bool icluster8_mlp(const ForceParams& P, const float2
     return true;
 }
 
-// All j-entries [jb, je) (at most 32) of one super-cluster i-entry.
-template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED>
+// All j-entries [jb, je) (at most 32) of one super-cluster i-entry.  PRUNE:
+// the j-entries that keep an interacting i-cluster within the prune radius
+// are appended in order to the pruned list at j_out + kept (the entry's
+// offsets in the outer list), as the separate prune kernel does.
+template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, bool PRUNE>
 __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s_lj, WarpSmem& W,
                                              const Lane8& L, int g0, bool center, int jb, int je,
                                              float2 (&fx)[kSuper8], float2 (&fy)[kSuper8],
                                              float2 (&fz)[kSuper8], float& e_lj, float& e_c,
-                                             unsigned& n_inc, const MlpTC* M, float* mo) {
+                                             unsigned& n_inc, const MlpTC* M, float* mo, int j_out, int& kept,
+                                             unsigned long long& keys) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int nt = je - jb;
@@ -398,6 +414,7 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
     int cjn = W.w[0] & kCjMask;
     float4 xjn = xyzq_j[cjn * 8];
     int tjn = type_j[cjn * 8];
+    unsigned my_keep = 0;   // PRUNE: kept i-cluster bits of j-entry `lane`
     for (int t = 0; t < nt; ++t) {
         const unsigned w = (unsigned)W.w[t];
         const int cjt = (int)(w & kCjMask);
@@ -413,6 +430,7 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
         tjn = type_j[cjn * 8];
         float fjx = 0.f, fjy = 0.f, fjz = 0.f;
         bool any = false;
+        unsigned keep = 0;
 #pragma unroll
         for (int k = 0; k < kSuper8; ++k) {
             if ((bits >> k) & 1u) {
@@ -426,15 +444,18 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
                         any |= icluster8_mlp<SHIFTED, false>(A.p, s_lj, W, L, k, diag, m, xj, nxj, tj, fx[k], fy[k],
                                                              fz[k], fjx, fjy, fjz, *M, mo);
                 } else if (!diag && m == ~0ull) {
-                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true>(A.p, s_lj, W, L, k, false, m, xj, nxj, tj,
-                                                                       fx[k], fy[k], fz[k], fjx, fjy, fjz,
-                                                                       e_lj, e_c, n_inc);
+                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true, PRUNE>(A.p, s_lj, W, L, k, false, m, xj, nxj,
+                                                                              tj, fx[k], fy[k], fz[k], fjx, fjy, fjz,
+                                                                              e_lj, e_c, n_inc, keep);
                 } else {
-                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, false>(A.p, s_lj, W, L, k, diag, m, xj, nxj, tj,
-                                                                        fx[k], fy[k], fz[k], fjx, fjy, fjz,
-                                                                        e_lj, e_c, n_inc);
+                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, false, PRUNE>(A.p, s_lj, W, L, k, diag, m, xj, nxj,
+                                                                               tj, fx[k], fy[k], fz[k], fjx, fjy,
+                                                                               fjz, e_lj, e_c, n_inc, keep);
                 }
             }
+        }
+        if constexpr (PRUNE) {
+            if (lane == t) my_keep = keep;
         }
         if (!any) continue;
         fjx += __shfl_xor_sync(full, fjx, 8);
@@ -445,11 +466,27 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
         fjz += __shfl_xor_sync(full, fjz, 16);
         if (L.ih == 0) atomicAdd(&A.fslot[cjt * 8 + L.j], make_float4(fjx, fjy, fjz, 0.0f));
     }
+    if constexpr (PRUNE) {
+        // compact the kept j-entries of this chunk, in order
+        const unsigned kb = __ballot_sync(full, my_keep != 0);
+        const int pos = __popc(kb & ((1u << lane) - 1u));
+        if (my_keep) {
+            const long long o = (long long)j_out + kept + pos;
+            A.cj_p[o] = (W.w[lane] & kCjMask) | (int)(my_keep << kSuperShift);
+#pragma unroll
+            for (int k = 0; k < kSuper8; ++k)
+                A.mask_p[k * A.jstride + o] = ((my_keep >> k) & 1u) ? W.m[k][lane] : 0ull;
+        }
+        kept += __popc(kb);
+        unsigned nk = __popc(my_keep);
+        for (int o = 16; o > 0; o >>= 1) nk += __shfl_xor_sync(full, nk, o);
+        keys += nk;
+    }
     __syncwarp();
 }
 
-template <int ELEC, bool ENERGY, bool FIT>
-__global__ void __launch_bounds__(32 * kForceWarps, ELEC == NB_ELEC_EWALD_MLP ? 4 : (ENERGY ? 5 : 7))
+template <int ELEC, bool ENERGY, bool FIT, bool PRUNE = false>
+__global__ void __launch_bounds__(32 * kForceWarps, ELEC == NB_ELEC_EWALD_MLP ? 4 : (ENERGY ? 5 : (PRUNE ? 6 : 7)))
 k_force8(ForceArgs A) {
     extern __shared__ float2 s_lj[];
     __shared__ WarpSmem s_w[kForceWarps];
@@ -487,6 +524,8 @@ k_force8(ForceArgs A) {
     float e_lj = 0.0f, e_c = 0.0f;
     unsigned n_inc = 0;
     int b_acc = -1;
+    int pb_acc = -1;                              // PRUNE: box of the pruned-list totals below
+    unsigned long long kept_total = 0, keys_total = 0;
     const int n_used = A.ient_used[A.nbox];
     // warps take i-entries from a counter (entries differ in length); the
     // next index is requested while the current entry is processed
@@ -505,9 +544,20 @@ k_force8(ForceArgs A) {
             flush_energy(A.acc, b_acc, e_lj, e_c, n_inc);
             b_acc = b;
         }
+        if (PRUNE && b != pb_acc) {
+            if (lane == 0 && pb_acc >= 0 && kept_total) {
+                atomicAdd(&A.stw[pb_acc].n_jent_pruned, kept_total);
+                atomicAdd(&A.stw[pb_acc].n_keys_pruned, keys_total);
+            }
+            kept_total = keys_total = 0;
+            pb_acc = b;
+        }
         const int4 ie = A.ient[e];
         const int q = ie.x, s = ie.y, jb = ie.z, je = ie.w;
-        if (jb >= je) continue;
+        if (jb >= je) {
+            if (PRUNE && lane == 0) A.ient_p[e] = make_int4(q, s, jb, jb);
+            continue;
+        }
         const int2 info = A.sc_info[q];
         const int g0 = info.x, n = info.y;
         float sh[3];
@@ -541,14 +591,19 @@ k_force8(ForceArgs A) {
         float2 fx[kSuper8], fy[kSuper8], fz[kSuper8];
 #pragma unroll
         for (int k = 0; k < kSuper8; ++k) fx[k] = fy[k] = fz[k] = make_float2(0.f, 0.f);
+        int kept = 0;
         for (int base = jb; base < je; base += 32) {
             const int bend = min(je, base + 32);
             if (center)
-                force_entry8<ELEC, ENERGY, FIT, false>(A, s_lj, W, L, g0, true, base, bend, fx, fy, fz, e_lj,
-                                                       e_c, n_inc, M, mo);
+                force_entry8<ELEC, ENERGY, FIT, false, PRUNE>(A, s_lj, W, L, g0, true, base, bend, fx, fy, fz,
+                                                              e_lj, e_c, n_inc, M, mo, jb, kept, keys_total);
             else
-                force_entry8<ELEC, ENERGY, FIT, true>(A, s_lj, W, L, g0, false, base, bend, fx, fy, fz, e_lj,
-                                                      e_c, n_inc, M, mo);
+                force_entry8<ELEC, ENERGY, FIT, true, PRUNE>(A, s_lj, W, L, g0, false, base, bend, fx, fy, fz,
+                                                             e_lj, e_c, n_inc, M, mo, jb, kept, keys_total);
+        }
+        if (PRUNE) {
+            if (lane == 0) A.ient_p[e] = make_int4(q, s, jb, jb + kept);
+            kept_total += kept;
         }
         // i-forces: per i-cluster, sum over the 8 lanes of each i row
         float tsum[3] = {0.f, 0.f, 0.f};
@@ -583,6 +638,10 @@ k_force8(ForceArgs A) {
         __syncwarp();
     }
     if (ENERGY) flush_energy(A.acc, b_acc, e_lj, e_c, n_inc);
+    if (PRUNE && lane == 0 && pb_acc >= 0 && kept_total) {
+        atomicAdd(&A.stw[pb_acc].n_jent_pruned, kept_total);
+        atomicAdd(&A.stw[pb_acc].n_keys_pruned, keys_total);
+    }
 }
 
 // Generic C = 4 kernel (super-clusters of one cluster): one warp per
@@ -680,10 +739,11 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
     if (ENERGY) flush_energy(A.acc, b_acc, e_lj, e_c, n_inc);
 }
 
-template <int ELEC, bool ENERGY, bool FIT>
+template <int ELEC, bool ENERGY, bool FIT, bool PRUNE = false>
 static cudaError_t launch_force_t(const ForceArgs& A, int C, int n_sm, cudaStream_t s) {
     const size_t smem = sizeof(float2) * A.p.ntypes * A.p.ntypes;
-    auto kern = (C == 8) ? k_force8<ELEC, ENERGY, FIT> : k_force4<ELEC, ENERGY, FIT>;
+    auto kern = PRUNE ? k_force8<ELEC, ENERGY, FIT, PRUNE>
+                      : ((C == 8) ? k_force8<ELEC, ENERGY, FIT> : k_force4<ELEC, ENERGY, FIT>);
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kForceWarps, smem);
     if (e != cudaSuccess) return e;
@@ -696,6 +756,27 @@ template <int ELEC, bool ENERGY>
 static cudaError_t launch_force_e(const ForceArgs& A, int C, int n_sm, cudaStream_t s) {
     if (ELEC == NB_ELEC_EWALD && A.p.use_fit) return launch_force_t<ELEC, ENERGY, true>(A, C, n_sm, s);
     return launch_force_t<ELEC, ENERGY, false>(A, C, n_sm, s);
+}
+
+// The tabulated kernel (forces only, 8-particle clusters): the table follows
+// the LJ table in dynamic shared memory.
+template <bool PRUNE>
+static cudaError_t launch_force_tab(const ForceArgs& A, int n_sm, cudaStream_t s) {
+    auto kern = k_force8<NB_ELEC_EWALD_TAB, false, true, PRUNE>;
+    const size_t smem = sizeof(float2) * (A.p.ntypes * A.p.ntypes + A.p.tab_n);
+    static bool attr_set = false;
+    cudaError_t e;
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kForceWarps, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    kern<<<n_sm * per_sm, 32 * kForceWarps, smem, s>>>(A);
+    return cudaGetLastError();
 }
 
 // The tabulated force factor G(w) = (erf(x) - 2x/sqrt(pi) exp(-x^2)) / x^3,
@@ -742,6 +823,10 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
     A.ient_used = ws.ient_used;
     A.ewald_tab = ws.ewald_tab;
     A.work = ws.work;
+    A.ient_p = ws.ient_p;
+    A.cj_p = ws.cj_p;
+    A.mask_p = ws.mask_p;
+    A.stw = ws.st;
     A.p = p;
     // the accumulators hold energies, pair counts and shift forces, which
     // only energy evaluations produce and read
@@ -750,23 +835,15 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
         e = cudaMemsetAsync(ws.acc, 0, sizeof(Accum) * ws.nbox, s);
         if (e != cudaSuccess) return e;
     }
-    if (p.elec == NB_ELEC_EWALD_TAB) {
-        // forces only, 8-particle clusters (checked by the caller)
-        auto kern = k_force8<NB_ELEC_EWALD_TAB, false, true>;
-        const size_t smem = sizeof(float2) * (A.p.ntypes * A.p.ntypes + A.p.tab_n);
-        static bool attr_set = false;
-        if (!attr_set) {
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kForceWarps, smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) per_sm = 1;
-        kern<<<n_sm * per_sm, 32 * kForceWarps, smem, s>>>(A);
-        return cudaGetLastError();
+    if (p.prune) {
+        // the fused force + prune kernel: forces only, 8-particle clusters,
+        // not the surrogate (checked by the caller), on the outer list
+        if (p.elec == NB_ELEC_EWALD_TAB) return launch_force_tab<true>(A, n_sm, s);
+        if (p.elec == NB_ELEC_RF) return launch_force_t<NB_ELEC_RF, false, false, true>(A, C, n_sm, s);
+        if (p.use_fit) return launch_force_t<NB_ELEC_EWALD, false, true, true>(A, C, n_sm, s);
+        return launch_force_t<NB_ELEC_EWALD, false, false, true>(A, C, n_sm, s);
     }
+    if (p.elec == NB_ELEC_EWALD_TAB) return launch_force_tab<false>(A, n_sm, s);
     if (p.elec == NB_ELEC_EWALD_MLP) {
         // forces only, 8-particle clusters (checked by the caller)
         auto kern = k_force8<NB_ELEC_EWALD_MLP, false, true>;

@@ -162,9 +162,12 @@ struct ForceParams {
     int tab_n;            // table intervals
     int ntypes;
     int use_pruned;
+    int prune;            // also prune the (outer) list being computed, at rp2
+    float rp2;
 };
 
 cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n_sm, cudaStream_t s);
+cudaError_t launch_prune_reset(const Workspace& ws, cudaStream_t s);
 cudaError_t launch_ewald_table(float2* tab, int n, double wmax, cudaStream_t s);
 cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int C, float* f_out, double* e_out,
                             double* vir_out, cudaStream_t s);

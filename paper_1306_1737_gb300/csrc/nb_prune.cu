@@ -261,6 +261,11 @@ __global__ void k_prune_reset(Workspace ws) {
     }
 }
 
+cudaError_t launch_prune_reset(const Workspace& ws, cudaStream_t s) {
+    k_prune_reset<<<1, 256, 0, s>>>(ws);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prune(const Workspace& ws, int C, float r_prune, int n_sm, cudaStream_t s) {
     PruneArgs A;
     A.ws = ws;
