@@ -695,6 +695,8 @@ def run_ours(args):
     force_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_FORCE]
     prune_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_PRUNE]
     fprune_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_FORCE_PRUNE]
+    final_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_FINALIZE]
+    coords_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_COORDS]
     search_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_SEARCH]
     grid_ms = [ms for kind, ms in spans if kind == nb.NB_KERNEL_GRID]
     pairs_outer = int(info.n_cluster_pairs) * 64
@@ -774,6 +776,9 @@ def run_ours(args):
                           "search": statistics.mean(search_ms) if search_ms else None,
                           "prune": statistics.mean(prune_ms) if prune_ms else None,
                           "force_prune": statistics.mean(fprune_ms) if fprune_ms else None,
+                          "finalize": statistics.mean(final_ms) if final_ms else None,
+                          "finalize_max": max(final_ms) if final_ms else None,
+                          "set_coords": statistics.mean(coords_ms) if coords_ms else None,
                           "force": t_force * 1e3},
             "list": {"clusters": int(info.n_clusters), "superclusters": int(info.n_superclusters),
                      "ientries": int(info.n_ientries), "jentries": int(info.n_jentries),

@@ -110,7 +110,9 @@ enum nb_kernel_kind {
     NB_KERNEL_FORCE = 3,   /* nb_compute's force/energy kernel */
     NB_KERNEL_FORCE_1X1 = 4, /* nb_compute_1x1's particle-pair force kernel */
     NB_KERNEL_RDF = 5,      /* nb_rdf's pair-distance histogram kernel */
-    NB_KERNEL_FORCE_PRUNE = 6 /* nb_prune_compute's fused force + prune kernel */
+    NB_KERNEL_FORCE_PRUNE = 6, /* nb_prune_compute's fused force + prune kernel */
+    NB_KERNEL_FINALIZE = 7,  /* forces back to caller order, energies and virial out */
+    NB_KERNEL_COORDS = 8     /* nb_set_coords (also inside the calls that take coordinates) */
 };
 
 /* --- context ------------------------------------------------------------ */

@@ -41,6 +41,8 @@ NB_KERNEL_FORCE = 3
 NB_KERNEL_FORCE_1X1 = 4
 NB_KERNEL_RDF = 5
 NB_KERNEL_FORCE_PRUNE = 6
+NB_KERNEL_FINALIZE = 7
+NB_KERNEL_COORDS = 8
 NB_RDF_MAX_BINS = 2048
 
 _lock = threading.Lock()

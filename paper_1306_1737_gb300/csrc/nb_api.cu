@@ -628,7 +628,9 @@ nb_status nb_set_coords(nb_ctx* c, const float* xyz, nb_stream stream) {
     if (!c->have_grid) return fail(c, NB_ERR_STATE, "nb_grid_put first");
     if (!xyz && c->n > 0) return fail(c, NB_ERR_ARG, "xyz is null");
     NB_CUDA(c, cudaSetDevice(c->device));
+    const int sp = span_begin(c, NB_KERNEL_COORDS, (cudaStream_t)stream);
     cudaError_t e = launch_set_coords(c->ws, c->C, xyz, (cudaStream_t)stream);
+    span_end(c, sp, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_coords kernel");
     c->n_launches += kLaunchesSetCoords;
     c->list_fresh = false;
@@ -685,7 +687,9 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     cudaError_t e = launch_force(c->ws, fp, c->C, c->n_sm, s);
     span_end(c, sp, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "force kernel");
+    const int sz = span_begin(c, NB_KERNEL_FINALIZE, s);
     e = launch_finalize(c->ws, fp, c->C, f, e_out, vir_out, s);
+    span_end(c, sz, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
     c->n_launches += 2 + (fp.want_energy ? 1 : 0);
     return NB_OK;
@@ -748,7 +752,9 @@ nb_status nb_prune_compute(nb_ctx* c, const nb_params* p, const float* xyz, floa
     c->r_prune = r_prune;
     c->have_pruned = true;
     c->last_valid = false;
+    const int sz = span_begin(c, NB_KERNEL_FINALIZE, s);
     e = launch_finalize(c->ws, fp, c->C, f, e_out, vir_out, s);
+    span_end(c, sz, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
     c->n_launches += 1 + (fp.want_energy ? 1 : 0);
     return NB_OK;
@@ -790,7 +796,9 @@ nb_status nb_compute_1x1(nb_ctx* c, const nb_params* p, const float* xyz, const 
     cudaError_t e = launch_force_1x1(c->ws, fp, c->C, max_nbr, nbr, count, s);
     span_end(c, sp, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "1x1 force kernel");
+    const int sz = span_begin(c, NB_KERNEL_FINALIZE, s);
     e = launch_finalize(c->ws, fp, c->C, f, nullptr, nullptr, s);
+    span_end(c, sz, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel");
     c->n_launches += 2;
     return NB_OK;
