@@ -486,7 +486,7 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
 }
 
 template <int ELEC, bool ENERGY, bool FIT, bool PRUNE = false>
-__global__ void __launch_bounds__(32 * kForceWarps, ELEC == NB_ELEC_EWALD_MLP ? 4 : (ENERGY ? 5 : (PRUNE ? 6 : 7)))
+__global__ void __launch_bounds__(32 * kForceWarps, ELEC == NB_ELEC_EWALD_MLP ? 4 : (ENERGY ? 5 : 7))
 k_force8(ForceArgs A) {
     extern __shared__ float2 s_lj[];
     __shared__ WarpSmem s_w[kForceWarps];
