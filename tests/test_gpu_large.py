@@ -5,7 +5,8 @@ the cluster-pair list and the pruned list compared key by key for sampled
 clusters, the forces of sampled particles (each against all 3M particles
 in the brute-force oracle) and of every particle (the oracle's cell-list
 tier) within 1e-4 of their RMS, and the FP64 energies and virial of the
-whole box within 1e-5 relative."""
+whole box within 1e-5 relative; the fused force + prune pass writes the
+same pruned list as the prune kernel."""
 import numpy as np
 import pytest
 
@@ -119,6 +120,18 @@ def test_config3_grid_list_prune_forces(env):
         fo5, _, _ = oracle.forces_brute(x5, b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx,
                                         b.box, oprm, sel=sel)
         emax, erms, _ = gp.force_errors(f5[sel], fo5)
+        assert emax < FORCE_TOL, (emax, erms)
+        # the fused force + prune pass on the same frame writes the same
+        # pruned list bit for bit (the separate pass above wrote it first, so
+        # the unused gaps match too) and forces of the same accuracy
+        _, ient_a, cj_a, m_a, _ = gb.list_arrays(1)
+        prm_f = nb.make_params("ewald", p["rc"], beta=p["beta"], want_energy=False)
+        nb.nb_prune_compute(gb.ctx, prm_f, torch.as_tensor(x5).to(gb.dev).contiguous(), rp, gb.f)
+        nb.nb_check(gb.ctx)
+        _, ient_b, cj_b, m_b, _ = gb.list_arrays(1)
+        assert np.array_equal(ient_a, ient_b) and np.array_equal(cj_a, cj_b) and np.array_equal(m_a, m_b)
+        f5b = gb.f.cpu().numpy().astype(np.float64)
+        emax, erms, _ = gp.force_errors(f5b[sel], fo5)
         assert emax < FORCE_TOL, (emax, erms)
     finally:
         gb.close()
