@@ -954,8 +954,10 @@ def run_batch(args):
         e2e_value = len(e2e_ms) * BATCH_H / (sum(e2e_ms) / 1000.0)
         del host
     groups_info = [{"C": g.spec.C, "nstlist": g.spec.nstlist, "rlist_nm": round(g.spec.rlist, 4),
+                    "nstprune": tuned.nstprune_of(g), "r_prune_nm": round(tuned.r_prune(g), 4),
                     "boxes": len(g.spec.boxes), "atoms": int(g.n)} for g in tuned.groups]
-    per_box = {int(k): f"{g.spec.C}/{g.spec.nstlist}" for g in tuned.groups for k in g.spec.boxes}
+    per_box = {int(k): f"{g.spec.C}/{g.spec.nstlist}/{tuned.nstprune_of(g)}" for g in tuned.groups
+               for k in g.spec.boxes}
     tuned.close()
 
     # 4. one context for all boxes (C = 8, nstlist 20, rlist 1.1), graph; its

@@ -7,7 +7,8 @@ step covers all boxes of a group in one launch (Sec. 2.3: the GPU needs tens
 of thousands of particles per launch to fill up; Sec. 4 reports the
 drop-off for small systems).  A step is a horizon of H frames; group g
 rebuilds its grid and list every nstlist_g frames (H a multiple of each),
-prunes every nstprune frames in between and evaluates forces every frame.
+prunes every nstprune_g frames in between (fused into that frame's force
+pass) and evaluates forces every frame.
 Groups run on their own CUDA streams, forked from and joined to the caller's
 stream, so small groups overlap; the whole step can be captured once in a
 CUDA graph and replayed.
@@ -28,6 +29,7 @@ class GroupSpec:
     nstlist: int             # frames per list lifetime
     rlist: float             # list radius (nm)
     boxes: list = field(default_factory=list)   # batch box indices
+    nstprune: int | None = None   # frames between prunes (None: the runner's)
 
 
 def scaled_rlist(rc: float, rlist0: float, nstlist0: int, nstlist: int) -> float:
@@ -108,9 +110,13 @@ class BatchRunner:
                        for g in groups if g.boxes]
         self.graph = None
 
+    def nstprune_of(self, g):
+        return self.nstprune if g.spec.nstprune is None else int(g.spec.nstprune)
+
     def r_prune(self, g):
         from paper_1306_1737_gb300 import workloads as w
-        return w.prune_radius(self.params["rc"], g.spec.rlist, self.nstprune) if self.nstprune else g.spec.rlist
+        nsp = self.nstprune_of(g)
+        return w.prune_radius(self.params["rc"], g.spec.rlist, nsp) if nsp else g.spec.rlist
 
     def _frame_ops(self, g, f, x, stream):
         """Launches of group g at frame f (coordinates x, a device tensor)."""
@@ -124,7 +130,7 @@ class BatchRunner:
             nb.nb_grid_put(ctx, x, g.boxes, stream)
             nb.nb_pairlist_build(ctx, float(np.float32(g.spec.rlist)), 0.0, g.excl_off, g.excl_idx, stream)
             nb.nb_compute(ctx, prm, None, g.F, g.E, g.V, stream)
-        elif self.nstprune and lf % self.nstprune == 0:
+        elif self.nstprune_of(g) and lf % self.nstprune_of(g) == 0:
             # prune while computing this frame's forces on the outer list
             nb.nb_prune_compute(ctx, prm, x, float(np.float32(self.r_prune(g))), g.F, g.E, g.V, stream)
         else:

@@ -5,7 +5,9 @@ count).  For every class and every candidate (cluster size C in {8, 4}, list
 lifetime nstlist with its scaled list radius) the class's boxes are run
 alone as one group for one horizon, captured in a CUDA graph, and timed with
 CUDA events; the candidate with the least device time per frame wins the
-class.  Winners are cached in a JSON file keyed by the GPU, the class's
+class.  The winner is then also timed with the other prune intervals of
+NSTPRUNES (each with its own prune radius, Sec. 2.3), and the fastest
+interval is kept.  Winners are cached in a JSON file keyed by the GPU, the class's
 sizes and the interaction parameters, so a later run with the same batch
 skips the timing.  Classes that chose the same candidate are merged into one
 group (one context).
@@ -28,6 +30,7 @@ from paper_1306_1737_gb300.batch import BatchRunner, GroupSpec, scaled_rlist
 
 CLUSTER_SIZES = (8, 4)
 NSTLISTS = (10, 20, 40)
+NSTPRUNES = (2, 5, 10)
 
 
 def _classes(counts, n_classes):
@@ -39,7 +42,7 @@ def _key(gpu, counts, boxes, params, rlist0, nstlist0, nstprune, H):
     d = {"gpu": gpu, "counts": [int(c) for c in counts], "boxes": np.round(boxes, 6).tolist(),
          "elec": params["elec"], "rc": params["rc"], "beta": params.get("beta"), "rlist0": rlist0,
          "nstlist0": nstlist0, "nstprune": nstprune, "H": H,
-         "candidates": [list(CLUSTER_SIZES), list(NSTLISTS)]}
+         "candidates": [list(CLUSTER_SIZES), list(NSTLISTS), list(NSTPRUNES)]}
     return hashlib.sha1(json.dumps(d, sort_keys=True).encode()).hexdigest()[:16]
 
 
@@ -93,7 +96,9 @@ def appendix_rlist(classes, c6c12, volume, params, nstlist, dt_ps=0.002, tempera
 def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nstprune, rlist0, nstlist0,
          n_classes=4, reps=3, cache_path=None, device=0, log=None, rlist_rule="sqrt", mass=None,
          tolerance=None):
-    """Returns (groups: list of GroupSpec, table: list of per-class results).
+    """Returns (groups: list of GroupSpec, table: list of per-class results;
+    a result key is "C/nstlist" at the configured prune interval or
+    "C/nstlist/nstprune").
 
     rlist_rule: "sqrt" scales the configured buffer with sqrt(nstlist /
     nstlist0); "appendix" sizes it with the Appendix's drift bound (needs
@@ -141,14 +146,28 @@ def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nst
                         log(f"class {len(cls)} boxes {int(counts[cls].min())}-{int(counts[cls].max())} atoms: "
                             f"C={C} nstlist={nst}: {t:.4f} ms/frame")
             best = min(times, key=times.get)
+            # second stage: other prune intervals for the winning shape and lifetime
+            bC, bn = map(int, best.split("/"))
+            for nsp in NSTPRUNES:
+                if nsp == nstprune or nsp >= bn:
+                    continue
+                spec = GroupSpec(bC, bn, rlist_of[bn], list(cls), nstprune=nsp)
+                t = time_group(spec, counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params,
+                               nstprune, device, reps)
+                times[f"{bC}/{bn}/{nsp}"] = t
+                if log:
+                    log(f"class {len(cls)} boxes: C={bC} nstlist={bn} nstprune={nsp}: {t:.4f} ms/frame")
+            best = min(times, key=times.get)
             ent = {"best": best, "ms_per_frame": times, "cached": False}
             cache[key] = {k: v for k, v in ent.items() if k != "cached"}
-        C, nst = map(int, ent["best"].split("/"))
-        choice.setdefault((C, nst), []).extend(cls)
+        parts = list(map(int, ent["best"].split("/")))
+        C, nst = parts[0], parts[1]
+        nsp = parts[2] if len(parts) > 2 else nstprune
+        choice.setdefault((C, nst, nsp), []).extend(cls)
         table.append({"boxes": len(cls), "atoms_min": int(counts[cls].min()), "atoms_max": int(counts[cls].max()),
                       "best": ent["best"], "ms_per_frame": ent["ms_per_frame"], "cached": ent["cached"]})
     if cache_path:
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
         json.dump(cache, open(cache_path, "w"), indent=1, sort_keys=True)
-    groups = [GroupSpec(C, nst, rlist_of[nst], sorted(b)) for (C, nst), b in sorted(choice.items())]
+    groups = [GroupSpec(C, nst, rlist_of[nst], sorted(b), nstprune=nsp) for (C, nst, nsp), b in sorted(choice.items())]
     return groups, table

@@ -155,7 +155,8 @@ def test_batch_box_change_and_errors(env):
 
 
 def test_batch_runner_groups_graph(env):
-    """Two groups (C = 8 with nstlist 10, C = 4 with nstlist 20) stepped over
+    """Two groups (C = 8 with nstlist 10 pruning every 2 frames, C = 4 with
+    nstlist 20 pruning every 5) stepped over
     20 frames on their own streams and captured in a CUDA graph: after a
     replay, every box's last-frame forces and energies match the oracle."""
     torch, dev, nb = env
@@ -165,7 +166,7 @@ def test_batch_runner_groups_graph(env):
     p = {"elec": "ewald", "rc": 1.0, "rlist": 1.1, "beta": 3.12}
     H = 20
     fr = torch.stack([torch.from_numpy(x) for x in w.frame_walk(B.xyz, B.mass, H, seed=7300)]).to(dev)
-    groups = [GroupSpec(8, 10, scaled_rlist(1.0, 1.1, 20, 10), [0, 2]),
+    groups = [GroupSpec(8, 10, scaled_rlist(1.0, 1.1, 20, 10), [0, 2], nstprune=2),
               GroupSpec(4, 20, 1.1, [1, 3])]
     r = BatchRunner(B.counts, B.boxes, B.q, B.types, nb.nb_lj_combine(B.sigma, B.eps), B.excl_off,
                     B.excl_idx, fr, groups, p, nstprune=5)
