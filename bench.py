@@ -95,6 +95,30 @@ def profiled_traffic(workload):
     return traffic if src == force_source_hash() else None
 
 
+def profiled_counters(workload):
+    """ncu issue and FP32-pipe figures of the force kernel from the committed
+    summary of this workload (None when taken on other kernel sources)."""
+    path = os.path.join(ROOT, "profiles", f"k_force8_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    keys = {"source-hash": "src", "issue-active-pct": "issue_slots_busy_pct",
+            "fma-pipe-cycles-active-pct": "fma_pipe_cycles_active_pct",
+            "fp32-lane-ops-pct": "fp32_lane_ops_pct_of_issue_peak", "counters-from": "profile"}
+    out = {}
+    for line in open(path):
+        k, _, v = line.partition(":")
+        if k.strip() in keys:
+            v = v.strip()
+            try:
+                v = float(v)
+            except ValueError:
+                pass
+            out[keys[k.strip()]] = v
+    if out.pop("src", None) != force_source_hash() or "issue_slots_busy_pct" not in out:
+        return None
+    return out
+
+
 def peaks():
     p = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -723,6 +747,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": "k_force8 (Ewald)" if elec == "ewald" else "k_force8 (RF)",
                 "achieved": achieved / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": profiled_traffic(args.workload),
+                "ncu": profiled_counters(args.workload),
                 "traffic_unit": "bytes per launch (dram read + write, ncu)",
                 "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {pk['sm_max_mhz']:.0f} MHz "
                                f"(max SM clock, {pk['source']})",
