@@ -95,6 +95,21 @@ def profiled_traffic(workload):
     return traffic if src == force_source_hash() else None
 
 
+def scaled_traffic(cluster_pairs):
+    """DRAM bytes of a force launch over cluster_pairs cluster pairs, scaled
+    from the 1M-box capture (the kernel reads each list entry and particle
+    once, so its traffic is proportional to the cluster pairs), or None when
+    that capture was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "k_force8_water1m.md")
+    t = profiled_traffic("water1m")
+    if t is None:
+        return None
+    for line in open(path):
+        if line.startswith("cluster-pairs-per-launch:"):
+            return t * cluster_pairs / float(line.split(":", 1)[1])
+    return None
+
+
 def profiled_counters(workload):
     """ncu issue and FP32-pipe figures of the force kernel from the committed
     summary of this workload (None when taken on other kernel sources)."""
@@ -1049,7 +1064,10 @@ def run_batch(args):
                       "per_box_choice": per_box},
             "roofline": {"bound": "alu", "kernel": "k_force8 (Ewald), one context for all 256 boxes",
                          "achieved": flops / t_force / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-                         "frac": flops / t_force / fp32_peak, "traffic": None,
+                         "frac": flops / t_force / fp32_peak, "traffic": scaled_traffic(listed / 64.0),
+                         "traffic_note": "dram read + write per launch, scaled by cluster pairs from the 1M-box "
+                                         "ncu capture (profiles/k_force8_water1m.md)",
+                         "ncu": profiled_counters("water1m"), "listed_pairs_per_launch": listed,
                          "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {pk['sm_max_mhz']:.0f} MHz "
                                         f"(max SM clock, {pk['source']})",
                          "algorithmic_flops_per_launch": flops, "launch_ms": t_force * 1e3},
