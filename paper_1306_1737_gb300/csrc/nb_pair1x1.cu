@@ -6,9 +6,9 @@
 //   neighbour list (every pair within rlist stored for both particles),
 //   one warp per i-entry; entries pack the neighbour's slot, the periodic
 //   shift and whether the pair is force-field excluded.
-// k_force_1x1: one thread per particle walks its neighbours, computes each
-//   pair with the cluster kernels' pair function (Sec. 3.2), keeps the force
-//   in registers and writes it once (no atomics: the list is full, each pair
+// k_force_1x1: 4 to 16 lanes per particle walk its neighbours, compute each
+//   pair with the cluster kernels' pair function (Sec. 3.2), sum the force
+//   with shuffles and write it once (no atomics: the list is full, each pair
 //   is computed twice).
 #include "nb_internal.cuh"
 #include "nb_pair.cuh"
@@ -106,10 +106,15 @@ struct Force1x1Args {
     const int* count;
 };
 
-// One thread per slot (consecutive threads hold neighbouring particles).
-// Neighbour slots come from the list, which holds current slots only.
-template <int ELEC, bool FIT>
+// TPP consecutive lanes per slot (consecutive slot groups hold neighbouring
+// particles): lane r of a group takes neighbours r, r + TPP, ... of the
+// slot's list, and the group sums its partial forces with shuffles, so a box
+// of a few ten thousand particles still fills the GPU (TPP = 16, 8 or 4 for
+// small, medium and large boxes: the fastest measured per size).  Neighbour
+// slots come from the list, which holds current slots only.
+template <int ELEC, bool FIT, int TPP>
 __global__ void __launch_bounds__(256) k_force_1x1(Force1x1Args A) {
+    constexpr int kTpp = TPP;
     extern __shared__ float2 s_lj[];
     const int nt2 = A.p.ntypes * A.p.ntypes;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
@@ -117,53 +122,73 @@ __global__ void __launch_bounds__(256) k_force_1x1(Force1x1Args A) {
         s_lj[k] = make_float2(6.0f * v.x, 12.0f * v.y);
     }
     __syncthreads();
+    const unsigned full = 0xffffffffu;
     const Workspace& W = A.ws;
+    const int r = threadIdx.x % kTpp;
     const long long nslot = (long long)W.clu_total * A.C;
-    for (long long si = blockIdx.x * (long long)blockDim.x + threadIdx.x; si < nslot;
-         si += (long long)gridDim.x * blockDim.x) {
-        // only the slots of each box's current clusters hold particles; the
-        // rest of the box's slot region is unused capacity
-        const int g = (int)(si / A.C);
-        const int b = find_box(W.lay.clu_off, W.nbox, g);
-        if (g - W.lay.clu_off[b] >= W.st[b].nclu) continue;
-        const int a = W.atom_of_slot[si];
-        if (a < 0 || a >= W.atom_total) continue;
-        const float* L = W.geo[b].L;
-        const float4 xi = W.xyzq[si];
-        const float qi = xi.w * A.p.fcoul;
-        const int ti = W.type_slot[si] * A.p.ntypes;
-        const int cnt = min(A.count[a], A.max_nbr);
-        const int* list = A.nbr + (long long)a * A.max_nbr;
-        float fx = 0.f, fy = 0.f, fz = 0.f;
-        for (int k = 0; k < cnt; ++k) {
-            const int v = list[k];
-            const int sj = (int)((unsigned)v >> kNbrSlotShift), s = v & (kNbrExclBit - 1);
-            const float bit = (v & kNbrExclBit) ? 0.0f : 1.0f;
-            const float4 xj = W.xyzq[sj];
-            float dx, dy, dz;
-            if (s == kShiftCenter) {
-                dx = xi.x - xj.x;
-                dy = xi.y - xj.y;
-                dz = xi.z - xj.z;
-            } else {
-                float sh[3], h, l;
-                shift_vector(s, L, sh);
-                two_sum(xi.x, sh[0], h, l);
-                dx = (h - xj.x) + l;
-                two_sum(xi.y, sh[1], h, l);
-                dy = (h - xj.y) + l;
-                two_sum(xi.z, sh[2], h, l);
-                dz = (h - xj.z) + l;
+    const long long stride = (long long)gridDim.x * (blockDim.x / kTpp);
+    // whole warps iterate together (the group reduction is a warp shuffle)
+    const long long warp_first = ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / kTpp;
+    for (long long base = warp_first; base < nslot; base += stride) {
+        const long long si = base + (threadIdx.x & 31) / kTpp;
+        bool live = si < nslot;
+        int a = -1, b = 0;
+        if (live) {
+            // only the slots of each box's current clusters hold particles; the
+            // rest of the box's slot region is unused capacity
+            const int g = (int)(si / A.C);
+            b = find_box(W.lay.clu_off, W.nbox, g);
+            if (g - W.lay.clu_off[b] >= W.st[b].nclu) live = false;
+            else {
+                a = W.atom_of_slot[si];
+                if (a < 0 || a >= W.atom_total) live = false;
             }
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const bool inc = r2 < A.p.rc2;
-            float fs, vl, vc;
-            pair_fn<ELEC, false, FIT>(A.p, inc, bit, r2, qi * xj.w, s_lj[ti + W.type_slot[sj]], fs, vl, vc);
-            fx = fmaf(fs, dx, fx);
-            fy = fmaf(fs, dy, fy);
-            fz = fmaf(fs, dz, fz);
         }
-        W.fslot[si] = make_float4(fx, fy, fz, 0.0f);
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (live) {
+            const float* L = W.geo[b].L;
+            xi = W.xyzq[si];
+            const float qi = xi.w * A.p.fcoul;
+            const int ti = W.type_slot[si] * A.p.ntypes;
+            const int cnt = min(A.count[a], A.max_nbr);
+            const int* list = A.nbr + (long long)a * A.max_nbr;
+            for (int k = r; k < cnt; k += kTpp) {
+                const int v = list[k];
+                const int sj = (int)((unsigned)v >> kNbrSlotShift), s = v & (kNbrExclBit - 1);
+                const float bit = (v & kNbrExclBit) ? 0.0f : 1.0f;
+                const float4 xj = W.xyzq[sj];
+                float dx, dy, dz;
+                if (s == kShiftCenter) {
+                    dx = xi.x - xj.x;
+                    dy = xi.y - xj.y;
+                    dz = xi.z - xj.z;
+                } else {
+                    float sh[3], h, l;
+                    shift_vector(s, L, sh);
+                    two_sum(xi.x, sh[0], h, l);
+                    dx = (h - xj.x) + l;
+                    two_sum(xi.y, sh[1], h, l);
+                    dy = (h - xj.y) + l;
+                    two_sum(xi.z, sh[2], h, l);
+                    dz = (h - xj.z) + l;
+                }
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const bool inc = r2 < A.p.rc2;
+                float fs, vl, vc;
+                pair_fn<ELEC, false, FIT>(A.p, inc, bit, r2, qi * xj.w, s_lj[ti + W.type_slot[sj]], fs, vl, vc);
+                fx = fmaf(fs, dx, fx);
+                fy = fmaf(fs, dy, fy);
+                fz = fmaf(fs, dz, fz);
+            }
+        }
+#pragma unroll
+        for (int o = kTpp / 2; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(full, fx, o);
+            fy += __shfl_xor_sync(full, fy, o);
+            fz += __shfl_xor_sync(full, fz, o);
+        }
+        if (live && r == 0) W.fslot[si] = make_float4(fx, fy, fz, 0.0f);
     }
 }
 
@@ -195,15 +220,25 @@ cudaError_t launch_force_1x1(const Workspace& ws, const ForceParams& p, int C, i
     A.nbr = nbr;
     A.count = count;
     const size_t smem = sizeof(float2) * p.ntypes * p.ntypes;
-    long long blocks = ((long long)ws.clu_total * C + 255) / 256;
+    const long long nslot = (long long)ws.clu_total * C;
+    const int tpp = nslot < (1 << 17) ? 16 : (nslot < (1 << 20) ? 8 : 4);
+    long long blocks = (nslot * tpp + 255) / 256;
     if (blocks > 65535) blocks = 65535;
     if (blocks < 1) blocks = 1;
-    if (p.elec == NB_ELEC_RF)
-        k_force_1x1<NB_ELEC_RF, false><<<(int)blocks, 256, smem, s>>>(A);
-    else if (p.use_fit)
-        k_force_1x1<NB_ELEC_EWALD, true><<<(int)blocks, 256, smem, s>>>(A);
-    else
-        k_force_1x1<NB_ELEC_EWALD, false><<<(int)blocks, 256, smem, s>>>(A);
+    const int nb = (int)blocks;
+    if (p.elec == NB_ELEC_RF) {
+        if (tpp == 16) k_force_1x1<NB_ELEC_RF, false, 16><<<nb, 256, smem, s>>>(A);
+        else if (tpp == 8) k_force_1x1<NB_ELEC_RF, false, 8><<<nb, 256, smem, s>>>(A);
+        else k_force_1x1<NB_ELEC_RF, false, 4><<<nb, 256, smem, s>>>(A);
+    } else if (p.use_fit) {
+        if (tpp == 16) k_force_1x1<NB_ELEC_EWALD, true, 16><<<nb, 256, smem, s>>>(A);
+        else if (tpp == 8) k_force_1x1<NB_ELEC_EWALD, true, 8><<<nb, 256, smem, s>>>(A);
+        else k_force_1x1<NB_ELEC_EWALD, true, 4><<<nb, 256, smem, s>>>(A);
+    } else {
+        if (tpp == 16) k_force_1x1<NB_ELEC_EWALD, false, 16><<<nb, 256, smem, s>>>(A);
+        else if (tpp == 8) k_force_1x1<NB_ELEC_EWALD, false, 8><<<nb, 256, smem, s>>>(A);
+        else k_force_1x1<NB_ELEC_EWALD, false, 4><<<nb, 256, smem, s>>>(A);
+    }
     return cudaGetLastError();
 }
 
