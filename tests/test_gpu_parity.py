@@ -14,7 +14,7 @@ from paper_1306_1737_gb300 import workloads as w
 
 pytestmark = pytest.mark.gpu
 
-FORCE_TOL = 1e-4   # max |dF| / RMS |F|  (spec bound)
+FORCE_TOL = 1e-4   # max |dF| / RMS |F|  (required force accuracy)
 EXEMPT_NM = 1e-6   # list keys this close to the threshold may differ
 E_TOL = 1e-5       # relative error of FP64 totals of FP32 pair terms
 
