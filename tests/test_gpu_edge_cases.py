@@ -2,7 +2,8 @@
 particles than a cluster, particles on cell edges and on the periodic
 boundaries (including coordinates in [-L, 0) and [L, 2L)), equal z values
 (ties broken by particle index), empty grid columns, and a box that is a
-single column."""
+single column; on each, the pair-distance histogram against the oracle and
+the fused force + prune pass against the separate prune."""
 import math
 
 import numpy as np
@@ -108,5 +109,28 @@ def test_edge_cases(gp, C):
             else:
                 assert np.abs(f).max() == 0.0, name
             assert np.allclose(e, eo, rtol=1e-5, atol=1e-6), (name, e, eo)
+            # pair-distance histogram on the fresh list
+            h = gb.torch.zeros((1, 51), dtype=gb.torch.int64, device=gb.dev)
+            nb.nb_rdf(gb.ctx, rlf, 50, -1, -1, 0, h)
+            hg = h.cpu().numpy()[0]
+            ho, near = oracle.rdf(b.xyz, b.types, b.box, rlf, 50, b.excl_off, b.excl_idx, delta=2e-6)
+            G = np.concatenate([[0], np.cumsum(hg[:50])])
+            H = np.concatenate([[0], np.cumsum(ho)])
+            assert np.all(np.abs(G - H) <= near), name
+            # the separate prune and the fused force + prune pass: the same pruned list
+            rp = 0.95
+            nb.nb_prune(gb.ctx, None, rp)
+            nb.nb_check(gb.ctx)
+            _, ient_a, cj_a, m_a, _ = gb.list_arrays(1)
+            nb.nb_prune_compute(gb.ctx, nb.make_params("ewald", rc, beta=3.12, want_energy=False), None, rp, gb.f)
+            nb.nb_check(gb.ctx)
+            _, ient_b, cj_b, m_b, _ = gb.list_arrays(1)
+            assert np.array_equal(ient_a, ient_b) and np.array_equal(cj_a, cj_b) and np.array_equal(m_a, m_b), name
+            f2 = gb.f.cpu().numpy().astype(np.float64)
+            if np.abs(fo).max() > 0:
+                emax, _, _ = gp.force_errors(f2, fo)
+                assert emax < 1e-4, (name, emax)
+            else:
+                assert np.abs(f2).max() == 0.0, name
         finally:
             gb.close()
