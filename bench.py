@@ -1025,7 +1025,7 @@ def run_batch(args):
             at = torch.as_tensor(g.atoms)
             hx = fr_cpu.index_select(1, at).contiguous().pin_memory()
             hf = torch.empty_like(hx).pin_memory()
-            host.append((hx, hf, torch.empty((g.n, 3), dtype=torch.float32, device=dev)))
+            host.append((hx, hf))
         del fr_cpu
         tuned.step(host=host)
         torch.cuda.synchronize()

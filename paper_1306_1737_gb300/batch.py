@@ -118,31 +118,34 @@ class BatchRunner:
         nsp = self.nstprune_of(g)
         return w.prune_radius(self.params["rc"], g.spec.rlist, nsp) if nsp else g.spec.rlist
 
-    def _frame_ops(self, g, f, x, stream):
-        """Launches of group g at frame f (coordinates x, a device tensor)."""
+    def _frame_ops(self, g, f, x, stream, F=None):
+        """Launches of group g at frame f (coordinates x, a device tensor;
+        forces into F, default the group's buffer)."""
         p = self.params
         lf = f % g.spec.nstlist
         energy = f == 0 or f == self.H - 1
         prm = nb.make_params(p["elec"], p["rc"], eps_rf=p.get("eps_rf", math.inf), beta=p.get("beta", 0.0),
                              want_energy=energy)
         ctx = g.cx.ctx
+        F = g.F if F is None else F
         if lf == 0:
             nb.nb_grid_put(ctx, x, g.boxes, stream)
             nb.nb_pairlist_build(ctx, float(np.float32(g.spec.rlist)), 0.0, g.excl_off, g.excl_idx, stream)
-            nb.nb_compute(ctx, prm, None, g.F, g.E, g.V, stream)
+            nb.nb_compute(ctx, prm, None, F, g.E, g.V, stream)
         elif self.nstprune_of(g) and lf % self.nstprune_of(g) == 0:
             # prune while computing this frame's forces on the outer list
-            nb.nb_prune_compute(ctx, prm, x, float(np.float32(self.r_prune(g))), g.F, g.E, g.V, stream)
+            nb.nb_prune_compute(ctx, prm, x, float(np.float32(self.r_prune(g))), F, g.E, g.V, stream)
         else:
-            nb.nb_compute(ctx, prm, x, g.F, g.E, g.V, stream)
+            nb.nb_compute(ctx, prm, x, F, g.E, g.V, stream)
 
     def step(self, concurrent=True, host=None):
         """One horizon of H frames for every group.  concurrent: each group
         on its own stream (forked from and joined to the current stream),
         else all groups one after another on the current stream.  host: per
-        group (pinned frames [H, n_g, 3], pinned forces [H, n_g, 3], device
-        buffer [n_g, 3]) -- each frame's coordinates are copied in and its
-        forces copied out inside the step."""
+        group (pinned frames [H, n_g, 3], pinned forces [H, n_g, 3]) -- each
+        frame's coordinates are copied in and its forces copied out inside
+        the step, on a copy stream per group and with two device buffers of
+        each, so the transfers overlap the neighbouring frames' kernels."""
         torch = self.torch
         main = torch.cuda.current_stream()
         fork = torch.cuda.Event()
@@ -152,20 +155,53 @@ class BatchRunner:
             if concurrent:
                 st.wait_event(fork)
             with torch.cuda.stream(st):
-                for f in range(self.H):
-                    if host is None:
-                        x = g.frames[f]
-                    else:
-                        hx, hf, xbuf = host[gi]
-                        xbuf.copy_(hx[f], non_blocking=True)
-                        x = xbuf
-                    self._frame_ops(g, f, x, st)
-                    if host is not None:
-                        hf[f].copy_(g.F, non_blocking=True)
+                if host is None:
+                    for f in range(self.H):
+                        self._frame_ops(g, f, g.frames[f], st)
+                else:
+                    self._host_frames(g, host[gi], st)
             if concurrent:
                 join = torch.cuda.Event()
                 join.record(st)
                 main.wait_event(join)
+
+    def _host_frames(self, g, host, st):
+        """The H frames of group g from pinned host frames to pinned host
+        forces: frame f + 1's coordinates are copied in while frame f
+        computes and frame f's forces are read back while frame f + 1
+        computes (copy stream, two buffers each, ordered by events)."""
+        torch = self.torch
+        hx, hf = host
+        if not hasattr(g, "pipe"):
+            dev = g.F.device
+            g.pipe = {"cs": torch.cuda.Stream(device=dev),
+                      "x": [torch.empty_like(g.F) for _ in range(2)],
+                      "F": [torch.empty_like(g.F) for _ in range(2)],
+                      "ev": [[torch.cuda.Event() for _ in range(2)] for _ in range(4)]}
+        cs, xb, Fb = g.pipe["cs"], g.pipe["x"], g.pipe["F"]
+        x_ready, x_free, f_done, f_free = g.pipe["ev"]
+        cs.wait_stream(st)
+        with torch.cuda.stream(cs):
+            xb[0].copy_(hx[0], non_blocking=True)
+            x_ready[0].record(cs)
+        for f in range(self.H):
+            k = f % 2
+            if f + 1 < self.H:
+                kn = (f + 1) % 2
+                cs.wait_event(x_free[kn])
+                with torch.cuda.stream(cs):
+                    xb[kn].copy_(hx[f + 1], non_blocking=True)
+                    x_ready[kn].record(cs)
+            st.wait_event(x_ready[k])
+            st.wait_event(f_free[k])
+            self._frame_ops(g, f, xb[k], st, Fb[k])
+            x_free[k].record(st)
+            f_done[k].record(st)
+            cs.wait_event(f_done[k])
+            with torch.cuda.stream(cs):
+                hf[f].copy_(Fb[k], non_blocking=True)
+                f_free[k].record(cs)
+        st.wait_stream(cs)
 
     def capture(self, concurrent=True):
         """Capture one step in a CUDA graph (after an eager step has set up
