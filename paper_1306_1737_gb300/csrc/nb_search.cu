@@ -64,8 +64,10 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
     __shared__ float4 s_h[kSearchWarps][NA];   // i particles shifted by the current shift: hi part
     __shared__ float4 s_l[kSearchWarps][NA];   // and lo part (TwoSum)
     __shared__ float s_bb[kSearchWarps][S][12];  // shifted BB: lo hi/lo, hi hi/lo per dimension
-    __shared__ int s_ex_r[kSearchWarps][kMaxExclPerSuper];
-    __shared__ int s_ex_s[kSearchWarps][kMaxExclPerSuper];
+    // the super-cluster's exclusions: one copy per warp, or one per block
+    // when the block's warps share the super-cluster
+    __shared__ int s_ex_r[COOP ? 1 : kSearchWarps][kMaxExclPerSuper];
+    __shared__ int s_ex_s[COOP ? 1 : kSearchWarps][kMaxExclPerSuper];
     __shared__ int s_buf_w[kSearchWarps][kJChunk];
     __shared__ unsigned long long s_buf_m[kSearchWarps][S][kJChunk];
     __shared__ float4 s_xc[kSearchWarps][COOP ? 32 * C : 1];  // particles of a batch's candidates
@@ -75,6 +77,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
     const float eps = 1e-4f;
     int b = 0;
     const int part = COOP ? wib : 0;
+    const int xw = COOP ? 0 : wib;   // the exclusion table this warp uses
     constexpr int P = COOP ? kSearchWarps : 1;
     constexpr int JC = COOP ? kJChunkCoop : kJChunk;   // j-entries per i-entry at most
     const int q0 = COOP ? blockIdx.x : blockIdx.x * kSearchWarps + wib;
@@ -121,12 +124,15 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                     const int qa = A.excl_idx[off + k];
                     const bool ok = qa >= 0 && qa < W.atom_total;
                     if (!ok) set_flag(st, NB_ERR_ARG);
-                    s_ex_r[wib][idx] = lane;
-                    s_ex_s[wib][idx] = ok ? W.slot_of_atom[qa] : -1;
+                    if (!COOP || wib == 0) {
+                        s_ex_r[xw][idx] = lane;
+                        s_ex_s[xw][idx] = ok ? W.slot_of_atom[qa] : -1;
+                    }
                 }
             }
             nex = min(total, kMaxExclPerSuper);
         }
+        if constexpr (COOP) __syncthreads();   // warp 0's exclusion table is complete
         __syncwarp();
 
         for (int s = 0; s < 27; ++s) {
@@ -379,8 +385,8 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                                 }
                                 unsigned lo32 = 0, hi32 = 0;
                                 for (int e = lane; e < nex; e += 32) {
-                                    const int sl = s_ex_s[wib][e];
-                                    const int r = s_ex_r[wib][e];
+                                    const int sl = s_ex_s[xw][e];
+                                    const int r = s_ex_r[xw][e];
                                     if (sl >= 0 && r / C == k && sl / C == bt) {
                                         const int bit = (r % C) * C + sl % C;
                                         if (bit < 32) lo32 |= 1u << bit;
