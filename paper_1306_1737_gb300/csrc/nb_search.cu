@@ -364,43 +364,48 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                             }
                         }
                     }
-                    unsigned accepted = __ballot_sync(full, acc != 0);
-                    while (accepted) {
-                        const int t = __ffs(accepted) - 1;
-                        accepted &= accepted - 1;
-                        const int bt = __shfl_sync(full, cb_, t);
-                        const unsigned at = __shfl_sync(full, acc, t);
-                        const unsigned realB = __shfl_sync(full, realB_mine, t);
+                    // exclusion masks of the accepted candidates, one candidate per
+                    // lane (bit i*C + j set: both particles real, distinct on the
+                    // diagonal, not force-field excluded), appended to the buffer in
+                    // lane order
+                    const unsigned accepted = __ballot_sync(full, acc != 0);
+                    unsigned long long my_m[S];
 #pragma unroll
-                        for (int k = 0; k < S; ++k) {
-                            unsigned long long m = 0;
-                            if ((at >> k) & 1u) {
-                                const unsigned realA = (realAll >> (k * C)) & ((1u << C) - 1u);
+                    for (int k = 0; k < S; ++k) {
+                        unsigned long long m = 0;
+                        if ((acc >> k) & 1u) {
+                            const unsigned realA = (realAll >> (k * C)) & ((1u << C) - 1u);
+                            unsigned long long rows = 0;   // bit i*C for every real i-particle
 #pragma unroll
-                                for (int i = 0; i < C; ++i)
-                                    if ((realA >> i) & 1u) m |= (unsigned long long)realB << (i * C);
-                                if (bt == g0 + k) {
-                                    if (s == kShiftCenter) m &= upper_mask<C>();
-                                    else m &= ~diag_mask<C>();
-                                }
-                                unsigned lo32 = 0, hi32 = 0;
-                                for (int e = lane; e < nex; e += 32) {
-                                    const int sl = s_ex_s[xw][e];
-                                    const int r = s_ex_r[xw][e];
-                                    if (sl >= 0 && r / C == k && sl / C == bt) {
-                                        const int bit = (r % C) * C + sl % C;
-                                        if (bit < 32) lo32 |= 1u << bit;
-                                        else hi32 |= 1u << (bit - 32);
-                                    }
-                                }
-                                lo32 = __reduce_or_sync(full, lo32);
-                                hi32 = __reduce_or_sync(full, hi32);
-                                m &= ~(((unsigned long long)hi32 << 32) | lo32);
+                            for (int i = 0; i < C; ++i)
+                                if ((realA >> i) & 1u) rows |= 1ull << (i * C);
+                            // rows of C bits never overlap, so the product places the
+                            // candidate's real j-bits in every real i-row
+                            m = rows * (unsigned long long)realB_mine;
+                            if (cb_ == g0 + k) {
+                                if (s == kShiftCenter) m &= upper_mask<C>();
+                                else m &= ~diag_mask<C>();
                             }
-                            if (lane == 0) s_buf_m[wib][k][nbuf] = m;
+                            for (int e = 0; e < nex; ++e) {
+                                const int sl = s_ex_s[xw][e];
+                                const int r = s_ex_r[xw][e];
+                                if (sl >= 0 && r / C == k && sl / C == cb_) m &= ~(1ull << ((r % C) * C + sl % C));
+                            }
                         }
-                        if (lane == 0) s_buf_w[wib][nbuf] = bt | (int)(at << kSuperShift);
-                        ++nbuf;
+                        my_m[k] = m;
+                    }
+                    const int n_acc = __popc(accepted);
+                    const int my_pos = __popc(accepted & ((1u << lane) - 1u));
+                    for (int done = 0; done < n_acc;) {
+                        const int take = min(JC - nbuf, n_acc - done);
+                        if (acc && my_pos >= done && my_pos < done + take) {
+                            const int slot = nbuf + my_pos - done;
+                            s_buf_w[wib][slot] = cb_ | (int)(acc << kSuperShift);
+#pragma unroll
+                            for (int k = 0; k < S; ++k) s_buf_m[wib][k][slot] = my_m[k];
+                        }
+                        nbuf += take;
+                        done += take;
                         if (nbuf == JC) flush();
                     }
                 }
