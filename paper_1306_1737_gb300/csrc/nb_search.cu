@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
         }
         // force-field exclusions of the super-cluster's particles: (row, excluded slot)
         int nex = 0;
+        int ex_lo = 0x7fffffff, ex_hi = -1;   // range of the excluded partners' clusters
         if (A.excl_off) {
             int cnt = 0, off = 0;
             if (aos >= 0) {
@@ -124,13 +125,20 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                     const int qa = A.excl_idx[off + k];
                     const bool ok = qa >= 0 && qa < W.atom_total;
                     if (!ok) set_flag(st, NB_ERR_ARG);
+                    const int sl = ok ? W.slot_of_atom[qa] : -1;
+                    if (sl >= 0) {
+                        ex_lo = min(ex_lo, sl / C);
+                        ex_hi = max(ex_hi, sl / C);
+                    }
                     if (!COOP || wib == 0) {
                         s_ex_r[xw][idx] = lane;
-                        s_ex_s[xw][idx] = ok ? W.slot_of_atom[qa] : -1;
+                        s_ex_s[xw][idx] = sl;
                     }
                 }
             }
             nex = min(total, kMaxExclPerSuper);
+            ex_lo = __reduce_min_sync(full, ex_lo);
+            ex_hi = __reduce_max_sync(full, ex_hi);
         }
         if constexpr (COOP) __syncthreads();   // warp 0's exclusion table is complete
         __syncwarp();
@@ -386,10 +394,14 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 6) k_search(SearchArgs A) {
                                 if (s == kShiftCenter) m &= upper_mask<C>();
                                 else m &= ~diag_mask<C>();
                             }
-                            for (int e = 0; e < nex; ++e) {
-                                const int sl = s_ex_s[xw][e];
-                                const int r = s_ex_r[xw][e];
-                                if (sl >= 0 && r / C == k && sl / C == cb_) m &= ~(1ull << ((r % C) * C + sl % C));
+                            // only candidates in the range of excluded partners' clusters scan
+                            if (cb_ >= ex_lo && cb_ <= ex_hi) {
+                                for (int e = 0; e < nex; ++e) {
+                                    const int sl = s_ex_s[xw][e];
+                                    const int r = s_ex_r[xw][e];
+                                    if (sl >= 0 && r / C == k && sl / C == cb_)
+                                        m &= ~(1ull << ((r % C) * C + sl % C));
+                                }
                             }
                         }
                         my_m[k] = m;
