@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnbcluster.so")
-SOURCES = ["nb_api.cu", "nb_grid.cu", "nb_search.cu", "nb_prune.cu", "nb_force.cu", "nb_noalloc.cu", "nb_mlp.cu", "nb_pair1x1.cu", "nb_buffer.cu", "nb_rdf.cu"]
+SOURCES = ["nb_api.cu", "nb_grid.cu", "nb_search.cu", "nb_prune.cu", "nb_force.cu", "nb_noalloc.cu", "nb_mlp.cu", "nb_pair1x1.cu", "nb_buffer.cu", "nb_rdf.cu", "nb_finalize.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

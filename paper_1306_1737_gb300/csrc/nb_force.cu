@@ -1,4 +1,5 @@
-// Cluster-pair force/energy kernel (Sec. 3, Fig. 6) and the FP64 reductions.
+// Cluster-pair force/energy kernels (Sec. 3, Fig. 6); the FP64 totals and the
+// return to the caller's order are in nb_finalize.cu.
 //
 // k_force8: one warp per i-entry {ci, shift, j-range} of 8-particle clusters.
 // Lane (ih = lane / 8, j = lane % 8) owns particle pairs (ih, j) and (ih+4, j)
@@ -860,133 +861,6 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
                              : launch_force_e<NB_ELEC_RF, false>(A, C, n_sm, s);
     return p.want_energy ? launch_force_e<NB_ELEC_EWALD, true>(A, C, n_sm, s)
                          : launch_force_e<NB_ELEC_EWALD, false>(A, C, n_sm, s);
-}
-
-// A warp's virial partial sums of box b added to the box's FP64 total, then cleared.
-__device__ __forceinline__ void virial_flush(const Workspace& ws, double (&w)[9], int b, int lane) {
-    const unsigned full = 0xffffffffu;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        for (int o = 16; o > 0; o >>= 1) w[k] += __shfl_xor_sync(full, w[k], o);
-        if (lane == 0 && b >= 0) atomicAdd(&ws.acc[b].vir_xf[k], w[k]);
-        w[k] = 0.0;
-    }
-}
-
-// Forces back to the caller's order (and zeroed for the next evaluation);
-// with energies, the FP64 sum per box over slots of x (x) f for the virial.
-// The slots are walked in order (coalesced reads of the slot forces, their
-// particles and coordinates) and each particle's force is scattered to the
-// caller's order; a gather in particle order instead waits on a random
-// slot read per particle.  Each warp takes a contiguous range of slots, 32
-// at a time, so its virial sums stay in registers until its box changes
-// (one set of FP64 atomics per warp and box).  Particles without a slot (a
-// column too long to grid, an error that is flagged) get zero force.
-__global__ void k_finalize(Workspace ws, int C, float* __restrict__ f_out, int want_vir) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ws.work[0] = 0;   // the force kernel's counter
-    const int n = ws.atom_total;
-    const long long nslot = (long long)ws.clu_total * C;
-    const long long n_warps = (long long)gridDim.x * (blockDim.x >> 5);
-    const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long groups = (nslot + 31) / 32;
-    const long long per = (groups + n_warps - 1) / n_warps;
-    const long long g_end = min(groups, (wg + 1) * per);
-    double w[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    int b_cur = -1;
-    for (long long g = wg * per; g < g_end; ++g) {
-        const long long s = g * 32 + lane;
-        int b = -1;
-        bool real = false;
-        float4 f = make_float4(0.f, 0.f, 0.f, 0.f), x = f;
-        if (s < nslot) {
-            const int cl = (int)(s / C);
-            b = find_box(ws.lay.clu_off, ws.nbox, cl);
-            // only the box's current clusters hold particles; the rest of its
-            // slot region is unused capacity (never written by the kernels)
-            if (cl - ws.lay.clu_off[b] < ws.st[b].nclu) {
-                const int p = ws.atom_of_slot[s];
-                f = ws.fslot[s];
-                ws.fslot[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (p >= 0 && p < n) {
-                    real = true;
-                    f_out[3 * (long long)p] = f.x;
-                    f_out[3 * (long long)p + 1] = f.y;
-                    f_out[3 * (long long)p + 2] = f.z;
-                    if (want_vir) x = ws.xyzq[s];
-                }
-            }
-        }
-        if (!want_vir) continue;
-        const int b0 = __shfl_sync(full, b, 0);   // lane 0 has a slot: g * 32 < nslot
-        const bool uniform = __all_sync(full, b < 0 || b == b0);
-        if (!uniform || b0 != b_cur) {
-            virial_flush(ws, w, b_cur, lane);
-            b_cur = uniform ? b0 : -1;
-        }
-        const double xa[3] = {x.x, x.y, x.z}, fb[3] = {f.x, f.y, f.z};
-        if (uniform) {
-            if (real) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) w[3 * a + c] += xa[a] * fb[c];
-            }
-        } else if (real) {
-            // 32 slots straddling two boxes: add this group directly
-            for (int a = 0; a < 3; ++a)
-                for (int c = 0; c < 3; ++c) atomicAdd(&ws.acc[b].vir_xf[3 * a + c], xa[a] * fb[c]);
-        }
-    }
-    if (want_vir) virial_flush(ws, w, b_cur, lane);
-    // particles without a slot
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int sl = ws.slot_of_atom[p];
-        if (sl < 0 || sl >= nslot) {
-            f_out[3 * (long long)p] = 0.f;
-            f_out[3 * (long long)p + 1] = 0.f;
-            f_out[3 * (long long)p + 2] = 0.f;
-        }
-    }
-}
-
-// Per box: energies out, and W = sum x (x) f + sum_s (s L) (x) f_shift.
-__global__ void k_finalize_small(Workspace ws, double* e_out, double* vir_out) {
-    for (int b = threadIdx.x; b < ws.nbox; b += blockDim.x) {
-        const Accum* acc = &ws.acc[b];
-        ws.st[b].n_pairs_rc = acc->n_inc;
-        if (e_out) {
-            e_out[2 * b] = acc->energy[0];
-            e_out[2 * b + 1] = acc->energy[1];
-        }
-        if (vir_out) {
-            const float* L = ws.geo[b].L;
-            double w[9];
-            for (int k = 0; k < 9; ++k) w[k] = acc->vir_xf[k];
-            for (int s = 0; s < 27; ++s) {
-                const double sv[3] = {(double)(s / 9 - 1) * L[0], (double)((s / 3) % 3 - 1) * L[1],
-                                      (double)(s % 3 - 1) * L[2]};
-                for (int a = 0; a < 3; ++a)
-                    for (int c = 0; c < 3; ++c) w[3 * a + c] += sv[a] * acc->fshift[s][c];
-            }
-            for (int k = 0; k < 9; ++k) vir_out[9 * b + k] = w[k];
-        }
-    }
-}
-
-cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int C, float* f_out, double* e_out,
-                            double* vir_out, cudaStream_t s) {
-    const int want_vir = (p.want_energy && vir_out) ? 1 : 0;
-    // enough warps to keep the gather/scatter in flight; fewer with the
-    // virial, whose per-warp FP64 flushes meet on one box's nine addresses
-    int blocks = (int)min(((long long)ws.clu_total * C + 255) / 256, (long long)1 << 20);
-    const int cap = want_vir ? 1024 : 4096;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    k_finalize<<<blocks, 256, 0, s>>>(ws, C, f_out, want_vir);
-    if (p.want_energy) k_finalize_small<<<1, 256, 0, s>>>(ws, e_out, vir_out);
-    return cudaGetLastError();
 }
 
 }  // namespace nbc
