@@ -197,3 +197,43 @@ def test_batch_runner_groups_graph(env):
                 o += b.n
     finally:
         r.close()
+
+
+def test_batch_runner_host_pipeline(env):
+    """The host path (frames copied in and forces read back on a copy stream,
+    two device buffers each): every frame's forces read back into host memory
+    match the oracle for that frame's coordinates, so no frame used a buffer
+    still being filled or read a force buffer already reused."""
+    torch, dev, nb = env
+    from paper_1306_1737_gb300.batch import BatchRunner, GroupSpec
+    boxes = [w.water_box(m, None, seed=7500 + k) for k, m in enumerate([600, 1100])]
+    B = w.concat(boxes)
+    p = {"elec": "ewald", "rc": 1.0, "rlist": 1.1, "beta": 3.12}
+    H = 10
+    frames = list(w.frame_walk(B.xyz, B.mass, H, seed=7600))
+    fr = torch.stack([torch.from_numpy(x) for x in frames]).to(dev)
+    r = BatchRunner(B.counts, B.boxes, B.q, B.types, nb.nb_lj_combine(B.sigma, B.eps), B.excl_off,
+                    B.excl_idx, fr, [GroupSpec(8, 10, 1.1, [0, 1], nstprune=3)], p, nstprune=5)
+    try:
+        g = r.groups[0]
+        at = torch.as_tensor(g.atoms)
+        hx = fr.cpu().index_select(1, at).contiguous().pin_memory()
+        hf = torch.zeros_like(hx).pin_memory()
+        r.step(host=[(hx, hf)])
+        torch.cuda.synchronize()
+        assert all(i.status == 0 for i in r.check())
+        oprm = oracle.make_params("ewald", float(np.float32(1.0)), beta=3.12)
+        off = B.offsets
+        for f in (0, 1, 3, 4, 8, 9):
+            F = hf[f].numpy().astype(np.float64)
+            o = 0
+            for k in g.box_index:
+                b = B.members[k]
+                x = frames[f][int(off[k]):int(off[k + 1])]
+                fo, _, _ = oracle.forces_brute(x, b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx, b.box, oprm)
+                rms = math.sqrt((fo ** 2).sum(1).mean())
+                emax = np.sqrt(((F[o:o + b.n] - fo) ** 2).sum(1)).max() / rms
+                assert emax < FORCE_TOL, (f, k, emax)
+                o += b.n
+    finally:
+        r.close()
