@@ -48,3 +48,15 @@ def test_status_strings_and_host_helpers(lib):
 def test_null_context_is_rejected(lib):
     assert lib.nb_destroy(None) == nb.NB_ERR_ARG
     assert lib.nb_grid_put(None, None, None, None) == nb.NB_ERR_ARG
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every call raises: there is no CPU path."""
+    monkeypatch.setattr(nb, "LIB_PATH", str(tmp_path / "libnbcluster.so"))
+    monkeypatch.setattr(nb, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        nb.load()
+    with pytest.raises(RuntimeError, match="missing"):
+        nb.nb_lj_combine([0.3], [0.5])
+    with pytest.raises(RuntimeError, match="missing"):
+        nb.nb_create(8, 0)
