@@ -42,7 +42,7 @@ typedef int nb_status;
 enum nb_status_code {
     NB_OK = 0,
     NB_ERR_ARG = 1,      /* null pointer, size or option out of range */
-    NB_ERR_BOX = 2,      /* box edge <= 0, or a radius >= half a box edge */
+    NB_ERR_BOX = 2,      /* box edge <= 0 or >= 1e30, or a radius >= half a box edge */
     NB_ERR_CAPACITY = 3, /* workspace or list capacity exceeded */
     NB_ERR_CUDA = 4,     /* a CUDA runtime call failed */
     NB_ERR_STATE = 5,    /* call out of order (no workspace, no grid, no list) */
@@ -145,8 +145,11 @@ nb_status nb_lj_combine(int ntypes, const double* sigma_host, const double* eps_
  * box_host[3] (nm), lists up to radius rlist_max (nm) and ntypes <= 64 LJ
  * types.  list_factor (>= 1; 0 = default 1.5) scales the density-based
  * estimate of the cluster-pair list capacity.  Fixes the context's plan (one
- * box); nb_set_workspace must follow.
- * Errors: NB_ERR_ARG, NB_ERR_BOX. */
+ * box); nb_set_workspace must follow.  The grid has at most 2^15 columns along
+ * x and along y (reached only by boxes far thinner than the column spacing).
+ * Errors: NB_ERR_ARG (more than 2^31 - 1 particles), NB_ERR_BOX,
+ * NB_ERR_CAPACITY (more than 2^31 - 1 slots, i-entries or j-entries, or more
+ * than 2^27 - 1 clusters: a j-entry word holds a 27-bit cluster index). */
 nb_status nb_workspace_query(nb_ctx* ctx, int n_atoms, const double* box_host, double rlist_max,
                              int ntypes, double list_factor, size_t* bytes);
 
@@ -157,7 +160,7 @@ nb_status nb_workspace_query(nb_ctx* ctx, int n_atoms, const double* box_host, d
  * batch-global), in a box of edges boxes_host[3b..3b+2] (nm) used to size its
  * grid and list capacity.  The plan (particles per box) is fixed until the
  * next query; box edges may change at every nb_grid_put within the capacity.
- * Errors: NB_ERR_ARG, NB_ERR_BOX. */
+ * Errors: as nb_workspace_query, with the limits on the sums over the boxes. */
 nb_status nb_workspace_query_boxes(nb_ctx* ctx, int nbox, const int* n_atoms_host,
                                    const double* boxes_host, double rlist_max, int ntypes,
                                    double list_factor, size_t* bytes);

@@ -18,8 +18,8 @@ using namespace nbc;
 namespace {
 
 struct BoxPlan {
-    int n, ncol_cap, nclu_cap, nsc_cap;
-    long long ient_cap, jent_cap;
+    int n, ncol_cap;
+    long long nclu_cap, nsc_cap, ient_cap, jent_cap;
 };
 
 constexpr int kGeoRing = 8;  // pinned staging buffers for box geometry uploads
@@ -116,8 +116,18 @@ static nb_status cuda_fail(nb_ctx* c, cudaError_t e, const char* where) {
 static bool box_ok(const double* box) {
     if (!box) return false;
     for (int k = 0; k < 3; ++k)
-        if (!(box[k] > 0.0) || !std::isfinite(box[k])) return false;
+        if (!(box[k] > 0.0) || !(box[k] < 1e30)) return false;
     return true;
+}
+
+// At most this many grid columns along x and along y, so that nx * ny fits
+// an int; only slab-like boxes far thinner than the column spacing reach it.
+constexpr int kMaxGridDim = 1 << 15;
+
+static int grid_extent(double L, double s) {
+    const double g = std::floor(L / s);
+    if (!(g >= 1.0)) return 1;
+    return g > (double)kMaxGridDim ? kMaxGridDim : (int)g;
 }
 
 // Grid dimensions (Sec. 2.3): spacing (C / rho)^(1/3) along x and y.
@@ -127,10 +137,8 @@ static void grid_dims(int n, const float L[3], int C, int* nx, int* ny) {
         const double Lx = L[0], Ly = L[1], Lz = L[2];
         const double rho = (double)n / (Lx * Ly * Lz);
         const double s = std::cbrt((double)C / rho);
-        gx = (int)std::floor(Lx / s);
-        gy = (int)std::floor(Ly / s);
-        if (gx < 1) gx = 1;
-        if (gy < 1) gy = 1;
+        gx = grid_extent(Lx, s);
+        gy = grid_extent(Ly, s);
     }
     *nx = gx;
     *ny = gy;
@@ -159,7 +167,7 @@ static BoxPlan plan_box(int n, const float L[3], int C, double rlist, double fac
     z.n = n;
     z.ncol_cap = nx * ny;
     const long long nslot = (long long)n + (long long)z.ncol_cap * (C - 1);
-    z.nclu_cap = (int)(nslot / C + 1);
+    z.nclu_cap = nslot / C + 1;
     z.nsc_cap = z.nclu_cap / S + z.ncol_cap + 1;
     const double V = (double)L[0] * L[1] * L[2];
     const double wx = (double)L[0] / nx, wy = (double)L[1] / ny;
@@ -172,8 +180,10 @@ static BoxPlan plan_box(int n, const float L[3], int C, double rlist, double fac
     double per = 0.5 * rho_c * vm + S;
     const double maxper = 0.5 * 27.0 * (double)z.nclu_cap + 1.0;
     if (per > maxper) per = maxper;
-    z.jent_cap = (long long)std::ceil(factor * per * (double)z.nsc_cap) + 64;
-    z.ient_cap = (long long)z.nsc_cap * 27 + z.jent_cap / kJChunkCoop + 64;
+    // saturated far above the 2^31-entry limit the query enforces
+    const double jent = std::ceil(factor * per * (double)z.nsc_cap) + 64.0;
+    z.jent_cap = jent < 1e15 ? (long long)jent : (long long)1e15;
+    z.ient_cap = z.nsc_cap * 27 + z.jent_cap / kJChunkCoop + 64;
     return z;
 }
 
@@ -252,8 +262,8 @@ static void set_plan(nb_ctx* c, const std::vector<BoxPlan>& plans) {
     for (int b = 0; b < nb; ++b) {
         c->atom_off[b + 1] = c->atom_off[b] + plans[b].n;
         c->col_off[b + 1] = c->col_off[b] + plans[b].ncol_cap + 1;
-        c->clu_off[b + 1] = c->clu_off[b] + plans[b].nclu_cap;
-        c->sc_off[b + 1] = c->sc_off[b] + plans[b].nsc_cap;
+        c->clu_off[b + 1] = c->clu_off[b] + (int)plans[b].nclu_cap;
+        c->sc_off[b + 1] = c->sc_off[b] + (int)plans[b].nsc_cap;
         c->ient_off[b + 1] = c->ient_off[b] + plans[b].ient_cap;
         c->jent_off[b + 1] = c->jent_off[b] + plans[b].jent_cap;
     }
@@ -470,7 +480,7 @@ nb_status nb_workspace_query_boxes(nb_ctx* c, int nbox, const int* n_atoms, cons
     long long total = 0;
     for (int b = 0; b < nbox; ++b) {
         if (n_atoms[b] < 0) return fail(c, NB_ERR_ARG, "negative particle count");
-        if (!box_ok(boxes + 3 * b)) return fail(c, NB_ERR_BOX, "box %d: edges must be positive", b);
+        if (!box_ok(boxes + 3 * b)) return fail(c, NB_ERR_BOX, "box %d: edges must be positive and below 1e30 nm", b);
         const float L[3] = {(float)boxes[3 * b], (float)boxes[3 * b + 1], (float)boxes[3 * b + 2]};
         plans[b] = plan_box(n_atoms[b], L, c->C, rlist_max, list_factor);
         total += n_atoms[b];
@@ -480,11 +490,14 @@ nb_status nb_workspace_query_boxes(nb_ctx* c, int nbox, const int* n_atoms, cons
     for (const BoxPlan& z : plans) {
         ient_sum += z.ient_cap;
         jent_sum += z.jent_cap;
-        slot_sum += (long long)z.nclu_cap * c->C;
+        slot_sum += z.nclu_cap * c->C;
     }
     // list and slot indices are stored as 32-bit integers
     if (ient_sum > 0x7fffffffLL || jent_sum > 0x7fffffffLL || slot_sum > 0x7fffffffLL)
         return fail(c, NB_ERR_CAPACITY, "list or slot capacity above 2^31 entries");
+    // a j-entry word keeps the j-cluster index in its low kSuperShift bits
+    if (slot_sum / c->C > (long long)kCjMask)
+        return fail(c, NB_ERR_CAPACITY, "more than 2^%d clusters", kSuperShift);
     set_plan(c, plans);
     *bytes = carve(c, nullptr, nullptr);
     return NB_OK;
@@ -493,7 +506,7 @@ nb_status nb_workspace_query_boxes(nb_ctx* c, int nbox, const int* n_atoms, cons
 nb_status nb_workspace_query(nb_ctx* c, int n, const double* box, double rlist_max, int ntypes,
                              double list_factor, size_t* bytes) {
     if (!c) return NB_ERR_ARG;
-    if (!box_ok(box)) return fail(c, NB_ERR_BOX, "box edges must be positive");
+    if (!box_ok(box)) return fail(c, NB_ERR_BOX, "box edges must be positive and below 1e30 nm");
     return nb_workspace_query_boxes(c, 1, &n, box, rlist_max, ntypes, list_factor, bytes);
 }
 
@@ -569,7 +582,7 @@ nb_status nb_grid_put(nb_ctx* c, const float* xyz, const double* boxes, nb_strea
     if (!boxes) return fail(c, NB_ERR_BOX, "box is null");
     std::vector<BoxGeom> geo(c->nbox);
     for (int b = 0; b < c->nbox; ++b) {
-        if (!box_ok(boxes + 3 * b)) return fail(c, NB_ERR_BOX, "box %d: edges must be positive", b);
+        if (!box_ok(boxes + 3 * b)) return fail(c, NB_ERR_BOX, "box %d: edges must be positive and below 1e30 nm", b);
         BoxGeom& g = geo[b];
         memset(&g, 0, sizeof(g));
         for (int k = 0; k < 3; ++k) g.L[k] = (float)boxes[3 * b + k];
@@ -577,7 +590,7 @@ nb_status nb_grid_put(nb_ctx* c, const float* xyz, const double* boxes, nb_strea
         grid_dims(nb_atoms, g.L, c->C, &g.nx, &g.ny);
         if (g.nx * g.ny > c->plan[b].ncol_cap)
             return fail(c, NB_ERR_CAPACITY, "box %d: grid has more columns than the workspace", b);
-        if ((long long)nb_atoms + (long long)g.nx * g.ny * (c->C - 1) > (long long)c->plan[b].nclu_cap * c->C)
+        if ((long long)nb_atoms + (long long)g.nx * g.ny * (c->C - 1) > c->plan[b].nclu_cap * c->C)
             return fail(c, NB_ERR_CAPACITY, "box %d: grid may need more slots than the workspace", b);
         g.inv_x = (float)((double)g.nx / (double)g.L[0]);
         g.inv_y = (float)((double)g.ny / (double)g.L[1]);

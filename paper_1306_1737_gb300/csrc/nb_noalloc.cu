@@ -105,14 +105,14 @@ extern "C" nb_status nb_grid_put_noalloc(int n, const float* xyz, const float* q
         if (!(box[k] > 0.0) || !(box[k] < 1e30)) return NB_ERR_BOX;
         g.L[k] = (float)box[k];
     }
-    // grid dimensions: spacing (C / rho)^(1/3) along x and y
+    // grid dimensions: spacing (C / rho)^(1/3) along x and y, at most 2^15
+    // columns along each (only slabs far thinner than the spacing reach it)
     {
         const double Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
         const double sp = std::cbrt((double)C / ((double)n / (Lx * Ly * Lz)));
-        g.nx = (int)std::floor(Lx / sp);
-        g.ny = (int)std::floor(Ly / sp);
-        if (g.nx < 1) g.nx = 1;
-        if (g.ny < 1) g.ny = 1;
+        const double gx = std::floor(Lx / sp), gy = std::floor(Ly / sp);
+        g.nx = !(gx >= 1.0) ? 1 : gx > 32768.0 ? 32768 : (int)gx;
+        g.ny = !(gy >= 1.0) ? 1 : gy > 32768.0 ? 32768 : (int)gy;
     }
     const long long ncol = (long long)g.nx * g.ny;
     const long long nslot_bound = (long long)n + ncol * (C - 1);

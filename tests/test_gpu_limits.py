@@ -1,0 +1,66 @@
+"""Limits of the workspace plan (host code behind a device context): a
+j-entry word holds a 27-bit cluster index, list and slot indices are 32-bit,
+the grid has at most 2^15 columns along x and y, and box edges are finite.
+Plans beyond a limit are refused with a status instead of being laid out
+with wrapped indices; no workspace is allocated here."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nb():
+    pytest.importorskip("torch")
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1306_1737_gb300 as nb
+    nb.load()
+    return nb
+
+
+def _status(nb, fn, *args):
+    try:
+        fn(*args)
+    except nb.NbError as e:
+        return e.status
+    return nb.NB_OK
+
+
+@pytest.mark.parametrize("C", [8, 4])
+def test_realistic_plans_are_accepted(nb, C):
+    ctx = nb.nb_create(C)
+    try:
+        for n, L in ((24000, 6.21), (3000000, 31.07)):
+            assert nb.nb_workspace_query(ctx, n, [L, L, L], 1.1, 2) > 0
+    finally:
+        nb.nb_destroy(ctx)
+
+
+def test_more_clusters_than_a_jword_holds(nb):
+    """1.1e9 particles at 0.05 per nm^3 with clusters of 8: the slot, i-entry
+    and j-entry counts stay below 2^31, the cluster count (1.38e8) does not
+    fit 27 bits."""
+    ctx = nb.nb_create(8)
+    try:
+        L = (1.1e9 / 0.05) ** (1.0 / 3.0)
+        assert _status(nb, nb.nb_workspace_query, ctx, 1_100_000_000, [L, L, L], 1.1, 2) == nb.NB_ERR_CAPACITY
+        assert "2^27" in nb.nb_last_error(ctx)
+    finally:
+        nb.nb_destroy(ctx)
+
+
+def test_degenerate_and_oversized_boxes(nb):
+    ctx = nb.nb_create(8)
+    try:
+        # a slab far thinner than the column spacing: the column count is capped, the slots overflow
+        assert _status(nb, nb.nb_workspace_query, ctx, 1000, [2.2e6, 2.2e6, 2e-12], 1.1, 2) == nb.NB_ERR_CAPACITY
+        assert _status(nb, nb.nb_workspace_query, ctx, 10, [1e31, 1.0, 1.0], 1.1, 2) == nb.NB_ERR_BOX
+        assert _status(nb, nb.nb_workspace_query, ctx, 10, [0.0, 1.0, 1.0], 1.1, 2) == nb.NB_ERR_BOX
+        # more than 2^31 - 1 particles over the boxes
+        assert _status(nb, nb.nb_workspace_query_boxes, ctx, [1_500_000_000, 1_500_000_000],
+                       [[1e3, 1e3, 1e3], [1e3, 1e3, 1e3]], 1.1, 2) == nb.NB_ERR_ARG
+        # the context still plans a valid box afterwards
+        assert nb.nb_workspace_query(ctx, 24000, [6.21, 6.21, 6.21], 1.1, 2) > 0
+    finally:
+        nb.nb_destroy(ctx)
