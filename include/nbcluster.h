@@ -175,7 +175,9 @@ nb_status nb_set_workspace(nb_ctx* ctx, void* ws_dev, size_t bytes);
 /* Particle charges (float [n]), LJ types (int [n], 0 <= type < ntypes) and the
  * LJ pair table c6c12_dev (float [ntypes][ntypes][2], e.g. nb_lj_combine;
  * shared by all boxes) are copied into the workspace on the stream.  Sec. 3.2.
- * n must equal the planned number of particles (summed over the boxes).
+ * n must equal the planned number of particles (summed over the boxes).  A
+ * type outside 0 .. ntypes - 1 is not read here: the next nb_grid_put uses
+ * type 0 for it and raises its box's NB_ERR_ARG device flag.
  * Errors: NB_ERR_ARG, NB_ERR_STATE (no workspace), NB_ERR_CAPACITY (n not the
  * planned number, or ntypes above 64), NB_ERR_CUDA. */
 nb_status nb_set_atoms(nb_ctx* ctx, int n, const float* q_dev, const int* type_dev, int ntypes,
@@ -191,7 +193,8 @@ nb_status nb_set_atoms(nb_ctx* ctx, int n, const float* q_dev, const int* type_d
  * at every replay): NB_ERR_STATE otherwise.
  * Errors: NB_ERR_ARG, NB_ERR_BOX, NB_ERR_STATE (no atoms set),
  * NB_ERR_CAPACITY (more columns/slots than the workspace holds), NB_ERR_CUDA;
- * device flags NB_ERR_COORD, NB_ERR_CAPACITY (column > 8192 particles). */
+ * device flags NB_ERR_COORD, NB_ERR_CAPACITY (column > 8192 particles),
+ * NB_ERR_ARG (an LJ type outside 0 .. ntypes - 1, used as type 0). */
 nb_status nb_grid_put(nb_ctx* ctx, const float* xyz_dev, const double* boxes_host, nb_stream stream);
 
 /* Cluster-pair search (Sec. 2.3, Fig. 3) with exclusion bitmasks (Sec. 2.4):

@@ -64,3 +64,30 @@ def test_degenerate_and_oversized_boxes(nb):
         assert nb.nb_workspace_query(ctx, 24000, [6.21, 6.21, 6.21], 1.1, 2) > 0
     finally:
         nb.nb_destroy(ctx)
+
+
+def test_type_out_of_range_is_flagged(nb):
+    """A particle type outside 0 .. ntypes - 1 is used as type 0 by the grid
+    and raises the box's NB_ERR_ARG flag; correct types clear it."""
+    import numpy as np
+    import torch
+    from paper_1306_1737_gb300 import workloads as w
+    b = w.water_box(600, None, seed=7600)
+    c6c12 = nb.nb_lj_combine(b.sigma, b.eps)
+    nt = int(c6c12.shape[0])
+    bad = np.asarray(b.types, dtype=np.int32).copy()
+    bad[3], bad[11] = nt, -1
+    cx = nb.Context(b.n, b.box, 1.0, b.q, bad, c6c12)
+    try:
+        ctx, dev = cx.ctx, cx.dev
+        x = torch.as_tensor(b.xyz, device=dev)
+        nb.nb_grid_put(ctx, x, b.box)
+        info = nb.nb_check(ctx, raise_on_error=False)
+        assert info.status == nb.NB_ERR_ARG
+        assert "type" in nb.nb_last_error(ctx)
+        good = torch.as_tensor(np.asarray(b.types, dtype=np.int32), device=dev)
+        nb.nb_set_atoms(ctx, b.n, cx.q, good, nt, cx.c6c12)
+        nb.nb_grid_put(ctx, x, b.box)
+        assert nb.nb_check(ctx, raise_on_error=False).status == nb.NB_OK
+    finally:
+        cx.close()
