@@ -245,7 +245,8 @@ nb_status nb_prune(nb_ctx* ctx, const float* xyz_dev, float r_prune, nb_stream s
  * NB_ELEC_EWALD_TAB (the correction factor from a table), compute forces
  * only: with want_energy set, the analytic Ewald kernel runs instead (forces,
  * energies and virial all analytic).
- * Errors: NB_ERR_ARG, NB_ERR_BOX (rc >= L/2 or rc > rlist), NB_ERR_STATE (no
+ * Errors: NB_ERR_ARG, NB_ERR_BOX (rc >= L/2, or rc above the list's radius:
+ * rlist, or after nb_prune the smaller of rlist and r_prune), NB_ERR_STATE (no
  * list; no network for NB_ELEC_EWALD_MLP), NB_ERR_CUDA. */
 nb_status nb_compute(nb_ctx* ctx, const nb_params* p, const float* xyz_dev, float* f_dev,
                      double* e_dev, double* vir_dev, nb_stream stream);

@@ -684,7 +684,8 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     }
     if (!(p->rc > 0.f)) return fail(c, NB_ERR_ARG, "rc must be positive");
     if (!(p->rc < 0.5f * min_edge(c))) return fail(c, NB_ERR_BOX, "rc must be below half the box");
-    const float rlive = c->have_pruned ? c->r_prune : c->rlist;
+    // a prune at a radius above the list's keeps the list's radius
+    const float rlive = c->have_pruned && c->r_prune < c->rlist ? c->r_prune : c->rlist;
     if (p->rc > rlive) return fail(c, NB_ERR_BOX, "rc above the list radius");
     if (p->elec != NB_ELEC_RF && !(p->beta >= 0.f)) return fail(c, NB_ERR_ARG, "beta must be >= 0");
     if (xyz) {

@@ -160,3 +160,23 @@ def test_prune_compute_errors(gp):
         nb.nb_check(gb.ctx)
     finally:
         gb.close()
+
+
+def test_compute_radius_after_a_wide_prune(gp):
+    """A prune at a radius above the list's keeps every listed pair; the list
+    still holds only the pairs within rlist, so a cut-off between rlist and
+    that prune radius is refused."""
+    import paper_1306_1737_gb300 as nb
+    b, p = w.config1()
+    gb = gp.GpuBox(b, p["rlist"])
+    try:
+        gb.grid()
+        gb.build(0.95)
+        nb.nb_prune(gb.ctx, None, 1.2)
+        with pytest.raises(nb.NbError) as ei:
+            nb.nb_compute(gb.ctx, nb.make_params("rf", 1.0), None, gb.f)
+        assert ei.value.status == nb.NB_ERR_BOX
+        nb.nb_compute(gb.ctx, nb.make_params("rf", 0.9), None, gb.f)
+        nb.nb_check(gb.ctx)
+    finally:
+        gb.close()
