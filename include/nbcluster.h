@@ -355,18 +355,24 @@ nb_status nb_prune_compute(nb_ctx* ctx, const nb_params* p, const float* xyz_dev
  * particles) expanded from the current outer cluster-pair list, for the
  * comparison the paper makes between cluster-pair (M x N) and particle-pair
  * (1 x 1) setups (Sec. 4-5, Table 3).  rlist must not exceed the radius of
- * the last nb_pairlist_build.  nbr_dev: int [n][max_nbr] entries, each
+ * the last nb_pairlist_build, and the coordinates must be the ones that list
+ * was built from (no nb_set_coords, nb_prune or nb_compute with new
+ * coordinates since).  nbr_dev: int [n][max_nbr] entries, each
  * (neighbour slot << 6) | (force-field excluded << 5) | shift index (the
  * shift applied to the particle owning the row); count_dev: int [n] entries
  * per particle (a row holds min(count, max_nbr); a count above max_nbr
  * raises the NB_ERR_CAPACITY device flag).  Caller order, device memory.
- * Errors: NB_ERR_ARG, NB_ERR_STATE (no list), NB_ERR_BOX, NB_ERR_CUDA. */
+ * Errors: NB_ERR_ARG, NB_ERR_STATE (no list, or new coordinates since it was
+ * built), NB_ERR_BOX, NB_ERR_CUDA. */
 nb_status nb_pairlist_1x1(nb_ctx* ctx, float rlist, int max_nbr, int* nbr_dev, int* count_dev,
                           nb_stream stream);
 
-/* Forces over a 1 x 1 list from nb_pairlist_1x1: one thread per particle,
- * the same pair interactions as nb_compute (RF or Ewald; forces only,
- * p->want_energy must be 0).  xyz_dev may be NULL (current coordinates);
+/* Forces over a 1 x 1 list from nb_pairlist_1x1: 16, 8 or 4 lanes per
+ * particle (fewer for more particles) summing its row, each pair computed for
+ * both of its particles (no atomics), with the same pair interactions as
+ * nb_compute (RF or Ewald; forces only, p->want_energy must be 0).  rc must
+ * not exceed the radius the list was built with (the list is the caller's:
+ * not checked).  xyz_dev may be NULL (current coordinates);
  * f_dev: float [n][3], caller order, overwritten.
  * Errors: NB_ERR_ARG, NB_ERR_STATE, NB_ERR_BOX, NB_ERR_CUDA. */
 nb_status nb_compute_1x1(nb_ctx* ctx, const nb_params* p, const float* xyz_dev, const int* nbr_dev,

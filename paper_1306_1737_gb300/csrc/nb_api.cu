@@ -779,6 +779,7 @@ nb_status nb_pairlist_1x1(nb_ctx* c, float rlist, int max_nbr, int* nbr, int* co
     if (!c->have_list) return fail(c, NB_ERR_STATE, "nb_pairlist_build first");
     if (!(rlist > 0.f) || max_nbr <= 0 || (c->n > 0 && (!nbr || !count)))
         return fail(c, NB_ERR_ARG, "pairlist_1x1: bad argument");
+    if (!c->list_fresh) return fail(c, NB_ERR_STATE, "pairlist_1x1: coordinates changed since the list was built");
     if (rlist > c->rlist) return fail(c, NB_ERR_BOX, "rlist above the cluster list's radius");
     NB_CUDA(c, cudaSetDevice(c->device));
     cudaError_t e = launch_pairlist_1x1(c->ws, c->C, rlist, max_nbr, nbr, count, c->n_sm, (cudaStream_t)stream);

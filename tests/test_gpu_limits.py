@@ -1,8 +1,10 @@
-"""Limits of the workspace plan (host code behind a device context): a
-j-entry word holds a 27-bit cluster index, list and slot indices are 32-bit,
-the grid has at most 2^15 columns along x and y, and box edges are finite.
-Plans beyond a limit are refused with a status instead of being laid out
-with wrapped indices; no workspace is allocated here."""
+"""Limits and state checks of the C ABI.  The workspace plan (host code
+behind a device context): a j-entry word holds a 27-bit cluster index, list
+and slot indices are 32-bit, the grid has at most 2^15 columns along x and
+y, and box edges are finite; plans beyond a limit are refused with a status
+instead of being laid out with wrapped indices (no workspace is allocated for
+them).  Particle types out of range are flagged on the device, and the 1 x 1
+list is refused for coordinates its cluster list was not built from."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -91,3 +93,29 @@ def test_type_out_of_range_is_flagged(nb):
         assert nb.nb_check(ctx, raise_on_error=False).status == nb.NB_OK
     finally:
         cx.close()
+
+
+def test_pairlist_1x1_needs_the_list_coordinates(nb):
+    """The 1 x 1 list holds every pair within rlist only for the coordinates
+    the cluster list was built from: after new coordinates it is refused
+    until the next build."""
+    import numpy as np
+    import gpu_path
+    from paper_1306_1737_gb300 import workloads as w
+    b, p = w.config1()
+    gb = gpu_path.GpuBox(b, p["rlist"])
+    torch = gb.torch
+    try:
+        gb.grid()
+        rl = float(np.float32(p["rlist"]))
+        gb.build(rl)
+        nbr = torch.zeros((b.n, 768), dtype=torch.int32, device=gb.dev)
+        cnt = torch.zeros(b.n, dtype=torch.int32, device=gb.dev)
+        nb.nb_set_coords(gb.ctx, torch.as_tensor(b.xyz).to(gb.dev))
+        assert _status(nb, nb.nb_pairlist_1x1, gb.ctx, rl, 768, nbr, cnt) == nb.NB_ERR_STATE
+        gb.build(rl)
+        nb.nb_pairlist_1x1(gb.ctx, rl, 768, nbr, cnt)
+        nb.nb_check(gb.ctx)
+        assert int(cnt.sum().item()) > 0
+    finally:
+        gb.close()
