@@ -21,8 +21,9 @@
  *    cudaStream_t; NULL = the legacy default stream) and performs no host
  *    synchronisation, so a sequence of calls can be captured in a CUDA graph.
  *    Errors that only the device can detect (list capacity overflow, a
- *    particle outside [-L, 2L), a column too long to sort on-chip) raise a
- *    device flag that nb_check() reads.
+ *    particle outside [-L, 2L), a column too long to sort on-chip, an LJ type
+ *    or exclusion index out of range) raise a device flag that nb_check()
+ *    reads.
  *  - Return value: NB_OK or an nb_status_code; nb_last_error() gives text.
  */
 #ifndef NBCLUSTER_H
@@ -46,7 +47,7 @@ enum nb_status_code {
     NB_ERR_CAPACITY = 3, /* workspace or list capacity exceeded */
     NB_ERR_CUDA = 4,     /* a CUDA runtime call failed */
     NB_ERR_STATE = 5,    /* call out of order (no workspace, no grid, no list) */
-    NB_ERR_TIMEOUT = 6,  /* a bounded device wait expired */
+    NB_ERR_TIMEOUT = 6,  /* a bounded device wait expired (reserved: no kernel waits) */
     NB_ERR_COORD = 7     /* a coordinate outside [-L, 2L) at gridding */
 };
 
@@ -89,11 +90,11 @@ typedef struct {
     int n_clusters;       /* clusters, including padded ones */
     int64_t n_ientries;   /* i-entries of the outer (rlist) list */
     int64_t n_jentries;   /* j-entries of the outer list */
-    int64_t n_jentries_pruned; /* j-entries kept by the last nb_prune (-1: none) */
+    int64_t n_jentries_pruned; /* j-entries kept by the last prune (nb_prune or nb_prune_compute; -1: none) */
     int64_t ient_capacity, jent_capacity;
     int64_t n_pairs_rc;   /* particle pairs inside rc in the last energy evaluation */
     int64_t n_cluster_pairs;        /* cluster pairs (i-cluster, j-cluster, shift) in the outer list */
-    int64_t n_cluster_pairs_pruned; /* cluster pairs kept by the last nb_prune (-1: none) */
+    int64_t n_cluster_pairs_pruned; /* cluster pairs kept by the last prune (-1: none) */
     int n_superclusters;  /* super-clusters (runs of up to super_size clusters of a column) */
     int super_size;       /* i-clusters per super-cluster: 2 for C = 8, 1 for C = 4 */
     int64_t n_launches;   /* kernels this context has launched */
@@ -208,7 +209,8 @@ nb_status nb_grid_put(nb_ctx* ctx, const float* xyz_dev, const double* boxes_hos
  * NULL for none.  They are read on the stream and must stay valid until it
  * reaches this call.
  * Errors: NB_ERR_ARG, NB_ERR_BOX (rlist >= L/2 of a box), NB_ERR_STATE (no grid),
- * NB_ERR_CUDA; device flag NB_ERR_CAPACITY (list or exclusion overflow). */
+ * NB_ERR_CUDA; device flags NB_ERR_CAPACITY (list or exclusion overflow),
+ * NB_ERR_ARG (an exclusion index outside 0 .. n - 1, ignored). */
 nb_status nb_pairlist_build(nb_ctx* ctx, float rlist, float rbb, const int* excl_off_dev,
                             const int* excl_idx_dev, nb_stream stream);
 
