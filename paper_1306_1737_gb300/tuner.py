@@ -111,8 +111,9 @@ def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nst
     cache = {}
     if cache_path and os.path.exists(cache_path):
         try:
-            cache = json.load(open(cache_path))
-        except Exception:
+            with open(cache_path) as fh:
+                cache = json.load(fh)
+        except (OSError, ValueError):
             cache = {}
     table = []
     choice = {}
@@ -125,8 +126,9 @@ def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nst
                     for nst in NSTLISTS}
     else:
         rlist_of = {nst: scaled_rlist(params["rc"], rlist0, nstlist0, nst) for nst in NSTLISTS}
+    rule = rlist_rule if rlist_rule != "appendix" else f"appendix:{tolerance}"
     for cls in _classes(counts, n_classes):
-        key = _key(gpu, counts[cls], boxes[cls], params, rlist0, nstlist0, nstprune, H) + rlist_rule
+        key = _key(gpu, counts[cls], boxes[cls], params, rlist0, nstlist0, nstprune, H) + rule
         if key in cache:
             ent = cache[key]
             ent["cached"] = True
@@ -145,7 +147,14 @@ def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nst
                     if log:
                         log(f"class {len(cls)} boxes {int(counts[cls].min())}-{int(counts[cls].max())} atoms: "
                             f"C={C} nstlist={nst}: {t:.4f} ms/frame")
+            if not times:
+                raise ValueError(f"no candidate fits the boxes of {int(counts[cls].min())}-"
+                                 f"{int(counts[cls].max())} particles: a horizon of {H} frames needs an "
+                                 f"nstlist in {NSTLISTS} dividing it, with a list radius below half the "
+                                 f"smallest box edge {float(boxes[cls].min()):.4g} nm")
             best = min(times, key=times.get)
+            if not np.isfinite(times[best]):
+                raise RuntimeError("every candidate of a size class failed its device check")
             # second stage: other prune intervals for the winning shape and lifetime
             bC, bn = map(int, best.split("/"))
             for nsp in NSTPRUNES:
@@ -167,7 +176,10 @@ def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nst
         table.append({"boxes": len(cls), "atoms_min": int(counts[cls].min()), "atoms_max": int(counts[cls].max()),
                       "best": ent["best"], "ms_per_frame": ent["ms_per_frame"], "cached": ent["cached"]})
     if cache_path:
-        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
-        json.dump(cache, open(cache_path, "w"), indent=1, sort_keys=True)
+        d = os.path.dirname(cache_path)
+        if d:
+            os.makedirs(d, exist_ok=True)
+        with open(cache_path, "w") as fh:
+            json.dump(cache, fh, indent=1, sort_keys=True)
     groups = [GroupSpec(C, nst, rlist_of[nst], sorted(b), nstprune=nsp) for (C, nst, nsp), b in sorted(choice.items())]
     return groups, table

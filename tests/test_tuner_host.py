@@ -103,3 +103,44 @@ def test_particle_classes_and_appendix_rlist():
     r = [tuner.appendix_rlist(cls, table, vol, p, nst) for nst in (10, 20, 40)]
     assert all(x > 1.0 for x in r)
     assert r[0] < r[1] < r[2]                             # a longer lifetime needs a larger buffer
+
+
+def _tune_args(counts, boxes, frames_len=40):
+    n = int(counts.sum())
+    frames = np.zeros((frames_len, 1, 3), np.float32)
+    p = {"elec": "ewald", "rc": 1.0, "rlist": 1.1, "beta": 3.12}
+    return (counts, boxes, np.zeros(n), np.zeros(n, np.int32), np.zeros((1, 2)), np.zeros(n + 1, np.int32),
+            np.zeros(0, np.int32), frames, p, 5, 1.1, 20)
+
+
+def test_cache_file_in_the_working_directory(tmp_path, monkeypatch):
+    counts, boxes = _batch(4)
+    monkeypatch.setattr(tuner, "time_group", lambda spec, *a, **k: float(spec.C + spec.nstlist))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda device=0: "fake gpu")
+    monkeypatch.chdir(tmp_path)
+    groups, _ = tuner.tune(*_tune_args(counts, boxes), n_classes=2, cache_path="cache.json")
+    assert (tmp_path / "cache.json").exists()
+    assert [(g.C, g.nstlist) for g in groups] == [(4, 10)]
+
+
+def test_no_candidate_fits_small_boxes(monkeypatch):
+    """Boxes of 1.5 nm: every list radius (>= rc = 1.0 nm) reaches half a box
+    edge, so nothing can be timed and the tuner says why."""
+    counts = np.array([300, 330])
+    boxes = np.full((2, 3), 1.5)
+    monkeypatch.setattr(tuner, "time_group", lambda *a, **k: pytest.fail("nothing should be timed"))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda device=0: "fake gpu")
+    with pytest.raises(ValueError, match="no candidate fits"):
+        tuner.tune(*_tune_args(counts, boxes), n_classes=1)
+    # a horizon no list lifetime divides
+    counts, boxes = _batch(2)
+    with pytest.raises(ValueError, match="no candidate fits"):
+        tuner.tune(*_tune_args(counts, boxes, frames_len=7), n_classes=1)
+
+
+def test_every_candidate_failing_raises(monkeypatch):
+    counts, boxes = _batch(3)
+    monkeypatch.setattr(tuner, "time_group", lambda *a, **k: float("inf"))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda device=0: "fake gpu")
+    with pytest.raises(RuntimeError, match="failed"):
+        tuner.tune(*_tune_args(counts, boxes), n_classes=1)
