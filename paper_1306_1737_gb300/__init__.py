@@ -152,11 +152,17 @@ def status_name(s: int) -> str:
 
 
 def _ptr(x):
-    """Device pointer of a torch tensor (or an int / None)."""
+    """Device pointer of a torch tensor (or an int / None).  A tensor must be
+    a contiguous CUDA tensor: every pointer the library takes addresses a
+    dense device array."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
+    if not x.is_cuda:
+        raise ValueError("the library takes device memory: pass a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("the library takes dense arrays: pass a contiguous tensor")
     return x.data_ptr()
 
 

@@ -60,3 +60,12 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         nb.nb_lj_combine([0.3], [0.5])
     with pytest.raises(RuntimeError, match="missing"):
         nb.nb_create(8, 0)
+
+
+def test_binding_refuses_host_tensors():
+    """Pointers handed to the library address device memory: a CPU tensor is
+    refused before any call (ints and None pass through unchanged)."""
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        nb._ptr(torch.zeros(3))
+    assert nb._ptr(None) is None and nb._ptr(4096) == 4096
