@@ -151,10 +151,14 @@ def status_name(s: int) -> str:
     return load().nb_status_string(int(s)).decode()
 
 
-def _ptr(x):
+_F32, _F64, _I32, _U64 = ("float32",), ("float64",), ("int32",), ("int64", "uint64")
+
+
+def _ptr(x, dtypes=None):
     """Device pointer of a torch tensor (or an int / None).  A tensor must be
     a contiguous CUDA tensor: every pointer the library takes addresses a
-    dense device array."""
+    dense device array; dtypes, where given, lists the element types the C
+    declaration reads."""
     if x is None:
         return None
     if isinstance(x, int):
@@ -163,6 +167,8 @@ def _ptr(x):
         raise ValueError("the library takes device memory: pass a CUDA tensor")
     if not x.is_contiguous():
         raise ValueError("the library takes dense arrays: pass a contiguous tensor")
+    if dtypes is not None and str(x.dtype).replace("torch.", "") not in dtypes:
+        raise ValueError(f"expected a {' or '.join(dtypes)} tensor, got {x.dtype}")
     return x.data_ptr()
 
 
@@ -244,27 +250,27 @@ def nb_set_workspace(ctx, ws, nbytes: int):
 
 
 def nb_set_atoms(ctx, n, q, types, ntypes, c6c12, stream=None):
-    _check(ctx, load().nb_set_atoms(ctx, int(n), _ptr(q), _ptr(types), int(ntypes), _ptr(c6c12),
+    _check(ctx, load().nb_set_atoms(ctx, int(n), _ptr(q, _F32), _ptr(types, _I32), int(ntypes), _ptr(c6c12, _F32),
                                     _stream(stream)))
 
 
 def nb_grid_put(ctx, xyz, boxes, stream=None):
     """boxes: the edges of one box (3 numbers) or of every box ([nbox][3])."""
     b = _boxes(boxes)
-    _check(ctx, load().nb_grid_put(ctx, _ptr(xyz), b.ctypes.data, _stream(stream)))
+    _check(ctx, load().nb_grid_put(ctx, _ptr(xyz, _F32), b.ctypes.data, _stream(stream)))
 
 
 def nb_pairlist_build(ctx, rlist, rbb=0.0, excl_off=None, excl_idx=None, stream=None):
-    _check(ctx, load().nb_pairlist_build(ctx, float(rlist), float(rbb), _ptr(excl_off),
-                                         _ptr(excl_idx), _stream(stream)))
+    _check(ctx, load().nb_pairlist_build(ctx, float(rlist), float(rbb), _ptr(excl_off, _I32),
+                                         _ptr(excl_idx, _I32), _stream(stream)))
 
 
 def nb_set_coords(ctx, xyz, stream=None):
-    _check(ctx, load().nb_set_coords(ctx, _ptr(xyz), _stream(stream)))
+    _check(ctx, load().nb_set_coords(ctx, _ptr(xyz, _F32), _stream(stream)))
 
 
 def nb_prune(ctx, xyz, r_prune, stream=None):
-    _check(ctx, load().nb_prune(ctx, _ptr(xyz), float(r_prune), _stream(stream)))
+    _check(ctx, load().nb_prune(ctx, _ptr(xyz, _F32), float(r_prune), _stream(stream)))
 
 
 def make_params(elec: str, rc: float, eps_rf: float = float("inf"), beta: float = 0.0,
@@ -277,8 +283,8 @@ def make_params(elec: str, rc: float, eps_rf: float = float("inf"), beta: float 
 
 
 def nb_compute(ctx, params: nb_params, xyz, f, e=None, vir=None, stream=None):
-    _check(ctx, load().nb_compute(ctx, C.byref(params), _ptr(xyz), _ptr(f), _ptr(e), _ptr(vir),
-                                  _stream(stream)))
+    _check(ctx, load().nb_compute(ctx, C.byref(params), _ptr(xyz, _F32), _ptr(f, _F32), _ptr(e, _F64),
+                                  _ptr(vir, _F64), _stream(stream)))
 
 
 def nb_check(ctx, stream=None, raise_on_error: bool = True) -> nb_info:
@@ -409,22 +415,23 @@ def nb_buffer_size(classes, c6c12, volume, params, t_ps, temperature, tolerance)
 
 
 def nb_pairlist_1x1(ctx, rlist, max_nbr, nbr, count, stream=None):
-    _check(ctx, load().nb_pairlist_1x1(ctx, float(rlist), int(max_nbr), _ptr(nbr), _ptr(count), _stream(stream)))
+    _check(ctx, load().nb_pairlist_1x1(ctx, float(rlist), int(max_nbr), _ptr(nbr, _I32), _ptr(count, _I32),
+                                       _stream(stream)))
 
 
 def nb_compute_1x1(ctx, params, xyz, nbr, count, max_nbr, f, stream=None):
-    _check(ctx, load().nb_compute_1x1(ctx, C.byref(params), _ptr(xyz), _ptr(nbr), _ptr(count), int(max_nbr),
-                                      _ptr(f), _stream(stream)))
+    _check(ctx, load().nb_compute_1x1(ctx, C.byref(params), _ptr(xyz, _F32), _ptr(nbr, _I32), _ptr(count, _I32),
+                                      int(max_nbr), _ptr(f, _F32), _stream(stream)))
 
 
 def nb_prune_compute(ctx, params, xyz, r_prune, f, e=None, vir=None, stream=None):
-    _check(ctx, load().nb_prune_compute(ctx, C.byref(params), _ptr(xyz), float(r_prune), _ptr(f), _ptr(e),
-                                        _ptr(vir), _stream(stream)))
+    _check(ctx, load().nb_prune_compute(ctx, C.byref(params), _ptr(xyz, _F32), float(r_prune), _ptr(f, _F32),
+                                        _ptr(e, _F64), _ptr(vir, _F64), _stream(stream)))
 
 
 def nb_rdf(ctx, r_max, nbins, type_a, type_b, accumulate, hist, stream=None):
     _check(ctx, load().nb_rdf(ctx, float(r_max), int(nbins), int(type_a), int(type_b), int(accumulate),
-                              _ptr(hist), _stream(stream)))
+                              _ptr(hist, _U64), _stream(stream)))
 
 
 def nb_set_surrogate(ctx, params, r_min, r_max, stream=None):

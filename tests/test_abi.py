@@ -69,3 +69,31 @@ def test_binding_refuses_host_tensors():
     with pytest.raises(ValueError, match="CUDA tensor"):
         nb._ptr(torch.zeros(3))
     assert nb._ptr(None) is None and nb._ptr(4096) == 4096
+
+
+def test_binding_checks_element_types():
+    """The typed pointer arguments of the hot-path calls accept only the
+    element type their C declaration reads (a stand-in object reports itself
+    as a CUDA tensor, so no device is needed)."""
+    torch = pytest.importorskip("torch")
+
+    class DeviceArray:
+        is_cuda = True
+
+        def __init__(self, dtype, contiguous=True):
+            self.dtype, self._c = dtype, contiguous
+
+        def is_contiguous(self):
+            return self._c
+
+        def data_ptr(self):
+            return 4096
+
+    assert nb._ptr(DeviceArray(torch.float32), nb._F32) == 4096
+    assert nb._ptr(DeviceArray(torch.int64), nb._U64) == 4096
+    with pytest.raises(ValueError, match="float32"):
+        nb._ptr(DeviceArray(torch.float64), nb._F32)
+    with pytest.raises(ValueError, match="int32"):
+        nb._ptr(DeviceArray(torch.int64), nb._I32)
+    with pytest.raises(ValueError, match="contiguous"):
+        nb._ptr(DeviceArray(torch.float32, contiguous=False), nb._F32)
