@@ -166,6 +166,13 @@ nb_status nb_workspace_query_boxes(nb_ctx* ctx, int nbox, const int* n_atoms_hos
                                    const double* boxes_host, double rlist_max, int ntypes,
                                    double list_factor, size_t* bytes);
 
+/* The bytes nb_workspace_query_boxes would return for a context of the given
+ * cluster size (4 or 8), computed without a context or a device (host
+ * arithmetic only), e.g. to size allocations ahead of time.
+ * Errors: as nb_workspace_query_boxes; NB_ERR_ARG for another cluster size. */
+nb_status nb_workspace_bytes(int cluster_size, int nbox, const int* n_atoms_host, const double* boxes_host,
+                             double rlist_max, int ntypes, double list_factor, size_t* bytes);
+
 /* Hand the context a device buffer of at least the queried size (256-byte
  * aligned).  The caller owns it and keeps it alive while the context uses
  * it.  Resets all state.  Errors: NB_ERR_ARG, NB_ERR_CAPACITY (too small). */

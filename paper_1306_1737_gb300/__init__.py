@@ -100,6 +100,7 @@ def load():
             "nb_workspace_query": ([P, i, P, C.c_double, i, C.c_double, C.POINTER(C.c_size_t)], st),
             "nb_workspace_query_boxes": ([P, i, P, P, C.c_double, i, C.c_double,
                                           C.POINTER(C.c_size_t)], st),
+            "nb_workspace_bytes": ([i, i, P, P, C.c_double, i, C.c_double, C.POINTER(C.c_size_t)], st),
             "nb_set_workspace": ([P, P, C.c_size_t], st),
             "nb_set_atoms": ([P, i, P, P, i, P, P], st),
             "nb_grid_put": ([P, P, P, P], st),
@@ -242,6 +243,22 @@ def nb_workspace_query_boxes(ctx, n_atoms, boxes, rlist_max: float, ntypes: int,
     _check(ctx, load().nb_workspace_query_boxes(ctx, int(n.shape[0]), n.ctypes.data, b.ctypes.data,
                                                 float(rlist_max), int(ntypes), float(list_factor),
                                                 C.byref(nbytes)))
+    return nbytes.value
+
+
+def nb_workspace_bytes(cluster_size, n_atoms, boxes, rlist_max: float, ntypes: int,
+                       list_factor: float = 0.0) -> int:
+    """Workspace bytes of a plan, computed on the host (no context, no device)."""
+    import numpy as np
+    n = np.ascontiguousarray(n_atoms, dtype=np.int32).reshape(-1)
+    b = _boxes(boxes)
+    if b.shape[0] != n.shape[0]:
+        raise ValueError("one box per particle count")
+    nbytes = C.c_size_t()
+    s = load().nb_workspace_bytes(int(cluster_size), int(n.shape[0]), n.ctypes.data, b.ctypes.data,
+                                  float(rlist_max), int(ntypes), float(list_factor), C.byref(nbytes))
+    if s != NB_OK:
+        raise NbError(s, "workspace plan refused")
     return nbytes.value
 
 

@@ -510,6 +510,14 @@ nb_status nb_workspace_query(nb_ctx* c, int n, const double* box, double rlist_m
     return nb_workspace_query_boxes(c, 1, &n, box, rlist_max, ntypes, list_factor, bytes);
 }
 
+nb_status nb_workspace_bytes(int cluster_size, int nbox, const int* n_atoms, const double* boxes,
+                             double rlist_max, int ntypes, double list_factor, size_t* bytes) {
+    if (cluster_size != 4 && cluster_size != 8) return NB_ERR_ARG;
+    nb_ctx plan;   // planning is host arithmetic: no device state is touched
+    plan.C = cluster_size;
+    return nb_workspace_query_boxes(&plan, nbox, n_atoms, boxes, rlist_max, ntypes, list_factor, bytes);
+}
+
 nb_status nb_set_workspace(nb_ctx* c, void* ws, size_t bytes) {
     if (!c || !ws) return fail(c, NB_ERR_ARG, "set_workspace: null");
     if (((uintptr_t)ws & 255) != 0) return fail(c, NB_ERR_ARG, "workspace must be 256-byte aligned");
