@@ -50,3 +50,57 @@ def test_force_source_hash_covers_the_force_kernel_files():
     assert len(h) == 12 and all(c in "0123456789abcdef" for c in h)
     for rel in bench.FORCE_SOURCES:
         assert os.path.exists(os.path.join(bench.ROOT, rel)), rel
+
+
+def _sampler(**attrs):
+    s = object.__new__(bench.ClockSampler)
+    s.proc = s.path = s.thread = s.nvml = s.handle = None
+    s.samples = []
+    for k, v in attrs.items():
+        setattr(s, k, v)
+    return s
+
+
+def test_clock_sampler_nvml_summary():
+    """NVML samples (SM MHz, clock-event-reason bits) reduce to the median
+    clock, the maximum clock NVML reports and the named reasons seen."""
+    import threading
+
+    class FakeNvml:
+        def nvmlDeviceGetMaxClockInfo(self, handle, kind, out):
+            assert kind == 1                       # SM clock domain
+            out._obj.value = 2070
+            return 0
+
+    t = threading.Thread(target=lambda: None)
+    t.start()
+    s = _sampler(nvml=FakeNvml(), thread=t, samples=[(2070, 0x4), (2055, 0x0), (2070, 0x8 | 0x4)])
+    out = s.stop()
+    assert out == {"sm_mhz": 2070, "sm_max_mhz": 2070, "reasons": ["hw_slowdown", "sw_power_cap"],
+                   "samples": 3, "source": "nvml"}
+
+
+def test_clock_sampler_nvidia_smi_summary(tmp_path):
+    """The nvidia-smi fallback: CSV rows of the query, reasons named where
+    their column says Active."""
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    path = tmp_path / "clocks.csv"
+    path.write_text("0, 2070, 2070, 910.2, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+                    "0, 1980, 2070, 1390.0, 0x0000000000000044, Not Active, Active, Not Active, Active\n"
+                    "0, 2070, 2070, 905.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+                    "garbage line\n")
+    s = _sampler(proc=FakeProc(), path=str(path))
+    out = s.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["hw_thermal_slowdown", "sw_power_cap"],
+                   "samples": 3, "source": "nvidia-smi"}
+    assert not path.exists()
+
+
+def test_clock_sampler_without_a_source():
+    assert _sampler().stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
