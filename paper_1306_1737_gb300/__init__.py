@@ -321,13 +321,13 @@ def nb_box_info(ctx, box: int) -> nb_info:
 
 def nb_get_grid(ctx, atom_of_slot=None, slot_of_atom=None, col_clu_start=None, xyzq=None,
                 type_slot=None, bb=None, col_of_atom=None, sc_info=None, stream=None):
-    _check(ctx, load().nb_get_grid(ctx, _ptr(atom_of_slot), _ptr(slot_of_atom), _ptr(col_clu_start),
-                                   _ptr(xyzq), _ptr(type_slot), _ptr(bb), _ptr(col_of_atom),
-                                   _ptr(sc_info), _stream(stream)))
+    _check(ctx, load().nb_get_grid(ctx, _ptr(atom_of_slot, _I32), _ptr(slot_of_atom, _I32),
+                                   _ptr(col_clu_start, _I32), _ptr(xyzq, _F32), _ptr(type_slot, _I32),
+                                   _ptr(bb, _F32), _ptr(col_of_atom, _I32), _ptr(sc_info, _I32), _stream(stream)))
 
 
 def nb_get_list(ctx, which, ient=None, cj=None, mask=None, stream=None):
-    _check(ctx, load().nb_get_list(ctx, int(which), _ptr(ient), _ptr(cj), _ptr(mask),
+    _check(ctx, load().nb_get_list(ctx, int(which), _ptr(ient, _I32), _ptr(cj, _I32), _ptr(mask, _U64),
                                    _stream(stream)))
 
 
@@ -350,9 +350,10 @@ def nb_grid_put_noalloc(n, xyz, q, types, ntypes, box, cluster_size, atom_of_slo
     """Gridding into caller-provided outputs with no device allocation
     anywhere (scratch in a fixed array inside the library); see the header."""
     b = (C.c_double * 3)(*[float(v) for v in box])
-    s = load().nb_grid_put_noalloc(int(n), _ptr(xyz), _ptr(q), _ptr(types), int(ntypes), b,
-                                   int(cluster_size), _ptr(atom_of_slot), _ptr(xyzq), _ptr(type_slot),
-                                   _ptr(bb), _ptr(col_clu_start), _ptr(info), int(max_slots),
+    s = load().nb_grid_put_noalloc(int(n), _ptr(xyz, _F32), _ptr(q, _F32), _ptr(types, _I32), int(ntypes), b,
+                                   int(cluster_size), _ptr(atom_of_slot, _I32), _ptr(xyzq, _F32),
+                                   _ptr(type_slot, _I32), _ptr(bb, _F32), _ptr(col_clu_start, _I32),
+                                   _ptr(info, _I32), int(max_slots),
                                    int(max_columns), _stream(stream))
     _check(None, s)
 
@@ -363,13 +364,13 @@ def _status(s, what):
 
 
 def nb_ewald_factor(r, beta, out, stream=None):
-    _status(load().nb_ewald_factor(_ptr(r), int(r.numel()), float(beta), _ptr(out), _stream(stream)),
+    _status(load().nb_ewald_factor(_ptr(r, _F64), int(r.numel()), float(beta), _ptr(out, _F64), _stream(stream)),
             "nb_ewald_factor")
 
 
 def nb_mlp_forward(params, r_min, r_max, r, y, stream=None):
-    _status(load().nb_mlp_forward(_ptr(params), float(r_min), float(r_max), _ptr(r), int(r.numel()), _ptr(y),
-                                  _stream(stream)), "nb_mlp_forward")
+    _status(load().nb_mlp_forward(_ptr(params, _F32), float(r_min), float(r_max), _ptr(r, _F32), int(r.numel()),
+                                  _ptr(y, _F32), _stream(stream)), "nb_mlp_forward")
 
 
 def nb_mlp_packed_bytes() -> int:
@@ -377,25 +378,27 @@ def nb_mlp_packed_bytes() -> int:
 
 
 def nb_mlp_pack(params, r_min, r_max, packed, stream=None):
-    _status(load().nb_mlp_pack(_ptr(params), float(r_min), float(r_max), _ptr(packed), _stream(stream)),
+    _status(load().nb_mlp_pack(_ptr(params, _F32), float(r_min), float(r_max), _ptr(packed), _stream(stream)),
             "nb_mlp_pack")
 
 
 def nb_mlp_forward_tc(packed, r, y, stream=None):
-    _status(load().nb_mlp_forward_tc(_ptr(packed), _ptr(r), int(r.numel()), _ptr(y), _stream(stream)),
+    _status(load().nb_mlp_forward_tc(_ptr(packed), _ptr(r, _F32), int(r.numel()), _ptr(y, _F32), _stream(stream)),
             "nb_mlp_forward_tc")
 
 
 def nb_mlp_loss_grad(params, r_min, r_max, r, t, w, grad, loss=None, stream=None):
-    _status(load().nb_mlp_loss_grad(_ptr(params), float(r_min), float(r_max), _ptr(r), _ptr(t), _ptr(w),
-                                    int(r.numel()), _ptr(grad), _ptr(loss), _stream(stream)), "nb_mlp_loss_grad")
+    _status(load().nb_mlp_loss_grad(_ptr(params, _F32), float(r_min), float(r_max), _ptr(r, _F32), _ptr(t, _F32),
+                                    _ptr(w, _F32), int(r.numel()), _ptr(grad, _F32), _ptr(loss, _F32),
+                                    _stream(stream)), "nb_mlp_loss_grad")
 
 
 def nb_mlp_train(params, state, r_min, r_max, r, t, w, batch, steps, step0, total_steps, lr_max, lr_min,
                  loss=None, stream=None):
-    _status(load().nb_mlp_train(_ptr(params), _ptr(state), float(r_min), float(r_max), _ptr(r), _ptr(t), _ptr(w),
+    _status(load().nb_mlp_train(_ptr(params, _F32), _ptr(state, _F32), float(r_min), float(r_max), _ptr(r, _F32),
+                                _ptr(t, _F32), _ptr(w, _F32),
                                 int(r.numel()), int(batch), int(steps), int(step0), int(total_steps),
-                                float(lr_max), float(lr_min), _ptr(loss), _stream(stream)), "nb_mlp_train")
+                                float(lr_max), float(lr_min), _ptr(loss, _F32), _stream(stream)), "nb_mlp_train")
 
 
 def _classes(classes):
@@ -452,7 +455,7 @@ def nb_rdf(ctx, r_max, nbins, type_a, type_b, accumulate, hist, stream=None):
 
 
 def nb_set_surrogate(ctx, params, r_min, r_max, stream=None):
-    _check(ctx, load().nb_set_surrogate(ctx, _ptr(params), float(r_min), float(r_max), _stream(stream)))
+    _check(ctx, load().nb_set_surrogate(ctx, _ptr(params, _F32), float(r_min), float(r_max), _stream(stream)))
 
 
 # --- convenience: boxes with their torch-allocated workspace ----------------
