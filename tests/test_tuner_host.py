@@ -144,3 +144,14 @@ def test_every_candidate_failing_raises(monkeypatch):
     monkeypatch.setattr(torch.cuda, "get_device_name", lambda device=0: "fake gpu")
     with pytest.raises(RuntimeError, match="failed"):
         tuner.tune(*_tune_args(counts, boxes), n_classes=1)
+
+
+def test_batch_runner_refuses_a_horizon_a_lifetime_does_not_divide():
+    """The check runs before any context is created (no device needed)."""
+    counts, boxes = _batch(2)
+    n = int(counts.sum())
+    frames = np.zeros((30, n, 3), np.float32)
+    with pytest.raises(ValueError, match="multiple"):
+        batch.BatchRunner(counts, boxes, np.zeros(n), np.zeros(n, np.int32), np.zeros((1, 1, 2)),
+                          np.zeros(n + 1, np.int32), np.zeros(0, np.int32), frames,
+                          [batch.GroupSpec(8, 20, 1.1, [0, 1])], {"elec": "ewald", "rc": 1.0}, 5)
