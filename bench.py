@@ -5,9 +5,12 @@ A step is one pair-list lifetime of the workload: grid the box
 (nb_grid_put), build the buffered cluster-pair list (nb_pairlist_build), then
 nstlist frames, each with new coordinates and one force evaluation
 (nb_compute; energies and virial on the first and last frame; every nstprune
-frames nb_prune_compute, which prunes the list in the same pass).  The headline value is force evaluations per second
-over the whole job.  Default workload: 24,000-atom water box, Ewald real
-space rc 1.0 nm, beta 3.12 nm^-1, rlist 1.1 nm, nstlist 20, prune every 5.
+frames nb_prune_compute, which prunes the list in the same pass).  The
+headline value is force evaluations per second over the whole job.  Default
+workload: the 3,000,000-atom water box (10% of molecules re-typed among 8 LJ
+types), Ewald real space rc 1.0 nm, beta 3.12 nm^-1, rlist 1.1 nm, nstlist
+40, prune every 5; its line also carries a block for the 24,000-atom box
+(nstlist 20) and one for the batch of 256 uneven boxes.
 
 --impl reference times the FP64 CPU oracle (its cell-list tier, the same
 pairs as the brute-force minimum-image loop) on the same workload and metric:
@@ -381,8 +384,8 @@ def run_reference(args):
     return 0
 
 
-def config_dict(args, box, p, desc):
-    return {"workload": args.workload, "description": desc, "n_atoms": int(box.n),
+def config_dict(args, box, p, desc, workload=None):
+    return {"workload": workload or args.workload, "description": desc, "n_atoms": int(box.n),
             "box_nm": [round(float(v), 6) for v in box.box], "elec": p["elec"], "rc_nm": p["rc"],
             "rlist_nm": p["rlist"], "beta_nm-1": p.get("beta"), "nstlist": p.get("nstlist", 1),
             "nstprune": p.get("nstprune", 0), "cluster": "8x8 cluster pairs (two 8x4 halves per warp), super-clusters of 2 i-clusters sharing a j-list",
@@ -582,13 +585,9 @@ def buffer_estimate(nb, box, p, nstlist, rlist, dt_ps=0.002, temperature=300.0):
             "model": "free flight (sigma^2 = t^2 kB T (1/m1 + 1/m2)), an upper bound for rigid water"}
 
 
-def run_ours(args):
-    import numpy as np
+def init_ranks():
+    """(dist or None, world size, rank, device) of this process; one GPU per rank."""
     import torch
-
-    import paper_1306_1737_gb300 as nb
-    from paper_1306_1737_gb300 import workloads as w
-
     ws_n, rank, local = dist_env()
     if ws_n > 1:
         import torch.distributed as dist
@@ -597,9 +596,39 @@ def run_ours(args):
     else:
         dist = None
         torch.cuda.set_device(0)
-    dev = torch.device("cuda", torch.cuda.current_device())
+    return dist, ws_n, rank, torch.device("cuda", torch.cuda.current_device())
+
+
+def run_ours(args):
+    import paper_1306_1737_gb300 as nb
+    dist, ws_n, rank, dev = init_ranks()
     nb.load()
-    desc, fn = workloads()[args.workload]
+    out = measure_box(args, args.workload, dist, ws_n, rank, dev, extras=True)
+    if out is not None and args.sub_blocks and args.workload == "water3m":
+        # the same path on the 24k box and on the batch of 256 boxes (this
+        # rank's GPU only; the other ranks wait at the closing barrier)
+        out["water24k"] = measure_box(args, "water24k", None, 1, 0, dev, extras=False)
+        out["batch256"] = measure_batch(args, None, 1, 0, dev, sub=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
+    """One box workload: graph-replayed steps (the headline), per-kernel
+    spans, the roofline of the force kernel, the end-to-end rate with host
+    buffers, and (extras) the oracle baseline and the comparison blocks.
+    Returns the JSON dict on rank 0, else None."""
+    import numpy as np
+    import torch
+
+    import paper_1306_1737_gb300 as nb
+    from paper_1306_1737_gb300 import workloads as w
+
+    desc, fn = workloads()[workload]
     box, p = fn()
     nstlist = int(p.get("nstlist", 1))
     nstprune = int(p.get("nstprune", 0))
@@ -798,8 +827,8 @@ def run_ours(args):
     achieved = flops / t_force
     roofline = {"bound": "alu", "kernel": "k_force8 (Ewald)" if elec == "ewald" else "k_force8 (RF)",
                 "achieved": achieved / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": profiled_traffic(args.workload),
-                "ncu": profiled_counters(args.workload),
+                "frac": achieved / fp32_peak, "traffic": profiled_traffic(workload),
+                "ncu": profiled_counters(workload),
                 "traffic_unit": "bytes per launch (dram read + write, ncu)",
                 "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {pk['sm_max_mhz']:.0f} MHz "
                                f"(max SM clock, {pk['source']})",
@@ -839,17 +868,20 @@ def run_ours(args):
                           / np.sqrt((Fd ** 2).sum(1).mean()))
         h2d = nstlist * box.n * 12
         d2h = nstlist * box.n * 12 + 16
-        cpu = cpu_baseline(box, p) if ws_n == 1 else None
-        surr = surrogate_ab(nb, ctx, box, p, xs, F, stream, dev) if elec == "ewald" and args.surrogate else None
-        cmp11 = compare_1x1(nb, ctx, box, p, xs[0], F, rlist, rprune, stream) if args.compare_1x1 else None
-        buf = buffer_estimate(nb, box, p, nstlist, rlist) if elec == "ewald" else None
-        tab = tabulated_ab(nb, ctx, p, xs[0], F, stream) if elec == "ewald" else None
-        pcf = pair_correlation(nb, ctx, box, xs[0], eo, ei, stream, rbb) if args.pair_correlation else None
+        ewald = elec == "ewald"
+        cpu = cpu_baseline(box, p) if ws_n == 1 and extras else None
+        surr = surrogate_ab(nb, ctx, box, p, xs, F, stream, dev) if ewald and args.surrogate and extras else None
+        cmp11 = compare_1x1(nb, ctx, box, p, xs[0], F, rlist, rprune, stream) if args.compare_1x1 and extras \
+            else None
+        buf = buffer_estimate(nb, box, p, nstlist, rlist) if ewald and extras else None
+        tab = tabulated_ab(nb, ctx, p, xs[0], F, stream) if ewald and extras else None
+        pcf = pair_correlation(nb, ctx, box, xs[0], eo, ei, stream, rbb) if args.pair_correlation and extras \
+            else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1000 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": config_dict(args, box, p, desc),
+            "data": "synthetic", "config": config_dict(args, box, p, desc, workload),
             "pair_interactions_per_s": listed_all * nstlist * args.steps * ws_n / total_s,
             "effective_pair_interactions_per_s": pairs_rc * nstlist * args.steps * ws_n / total_s,
             "force_kernel": {"ms": t_force * 1e3, "listed_pairs_per_s": listed / t_force,
@@ -883,13 +915,14 @@ def run_ours(args):
             "clocks": clocks,
             "status": nb.status_name(info0.status),
         }
+        if not extras:
+            for k in ("cpu_baseline", "surrogate", "particle_pair_1x1", "buffer_estimate", "tabulated_ewald",
+                      "pair_correlation"):
+                del out[k]
     cx.close()
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
-    if out is not None:
-        print(json.dumps(out), flush=True)
-    return 0
+    del xs, flush
+    torch.cuda.empty_cache()
+    return out
 
 
 BATCH_H = 40          # frames per batch step (a multiple of every tuned nstlist)
@@ -942,9 +975,23 @@ def batch_cpu_baseline(B, p, budget_s=15.0):
 
 
 def run_batch(args):
+    import paper_1306_1737_gb300 as nb
+    dist, ws_n, rank, dev = init_ranks()
+    nb.load()
+    out = measure_batch(args, dist, ws_n, rank, dev)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def measure_batch(args, dist, ws_n, rank, dev, sub=False):
     """The batch of 256 uneven boxes: tuned groups stepped in a CUDA graph,
     against one context for all boxes (graph) and one context per box
-    (plain launches, one box after another)."""
+    (plain launches, one box after another).  sub: a block of another
+    workload's line (no oracle baseline).  Returns the dict on rank 0."""
     import numpy as np
     import torch
 
@@ -952,16 +999,6 @@ def run_batch(args):
     from paper_1306_1737_gb300 import tuner
     from paper_1306_1737_gb300.batch import BatchRunner, GroupSpec
 
-    ws_n, rank, local = dist_env()
-    if ws_n > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        dist = None
-        torch.cuda.set_device(0)
-    dev = torch.device("cuda", torch.cuda.current_device())
-    nb.load()
     B, p = batch_workload()
     c6c12 = nb.nb_lj_combine(B.sigma, B.eps)
     frames = batch_frames(B, dev)
@@ -1089,7 +1126,7 @@ def run_batch(args):
         pk = peaks()
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         fp32_peak = n_sm * 128 * 2 * pk["sm_max_mhz"] * 1e6
-        cpu = batch_cpu_baseline(B, p) if ws_n == 1 else None
+        cpu = batch_cpu_baseline(B, p) if ws_n == 1 and not sub else None
         h2d = BATCH_H * B.n * 12
         out = {
             "metric": METRIC, "value": value, "unit": BATCH_UNIT, "n_gpus": ws_n, "steps": args.steps,
@@ -1123,15 +1160,12 @@ def run_batch(args):
             "clocks": clocks,
             "status": st_tuned[0] if len(set(st_tuned)) == 1 else st_tuned,
         }
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
-    if out is not None:
-        print(json.dumps(out), flush=True)
-    return 0
+    del frames, flush
+    torch.cuda.empty_cache()
+    return out
 
 
-def main():
+def make_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -1150,9 +1184,15 @@ def main():
                     help="skip the pair correlation (g(r) histogram) measurement")
     ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",
                     help="skip the learned Ewald factor A/B (Ewald workloads)")
-    ap.add_argument("--workload", default="water24k",
+    ap.add_argument("--no-sub-blocks", dest="sub_blocks", action="store_false",
+                    help="water3m: skip the water24k and batch256 blocks of the line")
+    ap.add_argument("--workload", default="water3m",
                     choices=["water24k", "water3m", "water1536", "water1m", "batch256"])
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = make_parser().parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

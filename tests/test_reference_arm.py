@@ -25,7 +25,7 @@ def _run(extra_env, *args):
 def test_reference_arm_prints_one_contract_line():
     pytest.importorskip("torch")
     import bench
-    r = _run({}, "--steps", "1", "--warmup", "3")
+    r = _run({}, "--steps", "1", "--warmup", "3", "--workload", "water24k")
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -49,3 +49,13 @@ def test_reference_arm_other_ranks_exit_without_work():
              "--warmup", "3")
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_default_workload_is_the_3m_box():
+    """With no flags the bench (and its reference arm) times the largest
+    single-GPU machine, the 3,000,000-atom Ewald workload."""
+    import bench
+    args = bench.make_parser().parse_args([])
+    assert args.workload == "water3m" and args.gpus == 1 and args.sub_blocks
+    desc, fn = bench.workloads()["water3m"]
+    assert "3,000,000" in desc
