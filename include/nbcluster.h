@@ -504,8 +504,11 @@ nb_status nb_set_surrogate(nb_ctx* ctx, const float* params_dev, float r_min, fl
  * ({xmin, ymin, zmin, 0, xmax, ymax, zmax, 0} per cluster), col_clu_start
  * int [max_columns + 1], info int [2] = {number of clusters, device flags
  * (1 << NB_ERR_COORD for a coordinate outside [-L, 2L), 1 << NB_ERR_ARG for
- * a type out of range)}.  Only the first clusters * C slots and nx * ny + 1
- * column entries are written.  xyzq and bb must be 16-byte aligned.
+ * a type out of range, 1 << NB_ERR_CAPACITY for a grid column holding more
+ * than 8192 particles: that column's particles get no slot, its clusters
+ * are dummies, and the call still returns NB_OK)}.  Only the first
+ * clusters * C slots and nx * ny + 1 column entries are written.  xyzq and
+ * bb must be 16-byte aligned.
  * The first call on a device (with that device current) looks up the
  * scratch array's device address; make that first call before any stream
  * capture.  All calls share the one array and each call clears the parts

@@ -345,10 +345,34 @@ def nb_profile_read(ctx, max_spans=256):
     return [(kinds[k], ms[k]) for k in range(cnt.value)]
 
 
+def _need(x, count, name):
+    """Raise if tensor x holds fewer than count elements (the C entry point
+    trusts the sizes it is given; raw integer pointers are the caller's
+    responsibility)."""
+    if x is not None and not isinstance(x, int) and x.numel() < count:
+        raise ValueError(f"{name} holds {x.numel()} elements, the call needs at least {count}")
+
+
 def nb_grid_put_noalloc(n, xyz, q, types, ntypes, box, cluster_size, atom_of_slot, xyzq, type_slot,
                         bb, col_clu_start, info, max_slots, max_columns, stream=None):
     """Gridding into caller-provided outputs with no device allocation
-    anywhere (scratch in a fixed array inside the library); see the header."""
+    anywhere (scratch in a fixed array inside the library); see the header.
+    Tensor arguments are checked against n, max_slots and max_columns first,
+    since the library writes up to those sizes."""
+    n, ms, mc, cs = int(n), int(max_slots), int(max_columns), int(cluster_size)
+    if n > 0:
+        _need(xyz, 3 * n, "xyz")
+        _need(q, n, "q")
+        _need(types, n, "types")
+    if ms > 0:
+        _need(atom_of_slot, ms, "atom_of_slot")
+        _need(type_slot, ms, "type_slot")
+        _need(xyzq, 4 * ms, "xyzq")
+        if cs in (4, 8):
+            _need(bb, 8 * (ms // cs), "bb")
+    if mc > 0:
+        _need(col_clu_start, mc + 1, "col_clu_start")
+    _need(info, 2, "info")
     b = (C.c_double * 3)(*[float(v) for v in box])
     s = load().nb_grid_put_noalloc(int(n), _ptr(xyz, _F32), _ptr(q, _F32), _ptr(types, _I32), int(ntypes), b,
                                    int(cluster_size), _ptr(atom_of_slot, _I32), _ptr(xyzq, _F32),

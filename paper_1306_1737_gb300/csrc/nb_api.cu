@@ -120,39 +120,6 @@ static bool box_ok(const double* box) {
     return true;
 }
 
-// At most this many grid columns along x and along y, so that nx * ny fits
-// an int; only slab-like boxes far thinner than the column spacing reach it.
-constexpr int kMaxGridDim = 1 << 15;
-
-static int grid_extent(double L, double s) {
-    const double g = std::floor(L / s);
-    if (!(g >= 1.0)) return 1;
-    return g > (double)kMaxGridDim ? kMaxGridDim : (int)g;
-}
-
-// Grid dimensions (Sec. 2.3): spacing (C / rho)^(1/3) along x and y.
-static void grid_dims(int n, const float L[3], int C, int* nx, int* ny) {
-    int gx = 1, gy = 1;
-    if (n > 0) {
-        const double Lx = L[0], Ly = L[1], Lz = L[2];
-        const double rho = (double)n / (Lx * Ly * Lz);
-        const double s = std::cbrt((double)C / rho);
-        gx = grid_extent(Lx, s);
-        gy = grid_extent(Ly, s);
-    }
-    *nx = gx;
-    *ny = gy;
-}
-
-static float dummy_spacing(const float L[3]) {
-    float m = L[0];
-    if (L[1] > m) m = L[1];
-    if (L[2] > m) m = L[2];
-    float g = 1.0f;
-    while (g < 4.0f * m) g *= 2.0f;
-    return g;
-}
-
 // Capacities of one box holding n particles in box L with lists up to rlist.
 // The number of j-entries is estimated from the density: j-clusters whose
 // bounding box is within rlist of a super-cluster's box (half of them,
@@ -230,6 +197,7 @@ static size_t carve(const nb_ctx* c, char* base, Workspace* ws) {
     w.keys = (unsigned long long*)take(sizeof(unsigned long long) * na);
     const size_t ns = (size_t)w.clu_total * C;
     w.xyzq = (float4*)take(sizeof(float4) * ns);
+    w.xjd = (float4*)take(sizeof(float4) * 2 * ns);
     w.atom_of_slot = (int*)take(sizeof(int) * ns);
     w.type_slot = (int*)take(sizeof(int) * ns);
     w.fslot = (float4*)take(sizeof(float4) * ns);
@@ -592,19 +560,12 @@ nb_status nb_grid_put(nb_ctx* c, const float* xyz, const double* boxes, nb_strea
     for (int b = 0; b < c->nbox; ++b) {
         if (!box_ok(boxes + 3 * b)) return fail(c, NB_ERR_BOX, "box %d: edges must be positive and below 1e30 nm", b);
         BoxGeom& g = geo[b];
-        memset(&g, 0, sizeof(g));
-        for (int k = 0; k < 3; ++k) g.L[k] = (float)boxes[3 * b + k];
         const int nb_atoms = c->plan[b].n;
-        grid_dims(nb_atoms, g.L, c->C, &g.nx, &g.ny);
+        g = box_geometry(nb_atoms, boxes + 3 * b, c->C);
         if (g.nx * g.ny > c->plan[b].ncol_cap)
             return fail(c, NB_ERR_CAPACITY, "box %d: grid has more columns than the workspace", b);
         if ((long long)nb_atoms + (long long)g.nx * g.ny * (c->C - 1) > c->plan[b].nclu_cap * c->C)
             return fail(c, NB_ERR_CAPACITY, "box %d: grid may need more slots than the workspace", b);
-        g.inv_x = (float)((double)g.nx / (double)g.L[0]);
-        g.inv_y = (float)((double)g.ny / (double)g.L[1]);
-        g.inv_cx = (float)g.nx / g.L[0];
-        g.inv_cy = (float)g.ny / g.L[1];
-        g.dummy_g = dummy_spacing(g.L);
     }
     NB_CUDA(c, cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;

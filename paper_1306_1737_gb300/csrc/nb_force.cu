@@ -1,19 +1,24 @@
 // Cluster-pair force/energy kernels (Sec. 3, Fig. 6); the FP64 totals and the
 // return to the caller's order are in nb_finalize.cu.
 //
-// k_force8: one warp per i-entry {ci, shift, j-range} of 8-particle clusters.
-// Lane (ih = lane / 8, j = lane % 8) owns particle pairs (ih, j) and (ih+4, j)
-// of every j-cluster, so the 8 x 8 cluster pair is two 8 x 4 halves spread
-// over the warp (one particle pair per thread and half).  The i-cluster stays
-// in registers, shifted by the entry's periodic image as an unevaluated FP32
-// sum hi + lo; each j-particle is one coalesced float4 load.  A pair is
-// computed when r^2 < rc^2 and either its mask bit is set (full LJ + Coulomb)
-// or it is a counted pair without the bit (force-field exclusion: only the
-// RF/Ewald correction, Sec. 2.4); the mask bit multiplies the plain terms
-// (Sec. 3.1: masking by multiplication, conditional on the cut-off).
-// j-forces are reduced over the 4 lanes sharing j with two shuffles and
-// added with one vector atomic per j-particle; i-forces are reduced at the
-// end of the entry and added once per i-particle.
+// k_force8: one warp per i-entry {super-cluster, shift, j-range} of
+// 8-particle clusters.  Lane (ih = lane / 8, j = lane % 8) owns particle pairs
+// (ih, j) and (ih+4, j) of every i-cluster and j-cluster, so the 8 x 8
+// cluster pair is two 8 x 4 halves spread over the warp, and the lane's two
+// pairs are the two halves of packed FP32x2 operations.  The super-cluster's
+// i-particles are staged in shared memory in that pairing, shifted by the
+// entry's periodic image as an unevaluated FP32 sum hi + lo; each j-particle
+// comes as two float4 of a duplicated layout ({-x, -x, -y, -y}, {-z, -z, q,
+// q}) so that it enters packed operations without register copies.  A pair
+// is computed when r^2 < rc^2 and either its mask bit is set (full LJ +
+// Coulomb) or it is a counted pair without the bit (force-field exclusion:
+// only the RF/Ewald correction, Sec. 2.4); the mask bit multiplies the plain
+// terms (Sec. 3.1: masking by multiplication, conditional on the cut-off).
+// j-entries whose interacting i-clusters all have full masks off the
+// diagonal (most of them) take a path with the cut-off as the only
+// condition.  j-forces are reduced over the 4 lanes sharing j with two
+// shuffles and added with one vector atomic per j-particle; i-forces are
+// reduced at the end of the entry and added once per i-particle.
 //
 // Pair functions (Sec. 3.2), with qq = f q_i q_j and e = mask bit:
 //   LJ      F/r = e (12 C12 r^-6 - 6 C6) r^-8,  V = e (C12 r^-6 - C6) r^-6
@@ -35,6 +40,7 @@ struct ForceArgs {
     const unsigned long long* mask;
     long long jstride;                // stride between the per-i-cluster mask arrays
     const float4* xyzq;
+    const float4* xjd;                // duplicated, negated j layout (two float4 per slot)
     const int* type_slot;
     float4* fslot;
     const float2* c6c12;
@@ -63,65 +69,8 @@ constexpr int kForceWarps = 4;
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 sel2(bool p, bool q, float2 v) {
     return make_float2(p ? v.x : 0.0f, q ? v.y : 0.0f);
-}
-
-// Two particle pairs of one lane (components x, y): lj0/lj1 = {-6 C6, 12 C12};
-// u: mask bit (full interaction); inc: pair counted and inside rc.  Pairs
-// that are not counted are computed on whatever r2 they have and selected
-// away (no NaN escapes the selects).
-template <int ELEC, bool ENERGY, bool FIT>
-__device__ __forceinline__ void pair2(const ForceParams& P, bool inc0, bool inc1, bool u0, bool u1,
-                                      float2 r2, float2 qq, float2 lj0, float2 lj1, float2& fs,
-                                      float& vlj, float& vc) {
-    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-    const float2 rinv2 = mul2(rinv, rinv);
-    const float2 rinv6 = mul2(mul2(rinv2, rinv2), rinv2);
-    const float2 c6n = make_float2(lj0.x, lj1.x), c12 = make_float2(lj0.y, lj1.y);
-    const float2 flj = sel2(u0, u1, mul2(mul2(fma2(c12, rinv6, c6n), rinv6), rinv2));
-    const float2 rinv3e = sel2(u0, u1, mul2(rinv, rinv2));
-    float2 fc;
-    if (ELEC == NB_ELEC_RF) {
-        fc = mul2(qq, add2(rinv3e, bc2(-P.two_k_rf)));
-    } else if (FIT) {
-        const float2 w = mul2(bc2(P.beta2), r2);
-        const float2 g = make_float2(ewald_fit_g(w.x), ewald_fit_g(w.y));
-        fc = mul2(qq, fma2(g, bc2(-P.beta3), rinv3e));
-    } else {
-        float rr[2] = {r2.x, r2.y}, ri[2] = {rinv.x, rinv.y}, re[2] = {rinv3e.x, rinv3e.y}, o[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const float r = rr[k] * ri[k];
-            const float br = P.beta * r;
-            // (erfc(br) - 1 + 2br/sqrt(pi) exp(-b^2 r^2)) / r^3 = -beta^3 G
-            o[k] = re[k] + (erfcf(br) - 1.0f + P.two_beta_sqrtpi * r * __expf(-br * br)) * ri[k] * ri[k] * ri[k];
-        }
-        fc = mul2(qq, make_float2(o[0], o[1]));
-    }
-    fs = sel2(inc0, inc1, add2(flj, fc));
-    if (ENERGY) {
-        // V_LJ = (C12 r^-6 - C6) r^-6
-        const float2 v6 = mul2(fma2(mul2(c12, bc2(1.0f / 12.0f)), rinv6, mul2(c6n, bc2(1.0f / 6.0f))), rinv6);
-        const float2 vl = sel2(inc0 && u0, inc1 && u1, v6);
-        const float2 rinve = sel2(u0, u1, rinv);
-        float2 v;
-        if (ELEC == NB_ELEC_RF) {
-            v = mul2(qq, fma2(bc2(P.k_rf), r2, add2(rinve, bc2(-P.c_rf))));
-        } else if (FIT) {
-            const float2 w = mul2(bc2(P.beta2), r2);
-            const float2 h = make_float2(ewald_fit_h(w.x), ewald_fit_h(w.y));
-            v = mul2(qq, fma2(h, bc2(-P.beta), rinve));
-        } else {
-            const float r0 = r2.x * rinv.x, r1 = r2.y * rinv.y;
-            v = mul2(qq, make_float2((erfcf(P.beta * r0) - 1.0f) * rinv.x + rinve.x,
-                                     (erfcf(P.beta * r1) - 1.0f) * rinv.y + rinve.y));
-        }
-        const float2 vsel = sel2(inc0, inc1, v);
-        vlj += vl.x + vl.y;
-        vc += vsel.x + vsel.y;
-    }
 }
 
 struct Lane8 {
@@ -131,6 +80,12 @@ struct Lane8 {
 };
 
 constexpr int kSuper8 = super_size(8);
+// Set in a staged j-word (sign bit, above the cluster index and the
+// interaction bits) when every i-cluster of the super-cluster interacts with
+// the j-cluster through an all-ones mask off the diagonal: the common case,
+// computed with the cut-off as the only condition.
+constexpr unsigned kFastBit = 1u << 31;
+static_assert(kSuperShift + kSuper8 <= 31, "interaction bits overlap the fast bit");
 
 // Per-warp shared staging of the force kernel.
 struct WarpSmem {
@@ -140,15 +95,36 @@ struct WarpSmem {
     float4 izq[kSuper8][4];   // {z, z', f q, f q'}
     float4 lxy[kSuper8][4];   // {x, x', y, y'} lo part of the shift
     float2 lz[kSuper8][4];    // {z, z'} lo part
-    int2 row[kSuper8][4];     // LJ row offsets (type * ntypes)
-    int w[32];                // j-entry words of the current chunk
+    int2 row[kSuper8][4];     // LJ row byte offsets (type * ntypes * 8)
+    int w[32];                // j-entry words of the current chunk (with the fast bit)
     unsigned long long m[kSuper8][32];  // their masks per i-cluster
 };
 
-// -x_j in both halves of a packed pair, per coordinate.
-struct NegJ {
-    float2 nx, ny, nz;
+// The j-particle of a lane with both halves of each packed pair holding it
+// (the lane's two particle pairs share j): -x, -y, -z, so that a distance
+// component is one packed add x_i + (-x_j), and the charge; from the
+// duplicated slot layout written with the coordinates.
+struct JPart {
+    float2 nx, ny, nz, q;
+    int t;   // LJ type, as a byte offset into a row of the {-6 C6, 12 C12} table
 };
+
+__device__ __forceinline__ JPart load_jpart(const float4* __restrict__ xjd, const int* __restrict__ type_slot,
+                                            int slot) {
+    const float4 a = xjd[2 * slot], b = xjd[2 * slot + 1];
+    JPart J;
+    J.nx = make_float2(a.x, a.y);
+    J.ny = make_float2(a.z, a.w);
+    J.nz = make_float2(b.x, b.y);
+    J.q = make_float2(b.z, b.w);
+    J.t = type_slot[slot] * (int)sizeof(float2);
+    return J;
+}
+
+// LJ table entry at a byte offset (row of the i-type plus column of the j-type).
+__device__ __forceinline__ float2 lj_entry(const float2* s_lj, int byte_off) {
+    return *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(s_lj) + byte_off);
+}
 
 // Distance vectors of the lane's two pairs with j-particle (xj) as packed
 // pairs, from the paired i layout: d = (x_i + shift) - x_j with the shift
@@ -169,10 +145,6 @@ __device__ __forceinline__ void pair_deltas(const WarpSmem& W, int k, int ih, fl
     }
 }
 
-// Force/energy of the lane's two pairs (x and y components) given squared
-// distances; scalar arithmetic wherever a parameter enters (constant
-// operands need no registers), packed only where both operands are pairs.
-// FULL: every pair inside rc is a full interaction (all-ones mask, no diagonal).
 // The Ewald force factor G(w), w = (beta r)^2, from the table in shared
 // memory: entry k = {G(k h), G((k+1) h) - G(k h)}, h = w_max / n, linear
 // interpolation (Sec. 3.2: the tabulated kernels).  t = r^2 beta^2 / h.
@@ -182,40 +154,55 @@ __device__ __forceinline__ float ewald_tab_g(const float2* tab, int n, float t) 
     return fmaf(t - (float)i, v.y, v.x);
 }
 
+// 1/sqrt(x) by the hardware's approximate reciprocal square root, denormals
+// flushed: squared distances of counted pairs are far above the denormal
+// range, and any other pair's result is selected away.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Force/energy of the lane's two pairs (x and y components) given squared
+// distances and the pair charge products qq = f q_i q_j.  Packed FP32x2 where
+// both operands are pairs; scalar where one operand is a constant (an
+// immediate or a kernel parameter is a direct operand of a scalar
+// instruction, while a packed one would first need the constant copied into
+// a register pair).  u0/u1: mask bits (full interaction); inc0/inc1: pair
+// counted and inside rc.  Pairs that are not counted are computed on
+// whatever r2 they have and selected away (no NaN escapes the selects).
+// FULL: every pair inside rc is a full interaction (all-ones mask, no
+// diagonal).
 template <int ELEC, bool ENERGY, bool FIT, bool FULL>
-__device__ __forceinline__ float2 pair_force2(const ForceParams& P, float2 r2, bool inc0, bool inc1,
-                                              bool u0, bool u1, float qq0, float qq1, float2 lj0,
-                                              float2 lj1, float& e_lj, float& e_c, const float2* s_tab) {
-    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+__device__ __forceinline__ float2 pair_force2(const ForceParams& P, float2 r2, bool inc0, bool inc1, bool u0,
+                                              bool u1, float2 qq, float2 lj0, float2 lj1, float& e_lj,
+                                              float& e_c, const float2* s_tab) {
+    const float2 rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
     const float2 rinv2 = mul2(rinv, rinv);
     float2 rinv3 = mul2(rinv, rinv2);
     const float2 rinv6 = mul2(rinv3, rinv3);
     // LJ (12 C12 r^-6 - 6 C6) r^-8 with lj = {-6 C6, 12 C12}
-    float flj0 = fmaf(lj0.y, rinv6.x, lj0.x) * rinv6.x * rinv2.x;
-    float flj1 = fmaf(lj1.y, rinv6.y, lj1.x) * rinv6.y * rinv2.y;
+    float2 flj = mul2(mul2(make_float2(fmaf(lj0.y, rinv6.x, lj0.x), fmaf(lj1.y, rinv6.y, lj1.x)), rinv6), rinv2);
     if (!FULL) {
-        flj0 = u0 ? flj0 : 0.0f;
-        flj1 = u1 ? flj1 : 0.0f;
+        flj = sel2(u0, u1, flj);
         rinv3 = sel2(u0, u1, rinv3);
     }
-    float fc0, fc1;
+    float2 fc;
     if (ELEC == NB_ELEC_RF) {
-        fc0 = qq0 * (rinv3.x - P.two_k_rf);
-        fc1 = qq1 * (rinv3.y - P.two_k_rf);
+        fc = mul2(qq, make_float2(rinv3.x - P.two_k_rf, rinv3.y - P.two_k_rf));
     } else if (ELEC == NB_ELEC_EWALD_TAB) {
-        fc0 = qq0 * fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.x * P.tab_scale), rinv3.x);
-        fc1 = qq1 * fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.y * P.tab_scale), rinv3.y);
+        fc = mul2(qq, make_float2(fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.x * P.tab_scale), rinv3.x),
+                                  fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.y * P.tab_scale), rinv3.y)));
     } else if (FIT) {
-        // the fitted factor for both pairs at once (packed FP32x2 Horner)
-        const float2 g2 = ewald_fit_g2(mul2(bc2(P.beta2), r2));
-        const float2 fc2 = mul2(make_float2(qq0, qq1), fma2(g2, bc2(-P.beta3), rinv3));
-        fc0 = fc2.x;
-        fc1 = fc2.y;
+        // the fitted factor (Horner with immediate coefficients)
+        const float g0 = ewald_fit_g(P.beta2 * r2.x), g1 = ewald_fit_g(P.beta2 * r2.y);
+        fc = mul2(qq, make_float2(fmaf(-P.beta3, g0, rinv3.x), fmaf(-P.beta3, g1, rinv3.y)));
     } else {
         const float r0 = r2.x * rinv.x, r1 = r2.y * rinv.y;
         const float b0 = P.beta * r0, b1 = P.beta * r1;
-        fc0 = qq0 * (rinv3.x + (erfcf(b0) - 1.0f + P.two_beta_sqrtpi * r0 * __expf(-b0 * b0)) * rinv2.x * rinv.x);
-        fc1 = qq1 * (rinv3.y + (erfcf(b1) - 1.0f + P.two_beta_sqrtpi * r1 * __expf(-b1 * b1)) * rinv2.y * rinv.y);
+        fc = mul2(qq, make_float2(
+            rinv3.x + (erfcf(b0) - 1.0f + P.two_beta_sqrtpi * r0 * __expf(-b0 * b0)) * rinv2.x * rinv.x,
+            rinv3.y + (erfcf(b1) - 1.0f + P.two_beta_sqrtpi * r1 * __expf(-b1 * b1)) * rinv2.y * rinv.y));
     }
     if (ENERGY) {
         // V_LJ = (C12 r^-6 - C6) r^-6;  V_C = qq (e/r - correction)
@@ -224,21 +211,19 @@ __device__ __forceinline__ float2 pair_force2(const ForceParams& P, float2 r2, b
         const float re0 = FULL || u0 ? rinv.x : 0.0f, re1 = FULL || u1 ? rinv.y : 0.0f;
         float vc0, vc1;
         if (ELEC == NB_ELEC_RF) {
-            vc0 = qq0 * (re0 + fmaf(P.k_rf, r2.x, -P.c_rf));
-            vc1 = qq1 * (re1 + fmaf(P.k_rf, r2.y, -P.c_rf));
+            vc0 = qq.x * (re0 + fmaf(P.k_rf, r2.x, -P.c_rf));
+            vc1 = qq.y * (re1 + fmaf(P.k_rf, r2.y, -P.c_rf));
         } else if (FIT) {
-            const float2 h2 = ewald_fit_h2(mul2(bc2(P.beta2), r2));
-            const float2 v2 = mul2(make_float2(qq0, qq1), fma2(h2, bc2(-P.beta), make_float2(re0, re1)));
-            vc0 = v2.x;
-            vc1 = v2.y;
+            vc0 = qq.x * fmaf(-P.beta, ewald_fit_h(P.beta2 * r2.x), re0);
+            vc1 = qq.y * fmaf(-P.beta, ewald_fit_h(P.beta2 * r2.y), re1);
         } else {
-            vc0 = qq0 * ((erfcf(P.beta * r2.x * rinv.x) - 1.0f) * rinv.x + re0);
-            vc1 = qq1 * ((erfcf(P.beta * r2.y * rinv.y) - 1.0f) * rinv.y + re1);
+            vc0 = qq.x * ((erfcf(P.beta * r2.x * rinv.x) - 1.0f) * rinv.x + re0);
+            vc1 = qq.y * ((erfcf(P.beta * r2.y * rinv.y) - 1.0f) * rinv.y + re1);
         }
         e_lj += (inc0 && (FULL || u0) ? vl0 : 0.0f) + (inc1 && (FULL || u1) ? vl1 : 0.0f);
         e_c += (inc0 ? vc0 : 0.0f) + (inc1 ? vc1 : 0.0f);
     }
-    return make_float2(inc0 ? flj0 + fc0 : 0.0f, inc1 ? flj1 + fc1 : 0.0f);
+    return sel2(inc0, inc1, add2(flj, fc));
 }
 
 // Add a warp's energy partial sums to box b's FP64 totals and clear them.
@@ -258,6 +243,14 @@ __device__ __forceinline__ void flush_energy(Accum* acc, int b, float& e_lj, flo
     n_inc = 0;
 }
 
+// Running force sums of a lane: i-forces per i-cluster, and the j-force of
+// the current j-cluster, each over the lane's two pairs as packed pairs.
+// The j-sum holds the force on i (the pair force times x_i - x_j); the
+// j-particle receives its negative.
+struct JSum {
+    float2 x, y, z;
+};
+
 // The pairs of i-cluster k (of the super-cluster) with one j-cluster.
 // Returns (warp-uniformly) whether any pair was inside rc.
 // PRUNE: also sets bit k of keep when a counted pair (any pair but, on the
@@ -265,12 +258,11 @@ __device__ __forceinline__ void flush_energy(Accum* acc, int b, float& e_lj, flo
 // with the same FP32 distances as the separate prune kernel.
 template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, bool FULL, bool PRUNE>
 __device__ __forceinline__ bool icluster8(const ForceParams& P, const float2* s_lj, const WarpSmem& W,
-                                          const Lane8& L, int k, bool diag, unsigned long long m,
-                                          float4 xj, const NegJ& nxj, int tj, float2& fx, float2& fy, float2& fz,
-                                          float& fjx, float& fjy, float& fjz, float& e_lj, float& e_c,
-                                          unsigned& n_inc, unsigned& keep) {
+                                          const Lane8& L, int2 row, int k, bool diag, unsigned long long m,
+                                          const JPart& J, float2& fx, float2& fy, float2& fz, JSum& G,
+                                          float& e_lj, float& e_c, unsigned& n_inc, unsigned& keep) {
     float2 dx, dy, dz, fq;
-    pair_deltas<SHIFTED>(W, k, L.ih, nxj.nx, nxj.ny, nxj.nz, dx, dy, dz, fq);
+    pair_deltas<SHIFTED>(W, k, L.ih, J.nx, J.ny, J.nz, dx, dy, dz, fq);
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     if constexpr (PRUNE) {
         const bool c0 = FULL || !(diag && L.lower0), c1 = FULL || !(diag && L.lower1);
@@ -288,19 +280,16 @@ __device__ __forceinline__ bool icluster8(const ForceParams& P, const float2* s_
         inc1 = inc1 && (u1 || !L.lower1);
     }
     if (!__any_sync(0xffffffffu, inc0 || inc1)) return false;
-    const int2 rw = W.row[k][L.ih];
-    const float2 lj0 = s_lj[rw.x + tj], lj1 = s_lj[rw.y + tj];
-    const float2 fs = pair_force2<ELEC, ENERGY, FIT, FULL>(P, r2, inc0, inc1, u0, u1, fq.x * xj.w,
-                                                           fq.y * xj.w, lj0, lj1, e_lj, e_c,
-                                                           s_lj + P.ntypes * P.ntypes);
+    const float2 lj0 = lj_entry(s_lj, row.x + J.t), lj1 = lj_entry(s_lj, row.y + J.t);
+    const float2 fs = pair_force2<ELEC, ENERGY, FIT, FULL>(P, r2, inc0, inc1, u0, u1, mul2(fq, J.q), lj0, lj1,
+                                                           e_lj, e_c, s_lj + P.ntypes * P.ntypes);
     if (ENERGY) n_inc += (unsigned)inc0 + (unsigned)inc1;
-    const float2 px = mul2(fs, dx), py = mul2(fs, dy), pz = mul2(fs, dz);
-    fx = add2(fx, px);
-    fy = add2(fy, py);
-    fz = add2(fz, pz);
-    fjx -= px.x + px.y;
-    fjy -= py.x + py.y;
-    fjz -= pz.x + pz.y;
+    fx = fma2(fs, dx, fx);
+    fy = fma2(fs, dy, fy);
+    fz = fma2(fs, dz, fz);
+    G.x = fma2(fs, dx, G.x);
+    G.y = fma2(fs, dy, G.y);
+    G.z = fma2(fs, dz, G.z);
     return true;
 }
 
@@ -311,14 +300,13 @@ __device__ __forceinline__ bool icluster8(const ForceParams& P, const float2* s_
 // correction.
 template <bool SHIFTED, bool FULL>
 __device__ __forceinline__ bool icluster8_mlp(const ForceParams& P, const float2* s_lj, const WarpSmem& W,
-                                              const Lane8& L, int k, bool diag, unsigned long long m,
-                                              float4 xj, const NegJ& nxj, int tj, float2& fx, float2& fy,
-                                              float2& fz,
-                                              float& fjx, float& fjy, float& fjz, const MlpTC& M, float* mo) {
+                                              const Lane8& L, int2 row, int k, bool diag, unsigned long long m,
+                                              const JPart& J, float2& fx, float2& fy, float2& fz, JSum& G,
+                                              const MlpTC& M, float* mo) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     float2 dx, dy, dz, fq;
-    pair_deltas<SHIFTED>(W, k, L.ih, nxj.nx, nxj.ny, nxj.nz, dx, dy, dz, fq);
+    pair_deltas<SHIFTED>(W, k, L.ih, J.nx, J.ny, J.nz, dx, dy, dz, fq);
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     bool u0 = true, u1 = true;
     if (!FULL) {
@@ -368,9 +356,8 @@ __device__ __forceinline__ bool icluster8_mlp(const ForceParams& P, const float2
         g0 = a0f ? ewald_fit_g(P.beta2 * r2.x) : 0.0f;
         g1 = a1f ? ewald_fit_g(P.beta2 * r2.y) : 0.0f;
     }
-    const int2 rw = W.row[k][L.ih];
-    const float2 lj0 = s_lj[rw.x + tj], lj1 = s_lj[rw.y + tj];
-    const float qq0 = fq.x * xj.w, qq1 = fq.y * xj.w;
+    const float2 lj0 = lj_entry(s_lj, row.x + J.t), lj1 = lj_entry(s_lj, row.y + J.t);
+    const float qq0 = fq.x * J.q.x, qq1 = fq.y * J.q.y;
     float flj0 = fmaf(lj0.y, rinv6.x, lj0.x) * rinv6.x * rinv2.x;
     float flj1 = fmaf(lj1.y, rinv6.y, lj1.x) * rinv6.y * rinv2.y;
     if (!FULL) {
@@ -380,13 +367,12 @@ __device__ __forceinline__ bool icluster8_mlp(const ForceParams& P, const float2
     const float fc0 = n0 ? qq0 * c0 * rinv3.x : qq0 * fmaf(-P.beta3, g0, u0 ? rinv3.x : 0.0f);
     const float fc1 = n1 ? qq1 * c1 * rinv3.y : qq1 * fmaf(-P.beta3, g1, u1 ? rinv3.y : 0.0f);
     const float2 fs = make_float2(inc0 ? flj0 + fc0 : 0.0f, inc1 ? flj1 + fc1 : 0.0f);
-    const float2 px = mul2(fs, dx), py = mul2(fs, dy), pz = mul2(fs, dz);
-    fx = add2(fx, px);
-    fy = add2(fy, py);
-    fz = add2(fz, pz);
-    fjx -= px.x + px.y;
-    fjy -= py.x + py.y;
-    fjz -= pz.x + pz.y;
+    fx = fma2(fs, dx, fx);
+    fy = fma2(fs, dy, fy);
+    fz = fma2(fs, dz, fz);
+    G.x = fma2(fs, dx, G.x);
+    G.y = fma2(fs, dy, G.y);
+    G.z = fma2(fs, dz, G.z);
     return true;
 }
 
@@ -396,62 +382,73 @@ __device__ __forceinline__ bool icluster8_mlp(const ForceParams& P, const float2
 // offsets in the outer list), as the separate prune kernel does.
 template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, bool PRUNE>
 __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s_lj, WarpSmem& W,
-                                             const Lane8& L, int g0, bool center, int jb, int je,
-                                             float2 (&fx)[kSuper8], float2 (&fy)[kSuper8],
+                                             const Lane8& L, const int2 (&row)[kSuper8], int g0, bool center,
+                                             int jb, int je, float2 (&fx)[kSuper8], float2 (&fy)[kSuper8],
                                              float2 (&fz)[kSuper8], float& e_lj, float& e_c,
                                              unsigned& n_inc, const MlpTC* M, float* mo, int j_out, int& kept,
                                              unsigned long long& keys) {
+    constexpr bool MLP = ELEC == NB_ELEC_EWALD_MLP;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int nt = je - jb;
+    // the chunk's j-words and masks, one entry per lane; the fast bit marks
+    // the words whose i-clusters all interact through full masks off the
+    // diagonal
     if (lane < nt) {
-        W.w[lane] = A.cj[jb + lane];
-#pragma unroll
-        for (int k = 0; k < kSuper8; ++k) W.m[k][lane] = A.mask[k * A.jstride + jb + lane];
-    }
-    __syncwarp();
-    const float4* xyzq_j = A.xyzq + L.j;
-    const int* type_j = A.type_slot + L.j;
-    int cjn = W.w[0] & kCjMask;
-    float4 xjn = xyzq_j[cjn * 8];
-    int tjn = type_j[cjn * 8];
-    unsigned my_keep = 0;   // PRUNE: kept i-cluster bits of j-entry `lane`
-    for (int t = 0; t < nt; ++t) {
-        const unsigned w = (unsigned)W.w[t];
-        const int cjt = (int)(w & kCjMask);
-        const unsigned bits = w >> kSuperShift;
-        const float4 xj = xjn;
-        NegJ nxj;
-        nxj.nx = make_float2(-xj.x, -xj.x);
-        nxj.ny = make_float2(-xj.y, -xj.y);
-        nxj.nz = make_float2(-xj.z, -xj.z);
-        const int tj = tjn;
-        cjn = W.w[min(t + 1, nt - 1)] & kCjMask;
-        xjn = xyzq_j[cjn * 8];
-        tjn = type_j[cjn * 8];
-        float fjx = 0.f, fjy = 0.f, fjz = 0.f;
-        bool any = false;
-        unsigned keep = 0;
+        const int w = A.cj[jb + lane];
+        const int cj = w & kCjMask;
+        bool fast = ((unsigned)w >> kSuperShift) == (1u << kSuper8) - 1u;
 #pragma unroll
         for (int k = 0; k < kSuper8; ++k) {
-            if ((bits >> k) & 1u) {
+            const unsigned long long m = A.mask[k * A.jstride + jb + lane];
+            W.m[k][lane] = m;
+            fast = fast && m == ~0ull && !(center && cj == g0 + k);
+        }
+        W.w[lane] = fast ? (int)((unsigned)w | kFastBit) : w;
+    }
+    __syncwarp();
+    unsigned my_keep = 0;   // PRUNE: kept i-cluster bits of j-entry `lane`
+    for (int t = 0; t < nt; ++t) {
+        const int w = W.w[t];
+        const int cjt = w & kCjMask;
+        const JPart J = load_jpart(A.xjd, A.type_slot, cjt * 8 + L.j);
+        JSum G;
+        G.x = G.y = G.z = make_float2(0.f, 0.f);
+        bool any = false;
+        unsigned keep = 0;
+        if (w < 0) {
+#pragma unroll
+            for (int k = 0; k < kSuper8; ++k) {
+                if constexpr (MLP)
+                    any |= icluster8_mlp<SHIFTED, true>(A.p, s_lj, W, L, row[k], k, false, ~0ull, J, fx[k], fy[k],
+                                                        fz[k], G, *M, mo);
+                else
+                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true, PRUNE>(A.p, s_lj, W, L, row[k], k, false,
+                                                                              ~0ull, J, fx[k], fy[k], fz[k], G,
+                                                                              e_lj, e_c, n_inc, keep);
+            }
+        } else {
+            const unsigned bits = ((unsigned)w >> kSuperShift) & ((1u << kSuper8) - 1u);
+#pragma unroll
+            for (int k = 0; k < kSuper8; ++k) {
+                if (!((bits >> k) & 1u)) continue;
                 const bool diag = center && (cjt == g0 + k);
                 const unsigned long long m = W.m[k][t];
-                if constexpr (ELEC == NB_ELEC_EWALD_MLP) {
+                if constexpr (MLP) {
                     if (!diag && m == ~0ull)
-                        any |= icluster8_mlp<SHIFTED, true>(A.p, s_lj, W, L, k, false, m, xj, nxj, tj, fx[k], fy[k],
-                                                            fz[k], fjx, fjy, fjz, *M, mo);
+                        any |= icluster8_mlp<SHIFTED, true>(A.p, s_lj, W, L, row[k], k, false, m, J, fx[k], fy[k],
+                                                            fz[k], G, *M, mo);
                     else
-                        any |= icluster8_mlp<SHIFTED, false>(A.p, s_lj, W, L, k, diag, m, xj, nxj, tj, fx[k], fy[k],
-                                                             fz[k], fjx, fjy, fjz, *M, mo);
+                        any |= icluster8_mlp<SHIFTED, false>(A.p, s_lj, W, L, row[k], k, diag, m, J, fx[k], fy[k],
+                                                             fz[k], G, *M, mo);
                 } else if (!diag && m == ~0ull) {
-                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true, PRUNE>(A.p, s_lj, W, L, k, false, m, xj, nxj,
-                                                                              tj, fx[k], fy[k], fz[k], fjx, fjy, fjz,
-                                                                              e_lj, e_c, n_inc, keep);
+                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true, PRUNE>(A.p, s_lj, W, L, row[k], k, false, m,
+                                                                              J, fx[k], fy[k], fz[k], G, e_lj, e_c,
+                                                                              n_inc, keep);
                 } else {
-                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, false, PRUNE>(A.p, s_lj, W, L, k, diag, m, xj, nxj,
-                                                                               tj, fx[k], fy[k], fz[k], fjx, fjy,
-                                                                               fjz, e_lj, e_c, n_inc, keep);
+                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, false, PRUNE>(A.p, s_lj, W, L, row[k], k, diag, m,
+                                                                               J, fx[k], fy[k], fz[k], G, e_lj,
+                                                                               e_c, n_inc, keep);
                 }
             }
         }
@@ -459,13 +456,15 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
             if (lane == t) my_keep = keep;
         }
         if (!any) continue;
+        // j-force: the lane's two pairs, then the 4 lanes sharing j
+        float fjx = G.x.x + G.x.y, fjy = G.y.x + G.y.y, fjz = G.z.x + G.z.y;
         fjx += __shfl_xor_sync(full, fjx, 8);
         fjy += __shfl_xor_sync(full, fjy, 8);
         fjz += __shfl_xor_sync(full, fjz, 8);
         fjx += __shfl_xor_sync(full, fjx, 16);
         fjy += __shfl_xor_sync(full, fjy, 16);
         fjz += __shfl_xor_sync(full, fjz, 16);
-        if (L.ih == 0) atomicAdd(&A.fslot[cjt * 8 + L.j], make_float4(fjx, fjy, fjz, 0.0f));
+        if (L.ih == 0) atomicAdd(&A.fslot[cjt * 8 + L.j], make_float4(-fjx, -fjy, -fjz, 0.0f));
     }
     if constexpr (PRUNE) {
         // compact the kept j-entries of this chunk, in order
@@ -486,8 +485,16 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
     __syncwarp();
 }
 
+// Blocks per SM the force kernels are compiled for (register budget): the
+// force and fused force + prune kernels at 7 blocks of 4 warps (72
+// registers), the energy kernel at 5 and the network's at 4.
+template <int ELEC, bool ENERGY, bool PRUNE>
+constexpr int force_min_blocks() {
+    return ELEC == NB_ELEC_EWALD_MLP ? 4 : (ENERGY ? 5 : 7);
+}
+
 template <int ELEC, bool ENERGY, bool FIT, bool PRUNE = false>
-__global__ void __launch_bounds__(32 * kForceWarps, ELEC == NB_ELEC_EWALD_MLP ? 4 : (ENERGY ? 5 : 7))
+__global__ void __launch_bounds__(32 * kForceWarps, force_min_blocks<ELEC, ENERGY, PRUNE>())
 k_force8(ForceArgs A) {
     extern __shared__ float2 s_lj[];
     __shared__ WarpSmem s_w[kForceWarps];
@@ -585,9 +592,12 @@ k_force8(ForceArgs A) {
             qxy[hh] = l.x;
             qxy[2 + hh] = l.y;
             qz[hh] = l.z;
-            pr[hh] = A.type_slot[g0 * 8 + lane] * A.p.ntypes;
+            pr[hh] = A.type_slot[g0 * 8 + lane] * A.p.ntypes * (int)sizeof(float2);
         }
         __syncwarp();
+        int2 row[kSuper8];
+#pragma unroll
+        for (int k = 0; k < kSuper8; ++k) row[k] = W.row[k][L.ih];
         const bool center = (s == kShiftCenter);
         float2 fx[kSuper8], fy[kSuper8], fz[kSuper8];
 #pragma unroll
@@ -596,11 +606,11 @@ k_force8(ForceArgs A) {
         for (int base = jb; base < je; base += 32) {
             const int bend = min(je, base + 32);
             if (center)
-                force_entry8<ELEC, ENERGY, FIT, false, PRUNE>(A, s_lj, W, L, g0, true, base, bend, fx, fy, fz,
+                force_entry8<ELEC, ENERGY, FIT, false, PRUNE>(A, s_lj, W, L, row, g0, true, base, bend, fx, fy, fz,
                                                               e_lj, e_c, n_inc, M, mo, jb, kept, keys_total);
             else
-                force_entry8<ELEC, ENERGY, FIT, true, PRUNE>(A, s_lj, W, L, g0, false, base, bend, fx, fy, fz,
-                                                             e_lj, e_c, n_inc, M, mo, jb, kept, keys_total);
+                force_entry8<ELEC, ENERGY, FIT, true, PRUNE>(A, s_lj, W, L, row, g0, false, base, bend, fx, fy,
+                                                             fz, e_lj, e_c, n_inc, M, mo, jb, kept, keys_total);
         }
         if (PRUNE) {
             if (lane == 0) A.ient_p[e] = make_int4(q, s, jb, jb + kept);
@@ -765,13 +775,9 @@ template <bool PRUNE>
 static cudaError_t launch_force_tab(const ForceArgs& A, int n_sm, cudaStream_t s) {
     auto kern = k_force8<NB_ELEC_EWALD_TAB, false, true, PRUNE>;
     const size_t smem = sizeof(float2) * (A.p.ntypes * A.p.ntypes + A.p.tab_n);
-    static bool attr_set = false;
-    cudaError_t e;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> smem_set{0};
+    cudaError_t e = smem_opt_in(kern, 64 * 1024, smem_set);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kForceWarps, smem);
     if (e != cudaSuccess) return e;
@@ -811,6 +817,7 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
     A.mask = p.use_pruned ? ws.mask_p : ws.mask;
     A.jstride = ws.jstride;
     A.xyzq = ws.xyzq;
+    A.xjd = ws.xjd;
     A.type_slot = ws.type_slot;
     A.fslot = ws.fslot;
     A.c6c12 = ws.c6c12;

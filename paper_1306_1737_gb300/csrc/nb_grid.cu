@@ -180,7 +180,9 @@ __global__ void __launch_bounds__(512) k_col_sort(Workspace ws, int C, int ntype
         ws.fslot[s] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (t < cnt_s) {
             const int a = (int)(s_key[t] & 0xffffffffull);
-            ws.xyzq[s] = ws.xw[a];
+            const float4 x = ws.xw[a];
+            ws.xyzq[s] = x;
+            if (ws.xjd) store_xjd(ws.xjd, s, x);
             ws.atom_of_slot[s] = a;
             ws.slot_of_atom[a] = (int)s;
             int ty = ws.type[a];
@@ -191,8 +193,10 @@ __global__ void __launch_bounds__(512) k_col_sort(Workspace ws, int C, int ntype
             ws.type_slot[s] = ty;
         } else {
             const long long sl = s - slot0;
-            ws.xyzq[s] = make_float4(-G.dummy_g * (float)(1 + (int)(sl % 4096)),
-                                     -G.dummy_g * (float)(1 + (int)(sl / 4096)), -G.dummy_g, 0.0f);
+            const float4 x = make_float4(-G.dummy_g * (float)(1 + (int)(sl % 4096)),
+                                         -G.dummy_g * (float)(1 + (int)(sl / 4096)), -G.dummy_g, 0.0f);
+            ws.xyzq[s] = x;
+            if (ws.xjd) store_xjd(ws.xjd, s, x);
             ws.atom_of_slot[s] = -1;
             ws.type_slot[s] = 0;
         }
@@ -221,12 +225,9 @@ cudaError_t launch_grid(const Workspace& ws, int C, int ntypes, const float* xyz
     k_scan_cols<<<ws.nbox, 1024, 0, s>>>(ws, C);
     if (n > 0) k_scatter<<<(n + 255) / 256, 256, 0, s>>>(ws);
     const size_t smem = sizeof(unsigned long long) * kMaxColumn;
-    static bool attr_set = false;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(k_col_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> smem_set{0};
+    e = smem_opt_in(k_col_sort, (int)smem, smem_set);
+    if (e != cudaSuccess) return e;
     k_col_sort<<<ws.col_total, 512, smem, s>>>(ws, C, ntypes);
     return cudaGetLastError();
 }
@@ -242,8 +243,10 @@ __global__ void k_set_coords(Workspace ws, int C, const float* __restrict__ xyz)
         const float4 o = ws.woff[a];
         const int s = ws.slot_of_atom[a];
         if (s < 0 || s >= nslot) continue;
-        ws.xyzq[s] = make_float4(__fadd_rn(xyz[3 * a], o.x), __fadd_rn(xyz[3 * a + 1], o.y),
-                                 __fadd_rn(xyz[3 * a + 2], o.z), ws.q[a]);
+        const float4 x = make_float4(__fadd_rn(xyz[3 * a], o.x), __fadd_rn(xyz[3 * a + 1], o.y),
+                                     __fadd_rn(xyz[3 * a + 2], o.z), ws.q[a]);
+        ws.xyzq[s] = x;
+        store_xjd(ws.xjd, s, x);
     }
 }
 

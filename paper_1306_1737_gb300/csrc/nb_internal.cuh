@@ -17,6 +17,8 @@
 //   fslot      : float4 per slot, force accumulators (w unused)
 #pragma once
 
+#include <atomic>
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -116,6 +118,10 @@ struct Workspace {
     unsigned long long* keys;  // sort keys in column order
     // per slot
     float4* xyzq;
+    // per slot, two float4: {-x, -x, -y, -y}, {-z, -z, q, q} -- the
+    // j-particle as the force kernel's packed pairs use it (both halves of a
+    // lane's pair share j), written with xyzq
+    float4* xjd;
     int* atom_of_slot;   // batch particle index, -1 for dummies
     int* type_slot;
     float4* fslot;
@@ -138,6 +144,74 @@ struct Workspace {
 };
 
 constexpr int kEwaldTabN = 2048;   // table intervals on w = (beta r)^2 in [0, kEwaldFitWMax]
+
+// ---------------------------------------------------------------------------
+// Host-side grid geometry (Sec. 2.3), shared by every gridding entry point so
+// that they place particles identically.
+
+// At most this many grid columns along x and along y, so that nx * ny fits
+// an int; only slab-like boxes far thinner than the column spacing reach it.
+constexpr int kMaxGridDim = 1 << 15;
+
+inline int grid_extent(double L, double s) {
+    const double g = std::floor(L / s);
+    if (!(g >= 1.0)) return 1;
+    return g > (double)kMaxGridDim ? kMaxGridDim : (int)g;
+}
+
+// Grid dimensions: spacing (C / rho)^(1/3) along x and y.
+inline void grid_dims(int n, const float L[3], int C, int* nx, int* ny) {
+    int gx = 1, gy = 1;
+    if (n > 0) {
+        const double Lx = L[0], Ly = L[1], Lz = L[2];
+        const double rho = (double)n / (Lx * Ly * Lz);
+        const double s = std::cbrt((double)C / rho);
+        gx = grid_extent(Lx, s);
+        gy = grid_extent(Ly, s);
+    }
+    *nx = gx;
+    *ny = gy;
+}
+
+// Dummy spacing: the smallest power of two at least 4 times the longest edge.
+inline float dummy_spacing(const float L[3]) {
+    float m = L[0];
+    if (L[1] > m) m = L[1];
+    if (L[2] > m) m = L[2];
+    float g = 1.0f;
+    while (g < 4.0f * m) g *= 2.0f;
+    return g;
+}
+
+// Geometry of a box of n particles with edges box[3] gridded with clusters of
+// C: FP32 edges, grid dimensions, the FP32 inverse spacings of the cell
+// decision and of the search's column ranges, and the dummy spacing.
+inline BoxGeom box_geometry(int n, const double box[3], int C) {
+    BoxGeom g{};
+    for (int k = 0; k < 3; ++k) g.L[k] = (float)box[k];
+    grid_dims(n, g.L, C, &g.nx, &g.ny);
+    g.inv_x = (float)((double)g.nx / (double)g.L[0]);
+    g.inv_y = (float)((double)g.ny / (double)g.L[1]);
+    g.inv_cx = (float)g.nx / g.L[0];
+    g.inv_cy = (float)g.ny / g.L[1];
+    g.dummy_g = dummy_spacing(g.L);
+    return g;
+}
+
+// Kernels whose dynamic shared memory exceeds the 48 KB default must opt in
+// per device: the first launch on each device sets the attribute (host
+// threads that race here set the same value).  done: one bit per device.
+template <typename Kern>
+inline cudaError_t smem_opt_in(Kern kern, int bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_grid(const Workspace& ws, int C, int ntypes, const float* xyz, cudaStream_t s);
@@ -233,6 +307,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// The two float4 of a slot's duplicated j layout (see Workspace::xjd).
+__device__ __forceinline__ void store_xjd(float4* xjd, long long s, float4 x) {
+    xjd[2 * s] = make_float4(-x.x, -x.x, -x.y, -x.y);
+    xjd[2 * s + 1] = make_float4(-x.z, -x.z, x.w, x.w);
 }
 
 __device__ __forceinline__ void shift_vector(int s, const float L[3], float sh[3]) {

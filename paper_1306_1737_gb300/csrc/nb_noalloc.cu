@@ -12,7 +12,6 @@
 // and keeps it; that first call should therefore happen before any stream
 // capture.  Every call shares the one array: calls whose work overlaps on the
 // GPU (different streams, or different host threads on one device) race.
-#include <cmath>
 #include <mutex>
 
 #include "nb_internal.cuh"
@@ -22,6 +21,16 @@ namespace nbc {
 constexpr int kNoallocMaxAtoms = 32768;
 constexpr int kNoallocMaxColumns = 4096;
 constexpr long long kNoallocMaxSlots = kNoallocMaxAtoms + (long long)kNoallocMaxColumns * 7;
+// Clusters and super-clusters of a grid with at most slots slots and
+// columns columns, as the entry point plans them (the super-cluster bound is
+// largest for clusters of 4, one cluster each).
+constexpr long long noalloc_clusters(long long slots, int C) { return slots / C + 1; }
+constexpr long long noalloc_superclusters(long long slots, long long columns, int C) {
+    return noalloc_clusters(slots, C) / super_size(C) + columns + 1;
+}
+constexpr long long kNoallocMaxSuperclusters = noalloc_superclusters(kNoallocMaxSlots, kNoallocMaxColumns, 4);
+static_assert(kNoallocMaxSuperclusters >= noalloc_superclusters(kNoallocMaxSlots, kNoallocMaxColumns, 8),
+              "super-cluster capacity");
 constexpr int kNoallocMaxDevices = 64;
 
 constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -40,7 +49,7 @@ constexpr size_t kOffColCount = align256(kOffKeys + sizeof(unsigned long long) *
 constexpr size_t kOffColAtomStart = align256(kOffColCount + sizeof(int) * (kNoallocMaxColumns + 1));
 constexpr size_t kOffColScStart = align256(kOffColAtomStart + sizeof(int) * (kNoallocMaxColumns + 1));
 constexpr size_t kOffScInfo = align256(kOffColScStart + sizeof(int) * (kNoallocMaxColumns + 1));
-constexpr size_t kOffFslot = align256(kOffScInfo + sizeof(int2) * (kNoallocMaxSlots / 4 + kNoallocMaxColumns + 1));
+constexpr size_t kOffFslot = align256(kOffScInfo + sizeof(int2) * kNoallocMaxSuperclusters);
 constexpr size_t kNoallocScratchBytes = align256(kOffFslot + sizeof(float4) * kNoallocMaxSlots);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
@@ -100,45 +109,22 @@ extern "C" nb_status nb_grid_put_noalloc(int n, const float* xyz, const float* q
         return NB_ERR_ARG;
     if (((uintptr_t)xyzq & 15) || ((uintptr_t)bb & 15)) return NB_ERR_ARG;
     if (!box) return NB_ERR_BOX;
-    BoxGeom g{};
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 3; ++k)
         if (!(box[k] > 0.0) || !(box[k] < 1e30)) return NB_ERR_BOX;
-        g.L[k] = (float)box[k];
-    }
-    // grid dimensions: spacing (C / rho)^(1/3) along x and y, at most 2^15
-    // columns along each (only slabs far thinner than the spacing reach it)
-    {
-        const double Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
-        const double sp = std::cbrt((double)C / ((double)n / (Lx * Ly * Lz)));
-        const double gx = std::floor(Lx / sp), gy = std::floor(Ly / sp);
-        g.nx = !(gx >= 1.0) ? 1 : gx > 32768.0 ? 32768 : (int)gx;
-        g.ny = !(gy >= 1.0) ? 1 : gy > 32768.0 ? 32768 : (int)gy;
-    }
+    // the same geometry as nb_grid_put (dimensions, inverse spacings, dummies)
+    const BoxGeom g = box_geometry(n, box, C);
     const long long ncol = (long long)g.nx * g.ny;
     const long long nslot_bound = (long long)n + ncol * (C - 1);
     if (n > kNoallocMaxAtoms || ncol > kNoallocMaxColumns || nslot_bound > kNoallocMaxSlots)
         return NB_ERR_CAPACITY;
     if (nslot_bound > max_slots || ncol > max_columns) return NB_ERR_CAPACITY;
-    g.inv_x = (float)((double)g.nx / (double)g.L[0]);
-    g.inv_y = (float)((double)g.ny / (double)g.L[1]);
-    g.inv_cx = (float)g.nx / g.L[0];
-    g.inv_cy = (float)g.ny / g.L[1];
-    {
-        float m = g.L[0];
-        if (g.L[1] > m) m = g.L[1];
-        if (g.L[2] > m) m = g.L[2];
-        float d = 1.0f;
-        while (d < 4.0f * m) d *= 2.0f;
-        g.dummy_g = d;
-    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return NB_ERR_CUDA;
     unsigned char* base = nullptr;
     if (noalloc_scratch(dev, &base) != cudaSuccess) return NB_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    const int S = super_size(C);
-    const int nclu_cap = (int)(nslot_bound / C + 1);
-    const int nsc_cap = nclu_cap / S + (int)ncol + 1;
+    const int nclu_cap = (int)noalloc_clusters(nslot_bound, C);
+    const int nsc_cap = (int)noalloc_superclusters(nslot_bound, ncol, C);
     Workspace ws{};
     ws.nbox = 1;
     ws.st = (DevState*)(base + kOffState);

@@ -97,3 +97,36 @@ def test_binding_checks_element_types():
         nb._ptr(DeviceArray(torch.int64), nb._I32)
     with pytest.raises(ValueError, match="contiguous"):
         nb._ptr(DeviceArray(torch.float32, contiguous=False), nb._F32)
+
+
+def test_noalloc_binding_checks_sizes_before_the_call():
+    """The binding compares each output tensor with n, max_slots and
+    max_columns before handing pointers to the library, which writes up to
+    those sizes (CPU tensors: the size check fires before the device check)."""
+    torch = pytest.importorskip("torch")
+    import paper_1306_1737_gb300 as nb
+    n, ms, mc, C = 100, 400, 50, 8
+
+    def args(**over):
+        a = dict(xyz=torch.zeros(3 * n), q=torch.zeros(n), types=torch.zeros(n, dtype=torch.int32),
+                 atom_of_slot=torch.zeros(ms, dtype=torch.int32), xyzq=torch.zeros(4 * ms),
+                 type_slot=torch.zeros(ms, dtype=torch.int32), bb=torch.zeros(8 * (ms // C)),
+                 col_clu_start=torch.zeros(mc + 1, dtype=torch.int32), info=torch.zeros(2, dtype=torch.int32))
+        a.update(over)
+        return a
+
+    def call(a):
+        nb.nb_grid_put_noalloc(n, a["xyz"], a["q"], a["types"], 1, [2.0, 2.0, 2.0], C, a["atom_of_slot"],
+                               a["xyzq"], a["type_slot"], a["bb"], a["col_clu_start"], a["info"], ms, mc)
+
+    for name, short in [("xyz", torch.zeros(3 * n - 1)), ("q", torch.zeros(n - 1)),
+                        ("types", torch.zeros(n - 1, dtype=torch.int32)),
+                        ("atom_of_slot", torch.zeros(ms - 1, dtype=torch.int32)),
+                        ("xyzq", torch.zeros(4 * ms - 1)), ("type_slot", torch.zeros(ms - 1, dtype=torch.int32)),
+                        ("bb", torch.zeros(8 * (ms // C) - 1)),
+                        ("col_clu_start", torch.zeros(mc, dtype=torch.int32)),
+                        ("info", torch.zeros(1, dtype=torch.int32))]:
+        with pytest.raises(ValueError, match=name):
+            call(args(**{name: short}))
+    with pytest.raises(ValueError, match="CUDA"):
+        call(args())

@@ -6,7 +6,9 @@ clusters, the forces of sampled particles (each against all 3M particles
 in the brute-force oracle) and of every particle (the oracle's cell-list
 tier) within 1e-4 of their RMS, and the FP64 energies and virial of the
 whole box within 1e-5 relative; the fused force + prune pass writes the
-same pruned list as the prune kernel."""
+same pruned list as the prune kernel.  The learned Ewald factor (the
+network trained on the GPU) gives the forces of sampled particles within
+5e-4 of their RMS on the same box."""
 import numpy as np
 import pytest
 
@@ -133,5 +135,30 @@ def test_config3_grid_list_prune_forces(env):
         f5b = gb.f.cpu().numpy().astype(np.float64)
         emax, erms, _ = gp.force_errors(f5b[sel], fo5)
         assert emax < FORCE_TOL, (emax, erms)
+    finally:
+        gb.close()
+
+
+def test_config3_surrogate_sampled(env):
+    """The surrogate kernel on the 3,000,000-particle box: forces of 2,048
+    seeded particles (each against all 3M in the brute-force oracle) within
+    5e-4 of their RMS, as on the 24,000-atom box."""
+    torch, nb, gp, (b, p) = env
+    from paper_1306_1737_gb300 import surrogate
+    r = w.surrogate_samples(1 << 20, surrogate.R_MIN, surrogate.R_MAX, seed=1005)
+    params, _ = surrogate.train(r, p["beta"], t=oracle.ewald_factor(r, p["beta"]))
+    gb = gp.GpuBox(b, p["rlist"])
+    try:
+        gb.grid()
+        gb.build(float(np.float32(p["rlist"])))
+        nb.nb_set_surrogate(gb.ctx, params, surrogate.R_MIN, surrogate.R_MAX)
+        f, _, _ = gb.compute(nb.make_params("ewald_mlp", p["rc"], beta=p["beta"], want_energy=False))
+        sel = np.random.default_rng(34).choice(b.n, 2048, replace=False)
+        oprm = oracle.make_params("ewald", float(np.float32(p["rc"])), beta=p["beta"], comb="lb")
+        fo, _, _ = oracle.forces_brute(b.xyz, b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx,
+                                       b.box, oprm, sel=sel)
+        emax, erms, _ = gp.force_errors(f[sel], fo)
+        print(f"\n3M surrogate, 2,048 sampled particles: max|dF|/rms {emax:.2e}, rms {erms:.2e}")
+        assert emax < 5e-4, (emax, erms)
     finally:
         gb.close()

@@ -19,15 +19,13 @@ def env():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_1306_1737_gb300 as nb
-    from paper_1306_1737_gb300 import build as nbbuild
-    nbbuild.build()
     nb.load()
     return torch, nb
 
 
-def reference_grid(torch, nb, b, C):
+def reference_grid(torch, nb, b, C, rlist=1.0):
     dev = torch.device("cuda", 0)
-    cx = nb.Context(b.n, b.box, 1.0, b.q, b.types, nb.nb_lj_combine(b.sigma, b.eps), cluster_size=C)
+    cx = nb.Context(b.n, b.box, rlist, b.q, b.types, nb.nb_lj_combine(b.sigma, b.eps), cluster_size=C)
     try:
         nb.nb_grid_put(cx.ctx, torch.as_tensor(b.xyz, device=dev), b.box)
         info = nb.nb_check(cx.ctx)
@@ -96,3 +94,57 @@ def test_noalloc_limits_and_cluster_size_4(env):
     with pytest.raises(nb.NbError) as ei:
         noalloc_grid(torch, nb, big, 8, max_slots=70000, max_columns=8192)
     assert ei.value.status == nb.NB_ERR_CAPACITY
+
+
+class _Slab:
+    """n uniform random particles (one LJ type, no charge) in a thin slab whose
+    grid has exactly 64 x 64 = 4,096 columns for clusters of C: the column
+    spacing (C a^2 h / n)^(1/3) is a / 64 for the height h = a n / (64^3 C)
+    (a = the slab's edge), and just below it for 0.99 of that height."""
+
+    def __init__(self, n, C, a=12.8, seed=3):
+        rng = np.random.default_rng(seed)
+        h = 0.99 * a * n / (64.0 ** 3 * C)
+        self.n = n
+        self.box = np.array([a, a, h])
+        self.xyz = (rng.random((n, 3)) * self.box).astype(np.float32)
+        self.q = np.zeros(n, np.float32)
+        self.types = np.zeros(n, np.int32)
+        self.ntypes = 1
+        self.sigma = np.array([0.3])
+        self.eps = np.array([0.5])
+
+
+@pytest.mark.parametrize("C", [8, 4])
+def test_noalloc_at_its_limits(env, C):
+    """32,768 particles on a 4,096-column grid (for C = 8 that is 61,440
+    slots, the fixed maximum) grid exactly as nb_grid_put grids them."""
+    torch, nb = env
+    b = _Slab(32768, C)
+    ref = reference_grid(torch, nb, b, C, rlist=0.05)   # list capacity for a slab 0.2-0.4 nm thick
+    assert ref["ncol"] == 4096
+    got = noalloc_grid(torch, nb, b, C, max_slots=61440, max_columns=4096)
+    same(ref, got)
+
+
+def test_noalloc_flags_an_overlong_column(env):
+    """A column with more than 8,192 particles is flagged (1 << NB_ERR_CAPACITY
+    in info[1]); its particles get no slot and every other particle does."""
+    torch, nb = env
+    rng = np.random.default_rng(9)
+    b = _Slab(16384, 8)
+    b.box = np.array([8.0, 8.0, 8.0])
+    xyz = rng.random((b.n, 3)) * b.box
+    crowd = np.arange(9000)
+    xyz[crowd, 0] = rng.random(crowd.size) * 0.3     # one grid column (spacing 0.63 nm)
+    xyz[crowd, 1] = rng.random(crowd.size) * 0.3
+    b.xyz = xyz.astype(np.float32)
+    got = noalloc_grid(torch, nb, b, 8, max_slots=40000, max_columns=2048)
+    assert got["flags"] & (1 << nb.NB_ERR_CAPACITY)
+    placed = got["aos"][got["aos"] >= 0]
+    assert len(np.unique(placed)) == placed.size
+    assert not np.isin(crowd, placed).any()
+    others = np.setdiff1d(np.arange(b.n), crowd)
+    in_crowd_column = (np.floor(b.xyz[others, 0] * np.float32(12 / 8.0)) == 0) & \
+                      (np.floor(b.xyz[others, 1] * np.float32(12 / 8.0)) == 0)
+    assert np.isin(others[~in_crowd_column], placed).all()
