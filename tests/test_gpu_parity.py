@@ -346,3 +346,29 @@ def test_tabulated_ewald_forces(gp, cfg2):
         assert emax < FORCE_TOL, (emax, erms)
     finally:
         gb.close()
+
+
+def test_repeated_evaluations_agree(gp):
+    """Twenty force evaluations in a row (energies on every other one) on the
+    24,000-particle box: energies and virial equal to 1e-6 relative each
+    time and forces equal up to the order of the FP32 additions (the work
+    counters, slot accumulators and FP64 totals come back to zero after
+    every evaluation)."""
+    import paper_1306_1737_gb300 as nb
+    b, p = w.config2()
+    gb = gp.GpuBox(b, p["rlist"])
+    try:
+        gb.grid()
+        gb.build(float(np.float32(p["rlist"])))
+        pe = nb.make_params("ewald", p["rc"], beta=p["beta"], want_energy=True)
+        pf = nb.make_params("ewald", p["rc"], beta=p["beta"], want_energy=False)
+        f0, e0, v0 = gb.compute(pe)
+        rms = np.sqrt((f0 ** 2).sum(1).mean())
+        for k in range(20):
+            f, e, v = gb.compute(pe if k % 2 else pf)
+            assert np.abs(f - f0).max() < 1e-5 * rms
+            if k % 2:
+                assert np.abs(e - e0).max() <= 1e-6 * np.abs(e0).max()
+                assert np.abs(v - v0).max() <= 1e-6 * np.abs(v0).max()
+    finally:
+        gb.close()
