@@ -88,6 +88,30 @@ def eval32(a, b, ws):
     return (P / Q).astype(np.float64), Q
 
 
+def monic(a, b):
+    """G's fit as lead * Pm(w) / Qm(w) with monic Pm, Qm (leading coefficient
+    1): returns (Pm's lower coefficients, Qm's lower coefficients, lead)."""
+    return a[:-1] / a[-1], b[:-1] / b[-1], a[-1] / b[-1]
+
+
+def eval32_monic_scaled(pm, qm, lead, beta, ws):
+    """FP32 evaluation as the force kernel does it: x = r^2 = w / beta^2, the
+    monic polynomials in x with beta folded into their coefficients
+    (c_k beta^(2(k - 4)), rounded to FP32), Horner with the first step x + c_3,
+    the quotient as P times the reciprocal of Q; relative to lead (the leading
+    ratio's beta^3 factor is the caller's)."""
+    b2 = beta * beta
+    pc = np.array([pm[k] * b2 ** (k - 4) for k in range(4)], np.float32)
+    qc = np.array([qm[k] * b2 ** (k - 4) for k in range(4)], np.float32)
+    x = (ws / b2).astype(np.float32)
+    P = (x + pc[3]).astype(np.float32)
+    Q = (x + qc[3]).astype(np.float32)
+    for k in (2, 1, 0):
+        P = (P * x + pc[k]).astype(np.float32)
+        Q = (Q * x + qc[k]).astype(np.float32)
+    return lead * (P * (np.float32(1.0) / Q).astype(np.float32)).astype(np.float64)
+
+
 def main():
     t = np.cos(np.pi * (np.arange(N_PTS) + 0.5) / N_PTS)
     ws = np.sort((t + 1) / 2 * W_MAX)
@@ -137,6 +161,27 @@ def main():
         lines.append("    const float q = %s;" % horner(b))
         lines.append("    return p * fit_rcp(q);")
         lines.append("}")
+    # G in monic form over x = r^2 (beta folded into the coefficients by the host)
+    a, b, _, _ = out["G"]
+    pm, qm, lead = monic(a, b)
+    fg = np.array([float(g_exact(w)) for w in ws])
+    errs = []
+    for beta in (2.0, 3.12, 4.0):
+        v = eval32_monic_scaled(pm, qm, lead, beta, ws)
+        errs.append(np.abs(v / fg - 1).max())
+    lines += [
+        "// G(w) = lead * Pm(w) / Qm(w) with monic Pm, Qm (below: their coefficients of",
+        "// w^0..w^3; w^4 has 1).  With x = r^2 = w / beta^2 the kernel evaluates",
+        "// Pm, Qm in x with coefficients c_k beta^(2(k-4)) (the common beta^8 cancels):",
+        "// max relative error in FP32 %.2e, %.2e, %.2e at beta 2, 3.12, 4 nm^-1." % tuple(errs),
+        "constexpr double kEwaldGMonicP[4] = {%s};" % ", ".join("%.17e" % v for v in pm),
+        "constexpr double kEwaldGMonicQ[4] = {%s};" % ", ".join("%.17e" % v for v in qm),
+        "constexpr double kEwaldGLead = %.17e;" % lead,
+        "// Pm or Qm at x with the host-scaled coefficients c[0..3] (Horner, first step x + c[3]).",
+        "__device__ __forceinline__ float ewald_monic4(float x, const float (&c)[4]) {",
+        "    return fmaf(fmaf(fmaf(x + c[3], x, c[2]), x, c[1]), x, c[0]);",
+        "}",
+    ]
     lines += ["}  // namespace nbc", ""]
     path = os.path.join(here, "nb_ewald_fit.h")
     open(path, "w").write("\n".join(lines))

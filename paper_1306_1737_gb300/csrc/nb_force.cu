@@ -194,9 +194,12 @@ __device__ __forceinline__ float2 pair_force2(const ForceParams& P, float2 r2, b
         fc = mul2(qq, make_float2(fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.x * P.tab_scale), rinv3.x),
                                   fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.y * P.tab_scale), rinv3.y)));
     } else if (FIT) {
-        // the fitted factor (Horner with immediate coefficients)
-        const float g0 = ewald_fit_g(P.beta2 * r2.x), g1 = ewald_fit_g(P.beta2 * r2.y);
-        fc = mul2(qq, make_float2(fmaf(-P.beta3, g0, rinv3.x), fmaf(-P.beta3, g1, rinv3.y)));
+        // the fitted factor as a quotient of monic polynomials in r^2 whose
+        // coefficients (beta folded in) are kernel parameters, i.e. direct
+        // operands of the multiply-adds
+        const float g0 = ewald_monic4(r2.x, P.fit_p) * fit_rcp(ewald_monic4(r2.x, P.fit_q));
+        const float g1 = ewald_monic4(r2.y, P.fit_p) * fit_rcp(ewald_monic4(r2.y, P.fit_q));
+        fc = mul2(qq, make_float2(fmaf(P.fit_k, g0, rinv3.x), fmaf(P.fit_k, g1, rinv3.y)));
     } else {
         const float r0 = r2.x * rinv.x, r1 = r2.y * rinv.y;
         const float b0 = P.beta * r0, b1 = P.beta * r1;
@@ -416,17 +419,15 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
         G.x = G.y = G.z = make_float2(0.f, 0.f);
         bool any = false;
         unsigned keep = 0;
-        if (w < 0) {
+        // (the network's form keeps one copy of each tile evaluator: its code
+        // is large, and a third copy for the fast path costs more in
+        // instruction fetch than the path saves)
+        if (!MLP && w < 0) {
 #pragma unroll
-            for (int k = 0; k < kSuper8; ++k) {
-                if constexpr (MLP)
-                    any |= icluster8_mlp<SHIFTED, true>(A.p, s_lj, W, L, row[k], k, false, ~0ull, J, fx[k], fy[k],
-                                                        fz[k], G, *M, mo);
-                else
-                    any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true, PRUNE>(A.p, s_lj, W, L, row[k], k, false,
-                                                                              ~0ull, J, fx[k], fy[k], fz[k], G,
-                                                                              e_lj, e_c, n_inc, keep);
-            }
+            for (int k = 0; k < kSuper8; ++k)
+                any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true, PRUNE>(A.p, s_lj, W, L, row[k], k, false, ~0ull,
+                                                                          J, fx[k], fy[k], fz[k], G, e_lj, e_c,
+                                                                          n_inc, keep);
         } else {
             const unsigned bits = ((unsigned)w >> kSuperShift) & ((1u << kSuper8) - 1u);
 #pragma unroll
