@@ -354,14 +354,7 @@ static nb_status force_params(nb_ctx* c, const nb_params* p, ForceParams* fp) {
     fp->beta2 = (float)((double)p->beta * p->beta);
     fp->beta3 = (float)((double)p->beta * p->beta * p->beta);
     fp->use_fit = ((double)p->beta * p->beta * rc * rc <= (double)kEwaldFitWMax) ? 1 : 0;
-    {
-        const double b2 = (double)p->beta * p->beta;
-        for (int k = 0; k < 4; ++k) {
-            fp->fit_p[k] = (float)(kEwaldGMonicP[k] * std::pow(b2, k - 4));
-            fp->fit_q[k] = (float)(kEwaldGMonicQ[k] * std::pow(b2, k - 4));
-        }
-        fp->fit_k = (float)(-b2 * (double)p->beta * kEwaldGLead);
-    }
+    fp->fit_k = (float)(-(double)p->beta * p->beta * p->beta * kEwaldGLead);
     if ((fp->elec == NB_ELEC_EWALD_MLP || fp->elec == NB_ELEC_EWALD_TAB) && !fp->use_fit)
         return fail(c, NB_ERR_ARG, "the surrogate and tabulated kernels need (beta rc)^2 <= %g",
                     (double)kEwaldFitWMax);

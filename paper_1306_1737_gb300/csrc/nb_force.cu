@@ -16,9 +16,9 @@
 // terms (Sec. 3.1: masking by multiplication, conditional on the cut-off).
 // j-entries whose interacting i-clusters all have full masks off the
 // diagonal (most of them) take a path with the cut-off as the only
-// condition.  j-forces are reduced over the 4 lanes sharing j with two
-// shuffles and added with one vector atomic per j-particle; i-forces are
-// reduced at the end of the entry and added once per i-particle.
+// condition.  Each lane adds its j-force (its two pairs' sum) with one
+// vector atomic per j-cluster; i-forces are reduced at the end of the entry
+// and added once per i-particle.
 //
 // Pair functions (Sec. 3.2), with qq = f q_i q_j and e = mask bit:
 //   LJ      F/r = e (12 C12 r^-6 - 6 C6) r^-8,  V = e (C12 r^-6 - C6) r^-6
@@ -194,11 +194,10 @@ __device__ __forceinline__ float2 pair_force2(const ForceParams& P, float2 r2, b
         fc = mul2(qq, make_float2(fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.x * P.tab_scale), rinv3.x),
                                   fmaf(-P.beta3, ewald_tab_g(s_tab, P.tab_n, r2.y * P.tab_scale), rinv3.y)));
     } else if (FIT) {
-        // the fitted factor as a quotient of monic polynomials in r^2 whose
-        // coefficients (beta folded in) are kernel parameters, i.e. direct
-        // operands of the multiply-adds
-        const float g0 = ewald_monic4(r2.x, P.fit_p) * fit_rcp(ewald_monic4(r2.x, P.fit_q));
-        const float g1 = ewald_monic4(r2.y, P.fit_p) * fit_rcp(ewald_monic4(r2.y, P.fit_q));
+        // the fitted factor as a quotient of monic polynomials in w whose
+        // coefficients are immediate operands; -beta^3 times the leading
+        // coefficients' ratio is fit_k
+        const float g0 = ewald_fit_gm(P.beta2 * r2.x), g1 = ewald_fit_gm(P.beta2 * r2.y);
         fc = mul2(qq, make_float2(fmaf(P.fit_k, g0, rinv3.x), fmaf(P.fit_k, g1, rinv3.y)));
     } else {
         const float r0 = r2.x * rinv.x, r1 = r2.y * rinv.y;
@@ -457,15 +456,11 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
             if (lane == t) my_keep = keep;
         }
         if (!any) continue;
-        // j-force: the lane's two pairs, then the 4 lanes sharing j
-        float fjx = G.x.x + G.x.y, fjy = G.y.x + G.y.y, fjz = G.z.x + G.z.y;
-        fjx += __shfl_xor_sync(full, fjx, 8);
-        fjy += __shfl_xor_sync(full, fjy, 8);
-        fjz += __shfl_xor_sync(full, fjz, 8);
-        fjx += __shfl_xor_sync(full, fjx, 16);
-        fjy += __shfl_xor_sync(full, fjy, 16);
-        fjz += __shfl_xor_sync(full, fjz, 16);
-        if (L.ih == 0) atomicAdd(&A.fslot[cjt * 8 + L.j], make_float4(-fjx, -fjy, -fjz, 0.0f));
+        // j-force: the lane's two pairs, added by every lane (the L2 adds
+        // the 4 lanes' contributions to a j-particle faster than two rounds
+        // of shuffles do)
+        atomicAdd(&A.fslot[cjt * 8 + L.j],
+                  make_float4(-(G.x.x + G.x.y), -(G.y.x + G.y.y), -(G.z.x + G.z.y), 0.0f));
     }
     if constexpr (PRUNE) {
         // compact the kept j-entries of this chunk, in order

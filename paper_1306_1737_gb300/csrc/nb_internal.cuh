@@ -231,9 +231,9 @@ struct ForceParams {
     float beta, two_beta_sqrtpi;
     float beta2, beta3;   // beta^2, beta^3 for the fitted correction
     int use_fit;          // (beta rc)^2 within the fitted range
-    // the force factor's fit in monic form over r^2 (beta folded in):
-    // -beta^3 G(beta^2 r^2) = fit_k Pm(r^2) / Qm(r^2)
-    float fit_p[4], fit_q[4], fit_k;
+    // -beta^3 times the leading-coefficient ratio of the force factor's fit
+    // in monic form: -beta^3 G(w) = fit_k Pm(w) / Qm(w)
+    float fit_k;
     float mlp_rmin;       // network input range starts here (surrogate kernel)
     float tab_scale;      // beta^2 n / w_max: r^2 to table coordinate (tabulated kernel)
     int tab_n;            // table intervals
