@@ -55,6 +55,8 @@ struct nb_ctx {
     int n = 0, ntypes = 0;
     bool have_atoms = false, have_grid = false, have_list = false, have_pruned = false;
     bool list_fresh = false;   // no new coordinates since the last list build
+    bool fslot_zero = false;   // the slot force accumulators hold zeros (cleared by the grid,
+                               // the coordinate update and the finalize with the virial)
     bool have_mlp = false;
     float mlp_rmin = 0.f, mlp_rmax = 0.f;
     float rlist = 0.f, r_prune = 0.f;
@@ -198,6 +200,7 @@ static size_t carve(const nb_ctx* c, char* base, Workspace* ws) {
     const size_t ns = (size_t)w.clu_total * C;
     w.xyzq = (float4*)take(sizeof(float4) * ns);
     w.xjd = (float4*)take(sizeof(float4) * 2 * ns);
+    w.woff_slot = (float4*)take(sizeof(float4) * ns);
     w.atom_of_slot = (int*)take(sizeof(int) * ns);
     w.type_slot = (int*)take(sizeof(int) * ns);
     w.fslot = (float4*)take(sizeof(float4) * ns);
@@ -578,6 +581,7 @@ nb_status nb_grid_put(nb_ctx* c, const float* xyz, const double* boxes, nb_strea
     if (e != cudaSuccess) return cuda_fail(c, e, "grid kernels");
     c->n_launches += kLaunchesGrid;
     c->have_grid = true;
+    c->fslot_zero = true;
     c->have_list = c->have_pruned = false;
     c->last_valid = false;
     return NB_OK;
@@ -606,6 +610,15 @@ nb_status nb_pairlist_build(nb_ctx* c, float rlist, float rbb, const int* excl_o
     return NB_OK;
 }
 
+// The force kernels add into the slot accumulators: clear them first unless
+// the grid, a coordinate update or the last finalize left them cleared.
+static nb_status clear_slot_forces(nb_ctx* c, cudaStream_t s) {
+    if (!c->fslot_zero)
+        NB_CUDA(c, cudaMemsetAsync(c->ws.fslot, 0, sizeof(float4) * (size_t)c->ws.clu_total * c->C, s));
+    c->fslot_zero = false;
+    return NB_OK;
+}
+
 nb_status nb_set_coords(nb_ctx* c, const float* xyz, nb_stream stream) {
     if (!c) return NB_ERR_ARG;
     if (!c->have_grid) return fail(c, NB_ERR_STATE, "nb_grid_put first");
@@ -613,6 +626,7 @@ nb_status nb_set_coords(nb_ctx* c, const float* xyz, nb_stream stream) {
     NB_CUDA(c, cudaSetDevice(c->device));
     const int sp = span_begin(c, NB_KERNEL_COORDS, (cudaStream_t)stream);
     cudaError_t e = launch_set_coords(c->ws, c->C, xyz, (cudaStream_t)stream);
+    c->fslot_zero = true;
     span_end(c, sp, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_coords kernel");
     c->n_launches += kLaunchesSetCoords;
@@ -668,11 +682,14 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(c, cudaSetDevice(c->device));
     const int sp = span_begin(c, NB_KERNEL_FORCE, s);
+    nb_status zs = clear_slot_forces(c, s);
+    if (zs != NB_OK) return zs;
     cudaError_t e = launch_force(c->ws, fp, c->C, c->n_sm, s);
     span_end(c, sp, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "force kernel");
     const int sz = span_begin(c, NB_KERNEL_FINALIZE, s);
     e = launch_finalize(c->ws, fp, c->C, f, e_out, vir_out, s);
+    c->fslot_zero = fp.want_energy != 0;
     span_end(c, sz, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
     c->n_launches += 2 + (fp.want_energy ? 1 : 0);
@@ -716,6 +733,8 @@ nb_status nb_prune_compute(nb_ctx* c, const nb_params* p, const float* xyz, floa
         fp.rp2 = r_prune * r_prune;
         fp.use_pruned = 0;
         const int sp = span_begin(c, NB_KERNEL_FORCE_PRUNE, s);
+        const nb_status zs = clear_slot_forces(c, s);
+        if (zs != NB_OK) return zs;
         e = launch_force(c->ws, fp, c->C, c->n_sm, s);
         span_end(c, sp, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "force + prune kernel");
@@ -728,6 +747,8 @@ nb_status nb_prune_compute(nb_ctx* c, const nb_params* p, const float* xyz, floa
         c->n_launches += kLaunchesPrune;
         fp.use_pruned = 1;
         const int sf = span_begin(c, NB_KERNEL_FORCE, s);
+        const nb_status zs = clear_slot_forces(c, s);
+        if (zs != NB_OK) return zs;
         e = launch_force(c->ws, fp, c->C, c->n_sm, s);
         span_end(c, sf, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "force kernel");
@@ -738,6 +759,7 @@ nb_status nb_prune_compute(nb_ctx* c, const nb_params* p, const float* xyz, floa
     c->last_valid = false;
     const int sz = span_begin(c, NB_KERNEL_FINALIZE, s);
     e = launch_finalize(c->ws, fp, c->C, f, e_out, vir_out, s);
+    c->fslot_zero = fp.want_energy != 0;
     span_end(c, sz, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
     c->n_launches += 1 + (fp.want_energy ? 1 : 0);
@@ -778,11 +800,13 @@ nb_status nb_compute_1x1(nb_ctx* c, const nb_params* p, const float* xyz, const 
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(c, cudaSetDevice(c->device));
     const int sp = span_begin(c, NB_KERNEL_FORCE_1X1, s);
+    c->fslot_zero = false;   // the 1 x 1 kernel overwrites the real slots' accumulators
     cudaError_t e = launch_force_1x1(c->ws, fp, c->C, max_nbr, nbr, count, s);
     span_end(c, sp, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "1x1 force kernel");
     const int sz = span_begin(c, NB_KERNEL_FINALIZE, s);
     e = launch_finalize(c->ws, fp, c->C, f, nullptr, nullptr, s);
+    c->fslot_zero = fp.want_energy != 0;
     span_end(c, sz, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel");
     c->n_launches += 2;

@@ -18,8 +18,8 @@ __device__ __forceinline__ void virial_flush(const Workspace& ws, double (&w)[9]
     }
 }
 
-// Forces back to the caller's order (and zeroed for the next evaluation);
-// with energies, the FP64 sum per box over slots of x (x) f for the virial.
+// With energies: forces back to the caller's order (and zeroed for the next
+// evaluation) and the FP64 sum per box over slots of x (x) f for the virial.
 // The slots are walked in order (coalesced reads of the slot forces, their
 // particles and coordinates) and each particle's force is scattered to the
 // caller's order; a gather in particle order instead waits on a random
@@ -120,9 +120,36 @@ __global__ void k_finalize_small(Workspace ws, double* e_out, double* vir_out) {
     }
 }
 
+// Forces to the caller's order without the virial: one thread per particle
+// reads its slot's accumulator (a gathered 16-byte read) and writes its
+// force in place (coalesced), leaving the accumulators as they are (the next
+// coordinate update or a memset clears them).  Scattered writes, of the
+// forces or of cleared accumulators, cost several times more than these
+// reads on this GPU.  Particles without a slot get zero force.
+__global__ void k_gather_forces(Workspace ws, int C, float* __restrict__ f_out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ws.work[0] = 0;   // the force kernel's counter
+    const int n = ws.atom_total;
+    const long long nslot = (long long)ws.clu_total * C;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        const int sl = ws.slot_of_atom[a];
+        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (sl >= 0 && sl < nslot) f = ws.fslot[sl];
+        f_out[3 * (long long)a] = f.x;
+        f_out[3 * (long long)a + 1] = f.y;
+        f_out[3 * (long long)a + 2] = f.z;
+    }
+}
+
 cudaError_t launch_finalize(const Workspace& ws, const ForceParams& p, int C, float* f_out, double* e_out,
                             double* vir_out, cudaStream_t s) {
     const int want_vir = (p.want_energy && vir_out) ? 1 : 0;
+    if (!p.want_energy) {
+        long long blocks = ((long long)ws.atom_total + 255) / 256;
+        if (blocks > 65535) blocks = 65535;
+        if (blocks < 1) blocks = 1;
+        k_gather_forces<<<(int)blocks, 256, 0, s>>>(ws, C, f_out);
+        return cudaGetLastError();
+    }
     // enough warps to keep the gather/scatter in flight; fewer with the
     // virial, whose per-warp FP64 flushes meet on one box's nine addresses
     int blocks = (int)min(((long long)ws.clu_total * C + 255) / 256, (long long)1 << 20);

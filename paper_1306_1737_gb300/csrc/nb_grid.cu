@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(512) k_col_sort(Workspace ws, int C, int ntype
             const float4 x = ws.xw[a];
             ws.xyzq[s] = x;
             if (ws.xjd) store_xjd(ws.xjd, s, x);
+            if (ws.woff_slot) ws.woff_slot[s] = ws.woff[a];
             ws.atom_of_slot[s] = a;
             ws.slot_of_atom[a] = (int)s;
             int ty = ws.type[a];
@@ -232,26 +233,34 @@ cudaError_t launch_grid(const Workspace& ws, int C, int ntypes, const float* xyz
     return cudaGetLastError();
 }
 
-// One thread per particle: its slot gets the new coordinates plus the wrap
-// offset of the last gridding, and its charge (no box lookup needed).  A
-// slot index outside the slot arrays (a column that was too long to grid
-// leaves its particles without slots; that error is flagged) is skipped.
+// One thread per slot of the current clusters (coalesced slot reads and
+// writes; one gathered read of the particle's new coordinates): the slot's
+// particle gets its new coordinates plus the wrap offset of the last
+// gridding (kept per slot), its charge stays; dummy slots keep theirs.  The
+// slot's force accumulator is cleared for the evaluation that follows.
+// Particles without a slot (a column too long to grid, an error that is
+// flagged) are not placed.
 __global__ void k_set_coords(Workspace ws, int C, const float* __restrict__ xyz) {
-    const int n = ws.atom_total;
     const long long nslot = (long long)ws.clu_total * C;
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
-        const float4 o = ws.woff[a];
-        const int s = ws.slot_of_atom[a];
-        if (s < 0 || s >= nslot) continue;
-        const float4 x = make_float4(__fadd_rn(xyz[3 * a], o.x), __fadd_rn(xyz[3 * a + 1], o.y),
-                                     __fadd_rn(xyz[3 * a + 2], o.z), ws.q[a]);
+    const int n = ws.atom_total;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nslot;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int cl = (int)(s / C);
+        const int b = find_box(ws.lay.clu_off, ws.nbox, cl);
+        if (cl - ws.lay.clu_off[b] >= ws.st[b].nclu) continue;   // capacity beyond the box's grid
+        ws.fslot[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int a = ws.atom_of_slot[s];
+        if (a < 0 || a >= n) continue;
+        const float4 o = ws.woff_slot[s];
+        const float4 x = make_float4(__fadd_rn(xyz[3 * (long long)a], o.x), __fadd_rn(xyz[3 * (long long)a + 1], o.y),
+                                     __fadd_rn(xyz[3 * (long long)a + 2], o.z), ws.xyzq[s].w);
         ws.xyzq[s] = x;
         store_xjd(ws.xjd, s, x);
     }
 }
 
 cudaError_t launch_set_coords(const Workspace& ws, int C, const float* xyz, cudaStream_t s) {
-    long long blocks = ((long long)ws.atom_total + 255) / 256;
+    long long blocks = ((long long)ws.clu_total * C + 255) / 256;
     if (blocks > 65535) blocks = 65535;
     if (blocks < 1) blocks = 1;
     k_set_coords<<<(int)blocks, 256, 0, s>>>(ws, C, xyz);

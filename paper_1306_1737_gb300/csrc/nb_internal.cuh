@@ -122,6 +122,7 @@ struct Workspace {
     // j-particle as the force kernel's packed pairs use it (both halves of a
     // lane's pair share j), written with xyzq
     float4* xjd;
+    float4* woff_slot;   // the wrap offset of the slot's particle (written by the grid)
     int* atom_of_slot;   // batch particle index, -1 for dummies
     int* type_slot;
     float4* fslot;
