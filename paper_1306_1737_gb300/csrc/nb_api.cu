@@ -55,8 +55,8 @@ struct nb_ctx {
     int n = 0, ntypes = 0;
     bool have_atoms = false, have_grid = false, have_list = false, have_pruned = false;
     bool list_fresh = false;   // no new coordinates since the last list build
-    bool fslot_zero = false;   // the slot force accumulators hold zeros (cleared by the grid,
-                               // the coordinate update and the finalize with the virial)
+    bool fslot_zero = false;   // the slot force accumulators hold zeros (cleared by the grid and
+                               // the coordinate update)
     bool have_mlp = false;
     float mlp_rmin = 0.f, mlp_rmax = 0.f;
     float rlist = 0.f, r_prune = 0.f;
@@ -611,7 +611,7 @@ nb_status nb_pairlist_build(nb_ctx* c, float rlist, float rbb, const int* excl_o
 }
 
 // The force kernels add into the slot accumulators: clear them first unless
-// the grid, a coordinate update or the last finalize left them cleared.
+// the grid or a coordinate update left them cleared.
 static nb_status clear_slot_forces(nb_ctx* c, cudaStream_t s) {
     if (!c->fslot_zero)
         NB_CUDA(c, cudaMemsetAsync(c->ws.fslot, 0, sizeof(float4) * (size_t)c->ws.clu_total * c->C, s));
@@ -689,7 +689,7 @@ nb_status nb_compute(nb_ctx* c, const nb_params* p, const float* xyz, float* f, 
     if (e != cudaSuccess) return cuda_fail(c, e, "force kernel");
     const int sz = span_begin(c, NB_KERNEL_FINALIZE, s);
     e = launch_finalize(c->ws, fp, c->C, f, e_out, vir_out, s);
-    c->fslot_zero = fp.want_energy != 0;
+    c->fslot_zero = false;
     span_end(c, sz, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
     c->n_launches += 2 + (fp.want_energy ? 1 : 0);
@@ -759,7 +759,7 @@ nb_status nb_prune_compute(nb_ctx* c, const nb_params* p, const float* xyz, floa
     c->last_valid = false;
     const int sz = span_begin(c, NB_KERNEL_FINALIZE, s);
     e = launch_finalize(c->ws, fp, c->C, f, e_out, vir_out, s);
-    c->fslot_zero = fp.want_energy != 0;
+    c->fslot_zero = false;
     span_end(c, sz, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
     c->n_launches += 1 + (fp.want_energy ? 1 : 0);
@@ -806,7 +806,7 @@ nb_status nb_compute_1x1(nb_ctx* c, const nb_params* p, const float* xyz, const 
     if (e != cudaSuccess) return cuda_fail(c, e, "1x1 force kernel");
     const int sz = span_begin(c, NB_KERNEL_FINALIZE, s);
     e = launch_finalize(c->ws, fp, c->C, f, nullptr, nullptr, s);
-    c->fslot_zero = fp.want_energy != 0;
+    c->fslot_zero = false;
     span_end(c, sz, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel");
     c->n_launches += 2;
