@@ -481,12 +481,13 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
     __syncwarp();
 }
 
-// Blocks per SM the force kernels are compiled for (register budget): the
-// force and fused force + prune kernels at 7 blocks of 4 warps (72
-// registers), the energy kernel at 5 and the network's at 4.
+// Blocks per SM the force kernels are compiled for (register budget, as
+// measured fastest): the force kernel at 7 blocks of 4 warps (72
+// registers), the energy and fused force + prune kernels at 6, the
+// network's at 4.
 template <int ELEC, bool ENERGY, bool PRUNE>
 constexpr int force_min_blocks() {
-    return ELEC == NB_ELEC_EWALD_MLP ? 4 : (ENERGY ? 5 : 7);
+    return ELEC == NB_ELEC_EWALD_MLP ? 4 : (ENERGY || PRUNE ? 6 : 7);
 }
 
 template <int ELEC, bool ENERGY, bool FIT, bool PRUNE = false>
