@@ -388,7 +388,7 @@ def config_dict(args, box, p, desc, workload=None):
     return {"workload": workload or args.workload, "description": desc, "n_atoms": int(box.n),
             "box_nm": [round(float(v), 6) for v in box.box], "elec": p["elec"], "rc_nm": p["rc"],
             "rlist_nm": p["rlist"], "beta_nm-1": p.get("beta"), "nstlist": p.get("nstlist", 1),
-            "nstprune": p.get("nstprune", 0), "cluster": "8x8 cluster pairs (two 8x4 halves per warp), super-clusters of 2 i-clusters sharing a j-list",
+            "nstprune": p.get("nstprune", 0), "rbb_nm": args.rbb, "cluster": "8x8 cluster pairs (two 8x4 halves per warp), super-clusters of 2 i-clusters sharing a j-list",
             "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}",
             "launch": "each step captured once as a CUDA graph and replayed",
             "seed": int(box.seed)}
@@ -1026,11 +1026,11 @@ def measure_batch(args, dist, ws_n, rank, dev, sub=False):
     cache = os.path.join(ROOT, "paper_1306_1737_gb300", "_build", "tune_cache.json")
     t0 = time.perf_counter()
     groups, table = tuner.tune(*common, p, nstprune, rl0, nst0, cache_path=cache, device=dev.index,
-                               rlist_rule=args.rlist_rule, mass=B.mass)
+                               rlist_rule=args.rlist_rule, mass=B.mass, rbb=args.rbb)
     tune_s = time.perf_counter() - t0
 
     # 2. tuned groups, graph
-    tuned = BatchRunner(*common, groups, p, nstprune, device=dev.index)
+    tuned = BatchRunner(*common, groups, p, nstprune, device=dev.index, rbb=args.rbb)
     l0 = tuned.launches()
     tuned.step()
     torch.cuda.synchronize()
@@ -1085,7 +1085,8 @@ def measure_batch(args, dist, ws_n, rank, dev, sub=False):
 
     # 4. one context for all boxes (C = 8, nstlist 20, rlist 1.1), graph; its
     #    eager step gives the force kernel's launch times for the roofline
-    one = BatchRunner(*common, [GroupSpec(8, nst0, rl0, list(range(B.nbox)))], p, nstprune, device=dev.index)
+    one = BatchRunner(*common, [GroupSpec(8, nst0, rl0, list(range(B.nbox)))], p, nstprune, device=dev.index,
+                      rbb=args.rbb)
     g1 = one.groups[0]
     nb.nb_profile(g1.cx.ctx, True)
     nb.nb_profile_read(g1.cx.ctx)
@@ -1102,7 +1103,7 @@ def measure_batch(args, dist, ws_n, rank, dev, sub=False):
 
     # 5. plain: one context per box, launches one box after another
     plain = BatchRunner(*common, [GroupSpec(8, nst0, rl0, [k]) for k in range(B.nbox)], p, nstprune,
-                        device=dev.index)
+                        device=dev.index, rbb=args.rbb)
     plain.step(concurrent=False)
     torch.cuda.synchronize()
     ms_plain = timed(lambda: plain.step(concurrent=False), max(1, min(args.steps, 3)))
@@ -1171,8 +1172,9 @@ def make_parser():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--rbb", type=float, default=0.0,
-                    help="bounding-box distance below which the search skips the particle test (nm; <0: rlist)")
+    ap.add_argument("--rbb", type=float, default=0.8,
+                    help="bounding-box distance below which the search skips the particle test (nm; <0: rlist; "
+                         "0: the particle test always runs)")
     ap.add_argument("--prune0", action="store_true", help="also prune right after each list build")
     ap.add_argument("--rlist-rule", default="sqrt", choices=["sqrt", "appendix"],
                     help="batch tuner: list radius per lifetime by sqrt scaling or by the Appendix drift bound")

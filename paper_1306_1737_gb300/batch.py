@@ -93,9 +93,10 @@ class BatchRunner:
     excl_off/excl_idx: batch arrays (exclusion partners batch-global)."""
 
     def __init__(self, counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, groups,
-                 params, nstprune, device=0, list_factor=0.0):
+                 params, nstprune, device=0, list_factor=0.0, rbb=0.0):
         import torch
         self.torch = torch
+        self.rbb = float(rbb)   # Fig. 3's bounding-box shortcut radius of the list builds (nm)
         self.counts = np.asarray(counts, dtype=np.int64)
         self.boxes = np.asarray(boxes, dtype=np.float64).reshape(-1, 3)
         self.atom_off = np.concatenate([[0], np.cumsum(self.counts)])
@@ -130,7 +131,9 @@ class BatchRunner:
         F = g.F if F is None else F
         if lf == 0:
             nb.nb_grid_put(ctx, x, g.boxes, stream)
-            nb.nb_pairlist_build(ctx, float(np.float32(g.spec.rlist)), 0.0, g.excl_off, g.excl_idx, stream)
+            rl = float(np.float32(g.spec.rlist))
+            nb.nb_pairlist_build(ctx, rl, rl if self.rbb < 0 else min(self.rbb, rl), g.excl_off, g.excl_idx,
+                                 stream)
             nb.nb_compute(ctx, prm, None, F, g.E, g.V, stream)
         elif self.nstprune_of(g) and lf % self.nstprune_of(g) == 0:
             # prune while computing this frame's forces on the outer list

@@ -47,11 +47,11 @@ def _key(gpu, counts, boxes, params, rlist0, nstlist0, nstprune, H):
 
 
 def time_group(spec, counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nstprune,
-               device, reps):
+               device, reps, rbb=0.0):
     """Device ms per frame of one group run alone (graph replays)."""
     import torch
     r = BatchRunner(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, [spec], params, nstprune,
-                    device=device)
+                    device=device, rbb=rbb)
     try:
         r.capture()
         r.replay()
@@ -95,7 +95,7 @@ def appendix_rlist(classes, c6c12, volume, params, nstlist, dt_ps=0.002, tempera
 
 def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nstprune, rlist0, nstlist0,
          n_classes=4, reps=3, cache_path=None, device=0, log=None, rlist_rule="sqrt", mass=None,
-         tolerance=None):
+         tolerance=None, rbb=0.0):
     """Returns (groups: list of GroupSpec, table: list of per-class results;
     a result key is "C/nstlist" at the configured prune interval or
     "C/nstlist/nstprune").
@@ -128,7 +128,7 @@ def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nst
         rlist_of = {nst: scaled_rlist(params["rc"], rlist0, nstlist0, nst) for nst in NSTLISTS}
     rule = rlist_rule if rlist_rule != "appendix" else f"appendix:{tolerance}"
     for cls in _classes(counts, n_classes):
-        key = _key(gpu, counts[cls], boxes[cls], params, rlist0, nstlist0, nstprune, H) + rule
+        key = _key(gpu, counts[cls], boxes[cls], params, rlist0, nstlist0, nstprune, H) + rule + f"/rbb{rbb:g}"
         if key in cache:
             ent = cache[key]
             ent["cached"] = True
@@ -142,7 +142,7 @@ def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nst
                         continue                    # list radius too large for these boxes
                     spec = GroupSpec(C, nst, rlist_of[nst], list(cls))
                     t = time_group(spec, counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params,
-                                   nstprune, device, reps)
+                                   nstprune, device, reps, rbb=rbb)
                     times[f"{C}/{nst}"] = t
                     if log:
                         log(f"class {len(cls)} boxes {int(counts[cls].min())}-{int(counts[cls].max())} atoms: "
@@ -162,7 +162,7 @@ def tune(counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params, nst
                     continue
                 spec = GroupSpec(bC, bn, rlist_of[bn], list(cls), nstprune=nsp)
                 t = time_group(spec, counts, boxes, q, types, c6c12, excl_off, excl_idx, frames, params,
-                               nstprune, device, reps)
+                               nstprune, device, reps, rbb=rbb)
                 times[f"{bC}/{bn}/{nsp}"] = t
                 if log:
                     log(f"class {len(cls)} boxes: C={bC} nstlist={bn} nstprune={nsp}: {t:.4f} ms/frame")
