@@ -81,6 +81,8 @@ class NbError(RuntimeError):
 def load():
     """Load libnbcluster.so (raises if it is missing)."""
     global _lib
+    if _lib is not None:
+        return _lib
     with _lock:
         if _lib is not None:
             return _lib
@@ -155,6 +157,9 @@ def status_name(s: int) -> str:
 _F32, _F64, _I32, _U64 = ("float32",), ("float64",), ("int32",), ("int64", "uint64")
 
 
+_DTYPE_NAMES = {}   # torch dtype -> its name (memoised: the check runs on every call)
+
+
 def _ptr(x, dtypes=None):
     """Device pointer of a torch tensor (or an int / None).  A tensor must be
     a contiguous CUDA tensor: every pointer the library takes addresses a
@@ -168,8 +173,12 @@ def _ptr(x, dtypes=None):
         raise ValueError("the library takes device memory: pass a CUDA tensor")
     if not x.is_contiguous():
         raise ValueError("the library takes dense arrays: pass a contiguous tensor")
-    if dtypes is not None and str(x.dtype).replace("torch.", "") not in dtypes:
-        raise ValueError(f"expected a {' or '.join(dtypes)} tensor, got {x.dtype}")
+    if dtypes is not None:
+        name = _DTYPE_NAMES.get(x.dtype)
+        if name is None:
+            name = _DTYPE_NAMES.setdefault(x.dtype, str(x.dtype).replace("torch.", ""))
+        if name not in dtypes:
+            raise ValueError(f"expected a {' or '.join(dtypes)} tensor, got {x.dtype}")
     return x.data_ptr()
 
 

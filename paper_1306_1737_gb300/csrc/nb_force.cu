@@ -25,6 +25,10 @@
 //   RF      F/r = qq (e r^-3 - 2k),             V = qq (e r^-1 + k r^2 - c_rf)
 //   Ewald   F/r = qq (erfc(br) - (1-e) + 2br/sqrt(pi) exp(-b^2 r^2)) r^-3,
 //           V = qq (erfc(br) - (1-e)) r^-1
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "nb_internal.cuh"
 #include "nb_ewald_fit.h"
 #include "nb_mlp.cuh"
@@ -747,15 +751,38 @@ __global__ void __launch_bounds__(32 * kForceWarps) k_force4(ForceArgs A) {
     if (ENERGY) flush_energy(A.acc, b_acc, e_lj, e_c, n_inc);
 }
 
+// Resident blocks per SM of a force kernel at kForceWarps warps and smem
+// bytes of dynamic shared memory, queried once per kernel, device and size
+// (the query costs microseconds of host time, every frame otherwise).  All
+// force kernels share one signature, so the kernel's address is in the key.
+static cudaError_t force_blocks_per_sm(void (*kern)(ForceArgs), size_t smem, int* per_sm) {
+    static std::mutex m;
+    static std::map<std::tuple<const void*, int, size_t>, int> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const auto key = std::make_tuple(reinterpret_cast<const void*>(kern), dev, smem);
+    std::lock_guard<std::mutex> lock(m);
+    const auto it = cache.find(key);
+    if (it != cache.end()) {
+        *per_sm = it->second;
+        return cudaSuccess;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, 32 * kForceWarps, smem);
+    if (e != cudaSuccess) return e;
+    if (*per_sm < 1) *per_sm = 1;
+    cache[key] = *per_sm;
+    return cudaSuccess;
+}
+
 template <int ELEC, bool ENERGY, bool FIT, bool PRUNE = false>
 static cudaError_t launch_force_t(const ForceArgs& A, int C, int n_sm, cudaStream_t s) {
     const size_t smem = sizeof(float2) * A.p.ntypes * A.p.ntypes;
     auto kern = PRUNE ? k_force8<ELEC, ENERGY, FIT, PRUNE>
                       : ((C == 8) ? k_force8<ELEC, ENERGY, FIT> : k_force4<ELEC, ENERGY, FIT>);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kForceWarps, smem);
+    const cudaError_t e = force_blocks_per_sm(kern, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
     kern<<<n_sm * per_sm, 32 * kForceWarps, smem, s>>>(A);
     return cudaGetLastError();
 }
@@ -776,9 +803,8 @@ static cudaError_t launch_force_tab(const ForceArgs& A, int n_sm, cudaStream_t s
     cudaError_t e = smem_opt_in(kern, 64 * 1024, smem_set);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kForceWarps, smem);
+    e = force_blocks_per_sm(kern, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
     kern<<<n_sm * per_sm, 32 * kForceWarps, smem, s>>>(A);
     return cudaGetLastError();
 }
@@ -854,9 +880,8 @@ cudaError_t launch_force(const Workspace& ws, const ForceParams& p, int C, int n
         auto kern = k_force8<NB_ELEC_EWALD_MLP, false, true>;
         const size_t smem = sizeof(float2) * A.p.ntypes * A.p.ntypes;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kForceWarps, smem);
+        e = force_blocks_per_sm(kern, smem, &per_sm);
         if (e != cudaSuccess) return e;
-        if (per_sm < 1) per_sm = 1;
         kern<<<n_sm * per_sm, 32 * kForceWarps, smem, s>>>(A);
         return cudaGetLastError();
     }

@@ -154,11 +154,13 @@ def test_batch_box_change_and_errors(env):
         cx.close()
 
 
-def test_batch_runner_groups_graph(env):
+@pytest.mark.parametrize("rbb", [0.0, 0.8])
+def test_batch_runner_groups_graph(env, rbb):
     """Two groups (C = 8 with nstlist 10 pruning every 2 frames, C = 4 with
     nstlist 20 pruning every 5) stepped over
     20 frames on their own streams and captured in a CUDA graph: after a
-    replay, every box's last-frame forces and energies match the oracle."""
+    replay, every box's last-frame forces and energies match the oracle.
+    rbb: the lists' bounding-box shortcut radius (0.8 nm, as the bench)."""
     torch, dev, nb = env
     from paper_1306_1737_gb300.batch import BatchRunner, GroupSpec, scaled_rlist
     boxes = [w.water_box(m, None, seed=7200 + k) for k, m in enumerate([520, 900, 610, 1400])]
@@ -169,7 +171,7 @@ def test_batch_runner_groups_graph(env):
     groups = [GroupSpec(8, 10, scaled_rlist(1.0, 1.1, 20, 10), [0, 2], nstprune=2),
               GroupSpec(4, 20, 1.1, [1, 3])]
     r = BatchRunner(B.counts, B.boxes, B.q, B.types, nb.nb_lj_combine(B.sigma, B.eps), B.excl_off,
-                    B.excl_idx, fr, groups, p, nstprune=5)
+                    B.excl_idx, fr, groups, p, nstprune=5, rbb=rbb)
     try:
         r.capture()
         for g in r.groups:
