@@ -681,12 +681,27 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
             else:
                 nb.nb_compute(ctx, prm, xf if f > 0 else None, F, E, V, stream)
 
+    efr = [energy_frame(f) for f in range(nstlist)]
+    native_e2e = args.fused_prune and not args.prune0   # the schedule nb_run_frames runs
+
+    def run_host(hx, hF, hE, hV, xbufs, Fbufs, Ebufs, Vbufs, cs):
+        """One list lifetime from pinned host frames to pinned host forces,
+        energies and virial in one call (nb_run_frames: the same calls as
+        step(), made by the library, with the transfers on a copy stream
+        overlapping the neighbouring frames' kernels)."""
+        nb.nb_run_frames(ctx, prm_f, hx, hF, xbufs, Fbufs, nbox=1, energy_frames=efr, e_host=hE, vir_host=hV,
+                         e_dev=Ebufs, vir_dev=Vbufs, build=True, boxes=box.box, rlist=rlist, rbb=rbb,
+                         excl_off=eo, excl_idx=ei, nstprune=nstprune, r_prune=rprune,
+                         stream=torch.cuda.current_stream(), copy_stream=cs)
+
     def step_host(hx, hF, hE, xbufs, Fbufs, cs, ev):
         """One list lifetime from pinned host frames to pinned host forces
-        through the same calls, with the transfers on a copy stream: frame
-        f + 1's coordinates are copied in while frame f computes, and frame
-        f's forces are read back while frame f + 1 computes (two device
-        buffers each, ordered by events)."""
+        through the same calls made from Python, with the transfers on a copy
+        stream: frame f + 1's coordinates are copied in while frame f
+        computes, and frame f's forces are read back while frame f + 1
+        computes (two device buffers each, ordered by events).  For the
+        schedules nb_run_frames does not run (a separate prune pass, a prune
+        right after the build)."""
         main = torch.cuda.current_stream()
         x_ready, x_free, f_done, f_free = ev
         with torch.cuda.stream(cs):
@@ -845,20 +860,32 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
         # the timed region
         hx = torch.as_tensor(frames).pin_memory()
         hF = torch.empty((nstlist, box.n, 3), dtype=torch.float32).pin_memory()
-        hE = torch.empty(2, dtype=torch.float64).pin_memory()
         xbufs = [torch.empty((box.n, 3), dtype=torch.float32, device=dev) for _ in range(2)]
         Fbufs = [torch.empty((box.n, 3), dtype=torch.float32, device=dev) for _ in range(2)]
         cs = torch.cuda.Stream(device=dev)
-        ev = tuple([torch.cuda.Event() for _ in range(2)] for _ in range(4))
+        if native_e2e:
+            hE = torch.zeros((nstlist, 1, 2), dtype=torch.float64).pin_memory()
+            hV = torch.zeros((nstlist, 1, 9), dtype=torch.float64).pin_memory()
+            Ebufs = [torch.empty((1, 2), dtype=torch.float64, device=dev) for _ in range(2)]
+            Vbufs = [torch.empty((1, 9), dtype=torch.float64, device=dev) for _ in range(2)]
+
+            def host_step():
+                run_host(hx, hF, hE, hV, xbufs, Fbufs, Ebufs, Vbufs, cs)
+        else:
+            hE = torch.empty(2, dtype=torch.float64).pin_memory()
+            ev = tuple([torch.cuda.Event() for _ in range(2)] for _ in range(4))
+
+            def host_step():
+                step_host(hx, hF, hE, xbufs, Fbufs, cs, ev)
         for _ in range(2):
-            step_host(hx, hF, hE, xbufs, Fbufs, cs, ev)
+            host_step()
         torch.cuda.synchronize()
         e2e_ms = []
         for k in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            step_host(hx, hF, hE, xbufs, Fbufs, cs, ev)
+            host_step()
             torch.cuda.synchronize()
             e2e_ms.append(1000 * (time.perf_counter() - t0))
         e2e_value = args.steps * nstlist / (sum(e2e_ms) / 1000.0)
@@ -867,7 +894,8 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
         e2e_check = float(np.sqrt(((hF[nstlist - 1].double().numpy() - Fd) ** 2).sum(1)).max()
                           / np.sqrt((Fd ** 2).sum(1).mean()))
         h2d = nstlist * box.n * 12
-        d2h = nstlist * box.n * 12 + 16
+        # forces of every frame; energies (and with nb_run_frames the virial) of the energy frames
+        d2h = nstlist * box.n * 12 + (sum(efr) * (16 + 72) if native_e2e else 16)
         ewald = elec == "ewald"
         cpu = cpu_baseline(box, p) if ws_n == 1 and extras else None
         surr = surrogate_ab(nb, ctx, box, p, xs, F, stream, dev) if ewald and args.surrogate and extras else None
@@ -903,7 +931,9 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "pipeline": "each frame's coordinates copied in and forces read back on a copy stream, "
+                    "pipeline": ("nb_run_frames, one call per list lifetime: " if native_e2e else
+                                 "per-frame calls from Python: ") +
+                                "each frame's coordinates copied in and forces read back on a copy stream, "
                                 "overlapped with the neighbouring frames' kernels (two buffers each)",
                     "max_dF_over_rms_vs_device_path": e2e_check},
             "surrogate": surr,

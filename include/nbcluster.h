@@ -358,6 +358,57 @@ nb_status nb_buffer_size(int nclass, const nb_particle_class* classes_host, int 
 nb_status nb_prune_compute(nb_ctx* ctx, const nb_params* p, const float* xyz_dev, float r_prune, float* f_dev,
                            double* e_dev, double* vir_dev, nb_stream stream);
 
+/* --- frames from host memory ---------------------------------------------------- */
+
+/* A run of frames whose coordinates are in host memory, for a caller that
+ * holds them there (a trajectory, or an integrator on the host).  The list
+ * is built on the first frame and reused, pruned every nstprune frames
+ * (Sec. 2.3: the Verlet buffer and pruning).  Frame f's coordinates are
+ * copied in on copy_stream while frame f - 1 computes on stream, and frame
+ * f's forces are copied out while frame f + 1 computes (two device buffers
+ * each, ordered by events the context owns), so with page-locked host
+ * memory the transfers overlap the kernels.  All host pointers must stay
+ * valid, and unmodified or unread, until the streams have finished. */
+typedef struct {
+    int n_frames;                 /* >= 1 */
+    int n_atoms, n_boxes;         /* the context's particle and box counts (the sizes below) */
+    const float* x_host;          /* float [n_frames][n][3], caller order (page-locked for overlap) */
+    float* f_host;                /* float [n_frames][n][3], overwritten */
+    const unsigned char* energy_frames_host; /* [n_frames]: nonzero = energies (and virial) on that
+                                     frame; NULL: forces only on every frame */
+    double* e_host;               /* double [n_frames][nbox][2], written on energy frames; may be NULL */
+    double* vir_host;             /* double [n_frames][nbox][9], written on energy frames; may be NULL */
+    float* x_dev[2];              /* device staging, float [n][3] each */
+    float* f_dev[2];              /* device staging, float [n][3] each */
+    double* e_dev[2];             /* device staging, double [nbox][2] each (when e_host) */
+    double* vir_dev[2];           /* device staging, double [nbox][9] each (when vir_host) */
+    int build;                    /* nonzero: grid and list on frame 0 (boxes_host, rlist, rbb,
+                                     exclusions as nb_grid_put and nb_pairlist_build); zero:
+                                     every frame updates the coordinates of the current list */
+    const double* boxes_host;     /* as nb_grid_put (build only) */
+    float rlist, rbb;             /* as nb_pairlist_build (build only) */
+    const int* excl_off_dev;      /* as nb_pairlist_build (build only) */
+    const int* excl_idx_dev;
+    int first_frame;              /* index of frame 0 within the list's lifetime (0 with build) */
+    int nstprune;                 /* frames f with first_frame + f > 0 and a multiple of nstprune
+                                     prune at r_prune in their force pass (nb_prune_compute);
+                                     0: no pruning */
+    float r_prune;
+} nb_frames;
+
+/* Forces (and, on the chosen frames, energies and virial) of every frame of
+ * fr with the interactions p (p->want_energy is ignored: energy_frames_host
+ * decides), as nb_compute and nb_prune_compute would give them frame by
+ * frame.  stream computes; copy_stream copies (must differ from stream; both
+ * on the context's device).  Returns after queuing the work: stream waits for
+ * copy_stream's last copy, so synchronising stream makes every output
+ * readable.  Errors: NB_ERR_ARG (null pointers, n_frames < 1, n_atoms or
+ * n_boxes not the context's, equal streams, nstprune < 0), and those of the calls it makes (nb_grid_put,
+ * nb_pairlist_build, nb_compute, nb_prune_compute), returned at the first
+ * failing frame with the frames before it queued. */
+nb_status nb_run_frames(nb_ctx* ctx, const nb_params* p, const nb_frames* fr, nb_stream stream,
+                        nb_stream copy_stream);
+
 /* --- the particle-pair (1 x 1) comparison path -------------------------------- */
 
 /* A full particle-pair Verlet list (every pair within rlist stored for both

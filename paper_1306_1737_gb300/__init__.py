@@ -68,6 +68,17 @@ class nb_info(C.Structure):
                 ("flags", C.c_uint32), ("n_boxes", C.c_int), ("atom_offset", C.c_int)]
 
 
+class nb_frames(C.Structure):
+    _fields_ = [("n_frames", C.c_int), ("n_atoms", C.c_int), ("n_boxes", C.c_int),
+                ("x_host", C.c_void_p), ("f_host", C.c_void_p), ("energy_frames_host", C.c_void_p),
+                ("e_host", C.c_void_p), ("vir_host", C.c_void_p),
+                ("x_dev", C.c_void_p * 2), ("f_dev", C.c_void_p * 2), ("e_dev", C.c_void_p * 2),
+                ("vir_dev", C.c_void_p * 2), ("build", C.c_int), ("boxes_host", C.c_void_p),
+                ("rlist", C.c_float), ("rbb", C.c_float), ("excl_off_dev", C.c_void_p),
+                ("excl_idx_dev", C.c_void_p), ("first_frame", C.c_int), ("nstprune", C.c_int),
+                ("r_prune", C.c_float)]
+
+
 class nb_particle_class(C.Structure):
     _fields_ = [("count", C.c_double), ("mass", C.c_double), ("charge", C.c_double), ("type", C.c_int)]
 
@@ -134,6 +145,7 @@ def load():
             "nb_compute_1x1": ([P, C.POINTER(nb_params), P, P, P, i, P, P], st),
             "nb_rdf": ([P, C.c_float, i, i, i, i, P, P], st),
             "nb_prune_compute": ([P, C.POINTER(nb_params), P, C.c_float, P, P, P, P], st),
+            "nb_run_frames": ([P, C.POINTER(nb_params), C.POINTER(nb_frames), P, P], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -480,6 +492,77 @@ def nb_compute_1x1(ctx, params, xyz, nbr, count, max_nbr, f, stream=None):
 def nb_prune_compute(ctx, params, xyz, r_prune, f, e=None, vir=None, stream=None):
     _check(ctx, load().nb_prune_compute(ctx, C.byref(params), _ptr(xyz, _F32), float(r_prune), _ptr(f, _F32),
                                         _ptr(e, _F64), _ptr(vir, _F64), _stream(stream)))
+
+
+def _host_ptr(x, dtype, name):
+    """Address of a contiguous host (CPU) tensor of the given torch dtype."""
+    if x is None:
+        return None
+    if x.is_cuda:
+        raise ValueError(f"{name} must be a host tensor (page-locked for overlapped copies)")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if str(x.dtype).replace("torch.", "") != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {x.dtype}")
+    return x.data_ptr()
+
+
+def nb_run_frames(ctx, params, x_host, f_host, x_dev, f_dev, nbox=1, energy_frames=None, e_host=None,
+                  vir_host=None, e_dev=None, vir_dev=None, build=False, boxes=None, rlist=0.0, rbb=0.0,
+                  excl_off=None, excl_idx=None, first_frame=0, nstprune=0, r_prune=0.0, stream=None,
+                  copy_stream=None):
+    """Frames from host memory through the calls of a list lifetime (see the
+    header).  x_host, f_host: host float32 [n_frames, n, 3] (page-locked for
+    overlap); x_dev, f_dev: two device float32 [n, 3] buffers each;
+    energy_frames: per-frame flags (or None); e_host [n_frames, nbox, 2] and
+    vir_host [n_frames, nbox, 9] host float64 with e_dev / vir_dev two device
+    float64 buffers of [nbox, 2] / [nbox, 9].  The host tensors must stay
+    alive until the streams finish."""
+    import numpy as np
+    import torch
+    if x_host.dim() != 3 or x_host.shape[2] != 3 or tuple(f_host.shape) != tuple(x_host.shape):
+        raise ValueError("x_host and f_host must both be [n_frames, n, 3]")
+    nf, n = int(x_host.shape[0]), int(x_host.shape[1])
+    fr = nb_frames()
+    fr.n_frames, fr.n_atoms, fr.n_boxes = nf, n, int(nbox)
+    fr.x_host = _host_ptr(x_host, "float32", "x_host")
+    fr.f_host = _host_ptr(f_host, "float32", "f_host")
+    ef = None
+    if energy_frames is not None:
+        ef = np.ascontiguousarray(np.asarray(energy_frames, dtype=bool).astype(np.uint8).reshape(-1))
+        if ef.shape[0] != nf:
+            raise ValueError("one energy flag per frame")
+        fr.energy_frames_host = ef.ctypes.data
+    for name, h, d, w in (("e", e_host, e_dev, 2), ("vir", vir_host, vir_dev, 9)):
+        if h is None:
+            continue
+        if h.numel() < nf * nbox * w:
+            raise ValueError(f"{name}_host holds {h.numel()} values, needs {nf * nbox * w}")
+        if d is None or len(d) != 2:
+            raise ValueError(f"{name}_host needs two device buffers {name}_dev")
+        setattr(fr, f"{name}_host", _host_ptr(h, "float64", f"{name}_host"))
+        arr = getattr(fr, f"{name}_dev")
+        for k in range(2):
+            _need(d[k], nbox * w, f"{name}_dev[{k}]")
+            arr[k] = _ptr(d[k], _F64)
+    if len(x_dev) != 2 or len(f_dev) != 2:
+        raise ValueError("two device buffers each for coordinates and forces")
+    for k in range(2):
+        _need(x_dev[k], 3 * n, f"x_dev[{k}]")
+        _need(f_dev[k], 3 * n, f"f_dev[{k}]")
+        fr.x_dev[k] = _ptr(x_dev[k], _F32)
+        fr.f_dev[k] = _ptr(f_dev[k], _F32)
+    b = None
+    if build:
+        b = _boxes(boxes)
+        fr.build, fr.boxes_host = 1, b.ctypes.data
+        fr.rlist, fr.rbb = float(rlist), float(rbb)
+        fr.excl_off_dev, fr.excl_idx_dev = _ptr(excl_off, _I32), _ptr(excl_idx, _I32)
+    fr.first_frame, fr.nstprune, fr.r_prune = int(first_frame), int(nstprune), float(r_prune)
+    if copy_stream is None:
+        raise ValueError("copy_stream: a second stream for the transfers")
+    _check(ctx, load().nb_run_frames(ctx, C.byref(params), C.byref(fr), _stream(stream), _stream(copy_stream)))
+    del ef, b   # read during the call
 
 
 def nb_rdf(ctx, r_max, nbins, type_a, type_b, accumulate, hist, stream=None):

@@ -67,6 +67,8 @@ struct nb_ctx {
     bool prof_keep = false;   // spans survive reads (graph replays re-record them)
     cudaEvent_t ev[2 * kMaxSpans] = {};
     int ev_kind[kMaxSpans] = {};
+    // nb_run_frames: x_ready[2], x_free[2], f_done[2], f_free[2]
+    cudaEvent_t run_ev[8] = {};
     int ev_n = 0;
     char err[512] = {0};
 };
@@ -409,6 +411,8 @@ nb_status nb_destroy(nb_ctx* c) {
     release_host(c);
     for (int k = 0; k < 2 * nb_ctx::kMaxSpans; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    for (int k = 0; k < 8; ++k)
+        if (c->run_ev[k]) cudaEventDestroy(c->run_ev[k]);
     delete c;
     return NB_OK;
 }
@@ -763,6 +767,96 @@ nb_status nb_prune_compute(nb_ctx* c, const nb_params* p, const float* xyz, floa
     span_end(c, sz, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernels");
     c->n_launches += 1 + (fp.want_energy ? 1 : 0);
+    return NB_OK;
+}
+
+// Frames from host memory: the per-frame calls of a list lifetime with the
+// transfers on a second stream.  Events (created on first use, owned by the
+// context): x_ready[k] (coordinates in buffer k), x_free[k] (buffer k read
+// by its frame's kernels), f_done[k] (forces of buffer k written), f_free[k]
+// (buffer k's outputs copied out).  A wait on an event that was never
+// recorded, or recorded by an earlier run and long complete, does not wait.
+nb_status nb_run_frames(nb_ctx* c, const nb_params* p, const nb_frames* fr, nb_stream stream,
+                        nb_stream copy_stream) {
+    if (!c) return NB_ERR_ARG;
+    if (!p || !fr) return fail(c, NB_ERR_ARG, "run_frames: null argument");
+    if (fr->n_frames < 1) return fail(c, NB_ERR_ARG, "run_frames: n_frames must be >= 1");
+    if (fr->n_atoms != c->n || fr->n_boxes != c->nbox)
+        return fail(c, NB_ERR_ARG, "run_frames: %d particles in %d boxes given, the context has %d in %d",
+                    fr->n_atoms, fr->n_boxes, c->n, c->nbox);
+    if (stream == copy_stream) return fail(c, NB_ERR_ARG, "run_frames: the copy stream must differ");
+    if (fr->nstprune < 0 || fr->first_frame < 0) return fail(c, NB_ERR_ARG, "run_frames: negative schedule");
+    if (c->n > 0 && (!fr->x_host || !fr->f_host)) return fail(c, NB_ERR_ARG, "run_frames: null host buffer");
+    for (int k = 0; k < 2; ++k) {
+        if (c->n > 0 && (!fr->x_dev[k] || !fr->f_dev[k]))
+            return fail(c, NB_ERR_ARG, "run_frames: null device buffer");
+        if ((fr->e_host && !fr->e_dev[k]) || (fr->vir_host && !fr->vir_dev[k]))
+            return fail(c, NB_ERR_ARG, "run_frames: null energy or virial staging");
+    }
+    if (fr->build && !fr->boxes_host) return fail(c, NB_ERR_ARG, "run_frames: build needs the boxes");
+    NB_CUDA(c, cudaSetDevice(c->device));
+    for (int k = 0; k < 8; ++k)
+        if (!c->run_ev[k]) NB_CUDA(c, cudaEventCreateWithFlags(&c->run_ev[k], cudaEventDisableTiming));
+    cudaEvent_t* x_ready = c->run_ev;
+    cudaEvent_t* x_free = c->run_ev + 2;
+    cudaEvent_t* f_done = c->run_ev + 4;
+    cudaEvent_t* f_free = c->run_ev + 6;
+    cudaStream_t s = (cudaStream_t)stream, cs = (cudaStream_t)copy_stream;
+    const size_t xb = (size_t)c->n * 3 * sizeof(float);
+    const size_t eb = (size_t)c->nbox * 2 * sizeof(double), vb = (size_t)c->nbox * 9 * sizeof(double);
+    // frame 0's coordinates; the copy stream first waits for any earlier
+    // use of buffer 0 on the compute stream
+    NB_CUDA(c, cudaStreamWaitEvent(cs, x_free[0], 0));
+    if (xb) NB_CUDA(c, cudaMemcpyAsync(fr->x_dev[0], fr->x_host, xb, cudaMemcpyHostToDevice, cs));
+    NB_CUDA(c, cudaEventRecord(x_ready[0], cs));
+    for (int f = 0; f < fr->n_frames; ++f) {
+        const int k = f & 1;
+        if (f + 1 < fr->n_frames) {
+            const int kn = k ^ 1;
+            NB_CUDA(c, cudaStreamWaitEvent(cs, x_free[kn], 0));   // frame f - 1 has read it
+            if (xb)
+                NB_CUDA(c, cudaMemcpyAsync(fr->x_dev[kn], fr->x_host + (size_t)(f + 1) * c->n * 3, xb,
+                                           cudaMemcpyHostToDevice, cs));
+            NB_CUDA(c, cudaEventRecord(x_ready[kn], cs));
+        }
+        NB_CUDA(c, cudaStreamWaitEvent(s, x_ready[k], 0));
+        NB_CUDA(c, cudaStreamWaitEvent(s, f_free[k], 0));   // frame f - 2's outputs are copied out
+        const bool energy = fr->energy_frames_host && fr->energy_frames_host[f];
+        nb_params q = *p;
+        q.want_energy = energy ? 1 : 0;
+        double* e_dev = energy && fr->e_host ? fr->e_dev[k] : nullptr;
+        double* v_dev = energy && fr->vir_host ? fr->vir_dev[k] : nullptr;
+        const float* x = fr->x_dev[k];
+        nb_status st;
+        if (f == 0 && fr->build) {
+            st = nb_grid_put(c, x, fr->boxes_host, stream);
+            if (st != NB_OK) return st;
+            st = nb_pairlist_build(c, fr->rlist, fr->rbb, fr->excl_off_dev, fr->excl_idx_dev, stream);
+            if (st != NB_OK) return st;
+            x = nullptr;   // the list's own coordinates
+        }
+        const int g = fr->first_frame + f;
+        if (fr->nstprune > 0 && g > 0 && g % fr->nstprune == 0)
+            st = nb_prune_compute(c, &q, x, fr->r_prune, fr->f_dev[k], e_dev, v_dev, stream);
+        else
+            st = nb_compute(c, &q, x, fr->f_dev[k], e_dev, v_dev, stream);
+        if (st != NB_OK) return st;
+        NB_CUDA(c, cudaEventRecord(x_free[k], s));
+        NB_CUDA(c, cudaEventRecord(f_done[k], s));
+        NB_CUDA(c, cudaStreamWaitEvent(cs, f_done[k], 0));
+        if (xb)
+            NB_CUDA(c, cudaMemcpyAsync(fr->f_host + (size_t)f * c->n * 3, fr->f_dev[k], xb,
+                                       cudaMemcpyDeviceToHost, cs));
+        if (e_dev)
+            NB_CUDA(c, cudaMemcpyAsync(fr->e_host + (size_t)f * c->nbox * 2, e_dev, eb, cudaMemcpyDeviceToHost,
+                                       cs));
+        if (v_dev)
+            NB_CUDA(c, cudaMemcpyAsync(fr->vir_host + (size_t)f * c->nbox * 9, v_dev, vb,
+                                       cudaMemcpyDeviceToHost, cs));
+        NB_CUDA(c, cudaEventRecord(f_free[k], cs));
+    }
+    // the compute stream waits for the last copy out
+    NB_CUDA(c, cudaStreamWaitEvent(s, f_free[(fr->n_frames - 1) & 1], 0));
     return NB_OK;
 }
 

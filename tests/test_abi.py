@@ -130,3 +130,27 @@ def test_noalloc_binding_checks_sizes_before_the_call():
             call(args(**{name: short}))
     with pytest.raises(ValueError, match="CUDA"):
         call(args())
+
+
+def test_run_frames_binding_checks_shapes_before_the_call():
+    """nb_run_frames' binding: host frames and forces of one shape [F, n, 3],
+    host tensors on the host, energy flags one per frame and two staging
+    buffers of sufficient size, all checked before the library is called
+    (which trusts the sizes against the context's particle count)."""
+    torch = pytest.importorskip("torch")
+    import paper_1306_1737_gb300 as nb
+    prm = nb.make_params("ewald", 1.0, beta=3.12, want_energy=False)
+    x = torch.zeros((4, 10, 3))
+    with pytest.raises(ValueError, match="n_frames, n, 3"):
+        nb.nb_run_frames(None, prm, x, torch.zeros((4, 11, 3)), [None, None], [None, None])
+    with pytest.raises(ValueError, match="n_frames, n, 3"):
+        nb.nb_run_frames(None, prm, torch.zeros((4, 10, 2)), torch.zeros((4, 10, 2)), [None, None],
+                         [None, None])
+    with pytest.raises(ValueError, match="one energy flag per frame"):
+        nb.nb_run_frames(None, prm, x, torch.zeros_like(x), [None, None], [None, None], energy_frames=[1, 0])
+    with pytest.raises(ValueError, match="two device buffers e_dev"):
+        nb.nb_run_frames(None, prm, x, torch.zeros_like(x), [None, None], [None, None],
+                         e_host=torch.zeros((4, 1, 2), dtype=torch.float64))
+    with pytest.raises(ValueError, match="x_dev"):
+        nb.nb_run_frames(None, prm, x, torch.zeros_like(x), [torch.zeros(29), torch.zeros(30)],
+                         [torch.zeros(30), torch.zeros(30)])
