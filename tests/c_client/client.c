@@ -29,5 +29,11 @@ int main(void) {
     printf("drift %d %.12e\n", s, drift);
     s = nb_buffer_size(2, cls, 2, c6c12, 6.21 * 6.21 * 6.21, &p, 0.038, 300.0, 0.00249, &rb);
     printf("size %d %.9f\n", s, rb);
+
+    /* the frame runner without a context: refused before any CUDA call */
+    nb_frames fr = {0};
+    fr.n_frames = 1;
+    s = nb_run_frames(NULL, &p, &fr, NULL, NULL);
+    printf("frames %d %s\n", s, nb_status_string(s));
     return 0;
 }

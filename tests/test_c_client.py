@@ -53,3 +53,4 @@ def test_c_client_matches_the_binding(client):
     rb = nb.nb_buffer_size(cls, t, vol, p, 0.038, 300.0, 0.00249)
     assert client["size"][0] == "0" and float(client["size"][1]) == pytest.approx(rb, abs=2e-9)
     assert np.isfinite(drift) and drift > 0 and 0 < rb < 1
+    assert client["frames"] == [str(nb.NB_ERR_ARG), "NB_ERR_ARG"]
