@@ -144,3 +144,70 @@ def test_run_frames_errors(env):
         torch.cuda.synchronize()
     finally:
         cx.close()
+
+
+@pytest.mark.parametrize("C", [8, 4])
+def test_run_frames_batch(env, C):
+    """Two boxes of uneven size in one context (C = 8: fused prune; C = 4:
+    prune kernel then force kernel), six frames, a prune every 3 frames,
+    energies and virial per box on frames 0 and 5: equal to the calls made
+    frame by frame."""
+    torch, dev, nb = env
+    B = w.concat([w.water_box(700, None, seed=7110), w.water_box(1300, None, seed=7111)])
+    rc, rl, beta, nstprune, nf = 1.0, 1.1, 3.12, 3, 6
+    rlf = float(np.float32(rl))
+    rp = float(np.float32(w.prune_radius(rc, rl, nstprune)))
+    disp = w.frame_displacements(B.mass, nf, seed=7112)
+    x = (B.xyz[None] + np.concatenate([np.zeros((1, B.n, 3), np.float32), np.cumsum(disp, 0)[:-1]]))
+    x = x.astype(np.float32)
+    c6c12 = nb.nb_lj_combine(B.sigma, B.eps)
+    prm = nb.make_params("ewald", rc, beta=beta, want_energy=False)
+    prm_e = nb.make_params("ewald", rc, beta=beta, want_energy=True)
+    eo = torch.as_tensor(B.excl_off, device=dev)
+    ei = torch.as_tensor(B.excl_idx, device=dev)
+    nbx = B.nbox
+    efr = np.array([1, 0, 0, 0, 0, 1], bool)
+    cx = nb.Context(B.counts, B.boxes, rl, B.q, B.types, c6c12, cluster_size=C)
+    ref = nb.Context(B.counts, B.boxes, rl, B.q, B.types, c6c12, cluster_size=C)
+    try:
+        xh = torch.as_tensor(x).pin_memory()
+        fh = torch.zeros((nf, B.n, 3), dtype=torch.float32).pin_memory()
+        eh = torch.zeros((nf, nbx, 2), dtype=torch.float64).pin_memory()
+        vh = torch.zeros((nf, nbx, 9), dtype=torch.float64).pin_memory()
+        xd = [torch.empty((B.n, 3), dtype=torch.float32, device=dev) for _ in range(2)]
+        fd = [torch.empty((B.n, 3), dtype=torch.float32, device=dev) for _ in range(2)]
+        ed = [torch.empty((nbx, 2), dtype=torch.float64, device=dev) for _ in range(2)]
+        vd = [torch.empty((nbx, 9), dtype=torch.float64, device=dev) for _ in range(2)]
+        main = torch.cuda.current_stream()
+        cs = torch.cuda.Stream(device=dev)
+        nb.nb_run_frames(cx.ctx, prm, xh, fh, xd, fd, nbox=nbx, energy_frames=efr, e_host=eh, vir_host=vh,
+                         e_dev=ed, vir_dev=vd, build=True, boxes=B.boxes, rlist=rlf, rbb=0.8, excl_off=eo,
+                         excl_idx=ei, nstprune=nstprune, r_prune=rp, stream=main, copy_stream=cs)
+        main.synchronize()
+        nb.nb_check(cx.ctx)
+        f = torch.zeros((B.n, 3), dtype=torch.float32, device=dev)
+        e = torch.zeros((nbx, 2), dtype=torch.float64, device=dev)
+        v = torch.zeros((nbx, 9), dtype=torch.float64, device=dev)
+        for k in range(nf):
+            xk = torch.as_tensor(x[k], device=dev)
+            q = prm_e if efr[k] else prm
+            if k == 0:
+                nb.nb_grid_put(ref.ctx, xk, B.boxes)
+                nb.nb_pairlist_build(ref.ctx, rlf, 0.8, eo, ei)
+                xk = None
+            ev = (e, v) if efr[k] else (None, None)
+            if k > 0 and k % nstprune == 0:
+                nb.nb_prune_compute(ref.ctx, q, xk, rp, f, *ev)
+            else:
+                nb.nb_compute(ref.ctx, q, xk, f, *ev)
+            fr = f.cpu().numpy().astype(np.float64)
+            rms = np.sqrt((fr ** 2).sum(1).mean())
+            assert np.abs(fh.numpy()[k] - fr).max() <= SAME_TOL * rms, k
+            if efr[k]:
+                er, vr = e.cpu().numpy(), v.cpu().numpy()
+                assert np.abs(eh.numpy()[k] - er).max() <= 1e-6 * np.abs(er).max(), k
+                assert np.abs(vh.numpy()[k] - vr).max() <= 1e-6 * np.abs(vr).max(), k
+        nb.nb_check(ref.ctx)
+    finally:
+        cx.close()
+        ref.close()

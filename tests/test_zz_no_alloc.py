@@ -23,9 +23,10 @@ def env():
     return torch, nb
 
 
-def reference_grid(torch, nb, b, C, rlist=1.0):
-    dev = torch.device("cuda", 0)
-    cx = nb.Context(b.n, b.box, rlist, b.q, b.types, nb.nb_lj_combine(b.sigma, b.eps), cluster_size=C)
+def reference_grid(torch, nb, b, C, rlist=1.0, device=0):
+    dev = torch.device("cuda", device)
+    cx = nb.Context(b.n, b.box, rlist, b.q, b.types, nb.nb_lj_combine(b.sigma, b.eps), cluster_size=C,
+                    device=device)
     try:
         nb.nb_grid_put(cx.ctx, torch.as_tensor(b.xyz, device=dev), b.box)
         info = nb.nb_check(cx.ctx)
@@ -44,8 +45,8 @@ def reference_grid(torch, nb, b, C, rlist=1.0):
         cx.close()
 
 
-def noalloc_grid(torch, nb, b, C, max_slots=40000, max_columns=2048):
-    dev = torch.device("cuda", 0)
+def noalloc_grid(torch, nb, b, C, max_slots=40000, max_columns=2048, device=0):
+    dev = torch.device("cuda", device)
     aos = torch.full((max_slots,), -7, dtype=torch.int32, device=dev)
     xyzq = torch.zeros((max_slots, 4), dtype=torch.float32, device=dev)
     ts = torch.zeros(max_slots, dtype=torch.int32, device=dev)
@@ -148,3 +149,20 @@ def test_noalloc_flags_an_overlong_column(env):
     in_crowd_column = (np.floor(b.xyz[others, 0] * np.float32(12 / 8.0)) == 0) & \
                       (np.floor(b.xyz[others, 1] * np.float32(12 / 8.0)) == 0)
     assert np.isin(others[~in_crowd_column], placed).all()
+
+
+def test_second_device_after_the_first(env):
+    """The large shared-memory opt-ins of the gridding kernels are made per
+    device: gridding through a context and without one on device 1, after
+    device 0 has been used in the same process, gives device 0's grid bit
+    for bit (skipped with one visible device)."""
+    torch, nb = env
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one CUDA device visible")
+    b = w.water_box(512, 2.48, seed=1001)
+    ref0 = reference_grid(torch, nb, b, 8)
+    with torch.cuda.device(1):
+        ref1 = reference_grid(torch, nb, b, 8, device=1)
+        got1 = noalloc_grid(torch, nb, b, 8, device=1)
+    same(ref0, dict(ref1, flags=0))
+    same(ref0, got1)
