@@ -25,6 +25,11 @@
  *    or exclusion index out of range) raise a device flag that nb_check()
  *    reads.
  *  - Return value: NB_OK or an nb_status_code; nb_last_error() gives text.
+ *  - A context keeps host-side state (plan, list state, events, the last
+ *    error): one host thread at a time may call with it.  Calls on different
+ *    contexts may run concurrently, as may the context-free entry points
+ *    except nb_grid_put_noalloc (one fixed scratch array per device: see its
+ *    own rule below).
  */
 #ifndef NBCLUSTER_H
 #define NBCLUSTER_H
