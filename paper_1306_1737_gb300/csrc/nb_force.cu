@@ -299,6 +299,51 @@ __device__ __forceinline__ bool icluster8(const ForceParams& P, const float2* s_
     return true;
 }
 
+// The common case of a j-entry, both i-clusters of the super-cluster with
+// all-ones masks off the diagonal: one warp vote for the entry (does any of
+// its 128 pairs lie inside rc?), then both 8 x 8 tiles as straight-line
+// code.  Without a branch between them the two tiles' chains of dependent
+// operations interleave, which hides their latencies (3M box: 2.6% less
+// time per force launch than a vote and a branch per tile); a tile with no
+// pair inside rc is computed as well and contributes zeros.
+// PRUNE: as icluster8, per tile.
+template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, bool PRUNE>
+__device__ __forceinline__ bool icluster8_both(const ForceParams& P, const float2* s_lj, const WarpSmem& W,
+                                               const Lane8& L, const int2 (&row)[kSuper8], const JPart& J,
+                                               float2 (&fx)[kSuper8], float2 (&fy)[kSuper8],
+                                               float2 (&fz)[kSuper8], JSum& G, float& e_lj, float& e_c,
+                                               unsigned& n_inc, unsigned& keep) {
+    static_assert(kSuper8 == 2, "a super-cluster of two 8-particle i-clusters");
+    float2 dx[2], dy[2], dz[2], fq[2], r2[2];
+    bool inc0[2], inc1[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        pair_deltas<SHIFTED>(W, k, L.ih, J.nx, J.ny, J.nz, dx[k], dy[k], dz[k], fq[k]);
+        r2[k] = fma2(dx[k], dx[k], fma2(dy[k], dy[k], mul2(dz[k], dz[k])));
+        if constexpr (PRUNE) {
+            if (__any_sync(0xffffffffu, r2[k].x < P.rp2 || r2[k].y < P.rp2)) keep |= 1u << k;
+        }
+        inc0[k] = r2[k].x < P.rc2;
+        inc1[k] = r2[k].y < P.rc2;
+    }
+    if (!__any_sync(0xffffffffu, inc0[0] || inc1[0] || inc0[1] || inc1[1])) return false;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float2 lj0 = lj_entry(s_lj, row[k].x + J.t), lj1 = lj_entry(s_lj, row[k].y + J.t);
+        const float2 fs = pair_force2<ELEC, ENERGY, FIT, true>(P, r2[k], inc0[k], inc1[k], true, true,
+                                                               mul2(fq[k], J.q), lj0, lj1, e_lj, e_c,
+                                                               s_lj + P.ntypes * P.ntypes);
+        if (ENERGY) n_inc += (unsigned)inc0[k] + (unsigned)inc1[k];
+        fx[k] = fma2(fs, dx[k], fx[k]);
+        fy[k] = fma2(fs, dy[k], fy[k]);
+        fz[k] = fma2(fs, dz[k], fz[k]);
+        G.x = fma2(fs, dx[k], G.x);
+        G.y = fma2(fs, dy[k], G.y);
+        G.z = fma2(fs, dz[k], G.z);
+    }
+    return true;
+}
+
 // The surrogate form of icluster8 (forces only): unmasked pairs inside rc
 // with r >= r_min take the Coulomb factor c(r) from the network, evaluated
 // for the whole 8 x 8 tile at once on the tensor cores; force-field-excluded
@@ -426,11 +471,8 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
         // is large, and a third copy for the fast path costs more in
         // instruction fetch than the path saves)
         if (!MLP && w < 0) {
-#pragma unroll
-            for (int k = 0; k < kSuper8; ++k)
-                any |= icluster8<ELEC, ENERGY, FIT, SHIFTED, true, PRUNE>(A.p, s_lj, W, L, row[k], k, false, ~0ull,
-                                                                          J, fx[k], fy[k], fz[k], G, e_lj, e_c,
-                                                                          n_inc, keep);
+            any = icluster8_both<ELEC, ENERGY, FIT, SHIFTED, PRUNE>(A.p, s_lj, W, L, row, J, fx, fy, fz, G, e_lj,
+                                                                    e_c, n_inc, keep);
         } else {
             const unsigned bits = ((unsigned)w >> kSuperShift) & ((1u << kSuper8) - 1u);
 #pragma unroll
