@@ -881,6 +881,8 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
             host_step()
         torch.cuda.synchronize()
         e2e_ms = []
+        e2e_sampler = ClockSampler(dev)
+        e2e_sampler.start()
         for k in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
@@ -888,6 +890,7 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
             host_step()
             torch.cuda.synchronize()
             e2e_ms.append(1000 * (time.perf_counter() - t0))
+        e2e_clocks = e2e_sampler.stop()
         e2e_value = args.steps * nstlist / (sum(e2e_ms) / 1000.0)
         # forces read back by the last step against the device path's (same frames)
         Fd = F.double().cpu().numpy()
@@ -935,7 +938,9 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
                                  "per-frame calls from Python: ") +
                                 "each frame's coordinates copied in and forces read back on a copy stream, "
                                 "overlapped with the neighbouring frames' kernels (two buffers each)",
-                    "max_dF_over_rms_vs_device_path": e2e_check},
+                    "max_dF_over_rms_vs_device_path": e2e_check,
+                    "step_ms_min_median_max": [min(e2e_ms), statistics.median(e2e_ms), max(e2e_ms)],
+                    "clocks": e2e_clocks},
             "surrogate": surr,
             "particle_pair_1x1": cmp11,
             "buffer_estimate": buf,
