@@ -1102,6 +1102,8 @@ def measure_batch(args, dist, ws_n, rank, dev, sub=False):
         tuned.step(host=host)
         torch.cuda.synchronize()
         e2e_ms = []
+        e2e_sampler = ClockSampler(dev)
+        e2e_sampler.start()
         for _ in range(max(1, min(args.steps, 5))):
             flush.zero_()
             torch.cuda.synchronize()
@@ -1109,6 +1111,7 @@ def measure_batch(args, dist, ws_n, rank, dev, sub=False):
             tuned.step(host=host)
             torch.cuda.synchronize()
             e2e_ms.append(1000 * (time.perf_counter() - t1))
+        e2e_clocks = e2e_sampler.stop()
         e2e_value = len(e2e_ms) * BATCH_H / (sum(e2e_ms) / 1000.0)
         del host
     groups_info = [{"C": g.spec.C, "nstlist": g.spec.nstlist, "rlist_nm": round(g.spec.rlist, 4),
@@ -1191,7 +1194,8 @@ def measure_batch(args, dist, ws_n, rank, dev, sub=False):
                                         f"(max SM clock, {pk['source']})",
                          "algorithmic_flops_per_launch": flops, "launch_ms": t_force * 1e3},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": BATCH_UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
+            "e2e": {"value": e2e_value, "unit": BATCH_UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+                    "clocks": e2e_clocks},
             "gpu_launches": int(launches_per_step * args.steps),
             "clocks": clocks,
             "status": st_tuned[0] if len(set(st_tuned)) == 1 else st_tuned,
