@@ -170,41 +170,31 @@ class BatchRunner:
 
     def _host_frames(self, g, host, st):
         """The H frames of group g from pinned host frames to pinned host
-        forces: frame f + 1's coordinates are copied in while frame f
-        computes and frame f's forces are read back while frame f + 1
-        computes (copy stream, two buffers each, ordered by events)."""
+        forces, one nb_run_frames call per list lifetime: frame f + 1's
+        coordinates are copied in while frame f computes and frame f's forces
+        are read back while frame f + 1 computes (copy stream, two buffers
+        each, ordered by events the context owns)."""
         torch = self.torch
         hx, hf = host
         if not hasattr(g, "pipe"):
             dev = g.F.device
             g.pipe = {"cs": torch.cuda.Stream(device=dev),
                       "x": [torch.empty_like(g.F) for _ in range(2)],
-                      "F": [torch.empty_like(g.F) for _ in range(2)],
-                      "ev": [[torch.cuda.Event() for _ in range(2)] for _ in range(4)]}
+                      "F": [torch.empty_like(g.F) for _ in range(2)]}
         cs, xb, Fb = g.pipe["cs"], g.pipe["x"], g.pipe["F"]
-        x_ready, x_free, f_done, f_free = g.pipe["ev"]
-        cs.wait_stream(st)
-        with torch.cuda.stream(cs):
-            xb[0].copy_(hx[0], non_blocking=True)
-            x_ready[0].record(cs)
-        for f in range(self.H):
-            k = f % 2
-            if f + 1 < self.H:
-                kn = (f + 1) % 2
-                cs.wait_event(x_free[kn])
-                with torch.cuda.stream(cs):
-                    xb[kn].copy_(hx[f + 1], non_blocking=True)
-                    x_ready[kn].record(cs)
-            st.wait_event(x_ready[k])
-            st.wait_event(f_free[k])
-            self._frame_ops(g, f, xb[k], st, Fb[k])
-            x_free[k].record(st)
-            f_done[k].record(st)
-            cs.wait_event(f_done[k])
-            with torch.cuda.stream(cs):
-                hf[f].copy_(Fb[k], non_blocking=True)
-                f_free[k].record(cs)
-        st.wait_stream(cs)
+        p = self.params
+        prm = nb.make_params(p["elec"], p["rc"], eps_rf=p.get("eps_rf", math.inf), beta=p.get("beta", 0.0),
+                             want_energy=False)
+        rl = float(np.float32(g.spec.rlist))
+        n_life = g.spec.nstlist
+        nsp = self.nstprune_of(g)
+        for f0 in range(0, self.H, n_life):
+            frames = range(f0, f0 + n_life)
+            nb.nb_run_frames(g.cx.ctx, prm, hx[f0:f0 + n_life], hf[f0:f0 + n_life], xb, Fb, nbox=len(g.boxes),
+                             energy_frames=[f == 0 or f == self.H - 1 for f in frames], build=True,
+                             boxes=g.boxes, rlist=rl, rbb=rl if self.rbb < 0 else min(self.rbb, rl),
+                             excl_off=g.excl_off, excl_idx=g.excl_idx, nstprune=nsp,
+                             r_prune=float(np.float32(self.r_prune(g))), stream=st, copy_stream=cs)
 
     def capture(self, concurrent=True):
         """Capture one step in a CUDA graph (after an eager step has set up
