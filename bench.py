@@ -23,6 +23,7 @@ slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -883,6 +884,8 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
         e2e_ms = []
         e2e_sampler = ClockSampler(dev)
         e2e_sampler.start()
+        gc_was = gc.isenabled()
+        gc.disable()   # a collection pause of this process's heap would leave the GPU idle mid-step
         for k in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
@@ -890,6 +893,8 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
             host_step()
             torch.cuda.synchronize()
             e2e_ms.append(1000 * (time.perf_counter() - t0))
+        if gc_was:
+            gc.enable()
         e2e_clocks = e2e_sampler.stop()
         e2e_value = args.steps * nstlist / (sum(e2e_ms) / 1000.0)
         # forces read back by the last step against the device path's (same frames)
@@ -1104,6 +1109,8 @@ def measure_batch(args, dist, ws_n, rank, dev, sub=False):
         e2e_ms = []
         e2e_sampler = ClockSampler(dev)
         e2e_sampler.start()
+        gc_was = gc.isenabled()
+        gc.disable()   # as for the single boxes
         for _ in range(max(1, min(args.steps, 5))):
             flush.zero_()
             torch.cuda.synchronize()
@@ -1111,6 +1118,8 @@ def measure_batch(args, dist, ws_n, rank, dev, sub=False):
             tuned.step(host=host)
             torch.cuda.synchronize()
             e2e_ms.append(1000 * (time.perf_counter() - t1))
+        if gc_was:
+            gc.enable()
         e2e_clocks = e2e_sampler.stop()
         e2e_value = len(e2e_ms) * BATCH_H / (sum(e2e_ms) / 1000.0)
         del host
