@@ -785,6 +785,8 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
     barrier()
     if sampler:
         sampler.start()
+    gc_was = gc.isenabled()
+    gc.disable()   # no collection pause between the start event and the replay
     for k in range(args.steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
@@ -794,6 +796,8 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
         b.record(stream)
         b.synchronize()
         step_ms.append(a.elapsed_time(b))
+    if gc_was:
+        gc.enable()
     barrier()
     clocks = sampler.stop() if sampler else None
     info = nb.nb_check(ctx, stream)
@@ -1048,6 +1052,8 @@ def measure_batch(args, dist, ws_n, rank, dev, sub=False):
 
     def timed(fn, steps):
         ms = []
+        gc_was = gc.isenabled()
+        gc.disable()   # no collection pause between the start event and the launches
         for _ in range(steps):
             flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
@@ -1057,6 +1063,8 @@ def measure_batch(args, dist, ws_n, rank, dev, sub=False):
             b.record()
             b.synchronize()
             ms.append(a.elapsed_time(b))
+        if gc_was:
+            gc.enable()
         return ms
 
     def statuses(r):
