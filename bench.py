@@ -164,8 +164,9 @@ def device_uuid(dev):
 
 class ClockSampler:
     """SM clock and clock-event-reason samples of this GPU while the timed
-    region runs: NVML (read-only queries through libnvidia-ml) every 2 ms in
-    a thread, else nvidia-smi every 200 ms."""
+    region runs: NVML (read-only queries through libnvidia-ml) every 50 ms in
+    a thread (at 500 queries per second the driver calls delayed some of the
+    host's own submissions), else nvidia-smi every 200 ms."""
 
     REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
                0x4: "sw_power_cap"}
@@ -202,7 +203,7 @@ class ClockSampler:
             if self.nvml.nvmlDeviceGetClockInfo(self.handle, 1, ctypes.byref(mhz)) == 0 and \
                     getr(self.handle, ctypes.byref(reasons)) == 0:
                 self.samples.append((mhz.value, reasons.value))
-            time.sleep(0.002)
+            time.sleep(0.05)
 
     def start(self):
         if self.nvml is not None:
@@ -685,15 +686,15 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
     efr = [energy_frame(f) for f in range(nstlist)]
     native_e2e = args.fused_prune and not args.prune0   # the schedule nb_run_frames runs
 
-    def run_host(hx, hF, hE, hV, xbufs, Fbufs, Ebufs, Vbufs, cs):
+    def run_host(hx, hF, hE, hV, xbufs, Fbufs, Ebufs, Vbufs):
         """One list lifetime from pinned host frames to pinned host forces,
         energies and virial in one call (nb_run_frames: the same calls as
         step(), made by the library, with the transfers on a copy stream
-        overlapping the neighbouring frames' kernels)."""
-        nb.nb_run_frames(ctx, prm_f, hx, hF, xbufs, Fbufs, nbox=1, energy_frames=efr, e_host=hE, vir_host=hV,
-                         e_dev=Ebufs, vir_dev=Vbufs, build=True, boxes=box.box, rlist=rlist, rbb=rbb,
-                         excl_off=eo, excl_idx=ei, nstprune=nstprune, r_prune=rprune,
-                         stream=torch.cuda.current_stream(), copy_stream=cs)
+        overlapping the neighbouring frames' kernels), its arguments
+        marshalled once."""
+        return nb.RunFrames(ctx, prm_f, hx, hF, xbufs, Fbufs, nbox=1, energy_frames=efr, e_host=hE, vir_host=hV,
+                            e_dev=Ebufs, vir_dev=Vbufs, build=True, boxes=box.box, rlist=rlist, rbb=rbb,
+                            excl_off=eo, excl_idx=ei, nstprune=nstprune, r_prune=rprune)
 
     def step_host(hx, hF, hE, xbufs, Fbufs, cs, ev):
         """One list lifetime from pinned host frames to pinned host forces
@@ -873,9 +874,10 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
             hV = torch.zeros((nstlist, 1, 9), dtype=torch.float64).pin_memory()
             Ebufs = [torch.empty((1, 2), dtype=torch.float64, device=dev) for _ in range(2)]
             Vbufs = [torch.empty((1, 9), dtype=torch.float64, device=dev) for _ in range(2)]
+            run = run_host(hx, hF, hE, hV, xbufs, Fbufs, Ebufs, Vbufs)
 
             def host_step():
-                run_host(hx, hF, hE, hV, xbufs, Fbufs, Ebufs, Vbufs, cs)
+                run(torch.cuda.current_stream(), cs)
         else:
             hE = torch.empty(2, dtype=torch.float64).pin_memory()
             ev = tuple([torch.cuda.Event() for _ in range(2)] for _ in range(4))
@@ -949,6 +951,7 @@ def measure_box(args, workload, dist, ws_n, rank, dev, extras=True):
                                 "overlapped with the neighbouring frames' kernels (two buffers each)",
                     "max_dF_over_rms_vs_device_path": e2e_check,
                     "step_ms_min_median_max": [min(e2e_ms), statistics.median(e2e_ms), max(e2e_ms)],
+                    "step_ms": [round(t, 3) for t in e2e_ms],
                     "clocks": e2e_clocks},
             "surrogate": surr,
             "particle_pair_1x1": cmp11,

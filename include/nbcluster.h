@@ -410,7 +410,16 @@ typedef struct {
  * readable.  Errors: NB_ERR_ARG (null pointers, n_frames < 1, n_atoms or
  * n_boxes not the context's, equal streams, nstprune < 0), and those of the calls it makes (nb_grid_put,
  * nb_pairlist_build, nb_compute, nb_prune_compute), returned at the first
- * failing frame with the frames before it queued. */
+ * failing frame with the frames before it queued.
+ * Runs with build set are the same work whenever their arguments are the
+ * same: every field of fr and *p, the box edges and energy flags (by value)
+ * and the context's state (workspace, atoms, network, geometry, profiling).
+ * The first such run is made call by call, the second is captured in a CUDA
+ * graph and later ones replay it on stream (its copies are graph nodes,
+ * copy_stream is not used); a replay reads the host frames anew, so new
+ * coordinates in the same buffers give their own forces.  Not while stream
+ * is being captured by the caller, nor with nb_profile on (those runs are
+ * made call by call). */
 nb_status nb_run_frames(nb_ctx* ctx, const nb_params* p, const nb_frames* fr, nb_stream stream,
                         nb_stream copy_stream);
 

@@ -507,6 +507,67 @@ def _host_ptr(x, dtype, name):
     return x.data_ptr()
 
 
+class RunFrames:
+    """The marshalled arguments of nb_run_frames, for repeated runs over the
+    same buffers: built (and checked) once, each call is then the C call
+    alone.  Arguments as nb_run_frames; the host and device tensors, the
+    energy flags and the boxes are kept referenced for the object's life."""
+
+    def __init__(self, ctx, params, x_host, f_host, x_dev, f_dev, nbox=1, energy_frames=None, e_host=None,
+                 vir_host=None, e_dev=None, vir_dev=None, build=False, boxes=None, rlist=0.0, rbb=0.0,
+                 excl_off=None, excl_idx=None, first_frame=0, nstprune=0, r_prune=0.0):
+        import numpy as np
+        if x_host.dim() != 3 or x_host.shape[2] != 3 or tuple(f_host.shape) != tuple(x_host.shape):
+            raise ValueError("x_host and f_host must both be [n_frames, n, 3]")
+        nf, n = int(x_host.shape[0]), int(x_host.shape[1])
+        fr = nb_frames()
+        fr.n_frames, fr.n_atoms, fr.n_boxes = nf, n, int(nbox)
+        fr.x_host = _host_ptr(x_host, "float32", "x_host")
+        fr.f_host = _host_ptr(f_host, "float32", "f_host")
+        self._ef = None
+        if energy_frames is not None:
+            ef = np.ascontiguousarray(np.asarray(energy_frames, dtype=bool).astype(np.uint8).reshape(-1))
+            if ef.shape[0] != nf:
+                raise ValueError("one energy flag per frame")
+            fr.energy_frames_host = ef.ctypes.data
+            self._ef = ef
+        for name, h, d, w in (("e", e_host, e_dev, 2), ("vir", vir_host, vir_dev, 9)):
+            if h is None:
+                continue
+            if h.numel() < nf * nbox * w:
+                raise ValueError(f"{name}_host holds {h.numel()} values, needs {nf * nbox * w}")
+            if d is None or len(d) != 2:
+                raise ValueError(f"{name}_host needs two device buffers {name}_dev")
+            setattr(fr, f"{name}_host", _host_ptr(h, "float64", f"{name}_host"))
+            arr = getattr(fr, f"{name}_dev")
+            for k in range(2):
+                _need(d[k], nbox * w, f"{name}_dev[{k}]")
+                arr[k] = _ptr(d[k], _F64)
+        if len(x_dev) != 2 or len(f_dev) != 2:
+            raise ValueError("two device buffers each for coordinates and forces")
+        for k in range(2):
+            _need(x_dev[k], 3 * n, f"x_dev[{k}]")
+            _need(f_dev[k], 3 * n, f"f_dev[{k}]")
+            fr.x_dev[k] = _ptr(x_dev[k], _F32)
+            fr.f_dev[k] = _ptr(f_dev[k], _F32)
+        self._boxes = None
+        if build:
+            self._boxes = _boxes(boxes)
+            fr.build, fr.boxes_host = 1, self._boxes.ctypes.data
+            fr.rlist, fr.rbb = float(rlist), float(rbb)
+            fr.excl_off_dev, fr.excl_idx_dev = _ptr(excl_off, _I32), _ptr(excl_idx, _I32)
+        fr.first_frame, fr.nstprune, fr.r_prune = int(first_frame), int(nstprune), float(r_prune)
+        self.ctx, self.params, self.fr = ctx, params, fr
+        self._keep = (x_host, f_host, x_dev, f_dev, e_host, vir_host, e_dev, vir_dev, excl_off, excl_idx)
+        self._fn = load().nb_run_frames
+
+    def __call__(self, stream=None, copy_stream=None):
+        if copy_stream is None:
+            raise ValueError("copy_stream: a second stream for the transfers")
+        _check(self.ctx, self._fn(self.ctx, C.byref(self.params), C.byref(self.fr), _stream(stream),
+                                  _stream(copy_stream)))
+
+
 def nb_run_frames(ctx, params, x_host, f_host, x_dev, f_dev, nbox=1, energy_frames=None, e_host=None,
                   vir_host=None, e_dev=None, vir_dev=None, build=False, boxes=None, rlist=0.0, rbb=0.0,
                   excl_off=None, excl_idx=None, first_frame=0, nstprune=0, r_prune=0.0, stream=None,
@@ -517,52 +578,10 @@ def nb_run_frames(ctx, params, x_host, f_host, x_dev, f_dev, nbox=1, energy_fram
     energy_frames: per-frame flags (or None); e_host [n_frames, nbox, 2] and
     vir_host [n_frames, nbox, 9] host float64 with e_dev / vir_dev two device
     float64 buffers of [nbox, 2] / [nbox, 9].  The host tensors must stay
-    alive until the streams finish."""
-    import numpy as np
-    import torch
-    if x_host.dim() != 3 or x_host.shape[2] != 3 or tuple(f_host.shape) != tuple(x_host.shape):
-        raise ValueError("x_host and f_host must both be [n_frames, n, 3]")
-    nf, n = int(x_host.shape[0]), int(x_host.shape[1])
-    fr = nb_frames()
-    fr.n_frames, fr.n_atoms, fr.n_boxes = nf, n, int(nbox)
-    fr.x_host = _host_ptr(x_host, "float32", "x_host")
-    fr.f_host = _host_ptr(f_host, "float32", "f_host")
-    ef = None
-    if energy_frames is not None:
-        ef = np.ascontiguousarray(np.asarray(energy_frames, dtype=bool).astype(np.uint8).reshape(-1))
-        if ef.shape[0] != nf:
-            raise ValueError("one energy flag per frame")
-        fr.energy_frames_host = ef.ctypes.data
-    for name, h, d, w in (("e", e_host, e_dev, 2), ("vir", vir_host, vir_dev, 9)):
-        if h is None:
-            continue
-        if h.numel() < nf * nbox * w:
-            raise ValueError(f"{name}_host holds {h.numel()} values, needs {nf * nbox * w}")
-        if d is None or len(d) != 2:
-            raise ValueError(f"{name}_host needs two device buffers {name}_dev")
-        setattr(fr, f"{name}_host", _host_ptr(h, "float64", f"{name}_host"))
-        arr = getattr(fr, f"{name}_dev")
-        for k in range(2):
-            _need(d[k], nbox * w, f"{name}_dev[{k}]")
-            arr[k] = _ptr(d[k], _F64)
-    if len(x_dev) != 2 or len(f_dev) != 2:
-        raise ValueError("two device buffers each for coordinates and forces")
-    for k in range(2):
-        _need(x_dev[k], 3 * n, f"x_dev[{k}]")
-        _need(f_dev[k], 3 * n, f"f_dev[{k}]")
-        fr.x_dev[k] = _ptr(x_dev[k], _F32)
-        fr.f_dev[k] = _ptr(f_dev[k], _F32)
-    b = None
-    if build:
-        b = _boxes(boxes)
-        fr.build, fr.boxes_host = 1, b.ctypes.data
-        fr.rlist, fr.rbb = float(rlist), float(rbb)
-        fr.excl_off_dev, fr.excl_idx_dev = _ptr(excl_off, _I32), _ptr(excl_idx, _I32)
-    fr.first_frame, fr.nstprune, fr.r_prune = int(first_frame), int(nstprune), float(r_prune)
-    if copy_stream is None:
-        raise ValueError("copy_stream: a second stream for the transfers")
-    _check(ctx, load().nb_run_frames(ctx, C.byref(params), C.byref(fr), _stream(stream), _stream(copy_stream)))
-    del ef, b   # read during the call
+    alive until the streams finish.  (RunFrames marshals these once for
+    repeated runs.)"""
+    RunFrames(ctx, params, x_host, f_host, x_dev, f_dev, nbox, energy_frames, e_host, vir_host, e_dev, vir_dev,
+              build, boxes, rlist, rbb, excl_off, excl_idx, first_frame, nstprune, r_prune)(stream, copy_stream)
 
 
 def nb_rdf(ctx, r_max, nbins, type_a, type_b, accumulate, hist, stream=None):

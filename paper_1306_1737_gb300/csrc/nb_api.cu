@@ -67,8 +67,17 @@ struct nb_ctx {
     bool prof_keep = false;   // spans survive reads (graph replays re-record them)
     cudaEvent_t ev[2 * kMaxSpans] = {};
     int ev_kind[kMaxSpans] = {};
-    // nb_run_frames: x_ready[2], x_free[2], f_done[2], f_free[2]
-    cudaEvent_t run_ev[8] = {};
+    // nb_run_frames: x_ready[2], x_free[2], f_done[2], f_free[2], fork
+    cudaEvent_t run_ev[9] = {};
+    // nb_run_frames: the graph of the last run's work, replayed when the
+    // next run has the same arguments; gen counts the changes (workspace,
+    // atoms, network, geometry, profiling) a captured run depends on
+    unsigned long long gen = 0;
+    std::vector<unsigned char> run_key;
+    int run_seen = 0;
+    cudaGraphExec_t run_exec = nullptr;
+    long long run_launches = 0;
+    cudaStream_t run_cap = nullptr;   // captures are made on this stream (the caller's may be the legacy one)
     int ev_n = 0;
     char err[512] = {0};
 };
@@ -268,6 +277,7 @@ static nb_status upload_geometry(nb_ctx* c, const std::vector<BoxGeom>& geo, cud
     c->geo_ev_used[k] = true;
     c->geo_host = geo;
     c->geo_uploaded = true;
+    ++c->gen;
     return NB_OK;
 }
 
@@ -411,8 +421,10 @@ nb_status nb_destroy(nb_ctx* c) {
     release_host(c);
     for (int k = 0; k < 2 * nb_ctx::kMaxSpans; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 9; ++k)
         if (c->run_ev[k]) cudaEventDestroy(c->run_ev[k]);
+    if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
+    if (c->run_cap) cudaStreamDestroy(c->run_cap);
     delete c;
     return NB_OK;
 }
@@ -501,6 +513,7 @@ nb_status nb_set_workspace(nb_ctx* c, void* ws, size_t bytes) {
     const size_t need = carve(c, nullptr, nullptr);
     if (bytes < need) return fail(c, NB_ERR_CAPACITY, "workspace has %zu bytes, needs %zu", bytes, need);
     NB_CUDA(c, cudaSetDevice(c->device));
+    ++c->gen;
     carve(c, (char*)ws, &c->ws);
     c->ws_base = (char*)ws;
     c->ws_bytes = bytes;
@@ -542,6 +555,7 @@ nb_status nb_set_atoms(nb_ctx* c, int n, const float* q, const int* type, int nt
     if (!c->ws_base) return fail(c, NB_ERR_STATE, "no workspace");
     if (n < 0 || (n > 0 && (!q || !type)) || ntypes <= 0 || !c6c12)
         return fail(c, NB_ERR_ARG, "set_atoms: bad argument");
+    ++c->gen;
     if (n != c->atom_off[c->nbox])
         return fail(c, NB_ERR_CAPACITY, "%d particles, the workspace is planned for %d", n, c->atom_off[c->nbox]);
     if (ntypes > c->ntypes_cap) return fail(c, NB_ERR_CAPACITY, "too many LJ types");
@@ -774,8 +788,119 @@ nb_status nb_prune_compute(nb_ctx* c, const nb_params* p, const float* xyz, floa
 // transfers on a second stream.  Events (created on first use, owned by the
 // context): x_ready[k] (coordinates in buffer k), x_free[k] (buffer k read
 // by its frame's kernels), f_done[k] (forces of buffer k written), f_free[k]
-// (buffer k's outputs copied out).  A wait on an event that was never
-// recorded, or recorded by an earlier run and long complete, does not wait.
+// (buffer k's outputs copied out), and a fork event that orders the copy
+// stream after all work queued on the compute stream before the run
+// (earlier runs, replayed graphs included).  Only the events recorded in
+// this run are waited on.
+static nb_status run_frames_enqueue(nb_ctx* c, const nb_params* p, const nb_frames* fr, cudaStream_t s,
+                                    cudaStream_t cs, bool captured) {
+    cudaEvent_t* x_ready = c->run_ev;
+    cudaEvent_t* x_free = c->run_ev + 2;
+    cudaEvent_t* f_done = c->run_ev + 4;
+    cudaEvent_t* f_free = c->run_ev + 6;
+    unsigned recorded = 0;   // the events recorded in this run (bit = index in run_ev)
+    auto record = [&](cudaEvent_t* ev, int k, cudaStream_t st) -> cudaError_t {
+        recorded |= 1u << (int)(ev - c->run_ev + k);
+        return cudaEventRecord(ev[k], st);
+    };
+    auto wait = [&](cudaStream_t st, cudaEvent_t* ev, int k) -> cudaError_t {
+        if (!((recorded >> (int)(ev - c->run_ev + k)) & 1u)) return cudaSuccess;
+        return cudaStreamWaitEvent(st, ev[k], 0);
+    };
+    const size_t xb = (size_t)c->n * 3 * sizeof(float);
+    const size_t eb = (size_t)c->nbox * 2 * sizeof(double), vb = (size_t)c->nbox * 9 * sizeof(double);
+    (void)captured;
+    NB_CUDA(c, cudaEventRecord(c->run_ev[8], s));
+    NB_CUDA(c, cudaStreamWaitEvent(cs, c->run_ev[8], 0));
+    // frame 0's coordinates
+    if (xb) NB_CUDA(c, cudaMemcpyAsync(fr->x_dev[0], fr->x_host, xb, cudaMemcpyHostToDevice, cs));
+    NB_CUDA(c, record(x_ready, 0, cs));
+    for (int f = 0; f < fr->n_frames; ++f) {
+        const int k = f & 1;
+        if (f + 1 < fr->n_frames) {
+            const int kn = k ^ 1;
+            NB_CUDA(c, wait(cs, x_free, kn));   // frame f - 1 has read it
+            if (xb)
+                NB_CUDA(c, cudaMemcpyAsync(fr->x_dev[kn], fr->x_host + (size_t)(f + 1) * c->n * 3, xb,
+                                           cudaMemcpyHostToDevice, cs));
+            NB_CUDA(c, record(x_ready, kn, cs));
+        }
+        NB_CUDA(c, wait(s, x_ready, k));
+        NB_CUDA(c, wait(s, f_free, k));   // frame f - 2's outputs are copied out
+        const bool energy = fr->energy_frames_host && fr->energy_frames_host[f];
+        nb_params q = *p;
+        q.want_energy = energy ? 1 : 0;
+        double* e_dev = energy && fr->e_host ? fr->e_dev[k] : nullptr;
+        double* v_dev = energy && fr->vir_host ? fr->vir_dev[k] : nullptr;
+        const float* x = fr->x_dev[k];
+        nb_status st;
+        if (f == 0 && fr->build) {
+            st = nb_grid_put(c, x, fr->boxes_host, s);
+            if (st != NB_OK) return st;
+            st = nb_pairlist_build(c, fr->rlist, fr->rbb, fr->excl_off_dev, fr->excl_idx_dev, s);
+            if (st != NB_OK) return st;
+            x = nullptr;   // the list's own coordinates
+        }
+        const int g = fr->first_frame + f;
+        if (fr->nstprune > 0 && g > 0 && g % fr->nstprune == 0)
+            st = nb_prune_compute(c, &q, x, fr->r_prune, fr->f_dev[k], e_dev, v_dev, s);
+        else
+            st = nb_compute(c, &q, x, fr->f_dev[k], e_dev, v_dev, s);
+        if (st != NB_OK) return st;
+        NB_CUDA(c, record(x_free, k, s));
+        NB_CUDA(c, record(f_done, k, s));
+        NB_CUDA(c, wait(cs, f_done, k));
+        if (xb)
+            NB_CUDA(c, cudaMemcpyAsync(fr->f_host + (size_t)f * c->n * 3, fr->f_dev[k], xb,
+                                       cudaMemcpyDeviceToHost, cs));
+        if (e_dev)
+            NB_CUDA(c, cudaMemcpyAsync(fr->e_host + (size_t)f * c->nbox * 2, e_dev, eb, cudaMemcpyDeviceToHost,
+                                       cs));
+        if (v_dev)
+            NB_CUDA(c, cudaMemcpyAsync(fr->vir_host + (size_t)f * c->nbox * 9, v_dev, vb,
+                                       cudaMemcpyDeviceToHost, cs));
+        NB_CUDA(c, record(f_free, k, cs));
+    }
+    // the compute stream waits for the last copy out
+    NB_CUDA(c, wait(s, f_free, (fr->n_frames - 1) & 1));
+    return NB_OK;
+}
+
+// The arguments a captured run depends on, as bytes: every field of the
+// frames description and the parameters, the box edges and energy flags the
+// call reads, and the context's generation.
+static std::vector<unsigned char> run_key(const nb_ctx* c, const nb_params* p, const nb_frames* fr) {
+    std::vector<unsigned char> k;
+    auto put = [&](const void* v, size_t n) {
+        const unsigned char* b = (const unsigned char*)v;
+        k.insert(k.end(), b, b + n);
+    };
+    put(&c->gen, sizeof(c->gen));
+    put(&p->elec, sizeof(p->elec));
+    put(&p->rc, sizeof(p->rc));
+    put(&p->eps_rf, sizeof(p->eps_rf));
+    put(&p->beta, sizeof(p->beta));
+    put(&fr->n_frames, sizeof(fr->n_frames));
+    const void* ptrs[] = {fr->x_host, fr->f_host, fr->energy_frames_host, fr->e_host, fr->vir_host,
+                          fr->x_dev[0], fr->x_dev[1], fr->f_dev[0], fr->f_dev[1], fr->e_dev[0],
+                          fr->e_dev[1], fr->vir_dev[0], fr->vir_dev[1], fr->excl_off_dev, fr->excl_idx_dev};
+    put(ptrs, sizeof(ptrs));
+    put(&fr->build, sizeof(fr->build));
+    put(&fr->rlist, sizeof(fr->rlist));
+    put(&fr->rbb, sizeof(fr->rbb));
+    put(&fr->first_frame, sizeof(fr->first_frame));
+    put(&fr->nstprune, sizeof(fr->nstprune));
+    put(&fr->r_prune, sizeof(fr->r_prune));
+    if (fr->boxes_host) put(fr->boxes_host, sizeof(double) * 3 * c->nbox);
+    if (fr->energy_frames_host) put(fr->energy_frames_host, (size_t)fr->n_frames);
+    return k;
+}
+
+// A run that builds its own list is the same work every time its arguments
+// are the same: the first such run is made eagerly, the second is captured
+// in a CUDA graph, and later ones replay the graph on the compute stream
+// (its copies are graph nodes; copy_stream is not used), which spares the
+// host a few microseconds per launch and the device the gaps between them.
 nb_status nb_run_frames(nb_ctx* c, const nb_params* p, const nb_frames* fr, nb_stream stream,
                         nb_stream copy_stream) {
     if (!c) return NB_ERR_ARG;
@@ -795,68 +920,67 @@ nb_status nb_run_frames(nb_ctx* c, const nb_params* p, const nb_frames* fr, nb_s
     }
     if (fr->build && !fr->boxes_host) return fail(c, NB_ERR_ARG, "run_frames: build needs the boxes");
     NB_CUDA(c, cudaSetDevice(c->device));
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 9; ++k)
         if (!c->run_ev[k]) NB_CUDA(c, cudaEventCreateWithFlags(&c->run_ev[k], cudaEventDisableTiming));
-    cudaEvent_t* x_ready = c->run_ev;
-    cudaEvent_t* x_free = c->run_ev + 2;
-    cudaEvent_t* f_done = c->run_ev + 4;
-    cudaEvent_t* f_free = c->run_ev + 6;
     cudaStream_t s = (cudaStream_t)stream, cs = (cudaStream_t)copy_stream;
-    const size_t xb = (size_t)c->n * 3 * sizeof(float);
-    const size_t eb = (size_t)c->nbox * 2 * sizeof(double), vb = (size_t)c->nbox * 9 * sizeof(double);
-    // frame 0's coordinates; the copy stream first waits for any earlier
-    // use of buffer 0 on the compute stream
-    NB_CUDA(c, cudaStreamWaitEvent(cs, x_free[0], 0));
-    if (xb) NB_CUDA(c, cudaMemcpyAsync(fr->x_dev[0], fr->x_host, xb, cudaMemcpyHostToDevice, cs));
-    NB_CUDA(c, cudaEventRecord(x_ready[0], cs));
-    for (int f = 0; f < fr->n_frames; ++f) {
-        const int k = f & 1;
-        if (f + 1 < fr->n_frames) {
-            const int kn = k ^ 1;
-            NB_CUDA(c, cudaStreamWaitEvent(cs, x_free[kn], 0));   // frame f - 1 has read it
-            if (xb)
-                NB_CUDA(c, cudaMemcpyAsync(fr->x_dev[kn], fr->x_host + (size_t)(f + 1) * c->n * 3, xb,
-                                           cudaMemcpyHostToDevice, cs));
-            NB_CUDA(c, cudaEventRecord(x_ready[kn], cs));
-        }
-        NB_CUDA(c, cudaStreamWaitEvent(s, x_ready[k], 0));
-        NB_CUDA(c, cudaStreamWaitEvent(s, f_free[k], 0));   // frame f - 2's outputs are copied out
-        const bool energy = fr->energy_frames_host && fr->energy_frames_host[f];
-        nb_params q = *p;
-        q.want_energy = energy ? 1 : 0;
-        double* e_dev = energy && fr->e_host ? fr->e_dev[k] : nullptr;
-        double* v_dev = energy && fr->vir_host ? fr->vir_dev[k] : nullptr;
-        const float* x = fr->x_dev[k];
-        nb_status st;
-        if (f == 0 && fr->build) {
-            st = nb_grid_put(c, x, fr->boxes_host, stream);
-            if (st != NB_OK) return st;
-            st = nb_pairlist_build(c, fr->rlist, fr->rbb, fr->excl_off_dev, fr->excl_idx_dev, stream);
-            if (st != NB_OK) return st;
-            x = nullptr;   // the list's own coordinates
-        }
-        const int g = fr->first_frame + f;
-        if (fr->nstprune > 0 && g > 0 && g % fr->nstprune == 0)
-            st = nb_prune_compute(c, &q, x, fr->r_prune, fr->f_dev[k], e_dev, v_dev, stream);
-        else
-            st = nb_compute(c, &q, x, fr->f_dev[k], e_dev, v_dev, stream);
-        if (st != NB_OK) return st;
-        NB_CUDA(c, cudaEventRecord(x_free[k], s));
-        NB_CUDA(c, cudaEventRecord(f_done[k], s));
-        NB_CUDA(c, cudaStreamWaitEvent(cs, f_done[k], 0));
-        if (xb)
-            NB_CUDA(c, cudaMemcpyAsync(fr->f_host + (size_t)f * c->n * 3, fr->f_dev[k], xb,
-                                       cudaMemcpyDeviceToHost, cs));
-        if (e_dev)
-            NB_CUDA(c, cudaMemcpyAsync(fr->e_host + (size_t)f * c->nbox * 2, e_dev, eb, cudaMemcpyDeviceToHost,
-                                       cs));
-        if (v_dev)
-            NB_CUDA(c, cudaMemcpyAsync(fr->vir_host + (size_t)f * c->nbox * 9, v_dev, vb,
-                                       cudaMemcpyDeviceToHost, cs));
-        NB_CUDA(c, cudaEventRecord(f_free[k], cs));
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NB_CUDA(c, cudaStreamIsCapturing(s, &cap));
+    const bool graphable = fr->build && !c->prof && cap == cudaStreamCaptureStatusNone;
+    std::vector<unsigned char> key = run_key(c, p, fr);
+    const bool same = graphable && key == c->run_key;
+    if (same && c->run_exec) {
+        NB_CUDA(c, cudaGraphLaunch(c->run_exec, s));
+        c->n_launches += c->run_launches;
+        return NB_OK;
     }
-    // the compute stream waits for the last copy out
-    NB_CUDA(c, cudaStreamWaitEvent(s, f_free[(fr->n_frames - 1) & 1], 0));
+    if (c->run_exec && !same) {
+        cudaGraphExecDestroy(c->run_exec);
+        c->run_exec = nullptr;
+    }
+    if (same && c->run_seen >= 1 && !c->run_cap)
+        NB_CUDA(c, cudaStreamCreateWithFlags(&c->run_cap, cudaStreamNonBlocking));
+    bool capturing = false;
+    if (same && c->run_seen >= 1) {
+        capturing = cudaStreamBeginCapture(c->run_cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (!capturing) cudaGetLastError();   // no graph this time: made call by call below
+    }
+    if (capturing) {
+        // the second run with these arguments: captured on the context's
+        // stream, then launched on the caller's
+        const long long n0 = c->n_launches;
+        const nb_status st = run_frames_enqueue(c, p, fr, c->run_cap, cs, true);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->run_cap, &g);
+        cudaError_t ei = cudaErrorUnknown;
+        if (st == NB_OK && e == cudaSuccess) ei = cudaGraphInstantiate(&c->run_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (st == NB_OK && e == cudaSuccess && ei == cudaSuccess) {
+            c->run_launches = c->n_launches - n0;
+            NB_CUDA(c, cudaGraphLaunch(c->run_exec, s));
+            return NB_OK;
+        }
+        // no graph for these arguments: this run and the next ones eagerly
+        c->run_exec = nullptr;
+        cudaGetLastError();
+        c->n_launches = n0;
+        if (st != NB_OK) {
+            c->run_key.clear();
+            c->run_seen = 0;
+            return st;
+        }
+        const nb_status st2 = run_frames_enqueue(c, p, fr, s, cs, false);
+        c->run_seen = -1000000;
+        return st2;
+    }
+    const nb_status st = run_frames_enqueue(c, p, fr, s, cs, false);
+    if (st != NB_OK || !graphable) {
+        c->run_key.clear();
+        c->run_seen = 0;
+        return st;
+    }
+    // remembered with the generation after the run (it may have uploaded geometry)
+    c->run_key = run_key(c, p, fr);
+    c->run_seen = same ? c->run_seen + 1 : 1;
     return NB_OK;
 }
 
@@ -936,6 +1060,7 @@ nb_status nb_set_surrogate(nb_ctx* c, const float* params, float r_min, float r_
     if (!c) return NB_ERR_ARG;
     if (!c->ws_base) return fail(c, NB_ERR_STATE, "no workspace");
     if (c->C != 8) return fail(c, NB_ERR_ARG, "the surrogate kernel needs 8-particle clusters");
+    ++c->gen;
     if (!params || !(r_min >= 0.f) || !(r_max > r_min) || !std::isfinite(r_max))
         return fail(c, NB_ERR_ARG, "set_surrogate: bad argument");
     NB_CUDA(c, cudaSetDevice(c->device));
@@ -991,6 +1116,7 @@ nb_status nb_box_info(nb_ctx* c, int box, nb_info* info) {
 
 nb_status nb_profile(nb_ctx* c, int enable) {
     if (!c) return NB_ERR_ARG;
+    ++c->gen;
     if (enable && !c->ev[0]) {
         NB_CUDA(c, cudaSetDevice(c->device));
         for (int k = 0; k < 2 * nb_ctx::kMaxSpans; ++k) NB_CUDA(c, cudaEventCreate(&c->ev[k]));

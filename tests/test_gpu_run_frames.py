@@ -211,3 +211,64 @@ def test_run_frames_batch(env, C):
     finally:
         cx.close()
         ref.close()
+
+
+def test_run_frames_replay(env):
+    """Identical runs: the first made call by call, the second captured in a
+    CUDA graph, later ones replayed.  Every run's forces agree with the
+    first's; a replay reads the host frames anew (new coordinates written
+    into the same buffer give their own forces, against the oracle); a run
+    with other arguments in between (another prune interval) is made call by
+    call, and the original arguments afterwards are right again."""
+    torch, dev, nb = env
+    b = w.water_box(1500, None, seed=7120)
+    rc, rl, beta = 1.0, 1.1, 3.12
+    rlf = float(np.float32(rl))
+    rp = float(np.float32(w.prune_radius(rc, rl, 5)))
+    xa = _frames(b, 6, seed=7121)
+    xb = _frames(b, 6, seed=7122)
+    c6c12 = nb.nb_lj_combine(b.sigma, b.eps)
+    prm = nb.make_params("ewald", rc, beta=beta, want_energy=False)
+    eo = torch.as_tensor(b.excl_off, device=dev)
+    ei = torch.as_tensor(b.excl_idx, device=dev)
+    cx = nb.Context(b.n, b.box, rl, b.q, b.types, c6c12)
+    try:
+        xh = torch.as_tensor(xa).pin_memory()
+        fh = torch.zeros((6, b.n, 3), dtype=torch.float32).pin_memory()
+        xd = [torch.empty((b.n, 3), dtype=torch.float32, device=dev) for _ in range(2)]
+        fd = [torch.empty((b.n, 3), dtype=torch.float32, device=dev) for _ in range(2)]
+        cs = torch.cuda.Stream(device=dev)
+        main = torch.cuda.current_stream()
+
+        def run(nstprune=2):
+            fh.zero_()
+            nb.nb_run_frames(cx.ctx, prm, xh, fh, xd, fd, build=True, boxes=b.box, rlist=rlf, rbb=0.8,
+                             excl_off=eo, excl_idx=ei, nstprune=nstprune, r_prune=rp, stream=main,
+                             copy_stream=cs)
+            main.synchronize()
+            nb.nb_check(cx.ctx)
+            return fh.numpy().astype(np.float64).copy()
+
+        first = run()
+        rms = np.sqrt((first ** 2).sum(-1).mean())
+        for _ in range(4):   # call by call, captured, then replays
+            assert np.abs(run() - first).max() <= SAME_TOL * rms
+        oprm = oracle.make_params("ewald", float(np.float32(rc)), beta=beta)
+
+        def check(F, x):
+            for k in (0, 3, 5):
+                fo, _, _ = oracle.forces_cells(x[k], b.q, b.types, b.sigma, b.eps, b.excl_off, b.excl_idx,
+                                               b.box, oprm)
+                r = np.sqrt((fo ** 2).sum(1).mean())
+                assert np.sqrt(((F[k] - fo) ** 2).sum(1)).max() < FORCE_TOL * r, k
+
+        check(first, xa)
+        xh.copy_(torch.as_tensor(xb))
+        check(run(), xb)                 # a replay with new coordinates in the same buffer
+        other = run(nstprune=3)          # other arguments: call by call
+        check(other, xb)
+        check(run(), xb)                 # the original arguments again
+        check(run(), xb)
+        check(run(), xb)
+    finally:
+        cx.close()
