@@ -210,7 +210,7 @@ static size_t carve(const nb_ctx* c, char* base, Workspace* ws) {
     w.keys = (unsigned long long*)take(sizeof(unsigned long long) * na);
     const size_t ns = (size_t)w.clu_total * C;
     w.xyzq = (float4*)take(sizeof(float4) * ns);
-    w.xjd = (float4*)take(sizeof(float4) * 2 * ns);
+    w.xjd = (float4*)take(sizeof(float4) * kJRecord * ((ns + 7) / 8));   // a record per group of 8 slots
     w.woff_slot = (float4*)take(sizeof(float4) * ns);
     w.atom_of_slot = (int*)take(sizeof(int) * ns);
     w.type_slot = (int*)take(sizeof(int) * ns);

@@ -9,7 +9,11 @@
 // i-particles are staged in shared memory in that pairing, shifted by the
 // entry's periodic image as an unevaluated FP32 sum hi + lo; each j-particle
 // comes as two float4 of a duplicated layout ({-x, -x, -y, -y}, {-z, -z, q,
-// q}) so that it enters packed operations without register copies.  A pair
+// q}) so that it enters packed operations without register copies.  The
+// j-clusters' records (that layout and the LJ types, 288 bytes) reach a
+// per-warp ring in shared memory by asynchronous copies, the next 8 entries'
+// while the current 8 are computed, so that no entry waits for its j-data
+// to come from L2.  A pair
 // is computed when r^2 < rc^2 and either its mask bit is set (full LJ +
 // Coulomb) or it is a counted pair without the bit (force-field exclusion:
 // only the RF/Ewald correction, Sec. 2.4); the mask bit multiplies the plain
@@ -44,7 +48,7 @@ struct ForceArgs {
     const unsigned long long* mask;
     long long jstride;                // stride between the per-i-cluster mask arrays
     const float4* xyzq;
-    const float4* xjd;                // duplicated, negated j layout (two float4 per slot)
+    const float4* xjd;                // j-cluster records: duplicated, negated j layout and LJ types
     const int* type_slot;
     float4* fslot;
     const float2* c6c12;
@@ -91,6 +95,21 @@ constexpr int kSuper8 = super_size(8);
 constexpr unsigned kFastBit = 1u << 31;
 static_assert(kSuperShift + kSuper8 <= 31, "interaction bits overlap the fast bit");
 
+// j-entries per group of the per-warp ring below.
+constexpr int kJGroup = 8;
+static_assert(kJGroup == 8, "the j-loop finds an entry's group as t >> 3");
+
+// One j-cluster's record of the duplicated j layout, as the bulk-copy engine
+// brings it: the 8 slots' {-x, -x, -y, -y}, their {-z, -z, q, q}, their LJ
+// types.
+struct JTile {
+    float4 a[8];
+    float4 b[8];
+    int t[8];
+};
+static_assert(sizeof(JTile) == kJRecord * sizeof(float4), "a record of the duplicated j layout");
+static_assert(sizeof(JTile) % 16 == 0, "bulk copies land on 16-byte boundaries");
+
 // Per-warp shared staging of the force kernel.
 struct WarpSmem {
     // i particles of the super-cluster, paired the way a lane uses them:
@@ -102,26 +121,60 @@ struct WarpSmem {
     int2 row[kSuper8][4];     // LJ row byte offsets (type * ntypes * 8)
     int w[32];                // j-entry words of the current chunk (with the fast bit)
     unsigned long long m[kSuper8][32];  // their masks per i-cluster
+    // a ring of two groups of j-clusters: the group being computed and the
+    // next, copied in while the current one is computed
+    JTile jt[2][kJGroup];
 };
+
+// Asynchronous 16-byte copies from global to shared memory (L2 only), in
+// per-thread groups.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most the newest group of this thread's copies is in flight
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Request the j-clusters of group g of the staged chunk (entries g * kJGroup
+// onwards, at most kJGroup of the chunk's nt) into ring buffer g & 1, whose
+// previous group every lane has read (the warp synchronises here; the reads
+// have completed, their values are in use): lane (k, q) = (lane / 4,
+// lane % 4) copies the 16-byte pieces q, q + 4, ... of entry k's record; one
+// commit group per lane.
+static_assert(kJGroup * 4 == 32 && kJRecord <= 20, "four lanes per record, at most five pieces each");
+__device__ __forceinline__ void jgroup_issue(const ForceArgs& A, WarpSmem& W, int g, int nt, int lane) {
+    const int t0 = g * kJGroup, k = lane >> 2, q = lane & 3;
+    __syncwarp();
+    if (t0 + k < nt) {
+        const long long cj = W.w[t0 + k] & kCjMask;
+        const float4* src = A.xjd + kJRecord * cj + q;
+        float4* dst = W.jt[g & 1][k].a + q;
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            if (q + 4 * i < kJRecord) cp_async16(dst + 4 * i, src + 4 * i);
+    }
+    cp_async_commit();
+}
 
 // The j-particle of a lane with both halves of each packed pair holding it
 // (the lane's two particle pairs share j): -x, -y, -z, so that a distance
 // component is one packed add x_i + (-x_j), and the charge; from the
-// duplicated slot layout written with the coordinates.
+// j-cluster's record in the warp's ring.
 struct JPart {
     float2 nx, ny, nz, q;
     int t;   // LJ type, as a byte offset into a row of the {-6 C6, 12 C12} table
 };
 
-__device__ __forceinline__ JPart load_jpart(const float4* __restrict__ xjd, const int* __restrict__ type_slot,
-                                            int slot) {
-    const float4 a = xjd[2 * slot], b = xjd[2 * slot + 1];
+__device__ __forceinline__ JPart load_jpart(const JTile& T, int j) {
+    const float4 a = T.a[j], b = T.b[j];
     JPart J;
     J.nx = make_float2(a.x, a.y);
     J.ny = make_float2(a.z, a.w);
     J.nz = make_float2(b.x, b.y);
     J.q = make_float2(b.z, b.w);
-    J.t = type_slot[slot] * (int)sizeof(float2);
+    J.t = T.t[j] * (int)sizeof(float2);
     return J;
 }
 
@@ -427,10 +480,12 @@ __device__ __forceinline__ bool icluster8_mlp(const ForceParams& P, const float2
     return true;
 }
 
-// All j-entries [jb, je) (at most 32) of one super-cluster i-entry.  PRUNE:
-// the j-entries that keep an interacting i-cluster within the prune radius
-// are appended in order to the pruned list at j_out + kept (the entry's
-// offsets in the outer list), as the separate prune kernel does.
+// All j-entries [jb, je) (at most 32) of one super-cluster i-entry.  The
+// j-clusters come through the warp's ring in groups of kJGroup entries, the
+// next group copied in while the current one is computed.  PRUNE: the
+// j-entries that keep an interacting i-cluster within the prune radius are
+// appended in order to the pruned list at j_out + kept (the entry's offsets
+// in the outer list), as the separate prune kernel does.
 template <int ELEC, bool ENERGY, bool FIT, bool SHIFTED, bool PRUNE>
 __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s_lj, WarpSmem& W,
                                              const Lane8& L, const int2 (&row)[kSuper8], int g0, bool center,
@@ -458,11 +513,21 @@ __device__ __forceinline__ void force_entry8(const ForceArgs& A, const float2* s
         W.w[lane] = fast ? (int)((unsigned)w | kFastBit) : w;
     }
     __syncwarp();
+    jgroup_issue(A, W, 0, nt, lane);
     unsigned my_keep = 0;   // PRUNE: kept i-cluster bits of j-entry `lane`
     for (int t = 0; t < nt; ++t) {
+        if ((t & (kJGroup - 1)) == 0) {
+            // group t / kJGroup starts: request the one after it (into the
+            // buffer of the group just finished; an empty commit group if
+            // there is none), then wait for this one
+            if (t + kJGroup < nt) jgroup_issue(A, W, (t >> 3) + 1, nt, lane);
+            else cp_async_commit();
+            cp_async_wait_prior();
+            __syncwarp();
+        }
         const int w = W.w[t];
         const int cjt = w & kCjMask;
-        const JPart J = load_jpart(A.xjd, A.type_slot, cjt * 8 + L.j);
+        const JPart J = load_jpart(W.jt[0][t & (2 * kJGroup - 1)], L.j);
         JSum G;
         G.x = G.y = G.z = make_float2(0.f, 0.f);
         bool any = false;

@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(512) k_col_sort(Workspace ws, int C, int ntype
                 ty = 0;
             }
             ws.type_slot[s] = ty;
+            if (ws.xjd) store_jtype(ws.xjd, s, ty);
         } else {
             const long long sl = s - slot0;
             const float4 x = make_float4(-G.dummy_g * (float)(1 + (int)(sl % 4096)),
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(512) k_col_sort(Workspace ws, int C, int ntype
             if (ws.xjd) store_xjd(ws.xjd, s, x);
             ws.atom_of_slot[s] = -1;
             ws.type_slot[s] = 0;
+            if (ws.xjd) store_jtype(ws.xjd, s, 0);
         }
     }
     __syncthreads();

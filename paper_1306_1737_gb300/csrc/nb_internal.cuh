@@ -120,7 +120,9 @@ struct Workspace {
     float4* xyzq;
     // per slot, two float4: {-x, -x, -y, -y}, {-z, -z, q, q} -- the
     // j-particle as the force kernel's packed pairs use it (both halves of a
-    // lane's pair share j), written with xyzq
+    // lane's pair share j), written with xyzq -- and its LJ type; one record
+    // of kJRecord float4 per group of 8 slots (an 8-particle cluster): the 8
+    // first halves, the 8 second halves, the 8 types, 288 contiguous bytes
     float4* xjd;
     float4* woff_slot;   // the wrap offset of the slot's particle (written by the grid)
     int* atom_of_slot;   // batch particle index, -1 for dummies
@@ -313,10 +315,16 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// The two float4 of a slot's duplicated j layout (see Workspace::xjd).
+// The two float4 of a slot's duplicated j layout and its LJ type (see
+// Workspace::xjd).
+constexpr int kJRecord = 18;
 __device__ __forceinline__ void store_xjd(float4* xjd, long long s, float4 x) {
-    xjd[2 * s] = make_float4(-x.x, -x.x, -x.y, -x.y);
-    xjd[2 * s + 1] = make_float4(-x.z, -x.z, x.w, x.w);
+    float4* g = xjd + kJRecord * (s >> 3) + (s & 7);
+    g[0] = make_float4(-x.x, -x.x, -x.y, -x.y);
+    g[8] = make_float4(-x.z, -x.z, x.w, x.w);
+}
+__device__ __forceinline__ void store_jtype(float4* xjd, long long s, int type) {
+    reinterpret_cast<int*>(xjd + kJRecord * (s >> 3) + 16)[s & 7] = type;
 }
 
 __device__ __forceinline__ void shift_vector(int s, const float L[3], float sh[3]) {
