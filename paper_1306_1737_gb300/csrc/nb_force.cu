@@ -99,8 +99,8 @@ static_assert(kSuperShift + kSuper8 <= 31, "interaction bits overlap the fast bi
 constexpr int kJGroup = 8;
 static_assert(kJGroup == 8, "the j-loop finds an entry's group as t >> 3");
 
-// One j-cluster's record of the duplicated j layout, as the bulk-copy engine
-// brings it: the 8 slots' {-x, -x, -y, -y}, their {-z, -z, q, q}, their LJ
+// One j-cluster's record of the duplicated j layout, as the ring's copies
+// bring it: the 8 slots' {-x, -x, -y, -y}, their {-z, -z, q, q}, their LJ
 // types.
 struct JTile {
     float4 a[8];
@@ -108,7 +108,7 @@ struct JTile {
     int t[8];
 };
 static_assert(sizeof(JTile) == kJRecord * sizeof(float4), "a record of the duplicated j layout");
-static_assert(sizeof(JTile) % 16 == 0, "bulk copies land on 16-byte boundaries");
+static_assert(sizeof(JTile) % 16 == 0, "16-byte copies land on 16-byte boundaries");
 
 // Per-warp shared staging of the force kernel.
 struct WarpSmem {
